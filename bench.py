@@ -1,0 +1,323 @@
+#!/usr/bin/env python3
+"""Throughput of one full Lagrange-Remap time step (Lagrange phase + DirectCF
+remap with VOF/PLIC material fluxes + dual momentum remap + CFL minimum) on
+GB300, in cell-updates/s.
+
+Workload: the three-material triple point, 1400 x 600 cells on [0,7]x[0,3],
+FP64 (synthetic initial state, seeded generator).  One step = one lr_step.
+The state stays resident in HBM; an L2 flush (a 512 MB write) separates the
+timed steps and is not timed.  With --gpus N (torchrun), every rank runs its
+own replica (no data-path collective: "scaling": "weak").
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lr|reference]
+
+--impl reference times the plain FP64 CPU oracle (the method as the paper
+defines it) on the same workload and metric.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s (Lagrange+remap)"
+UNIT = "cell-updates/s"
+WORKLOAD = "triple_point_1400x600_3mat_fp64"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="lr", choices=["lr", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-baseline-steps", type=int, default=20)
+    return ap.parse_args()
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.gpu_id is not None:
+            cmd += ["-i", str(self.gpu_id)]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() in ("active", "yes", "1"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# FP64 operations per unit of the dominant kernels (pure-material path), from
+# the static operation count in DESIGN.md ("Roofline"): adds, multiplies and
+# FMAs count 1, a division 1 and a square root 1 (algorithmic count, not the
+# hardware instruction count).
+FLOPS_PER_UNIT = {
+    "lr_mat_flux": 78.0,      # per canonical node (one X face, one Y face, one corner)
+    "lr_dual_flux": 186.0,    # per dual index (one dual X face, Y face, two corners)
+    "lr_cell_pre": 74.0,      # per cell (three materials, one present)
+    "lr_cell_lag": 51.0,      # per canonical node (one cell, two faces)
+    "lr_cell_update": 72.0,   # per cell
+    "lr_cell_cf": 24.0,       # per cell
+    "lr_node_half": 19.0,     # per node
+    "lr_node_update": 47.0,   # per node
+}
+
+
+def units_per_launch(kernel, nx, ny):
+    if kernel in ("lr_cell_pre", "lr_cell_update", "lr_cell_cf"):
+        return nx * ny
+    if kernel == "lr_dual_flux":
+        return (nx + 2) * (ny + 2)
+    return (nx + 1) * (ny + 1)
+
+
+def fp64_peak_flops(sm_mhz=None):
+    """FP64 peak of the GPU from its unit counts: 152 SMs x 2 DFMA lanes per
+    clock x 2 flops x the maximum SM clock (2.07 GHz) = 1.259 TFLOP/s."""
+    return 152 * 2 * 2 * 2.07e9
+
+
+def cpu_baseline(steps):
+    import oracle
+    from paper_2208_13409_gb300 import problems as P
+
+    pr = P.triple_point()
+    o = oracle.Oracle(pr)
+    o.step()  # first step outside the sample
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        o.step()
+    el = time.perf_counter() - t0
+    return {"value": pr.cells * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} steps of the 1400x600 triple point after one unsampled step, single thread"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle
+    from paper_2208_13409_gb300 import problems as P
+
+    pr = P.triple_point()
+    o = oracle.Oracle(pr)
+    for _ in range(args.warmup):
+        o.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step()
+    el = time.perf_counter() - t0
+    val = pr.cells * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "nx": pr.nx, "ny": pr.ny, "nmat": 3},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} steps of the 1400x600 triple point after {args.warmup} warm-up steps, single thread"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_lr(args, world, rank, local):
+    import numpy as np
+    import torch
+    from paper_2208_13409_gb300 import lr, problems as P
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    pr = P.triple_point()
+    cells = pr.cells
+    sim = lr.Sim(pr)
+    stream = sim.stream
+    for _ in range(args.warmup):
+        sim.step(sync=False)
+    sim.sync()
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 512 MB > L2
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    gpu_id = None
+    try:
+        gpu_id = str(torch.cuda.get_device_properties(local).uuid)
+        if not gpu_id.startswith("GPU-"):
+            gpu_id = "GPU-" + gpu_id
+    except Exception:
+        gpu_id = None
+    sampler = ClockSampler(gpu_id)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    wall0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for q in range(K):
+            flush.fill_(float(q))
+            ev[q][0].record(stream)
+            sim.step(sync=False)
+            ev[q][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    sim.sync()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    tmax = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    ms_max = float(tmax.item())
+    value = world * cells * K / (ms_max * 1e-3)
+
+    # ---- per-kernel durations (separate profiled pass, events on the library stream)
+    sim.set_profiling(True)
+    with torch.cuda.stream(stream):
+        for q in range(K):
+            flush.fill_(float(q))
+            sim.step(sync=False)
+    sim.sync()
+    kt = sim.kernel_times()
+    sim.set_profiling(False)
+    dom = max(kt, key=lambda k: kt[k][1])
+    dom_ms = kt[dom][1] / max(kt[dom][0], 1)
+    flops = FLOPS_PER_UNIT.get(dom, 0.0) * units_per_launch(dom, pr.nx, pr.ny)
+    achieved = flops / (dom_ms * 1e-3) / 1e12
+    peak = fp64_peak_flops() / 1e12
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        try:
+            traffic = json.load(open(tpath)).get(dom)
+        except Exception:
+            traffic = None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": dom,
+                "kernel_ms": dom_ms, "peak_source": "FP64: 152 SMs x 4 flop/clk x 2.07 GHz (unit counts)"}
+    peaks = load_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    alg_bytes = 16 * (3 * pr.nmat + 2)  # read + write the state once per cell-step
+    step_ms = ms_max / K
+    hbm_frac = cells * alg_bytes / (step_ms * 1e-3) / (hbm * 1e9)
+
+    # ---- end to end through the C ABI with pinned host buffers
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    hp = pr.copy(k=pin(pr.k), rho=pin(pr.rho), p=pin(pr.p), ux=pin(pr.ux), uy=pin(pr.uy))
+    outs = {f: pin(np.zeros(sim.get(f).shape)) for f in (lr.F_K, lr.F_RHO_MAT, lr.F_E_MAT, lr.F_UX, lr.F_UY)}
+    h2d = sum(a.nbytes for a in (hp.k, hp.rho, hp.p, hp.ux, hp.uy))
+    d2h = sum(a.nbytes for a in outs.values())
+    n_e2e = max(3, min(K, 30))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L = lr.load()
+    import ctypes
+    for q in range(n_e2e):
+        sim.init(hp)
+        sim.step(sync=False)
+        for f, a in outs.items():
+            rc = L.lr_get_fields(sim._h, f, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), a.size)
+            if rc != 0:
+                raise RuntimeError("lr_get_fields failed")
+    e2e_s = (time.perf_counter() - t0) / n_e2e
+    e2e_val = world * cells / e2e_s
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_baseline_steps)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+                "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "nx": pr.nx, "ny": pr.ny, "nmat": pr.nmat,
+                           "l2": "flushed between timed steps (512 MB write, untimed)",
+                           "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                "gpu_launches": K * (sim.launches_per_step() + 1),
+                "roofline": roofline,
+                "hbm_alg_frac": {"achieved_gbs": cells * alg_bytes / (step_ms * 1e-3) / 1e9, "peak_gbs": hbm,
+                                 "frac": hbm_frac, "bytes_per_cell": alg_bytes},
+                "kernels_ms": {k: v[1] / max(v[0], 1) for k, v in kt.items()},
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "clocks": clocks, "wall_s": wall}
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    run_lr(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -21,6 +21,7 @@ CORNER_UPWIND, CORNER_DIAG = 0, 1
 
 F_K, F_RHO_MAT, F_E_MAT, F_P, F_RHO, F_E, F_UX, F_UY, F_CONS, F_C = range(10)
 F_UHX, F_UHY, F_VOL_LAGCF, F_E_LAG, F_FX, F_FY, F_FC, F_MX, F_MY, F_MC, F_Q, F_DT = range(20, 32)
+F_CUTS, F_XA, F_YA, F_CA = range(32, 36)
 
 
 class Config(ctypes.Structure):
@@ -168,6 +169,14 @@ class Oracle:
             return out.reshape(ny, nx + 1)
         if field in (F_FY, F_MY):
             return out.reshape(ny + 1, nx)
+        if field == F_CUTS:
+            return out.reshape(6, ny, nx)
+        if field == F_XA:
+            return out.reshape(M, ny, nx + 1)
+        if field == F_YA:
+            return out.reshape(M, ny + 1, nx)
+        if field == F_CA:
+            return out.reshape(M, ny + 1, nx + 1)
         return out
 
 

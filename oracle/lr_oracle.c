@@ -1241,6 +1241,10 @@ long orc_size(const orc* s, int field) {
     case ORC_F_FY: case ORC_F_MY: return (long)(s->ny + 1) * s->nx;
     case ORC_F_CONS: return 8;
     case ORC_F_DT: return 1;
+    case ORC_F_CUTS: return 6 * c;
+    case ORC_F_XA: return (long)s->M * s->ny * (s->nx + 1);
+    case ORC_F_YA: return (long)s->M * (s->ny + 1) * s->nx;
+    case ORC_F_CA: return (long)s->M * n;
   }
   return -1;
 }
@@ -1337,6 +1341,32 @@ int orc_get(orc* s, int field, double* out, long n) {
       return 0;
     case ORC_F_DT:
       out[0] = s->lastdt;
+      return 0;
+    case ORC_F_CUTS:
+      for (int z = 0; z < 6; ++z)
+        for (int j = 0; j < ny; ++j)
+          for (int i = 0; i < nx; ++i) {
+            int c = CI(s, i, j), q = z / 3;
+            out[z * cc + (long)j * nx + i] = (q < s->ncut[c] && q < MAXM - 1) ? s->cn[q][z % 3][c] : 0.0;
+          }
+      return 0;
+    case ORC_F_XA:
+      for (int a = 0; a < M; ++a)
+        for (int j = 0; j < ny; ++j)
+          for (int i = 0; i <= nx; ++i)
+            out[(long)a * ny * (nx + 1) + (long)j * (nx + 1) + i] = s->xA[a][XI(s, i, j)];
+      return 0;
+    case ORC_F_YA:
+      for (int a = 0; a < M; ++a)
+        for (int j = 0; j <= ny; ++j)
+          for (int i = 0; i < nx; ++i)
+            out[(long)a * (ny + 1) * nx + (long)j * nx + i] = s->yA[a][YI(s, i, j)];
+      return 0;
+    case ORC_F_CA:
+      for (int a = 0; a < M; ++a)
+        for (int j = 0; j <= ny; ++j)
+          for (int i = 0; i <= nx; ++i)
+            out[(long)a * (ny + 1) * (nx + 1) + (long)j * (nx + 1) + i] = s->cA[a][NI(s, i, j)];
       return 0;
     case ORC_F_CONS: {
       double ma[MAXM] = {0, 0, 0}, mt = 0.0, ei = 0.0, px = 0.0, py = 0.0, ek = 0.0;

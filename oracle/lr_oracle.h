@@ -59,7 +59,11 @@ enum {
   ORC_F_MY = 28,      /* [ny+1][nx] Y-face mass flux, signed */
   ORC_F_MC = 29,      /* [(ny+1)][(nx+1)] corner mass flux magnitude */
   ORC_F_Q = 30,       /* [ny][nx] pseudo-viscosity Q^n */
-  ORC_F_DT = 31       /* [1] last dt */
+  ORC_F_DT = 31,      /* [1] last dt */
+  ORC_F_CUTS = 32,    /* [6][ny][nx] interface lines of mixed cells: n0x, n0y, d0, n1x, n1y, d1 */
+  ORC_F_XA = 33,      /* [nmat][ny][nx+1] per-material X-face volume flux, signed */
+  ORC_F_YA = 34,      /* [nmat][ny+1][nx] per-material Y-face volume flux, signed */
+  ORC_F_CA = 35       /* [nmat][(ny+1)][(nx+1)] per-material corner volume flux */
 };
 
 orc* orc_create(const orc_config* cfg, const double* gamma, const double* pinf);

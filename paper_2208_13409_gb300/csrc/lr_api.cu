@@ -1,0 +1,667 @@
+// lr_api.cu -- the C ABI of include/lr.h: context, device arena, launches,
+// CUDA graphs for lr_run, field read-back and kernel timing.
+#include "../../include/lr.h"
+#include "lr_dev.cuh"
+
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+#include <vector>
+
+struct lr_ctx {
+  lr_config cfg;
+  LrGrid g;
+  LrState st[2];
+  int cur;
+  LrWork w;
+  char* arena;
+  size_t arena_bytes;
+  bool own_arena;
+  cudaStream_t stream;
+  bool own_stream;
+  bool have_mats, inited;
+  int sticky;
+  char msg[512];
+  cudaGraphExec_t gexec[2];
+  bool gvalid[2];
+  bool prof;
+  struct Pend { int kid; cudaEvent_t a, b; };
+  std::vector<Pend> pend;
+  double acc_ms[LRK_COUNT];
+  long acc_n[LRK_COUNT];
+  double* tmp;      // device scratch for field views (max field size)
+  size_t tmp_elems;
+  double* rows;     // device scratch for conservation partial sums
+};
+
+namespace {
+
+void setmsg(lr_ctx* c, const char* fmt, ...) {
+  if (!c) return;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(c->msg, sizeof(c->msg), fmt, ap);
+  va_end(ap);
+}
+
+lr_status cuda_fail(lr_ctx* c, cudaError_t e, const char* where) {
+  setmsg(c, "CUDA error in %s: %s", where, cudaGetErrorString(e));
+  return LR_ERR_CUDA;
+}
+
+#define CK(call, where)                                    \
+  do {                                                     \
+    cudaError_t _e = (call);                               \
+    if (_e != cudaSuccess) return cuda_fail(ctx, _e, where); \
+  } while (0)
+
+// Bump allocator over the arena; with base == nullptr it only measures.
+struct Bump {
+  char* base;
+  size_t off;
+  template <class T>
+  T* take(size_t n) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += n * sizeof(T);
+    return p;
+  }
+};
+
+bool config_ok(const lr_config* c, char* why, size_t nwhy) {
+  if (!c) { snprintf(why, nwhy, "null config"); return false; }
+  if (c->nx < 2 || c->ny < 2) { snprintf(why, nwhy, "nx, ny must be >= 2"); return false; }
+  if ((double)c->nx * (double)c->ny > (double)(1 << 28)) { snprintf(why, nwhy, "nx*ny above 2^28"); return false; }
+  if (c->nmat < 1 || c->nmat > LR_MAXM) { snprintf(why, nwhy, "nmat must be 1..3"); return false; }
+  if (!(c->x1 > c->x0) || !(c->y1 > c->y0)) { snprintf(why, nwhy, "empty domain"); return false; }
+  if (c->bc[0] != c->bc[1] || c->bc[2] != c->bc[3]) { snprintf(why, nwhy, "bc[0]==bc[1] and bc[2]==bc[3] required"); return false; }
+  for (int q = 0; q < 4; ++q)
+    if (c->bc[q] != LR_BC_REFLECT && c->bc[q] != LR_BC_PERIODIC) { snprintf(why, nwhy, "bad bc"); return false; }
+  if (!(c->cfl > 0.0) || c->cfl > 1.0) { snprintf(why, nwhy, "cfl must be in (0,1]"); return false; }
+  if (c->a1 < 0.0 || c->a2 < 0.0) { snprintf(why, nwhy, "negative viscosity coefficient"); return false; }
+  if (c->face_order != 1 && c->face_order != 2) { snprintf(why, nwhy, "face_order must be 1 or 2"); return false; }
+  if (c->corner_recon != LR_CORNER_UPWIND && c->corner_recon != LR_CORNER_DIAG) { snprintf(why, nwhy, "bad corner_recon"); return false; }
+  if (c->precision != LR_FP64) { snprintf(why, nwhy, "only LR_FP64 is available"); return false; }
+  if (c->dt_fixed < 0.0) { snprintf(why, nwhy, "dt_fixed < 0"); return false; }
+  return true;
+}
+
+// Lay out every device array; returns the arena size.
+size_t layout(const lr_config* cfg, char* base, LrState* st, LrWork* w, double** tmp, size_t* tmp_elems,
+              double** rows) {
+  Bump b{base, 0};
+  size_t nx = cfg->nx, ny = cfg->ny, M = cfg->nmat;
+  size_t nc = nx * ny, nn = (nx + 1) * (ny + 1), nfx = (nx + 1) * ny, nfy = nx * (ny + 1);
+  size_t nd = (nx + 2) * (ny + 2);
+  LrState s[2];
+  LrWork W;
+  memset(s, 0, sizeof(s));
+  memset(&W, 0, sizeof(W));
+  for (int q = 0; q < 2; ++q) {
+    for (size_t a = 0; a < M; ++a) { s[q].k[a] = b.take<double>(nc); s[q].r[a] = b.take<double>(nc); s[q].e[a] = b.take<double>(nc); }
+    s[q].ux = b.take<double>(nn); s[q].uy = b.take<double>(nn);
+  }
+  W.scal = b.take<double>(8);
+  W.red = b.take<unsigned long long>(2);
+  W.err = b.take<int>(2);
+  W.pux = b.take<double>(nn); W.puy = b.take<double>(nn);
+  W.mc = b.take<double>(nc); W.Q = b.take<double>(nc); W.Pi = b.take<double>(nc); W.cc = b.take<double>(nc);
+  for (size_t a = 0; a < M; ++a) { W.Ph[a] = b.take<double>(nc); W.elag[a] = b.take<double>(nc); W.rcf[a] = b.take<double>(nc); }
+  W.ox = b.take<double>(nc); W.oy = b.take<double>(nc); W.wx = b.take<double>(nc); W.wy = b.take<double>(nc);
+  W.vcf = b.take<double>(nc);
+  for (int q = 0; q < 6; ++q) W.cut[q] = b.take<double>(nc);
+  W.uhx = b.take<double>(nn); W.uhy = b.take<double>(nn); W.ddx = b.take<double>(nn); W.ddy = b.take<double>(nn);
+  W.ulx = b.take<double>(nn); W.uly = b.take<double>(nn);
+  W.fx = b.take<double>(nfx); W.fxb = b.take<double>(nfx); W.fxlo = b.take<double>(nfx); W.fxhi = b.take<double>(nfx);
+  W.fy = b.take<double>(nfy); W.fyb = b.take<double>(nfy); W.fylo = b.take<double>(nfy); W.fyhi = b.take<double>(nfy);
+  if (M > 1)
+    for (size_t a = 0; a < M; ++a) { W.xAm[a] = b.take<double>(nfx); W.yAm[a] = b.take<double>(nfy); W.cAm[a] = b.take<double>(nn); }
+  for (size_t a = 0; a < M; ++a) {
+    W.xA[a] = b.take<double>(nfx); W.xMm[a] = b.take<double>(nfx); W.xE[a] = b.take<double>(nfx);
+    W.yA[a] = b.take<double>(nfy); W.yMm[a] = b.take<double>(nfy); W.yE[a] = b.take<double>(nfy);
+    W.cA[a] = b.take<double>(nn); W.cMm[a] = b.take<double>(nn); W.cE[a] = b.take<double>(nn);
+  }
+  W.MX = b.take<double>(nfx); W.MY = b.take<double>(nfy); W.Mpp = b.take<double>(nn); W.Mpm = b.take<double>(nn);
+  for (int q = 0; q < 3; ++q) { W.dX[q] = b.take<double>(nd); W.dY[q] = b.take<double>(nd); W.dPP[q] = b.take<double>(nd); W.dPM[q] = b.take<double>(nd); }
+  size_t te = M * nc > nn ? M * nc : nn;
+  if (6 * nc > te) te = 6 * nc;
+  if (M * nn > te) te = M * nn;
+  if (nd > te) te = nd;
+  double* t = b.take<double>(te);
+  double* r = b.take<double>(8 * ((ny + 1) > 64 ? (ny + 1) : 64));
+  if (st) { st[0] = s[0]; st[1] = s[1]; }
+  if (w) *w = W;
+  if (tmp) *tmp = t;
+  if (tmp_elems) *tmp_elems = te;
+  if (rows) *rows = r;
+  return b.off + 256;
+}
+
+void fill_grid(lr_ctx* c) {
+  LrGrid& g = c->g;
+  const lr_config& f = c->cfg;
+  g.nx = f.nx; g.ny = f.ny; g.M = f.nmat;
+  g.perx = f.bc[0] == LR_BC_PERIODIC;
+  g.pery = f.bc[2] == LR_BC_PERIODIC;
+  g.nxu = g.perx ? g.nx : g.nx + 1;
+  g.nyu = g.pery ? g.ny : g.ny + 1;
+  g.dx = (f.x1 - f.x0) / f.nx;
+  g.dy = (f.y1 - f.y0) / f.ny;
+  g.V = g.dx * g.dy;
+  g.L = sqrt(g.dx * g.dy);
+  g.hmin = g.dx < g.dy ? g.dx : g.dy;
+  g.D = sqrt(g.dx * g.dx + g.dy * g.dy);
+  g.cfl = f.cfl; g.a1 = f.a1; g.a2 = f.a2; g.dt_fixed = f.dt_fixed;
+  g.face_o2 = f.face_order == 2;
+  g.corner_o2 = f.corner_recon == LR_CORNER_DIAG;
+}
+
+void drop_graphs(lr_ctx* c) {
+  for (int q = 0; q < 2; ++q)
+    if (c->gvalid[q]) { cudaGraphExecDestroy(c->gexec[q]); c->gvalid[q] = false; }
+}
+
+lr_status check_sticky(lr_ctx* ctx) {
+  if (ctx->sticky != LR_OK) return (lr_status)ctx->sticky;
+  int e[2];
+  CK(cudaMemcpyAsync(e, ctx->w.err, sizeof(e), cudaMemcpyDeviceToHost, ctx->stream), "error word");
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  if (e[0] != 0) {
+    ctx->sticky = LR_ERR_NUMERIC;
+    setmsg(ctx, "numeric failure (bits 0x%x: %s%s%s%s%s) first at index %d", e[0],
+           (e[0] & LR_DERR_VOLUME) ? "volume " : "", (e[0] & LR_DERR_SOUND) ? "sound-speed " : "",
+           (e[0] & LR_DERR_MASS) ? "mass " : "", (e[0] & LR_DERR_NAN) ? "nan " : "",
+           (e[0] & LR_DERR_GEOM) ? "flux-geometry " : "", e[1]);
+    return LR_ERR_NUMERIC;
+  }
+  return LR_OK;
+}
+
+cudaError_t enqueue_step(lr_ctx* ctx, int from) {
+  const LrState& cur = ctx->st[from];
+  const LrState& nxt = ctx->st[1 - from];
+  for (int k = 0; k < LRK_COUNT; ++k) {
+    if (ctx->prof) {
+      lr_ctx::Pend p;
+      p.kid = k;
+      cudaEventCreate(&p.a);
+      cudaEventCreate(&p.b);
+      cudaEventRecord(p.a, ctx->stream);
+      cudaError_t e = lr_launch(k, ctx->g, cur, nxt, ctx->w, ctx->stream);
+      cudaEventRecord(p.b, ctx->stream);
+      ctx->pend.push_back(p);
+      if (e != cudaSuccess) return e;
+    } else {
+      cudaError_t e = lr_launch(k, ctx->g, cur, nxt, ctx->w, ctx->stream);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+lr_status ensure_graph(lr_ctx* ctx, int from) {
+  if (ctx->gvalid[from]) return LR_OK;
+  cudaGraph_t gr;
+  CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+  cudaError_t e = enqueue_step(ctx, from);
+  cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &gr);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "capture launch");
+  if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "end capture");
+  e = cudaGraphInstantiate(&ctx->gexec[from], gr, 0);
+  cudaGraphDestroy(gr);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "graph instantiate");
+  ctx->gvalid[from] = true;
+  return LR_OK;
+}
+
+lr_status create_common(const lr_config* cfg, void* mem, size_t bytes, bool own, lr_ctx** out) {
+  if (!out) return LR_ERR_ARG;
+  *out = nullptr;
+  char why[160];
+  if (!config_ok(cfg, why, sizeof(why))) return LR_ERR_ARG;
+  lr_ctx* ctx = new lr_ctx();
+  ctx->cfg = *cfg;
+  fill_grid(ctx);
+  size_t need = layout(cfg, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+  if (own) {
+    cudaError_t e = cudaMalloc(&mem, need);
+    if (e != cudaSuccess) { delete ctx; return LR_ERR_OOM; }
+    bytes = need;
+  } else {
+    if (!mem || bytes < need || (reinterpret_cast<uintptr_t>(mem) & 255)) { delete ctx; return LR_ERR_OOM; }
+  }
+  ctx->arena = static_cast<char*>(mem);
+  ctx->arena_bytes = bytes;
+  ctx->own_arena = own;
+  layout(cfg, ctx->arena, ctx->st, &ctx->w, &ctx->tmp, &ctx->tmp_elems, &ctx->rows);
+  if (cfg->cuda_stream) {
+    ctx->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
+    ctx->own_stream = false;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      if (own) cudaFree(mem);
+      delete ctx;
+      return LR_ERR_CUDA;
+    }
+    ctx->own_stream = true;
+  }
+  ctx->sticky = LR_OK;
+  if (lr_launch_reset(ctx->w, ctx->stream) != cudaSuccess ||
+      cudaMemsetAsync(ctx->w.pux, 0, sizeof(double) * (cfg->nx + 1) * (cfg->ny + 1), ctx->stream) != cudaSuccess ||
+      cudaMemsetAsync(ctx->w.puy, 0, sizeof(double) * (cfg->nx + 1) * (cfg->ny + 1), ctx->stream) != cudaSuccess ||
+      cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    if (own) cudaFree(mem);
+    delete ctx;
+    return LR_ERR_CUDA;
+  }
+  *out = ctx;
+  return LR_OK;
+}
+
+// ------------------------------------------------ field views (device)
+__global__ void gather_node(const double* src, double* dst, int nx, int ny, int perx, int pery) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i > nx || j > ny) return;
+  int mi = perx ? i % nx : i, mj = pery ? j % ny : j;
+  dst[j * (nx + 1) + i] = src[mj * (nx + 1) + mi];
+}
+// Interface lines of the last step, masked to the cells that were mixed
+// (the pre-step state is still in the other half of the double buffer).
+__global__ void gather_cuts(LrGrid g, LrState prev, LrWork w, double* dst) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i >= g.nx || j >= g.ny) return;
+  int c = j * g.nx + i, np = 0;
+  for (int a = 0; a < g.M; ++a) np += prev.k[a][c] > 0.0;
+  size_t nc = (size_t)g.nx * g.ny;
+  for (int z = 0; z < 6; ++z) dst[z * nc + c] = (np >= 2 + z / 3) ? w.cut[z][c] : 0.0;
+}
+__global__ void gather_xface(const double* src, double* dst, int nx, int ny, int perx) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i > nx || j >= ny) return;
+  int mi = perx ? i % nx : i;
+  dst[j * (nx + 1) + i] = src[j * (nx + 1) + mi];
+}
+__global__ void gather_yface(const double* src, double* dst, int nx, int ny, int pery) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i >= nx || j > ny) return;
+  int mj = pery ? j % ny : j;
+  dst[j * nx + i] = src[mj * nx + i];
+}
+// Mixture fields from the state: P = sum k P_a, rho = sum k rho_a, e = sum(m e)/m.
+__global__ void mixture(LrGrid g, LrState s, double* out, int which) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i >= g.nx || j >= g.ny) return;
+  int c = j * g.nx + i;
+  double P = 0.0, R = 0.0, me = 0.0;
+  for (int a = 0; a < g.M; ++a) {
+    double ka = s.k[a][c];
+    if (!(ka > 0.0)) continue;
+    double ra = s.r[a][c], ea = s.e[a][c];
+    P += ka * ((g.gam[a] - 1.0) * ra * ea - g.pin[a]);
+    R += ka * ra;
+    me += ka * ra * ea;
+  }
+  out[c] = which == 0 ? P : which == 1 ? R : me / R;
+}
+// Conservation sums, one thread per row (deterministic order), then rows
+// summed in order by one thread.
+__global__ void cons_rows(LrGrid g, LrState s, double* rows) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  int nyu = g.pery ? g.ny : g.ny + 1, nxu = g.perx ? g.nx : g.nx + 1;
+  if (j >= nyu) return;
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (j < g.ny)
+    for (int i = 0; i < g.nx; ++i) {
+      int c = j * g.nx + i;
+      for (int a = 0; a < g.M; ++a) {
+        double m = s.r[a][c] * s.k[a][c] * g.V;
+        acc[a] += m; acc[3] += m; acc[6] += m * s.e[a][c];
+      }
+    }
+  for (int i = 0; i < nxu; ++i) {
+    double mp = 0.0;
+    for (int b = -1; b <= 0; ++b)
+      for (int a2 = -1; a2 <= 0; ++a2) {
+        int ci = i + a2, cj = j + b;
+        if (ci < 0) ci = g.perx ? ci + g.nx : -1 - ci;
+        if (ci >= g.nx) ci = g.perx ? ci - g.nx : 2 * g.nx - 1 - ci;
+        if (cj < 0) cj = g.pery ? cj + g.ny : -1 - cj;
+        if (cj >= g.ny) cj = g.pery ? cj - g.ny : 2 * g.ny - 1 - cj;
+        int c = cj * g.nx + ci;
+        for (int a = 0; a < g.M; ++a) mp += 0.25 * s.r[a][c] * s.k[a][c] * g.V;
+      }
+    double wgt = 1.0;
+    if (!g.perx && (i == 0 || i == g.nx)) wgt *= 0.5;
+    if (!g.pery && (j == 0 || j == g.ny)) wgt *= 0.5;
+    int n = j * (g.nx + 1) + i;
+    double u = s.ux[n], v = s.uy[n];
+    acc[4] += wgt * mp * u; acc[5] += wgt * mp * v;
+    acc[7] += 0.5 * wgt * mp * (u * u + v * v);
+  }
+  for (int q = 0; q < 8; ++q) rows[8 * j + q] = acc[q];
+}
+__global__ void cons_sum(const double* rows, int nrows, double* out) {
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int j = 0; j < nrows; ++j)
+    for (int q = 0; q < 8; ++q) acc[q] += rows[8 * j + q];
+  for (int q = 0; q < 7; ++q) out[q] = acc[q];
+  out[7] = acc[6] + acc[7];
+}
+
+lr_status field_to_device(lr_ctx* ctx, int field, double* dst) {
+  const LrGrid& g = ctx->g;
+  const LrState& s = ctx->st[ctx->cur];
+  size_t nc = (size_t)g.nx * g.ny;
+  cudaStream_t st = ctx->stream;
+  dim3 b(128);
+  dim3 gn((g.nx + 1 + 127) / 128, g.ny + 1), gc((g.nx + 127) / 128, g.ny);
+  switch (field) {
+    case LR_F_K: case LR_F_RHO_MAT: case LR_F_E_MAT: case LR_F_E_LAG:
+      for (int a = 0; a < g.M; ++a) {
+        const double* src = field == LR_F_K ? s.k[a] : field == LR_F_RHO_MAT ? s.r[a]
+                          : field == LR_F_E_MAT ? s.e[a] : ctx->w.elag[a];
+        CK(cudaMemcpyAsync(dst + a * nc, src, nc * sizeof(double), cudaMemcpyDeviceToDevice, st), "copy field");
+      }
+      return LR_OK;
+    case LR_F_P: case LR_F_RHO: case LR_F_E:
+      mixture<<<gc, b, 0, st>>>(g, s, dst, field == LR_F_P ? 0 : field == LR_F_RHO ? 1 : 2);
+      CK(cudaGetLastError(), "mixture");
+      return LR_OK;
+    case LR_F_C: case LR_F_VOL_LAGCF: case LR_F_Q: {
+      const double* src = field == LR_F_C ? ctx->w.cc : field == LR_F_Q ? ctx->w.Q : ctx->w.vcf;
+      CK(cudaMemcpyAsync(dst, src, nc * sizeof(double), cudaMemcpyDeviceToDevice, st), "copy field");
+      return LR_OK;
+    }
+    case LR_F_UX: case LR_F_UY: case LR_F_UHX: case LR_F_UHY: {
+      const double* src = field == LR_F_UX ? s.ux : field == LR_F_UY ? s.uy
+                        : field == LR_F_UHX ? ctx->w.uhx : ctx->w.uhy;
+      gather_node<<<gn, b, 0, st>>>(src, dst, g.nx, g.ny, g.perx, g.pery);
+      CK(cudaGetLastError(), "gather_node");
+      return LR_OK;
+    }
+    case LR_F_FX: case LR_F_MX:
+      gather_xface<<<gn, b, 0, st>>>(field == LR_F_FX ? ctx->w.fx : ctx->w.MX, dst, g.nx, g.ny, g.perx);
+      CK(cudaGetLastError(), "gather_xface");
+      return LR_OK;
+    case LR_F_FY: case LR_F_MY:
+      gather_yface<<<gn, b, 0, st>>>(field == LR_F_FY ? ctx->w.fy : ctx->w.MY, dst, g.nx, g.ny, g.pery);
+      CK(cudaGetLastError(), "gather_yface");
+      return LR_OK;
+    case LR_F_FC: case LR_F_MC:
+      CK(lr_launch_corner_debug(g, ctx->w, field == LR_F_FC ? dst : nullptr, field == LR_F_MC ? dst : nullptr, st),
+         "corner view");
+      return LR_OK;
+    case LR_F_DT:
+      CK(cudaMemcpyAsync(dst, ctx->w.scal + 2, sizeof(double), cudaMemcpyDeviceToDevice, st), "dt");
+      return LR_OK;
+    case LR_F_CUTS:
+      gather_cuts<<<gc, b, 0, st>>>(g, ctx->st[1 - ctx->cur], ctx->w, dst);
+      CK(cudaGetLastError(), "gather_cuts");
+      return LR_OK;
+    case LR_F_XA: case LR_F_YA: case LR_F_CA:
+      for (int a = 0; a < g.M; ++a) {
+        if (field == LR_F_XA)
+          gather_xface<<<gn, b, 0, st>>>(ctx->w.xA[a], dst + (size_t)a * (g.nx + 1) * g.ny, g.nx, g.ny, g.perx);
+        else if (field == LR_F_YA)
+          gather_yface<<<gn, b, 0, st>>>(ctx->w.yA[a], dst + (size_t)a * g.nx * (g.ny + 1), g.nx, g.ny, g.pery);
+        else
+          gather_node<<<gn, b, 0, st>>>(ctx->w.cA[a], dst + (size_t)a * (g.nx + 1) * (g.ny + 1), g.nx, g.ny, g.perx, g.pery);
+      }
+      CK(cudaGetLastError(), "gather per-material flux");
+      return LR_OK;
+    case LR_F_CONS: {
+      int nrows = g.pery ? g.ny : g.ny + 1;
+      cons_rows<<<(nrows + 63) / 64, 64, 0, st>>>(g, s, ctx->rows);
+      cons_sum<<<1, 1, 0, st>>>(ctx->rows, nrows, dst);
+      CK(cudaGetLastError(), "cons");
+      return LR_OK;
+    }
+  }
+  setmsg(ctx, "unknown field %d", field);
+  return LR_ERR_ARG;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lr_config_default(lr_config* c) {
+  if (!c) return;
+  memset(c, 0, sizeof(*c));
+  c->nmat = 1;
+  c->x1 = 1.0;
+  c->y1 = 1.0;
+  c->cfl = 0.25;
+  c->a1 = 0.5;
+  c->a2 = 1.0;
+  c->face_order = 2;
+  c->corner_recon = LR_CORNER_DIAG;
+  c->precision = LR_FP64;
+}
+
+lr_status lr_workspace_bytes(const lr_config* cfg, size_t* bytes) {
+  char why[160];
+  if (!bytes || !config_ok(cfg, why, sizeof(why))) return LR_ERR_ARG;
+  *bytes = layout(cfg, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+  return LR_OK;
+}
+
+lr_status lr_create(const lr_config* cfg, lr_ctx** out) { return create_common(cfg, nullptr, 0, true, out); }
+
+lr_status lr_create_in(const lr_config* cfg, void* dev_mem, size_t bytes, lr_ctx** out) {
+  return create_common(cfg, dev_mem, bytes, false, out);
+}
+
+lr_status lr_set_materials(lr_ctx* ctx, int nmat, const lr_material* mats) {
+  if (!ctx) return LR_ERR_ARG;
+  if (nmat != ctx->cfg.nmat || !mats) { setmsg(ctx, "lr_set_materials: need %d materials", ctx->cfg.nmat); return LR_ERR_ARG; }
+  for (int a = 0; a < nmat; ++a) {
+    if (!(mats[a].gamma > 1.0) || !(mats[a].pi >= 0.0)) { setmsg(ctx, "material %d: gamma > 1, pi >= 0 required", a); return LR_ERR_ARG; }
+  }
+  for (int a = 0; a < nmat; ++a) { ctx->g.gam[a] = mats[a].gamma; ctx->g.pin[a] = mats[a].pi; }
+  ctx->have_mats = true;
+  drop_graphs(ctx);
+  return LR_OK;
+}
+
+lr_status lr_init(lr_ctx* ctx, const double* k, const double* rho, const double* p, const double* ux,
+                  const double* uy) {
+  if (!ctx) return LR_ERR_ARG;
+  if (!ctx->have_mats) { setmsg(ctx, "lr_init before lr_set_materials"); return LR_ERR_STATE; }
+  if (!k || !rho || !p || !ux || !uy) { setmsg(ctx, "lr_init: null array"); return LR_ERR_ARG; }
+  const LrGrid& g = ctx->g;
+  size_t nc = (size_t)g.nx * g.ny, nn = (size_t)(g.nx + 1) * (g.ny + 1);
+  ctx->cur = 0;
+  LrState& s = ctx->st[0];
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  for (int a = 0; a < g.M; ++a) {
+    CK(cudaMemcpyAsync(s.k[a], k + a * nc, nc * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload k");
+    CK(cudaMemcpyAsync(s.r[a], rho + a * nc, nc * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload rho");
+    CK(cudaMemcpyAsync(s.e[a], p + a * nc, nc * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload p");
+  }
+  CK(cudaMemcpyAsync(s.ux, ux, nn * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload ux");
+  CK(cudaMemcpyAsync(s.uy, uy, nn * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload uy");
+  CK(lr_launch_reset(ctx->w, ctx->stream), "reset");
+  CK(lr_launch_prepare_init(g, s, ctx->w, ctx->stream), "prepare");
+  CK(lr_launch_init_cfl(g, s, ctx->w, ctx->stream), "initial cfl");
+  ctx->sticky = LR_OK;
+  ctx->inited = false;
+  lr_status st = check_sticky(ctx);
+  if (st != LR_OK) {
+    setmsg(ctx, "lr_init: invalid initial state (k outside [0,1], sum k != 1, or rho <= 0)");
+    ctx->sticky = LR_OK;
+    return LR_ERR_ARG;
+  }
+  ctx->inited = true;
+  return LR_OK;
+}
+
+lr_status lr_set_prescribed_velocity(lr_ctx* ctx, const double* ux, const double* uy) {
+  if (!ctx) return LR_ERR_ARG;
+  size_t nn = (size_t)(ctx->g.nx + 1) * (ctx->g.ny + 1);
+  if (!ux || !uy) {
+    ctx->g.presc = 0;
+  } else {
+    CK(cudaMemcpyAsync(ctx->w.pux, ux, nn * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload pu");
+    CK(cudaMemcpyAsync(ctx->w.puy, uy, nn * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload pu");
+    CK(cudaStreamSynchronize(ctx->stream), "sync");
+    ctx->g.presc = 1;
+  }
+  drop_graphs(ctx);
+  return LR_OK;
+}
+
+lr_status lr_step(lr_ctx* ctx, double t_end, double* dt_taken) {
+  if (!ctx) return LR_ERR_ARG;
+  if (!ctx->inited) { setmsg(ctx, "lr_step before lr_init"); return LR_ERR_STATE; }
+  if (ctx->sticky != LR_OK) return (lr_status)ctx->sticky;
+  CK(lr_launch_set_scalar(ctx->w.scal + 3, t_end, ctx->stream), "set t_end");
+  CK(enqueue_step(ctx, ctx->cur), "step launch");
+  ctx->cur = 1 - ctx->cur;
+  if (dt_taken) {
+    lr_status s = check_sticky(ctx);
+    if (s != LR_OK) return s;
+    CK(cudaMemcpy(dt_taken, ctx->w.scal + 2, sizeof(double), cudaMemcpyDeviceToHost), "read dt");
+  }
+  return LR_OK;
+}
+
+lr_status lr_run(lr_ctx* ctx, double t_end, long max_steps, long* steps_done, double* t_now) {
+  if (!ctx) return LR_ERR_ARG;
+  if (!ctx->inited) { setmsg(ctx, "lr_run before lr_init"); return LR_ERR_STATE; }
+  if (ctx->sticky != LR_OK) return (lr_status)ctx->sticky;
+  if (max_steps < 0) return LR_ERR_ARG;
+  double s0[5];
+  CK(cudaMemcpyAsync(s0, ctx->w.scal, sizeof(s0), cudaMemcpyDeviceToHost, ctx->stream), "read scalars");
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  CK(lr_launch_set_scalar(ctx->w.scal + 3, t_end, ctx->stream), "set t_end");
+  const long chunk = 64;
+  long done = 0;
+  while (done < max_steps) {
+    long n = max_steps - done < chunk ? max_steps - done : chunk;
+    for (long q = 0; q < n; ++q) {
+      if (ctx->prof) {
+        CK(enqueue_step(ctx, ctx->cur), "step launch");
+      } else {
+        lr_status s = ensure_graph(ctx, ctx->cur);
+        if (s != LR_OK) return s;
+        CK(cudaGraphLaunch(ctx->gexec[ctx->cur], ctx->stream), "graph launch");
+      }
+      ctx->cur = 1 - ctx->cur;
+    }
+    done += n;
+    double sc[5];
+    CK(cudaMemcpyAsync(sc, ctx->w.scal, sizeof(sc), cudaMemcpyDeviceToHost, ctx->stream), "read scalars");
+    lr_status s = check_sticky(ctx);
+    if (s != LR_OK) return s;
+    if (!(sc[0] < t_end)) break;
+  }
+  double sc[5];
+  CK(cudaMemcpyAsync(sc, ctx->w.scal, sizeof(sc), cudaMemcpyDeviceToHost, ctx->stream), "read scalars");
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  if (steps_done) *steps_done = (long)(sc[4] - s0[4] + 0.5);
+  if (t_now) *t_now = sc[0];
+  return LR_OK;
+}
+
+lr_status lr_sync(lr_ctx* ctx) {
+  if (!ctx) return LR_ERR_ARG;
+  return check_sticky(ctx);
+}
+
+size_t lr_field_size(const lr_ctx* ctx, int field) {
+  if (!ctx) return 0;
+  size_t nx = ctx->g.nx, ny = ctx->g.ny, M = ctx->g.M;
+  switch (field) {
+    case LR_F_K: case LR_F_RHO_MAT: case LR_F_E_MAT: case LR_F_E_LAG: return M * nx * ny;
+    case LR_F_P: case LR_F_RHO: case LR_F_E: case LR_F_C: case LR_F_VOL_LAGCF: case LR_F_Q: return nx * ny;
+    case LR_F_UX: case LR_F_UY: case LR_F_UHX: case LR_F_UHY: case LR_F_FC: case LR_F_MC: return (nx + 1) * (ny + 1);
+    case LR_F_FX: case LR_F_MX: return (nx + 1) * ny;
+    case LR_F_FY: case LR_F_MY: return nx * (ny + 1);
+    case LR_F_CONS: return 8;
+    case LR_F_DT: return 1;
+    case LR_F_CUTS: return 6 * nx * ny;
+    case LR_F_XA: return M * (nx + 1) * ny;
+    case LR_F_YA: return M * nx * (ny + 1);
+    case LR_F_CA: return M * (nx + 1) * (ny + 1);
+  }
+  return 0;
+}
+
+lr_status lr_get_fields(lr_ctx* ctx, int field, double* host_out, size_t n_elems) {
+  if (!ctx || !host_out) return LR_ERR_ARG;
+  size_t need = lr_field_size(ctx, field);
+  if (need == 0 || n_elems < need) { setmsg(ctx, "lr_get_fields: field %d needs %zu elements", field, need); return LR_ERR_ARG; }
+  if (!ctx->inited) { setmsg(ctx, "lr_get_fields before lr_init"); return LR_ERR_STATE; }
+  lr_status s = field_to_device(ctx, field, ctx->tmp);
+  if (s != LR_OK) return s;
+  CK(cudaMemcpyAsync(host_out, ctx->tmp, need * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "download");
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  return LR_OK;
+}
+
+lr_status lr_get_fields_device(lr_ctx* ctx, int field, double* dev_out, size_t n_elems) {
+  if (!ctx || !dev_out) return LR_ERR_ARG;
+  size_t need = lr_field_size(ctx, field);
+  if (need == 0 || n_elems < need) return LR_ERR_ARG;
+  if (!ctx->inited) return LR_ERR_STATE;
+  return field_to_device(ctx, field, dev_out);
+}
+
+lr_status lr_time(lr_ctx* ctx, double* t, double* dt_next) {
+  if (!ctx) return LR_ERR_ARG;
+  double sc[5];
+  CK(cudaMemcpyAsync(sc, ctx->w.scal, sizeof(sc), cudaMemcpyDeviceToHost, ctx->stream), "read scalars");
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  if (t) *t = sc[0];
+  if (dt_next) *dt_next = ctx->g.dt_fixed > 0.0 ? ctx->g.dt_fixed : sc[1];
+  return LR_OK;
+}
+
+int lr_launches_per_step(const lr_ctx* ctx) { return ctx ? (int)LRK_COUNT : 0; }
+
+lr_status lr_set_profiling(lr_ctx* ctx, int on) {
+  if (!ctx) return LR_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  for (auto& p : ctx->pend) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+  ctx->pend.clear();
+  for (int k = 0; k < LRK_COUNT; ++k) { ctx->acc_ms[k] = 0.0; ctx->acc_n[k] = 0; }
+  ctx->prof = on != 0;
+  return LR_OK;
+}
+
+int lr_kernel_times(lr_ctx* ctx, const char** names, long* launches, double* ms, int n) {
+  if (!ctx) return 0;
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& p : ctx->pend) {
+    float t = 0.0f;
+    if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) { ctx->acc_ms[p.kid] += t; ctx->acc_n[p.kid] += 1; }
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  ctx->pend.clear();
+  int m = n < (int)LRK_COUNT ? n : (int)LRK_COUNT;
+  for (int k = 0; k < m; ++k) {
+    if (names) names[k] = lr_kernel_names[k];
+    if (launches) launches[k] = ctx->acc_n[k];
+    if (ms) ms[k] = ctx->acc_ms[k];
+  }
+  return LRK_COUNT;
+}
+
+void lr_destroy(lr_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  drop_graphs(ctx);
+  for (auto& p : ctx->pend) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  if (ctx->own_arena) cudaFree(ctx->arena);
+  delete ctx;
+}
+
+const char* lr_last_error(const lr_ctx* ctx) { return ctx ? ctx->msg : "null context"; }
+
+}  // extern "C"

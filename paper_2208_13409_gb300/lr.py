@@ -1,0 +1,273 @@
+"""Thin ctypes binding of the C ABI in include/lr.h (argument marshalling
+only; every phase of the step runs in the CUDA library).
+
+PyTorch supplies the device memory (one arena tensor per simulation, from
+its caching allocator) and the CUDA stream (torch's current stream) when it
+is available; the library allocates its own otherwise.  ``load()`` raises if
+the library cannot be built or loaded: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import re
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lr.h")
+
+OK, ERR_ARG, ERR_OOM, ERR_NUMERIC, ERR_TIMEOUT, ERR_STATE, ERR_CUDA = 0, -1, -2, -3, -4, -5, -6
+BC_REFLECT, BC_PERIODIC = 0, 1
+CORNER_UPWIND, CORNER_DIAG = 0, 1
+FP64 = 0
+F_K, F_RHO_MAT, F_E_MAT, F_P, F_RHO, F_E, F_UX, F_UY, F_CONS, F_C = range(10)
+F_UHX, F_UHY, F_VOL_LAGCF, F_E_LAG, F_FX, F_FY, F_FC, F_MX, F_MY, F_MC, F_Q, F_DT = range(20, 32)
+F_CUTS, F_XA, F_YA, F_CA = range(32, 36)
+
+
+class LrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"lr status {status}: {msg}")
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+        ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+        ("nmat", ctypes.c_int),
+        ("cfl", ctypes.c_double), ("a1", ctypes.c_double), ("a2", ctypes.c_double),
+        ("bc", ctypes.c_int * 4),
+        ("precision", ctypes.c_int), ("face_order", ctypes.c_int), ("corner_recon", ctypes.c_int),
+        ("dt_fixed", ctypes.c_double),
+        ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
+class Material(ctypes.Structure):
+    _fields_ = [("eos", ctypes.c_int), ("gamma", ctypes.c_double), ("pi", ctypes.c_double)]
+
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def declared_symbols() -> list:
+    """Names of the functions declared in include/lr.h."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lr_[a-z_]+)\s*\(", text)))
+
+
+def load(build_if_missing: bool = True):
+    """Load (building first if needed) the CUDA library; raises on failure."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing")
+    L = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    L.lr_config_default.argtypes = [ctypes.POINTER(Config)]
+    L.lr_config_default.restype = None
+    L.lr_workspace_bytes.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_size_t)]
+    L.lr_create.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(vp)]
+    L.lr_create_in.argtypes = [ctypes.POINTER(Config), vp, ctypes.c_size_t, ctypes.POINTER(vp)]
+    L.lr_set_materials.argtypes = [vp, ctypes.c_int, ctypes.POINTER(Material)]
+    L.lr_init.argtypes = [vp, _dp, _dp, _dp, _dp, _dp]
+    L.lr_set_prescribed_velocity.argtypes = [vp, _dp, _dp]
+    L.lr_step.argtypes = [vp, ctypes.c_double, _dp]
+    L.lr_run.argtypes = [vp, ctypes.c_double, ctypes.c_long, ctypes.POINTER(ctypes.c_long), _dp]
+    L.lr_sync.argtypes = [vp]
+    L.lr_field_size.argtypes = [vp, ctypes.c_int]
+    L.lr_field_size.restype = ctypes.c_size_t
+    L.lr_get_fields.argtypes = [vp, ctypes.c_int, _dp, ctypes.c_size_t]
+    L.lr_get_fields_device.argtypes = [vp, ctypes.c_int, vp, ctypes.c_size_t]
+    L.lr_time.argtypes = [vp, _dp, _dp]
+    L.lr_launches_per_step.argtypes = [vp]
+    L.lr_launches_per_step.restype = ctypes.c_int
+    L.lr_set_profiling.argtypes = [vp, ctypes.c_int]
+    L.lr_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_long),
+                                  _dp, ctypes.c_int]
+    L.lr_kernel_times.restype = ctypes.c_int
+    L.lr_destroy.argtypes = [vp]
+    L.lr_destroy.restype = None
+    L.lr_last_error.argtypes = [vp]
+    L.lr_last_error.restype = ctypes.c_char_p
+    for name in ("lr_workspace_bytes", "lr_create", "lr_create_in", "lr_set_materials", "lr_init",
+                 "lr_set_prescribed_velocity", "lr_step", "lr_run", "lr_sync", "lr_get_fields",
+                 "lr_get_fields_device", "lr_time", "lr_set_profiling"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _c64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def make_config(problem, stream: Optional[int] = None) -> Config:
+    c = Config()
+    load().lr_config_default(ctypes.byref(c))
+    c.nx, c.ny = problem.nx, problem.ny
+    c.x0, c.x1, c.y0, c.y1 = problem.x0, problem.x1, problem.y0, problem.y1
+    c.nmat = problem.nmat
+    c.cfl, c.a1, c.a2 = problem.cfl, problem.a1, problem.a2
+    for q in range(4):
+        c.bc[q] = problem.bc[q]
+    c.precision = FP64
+    c.face_order = problem.face_order
+    c.corner_recon = problem.corner_recon
+    c.dt_fixed = problem.dt_fixed
+    c.cuda_stream = stream
+    return c
+
+
+class Sim:
+    """One simulation on the GPU behind the C ABI."""
+
+    def __init__(self, problem, use_torch: bool = True):
+        L = load()
+        self.p = problem
+        self._arena = None
+        self.stream = None
+        stream = None
+        if use_torch:
+            import torch
+            if not torch.cuda.is_available():
+                raise RuntimeError("CUDA device required")
+            cs = torch.cuda.current_stream()
+            # the library runs on a real stream so that torch events can be
+            # recorded on it; the legacy default stream gets a private one
+            self.stream = cs if cs.cuda_stream != 0 else torch.cuda.Stream()
+            stream = self.stream.cuda_stream
+        self.cfg = make_config(problem, stream)
+        h = ctypes.c_void_p()
+        if use_torch:
+            import torch
+            nbytes = ctypes.c_size_t()
+            self._check(L.lr_workspace_bytes(ctypes.byref(self.cfg), ctypes.byref(nbytes)), None)
+            self._arena = torch.empty(int(nbytes.value) + 256, dtype=torch.uint8, device="cuda")
+            base = self._arena.data_ptr()
+            base = (base + 255) & ~255
+            rc = L.lr_create_in(ctypes.byref(self.cfg), ctypes.c_void_p(base), nbytes.value, ctypes.byref(h))
+        else:
+            rc = L.lr_create(ctypes.byref(self.cfg), ctypes.byref(h))
+        if rc != OK or not h.value:
+            raise LrError(rc, "lr_create failed")
+        self._h = h
+        mats = (Material * problem.nmat)()
+        for a in range(problem.nmat):
+            mats[a].eos = 1 if problem.pinf[a] > 0 else 0
+            mats[a].gamma = float(problem.gamma[a])
+            mats[a].pi = float(problem.pinf[a])
+        self._check(L.lr_set_materials(self._h, problem.nmat, mats))
+        self.init(problem)
+
+    def _check(self, rc, h="self"):
+        if rc != OK:
+            msg = load().lr_last_error(self._h if h == "self" else None)
+            raise LrError(rc, msg.decode() if msg else "")
+
+    def init(self, problem):
+        k, r, p = _c64(problem.k), _c64(problem.rho), _c64(problem.p)
+        ux, uy = _c64(problem.ux), _c64(problem.uy)
+        self._check(load().lr_init(self._h, _ptr(k), _ptr(r), _ptr(p), _ptr(ux), _ptr(uy)))
+
+    def set_prescribed(self, ux, uy):
+        self._pv = (_c64(ux), _c64(uy))
+        self._check(load().lr_set_prescribed_velocity(self._h, _ptr(self._pv[0]), _ptr(self._pv[1])))
+
+    def step(self, t_end: float = 1e300, sync: bool = True) -> Optional[float]:
+        if sync:
+            dt = ctypes.c_double()
+            self._check(load().lr_step(self._h, t_end, ctypes.byref(dt)))
+            return dt.value
+        self._check(load().lr_step(self._h, t_end, None))
+        return None
+
+    def run(self, nsteps: int, t_end: float = 1e300):
+        n = ctypes.c_long()
+        t = ctypes.c_double()
+        self._check(load().lr_run(self._h, t_end, nsteps, ctypes.byref(n), ctypes.byref(t)))
+        return n.value, t.value
+
+    def sync(self):
+        self._check(load().lr_sync(self._h))
+
+    @property
+    def t(self) -> float:
+        t = ctypes.c_double()
+        self._check(load().lr_time(self._h, ctypes.byref(t), None))
+        return t.value
+
+    def dt_next(self) -> float:
+        d = ctypes.c_double()
+        self._check(load().lr_time(self._h, None, ctypes.byref(d)))
+        return d.value
+
+    def get(self, field: int) -> np.ndarray:
+        L = load()
+        n = L.lr_field_size(self._h, field)
+        out = np.empty(n, dtype=np.float64)
+        self._check(L.lr_get_fields(self._h, field, _ptr(out), n))
+        nx, ny, M = self.p.nx, self.p.ny, self.p.nmat
+        if field in (F_K, F_RHO_MAT, F_E_MAT, F_E_LAG):
+            return out.reshape(M, ny, nx)
+        if field in (F_P, F_RHO, F_E, F_C, F_VOL_LAGCF, F_Q):
+            return out.reshape(ny, nx)
+        if field in (F_UX, F_UY, F_UHX, F_UHY, F_FC, F_MC):
+            return out.reshape(ny + 1, nx + 1)
+        if field in (F_FX, F_MX):
+            return out.reshape(ny, nx + 1)
+        if field in (F_FY, F_MY):
+            return out.reshape(ny + 1, nx)
+        if field == F_CUTS:
+            return out.reshape(6, ny, nx)
+        if field == F_XA:
+            return out.reshape(M, ny, nx + 1)
+        if field == F_YA:
+            return out.reshape(M, ny + 1, nx)
+        if field == F_CA:
+            return out.reshape(M, ny + 1, nx + 1)
+        return out
+
+    def get_device(self, field: int, out_ptr: int, n: int):
+        self._check(load().lr_get_fields_device(self._h, field, ctypes.c_void_p(out_ptr), n))
+
+    def launches_per_step(self) -> int:
+        return load().lr_launches_per_step(self._h)
+
+    def set_profiling(self, on: bool):
+        self._check(load().lr_set_profiling(self._h, 1 if on else 0))
+
+    def kernel_times(self):
+        L = load()
+        n = 16
+        names = (ctypes.c_char_p * n)()
+        cnt = (ctypes.c_long * n)()
+        ms = (ctypes.c_double * n)()
+        k = L.lr_kernel_times(self._h, names, cnt, ms, n)
+        return {names[q].decode(): (cnt[q], ms[q]) for q in range(min(k, n))}
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            load().lr_destroy(h)
+            self._h = ctypes.c_void_p()
+        self._arena = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,39 @@
+"""The CUDA library builds for sm_103a, loads, and exports every entry point
+that include/lr.h declares.  No compute call is made (no GPU needed)."""
+import ctypes
+
+import pytest
+
+from paper_2208_13409_gb300 import lr, problems as P
+
+
+def test_header_declares_the_boundary():
+    names = lr.declared_symbols()
+    for core in ("lr_create", "lr_set_materials", "lr_init", "lr_step", "lr_run", "lr_get_fields",
+                 "lr_destroy", "lr_last_error"):
+        assert core in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = lr.load()
+    missing = [n for n in lr.declared_symbols() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_host_side_validation_without_gpu():
+    L = lr.load()
+    cfg = lr.make_config(P.sod(nx=16))
+    nbytes = ctypes.c_size_t()
+    assert L.lr_workspace_bytes(ctypes.byref(cfg), ctypes.byref(nbytes)) == lr.OK
+    assert nbytes.value > 16 * 4 * 8
+    bad = lr.make_config(P.sod(nx=16))
+    bad.nx = 1
+    h = ctypes.c_void_p()
+    assert L.lr_create(ctypes.byref(bad), ctypes.byref(h)) == lr.ERR_ARG and not h.value
+    bad = lr.make_config(P.sod(nx=16))
+    bad.nmat = 4
+    assert L.lr_workspace_bytes(ctypes.byref(bad), ctypes.byref(nbytes)) == lr.ERR_ARG
+    bad = lr.make_config(P.sod(nx=16))
+    bad.bc[0] = lr.BC_PERIODIC  # xlo != xhi
+    assert L.lr_workspace_bytes(ctypes.byref(bad), ctypes.byref(nbytes)) == lr.ERR_ARG
+    assert L.lr_last_error(None) == b"null context"
