@@ -192,6 +192,31 @@ int lr_kernel_times(lr_ctx* ctx, const char** names, long* launches, double* ms,
 void lr_destroy(lr_ctx* ctx);
 const char* lr_last_error(const lr_ctx* ctx);
 
+/* Allocation-free CFL time step.  The paper has no counterpart: this is a
+ * service for callers that may not allocate device memory when they need a
+ * time step (all device memory already reserved by another framework's
+ * caching allocator, or a latency-critical loop that must not reach
+ * cudaMalloc).  It computes the same rule as lr_step,
+ * dt = cfl * min(dx,dy) / max_p (max over the node's cells of c_c + |u_p|),
+ * from a state held in caller-owned device memory:
+ *   k, rho, e  device [nmat][ny][nx] (volume fractions, densities, specific
+ *              internal energies, as lr_get_fields_device returns them);
+ *   ux, uy     device [(ny+1)][(nx+1)];
+ *   dt_out     device pointer to one double that receives dt;
+ * cfg supplies nx, ny, domain, nmat, cfl, bc and the stream
+ * (cfg->cuda_stream, NULL = the legacy default stream); mats[nmat] the EOS.
+ * The work is enqueued on that stream; nothing is synchronised.
+ * Scratch is a fixed array inside the library (8 MiB on every GPU that loads
+ * it, kept until the process exits): nx*ny above 2^20 is rejected with
+ * LR_ERR_ARG.  No cudaMalloc/cudaFree or other allocating call is made.  The
+ * first call on a device looks up the scratch address on that device (make
+ * that first call before any stream capture).  All calls share the scratch,
+ * so calls that overlap on the GPU (other streams, other host threads) race:
+ * serialise them. */
+lr_status lr_cfl_dt_noalloc(const lr_config* cfg, const lr_material* mats, const double* k,
+                            const double* rho, const double* e, const double* ux, const double* uy,
+                            double* dt_out);
+
 #ifdef __cplusplus
 }
 #endif

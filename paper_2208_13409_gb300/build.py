@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblr.so")
-SOURCES = ["lr_kernels.cu", "lr_api.cu"]
+SOURCES = ["lr_kernels.cu", "lr_api.cu", "lr_noalloc.cu"]
 HEADERS = ["lr_dev.cuh", os.path.join("..", "..", "include", "lr.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]

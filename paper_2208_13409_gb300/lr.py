@@ -99,6 +99,8 @@ def load(build_if_missing: bool = True):
     L.lr_destroy.restype = None
     L.lr_last_error.argtypes = [vp]
     L.lr_last_error.restype = ctypes.c_char_p
+    L.lr_cfl_dt_noalloc.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(Material), vp, vp, vp, vp, vp, vp]
+    L.lr_cfl_dt_noalloc.restype = ctypes.c_int
     for name in ("lr_workspace_bytes", "lr_create", "lr_create_in", "lr_set_materials", "lr_init",
                  "lr_set_prescribed_velocity", "lr_step", "lr_run", "lr_sync", "lr_get_fields",
                  "lr_get_fields_device", "lr_time", "lr_set_profiling"):
