@@ -35,11 +35,15 @@ WORKLOAD = "triple_point_1400x600_3mat_fp64"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="lr", choices=["lr", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-baseline-steps", type=int, default=20)
+    ap.add_argument("--t-start", type=float, default=2.0,
+                    help="advance the workload to this time before warm-up and timing (run ends at t=5)")
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="init + warm-up + K steps of the workload and exit (for ncu captures)")
     return ap.parse_args()
 
 
@@ -112,19 +116,18 @@ def load_peaks():
         return {}
 
 
-# FP64 operations per unit of the dominant kernels (pure-material path), from
-# the static operation count in DESIGN.md ("Roofline"): adds, multiplies and
-# FMAs count 1, a division 1 and a square root 1 (algorithmic count, not the
-# hardware instruction count).
+# FP64 operations per unit of each kernel, counted on the source for the
+# single-material path with every flux active (kernel table): adds,
+# multiplies, FMAs, divisions and square roots count 1 each.
 FLOPS_PER_UNIT = {
-    "lr_mat_flux": 78.0,      # per canonical node (one X face, one Y face, one corner)
-    "lr_dual_flux": 186.0,    # per dual index (one dual X face, Y face, two corners)
-    "lr_cell_pre": 74.0,      # per cell (three materials, one present)
-    "lr_cell_lag": 51.0,      # per canonical node (one cell, two faces)
-    "lr_cell_update": 72.0,   # per cell
-    "lr_cell_cf": 24.0,       # per cell
-    "lr_node_half": 19.0,     # per node
-    "lr_node_update": 47.0,   # per node
+    "lr_cell_pre": 79.0,      # per cell
+    "lr_node_half": 25.0,     # per node
+    "lr_cell_lag": 74.0,      # per node-grid point (one cell, one X face, one Y face)
+    "lr_cell_cf": 14.0,       # per cell
+    "lr_mat_flux": 152.0,     # per node-grid point (one X face, one Y face, one corner)
+    "lr_cell_update": 41.0,   # per cell
+    "lr_dual_flux": 210.0,    # per dual index (dual X face, dual Y face, two dual corners)
+    "lr_node_update": 38.0,   # per node
 }
 
 
@@ -134,6 +137,20 @@ def units_per_launch(kernel, nx, ny):
     if kernel == "lr_dual_flux":
         return (nx + 2) * (ny + 2)
     return (nx + 1) * (ny + 1)
+
+
+def kernel_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
+    None when the kernel source has changed since the counters were taken."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        src = open(os.path.join(ROOT, "paper_2208_13409_gb300", "csrc", "lr_kernels.cu"), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] != rec["kernel_source_sha256_prefix"]:
+            return None
+        return rec["dram_bytes_per_launch"].get(kernel.split("<")[0])
+    except Exception:
+        return None
 
 
 def fp64_peak_flops(sm_mhz=None):
@@ -196,6 +213,10 @@ def run_lr(args, world, rank, local):
     cells = pr.cells
     sim = lr.Sim(pr)
     stream = sim.stream
+    if args.t_start > 0:
+        pre_steps, _ = sim.run(1 << 30, args.t_start)  # developed flow, mid-run
+    else:
+        pre_steps = 0
     for _ in range(args.warmup):
         sim.step(sync=False)
     sim.sync()
@@ -249,13 +270,7 @@ def run_lr(args, world, rank, local):
     flops = FLOPS_PER_UNIT.get(dom, 0.0) * units_per_launch(dom, pr.nx, pr.ny)
     achieved = flops / (dom_ms * 1e-3) / 1e12
     peak = fp64_peak_flops() / 1e12
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tpath):
-        try:
-            traffic = json.load(open(tpath)).get(dom)
-        except Exception:
-            traffic = None
+    traffic = kernel_traffic(dom)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": dom,
                 "kernel_ms": dom_ms, "peak_source": "FP64: 152 SMs x 4 flop/clk x 2.07 GHz (unit counts)"}
@@ -294,6 +309,7 @@ def run_lr(args, world, rank, local):
                 "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "nx": pr.nx, "ny": pr.ny, "nmat": pr.nmat,
+                           "t_start": args.t_start, "steps_before_timing": pre_steps + args.warmup,
                            "l2": "flushed between timed steps (512 MB write, untimed)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
                 "gpu_launches": K * (sim.launches_per_step() + 1),
@@ -310,9 +326,26 @@ def run_lr(args, world, rank, local):
         dist.destroy_process_group()
 
 
+def run_kernels_only(args):
+    """The workload's steps and nothing else, for profiler captures."""
+    import torch
+    from paper_2208_13409_gb300 import lr, problems as P
+
+    sim = lr.Sim(P.triple_point())
+    if args.t_start > 0:
+        sim.run(1 << 30, args.t_start)
+    for _ in range(args.warmup + args.steps):
+        sim.step(sync=False)
+    sim.sync()
+    torch.cuda.synchronize()
+
+
 def main():
     args = parse()
     world, rank, local = dist_setup()
+    if args.kernels_only:
+        run_kernels_only(args)
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
         return

@@ -104,11 +104,13 @@ size_t layout(const lr_config* cfg, char* base, LrState* st, LrWork* w, double**
     s[q].ux = b.take<double>(nn); s[q].uy = b.take<double>(nn);
   }
   W.scal = b.take<double>(8);
-  W.red = b.take<unsigned long long>(2);
+  W.red = b.take<unsigned long long>(4);
+  W.mixed = b.take<int>(nc);
   W.err = b.take<int>(2);
   W.pux = b.take<double>(nn); W.puy = b.take<double>(nn);
   W.mc = b.take<double>(nc); W.Q = b.take<double>(nc); W.Pi = b.take<double>(nc); W.cc = b.take<double>(nc);
-  for (size_t a = 0; a < M; ++a) { W.Ph[a] = b.take<double>(nc); W.elag[a] = b.take<double>(nc); W.rcf[a] = b.take<double>(nc); }
+  for (size_t a = 0; a < M; ++a) { W.elc[a] = b.take<double>(nc); W.elag[a] = b.take<double>(nc); W.rcf[a] = b.take<double>(nc); }
+  W.mask = b.take<unsigned char>(nc);
   W.ox = b.take<double>(nc); W.oy = b.take<double>(nc); W.wx = b.take<double>(nc); W.wy = b.take<double>(nc);
   W.vcf = b.take<double>(nc);
   for (int q = 0; q < 6; ++q) W.cut[q] = b.take<double>(nc);
@@ -153,6 +155,12 @@ void fill_grid(lr_ctx* c) {
   g.L = sqrt(g.dx * g.dy);
   g.hmin = g.dx < g.dy ? g.dx : g.dy;
   g.D = sqrt(g.dx * g.dx + g.dy * g.dy);
+  g.inv2dx = 1.0 / (2.0 * g.dx);
+  g.inv2dy = 1.0 / (2.0 * g.dy);
+  g.inv8dx = 1.0 / (8.0 * g.dx);
+  g.inv8dy = 1.0 / (8.0 * g.dy);
+  g.invV = 1.0 / g.V;
+  g.invD = 1.0 / g.D;
   g.cfl = f.cfl; g.a1 = f.a1; g.a2 = f.a2; g.dt_fixed = f.dt_fixed;
   g.face_o2 = f.face_order == 2;
   g.corner_o2 = f.corner_recon == LR_CORNER_DIAG;
@@ -538,9 +546,16 @@ lr_status lr_run(lr_ctx* ctx, double t_end, long max_steps, long* steps_done, do
   CK(cudaMemcpyAsync(s0, ctx->w.scal, sizeof(s0), cudaMemcpyDeviceToHost, ctx->stream), "read scalars");
   CK(cudaStreamSynchronize(ctx->stream), "sync");
   CK(lr_launch_set_scalar(ctx->w.scal + 3, t_end, ctx->stream), "set t_end");
-  const long chunk = 64;
-  long done = 0;
-  while (done < max_steps) {
+  // Steps are enqueued in chunks; after each chunk t and the next CFL dt are
+  // read back and the next chunk is sized from the time left, so few no-op
+  // steps (t already at t_end) are enqueued.
+  long done = 0, chunk = 64;
+  double t_cur = s0[0], dt_cur = ctx->g.dt_fixed > 0.0 ? ctx->g.dt_fixed : s0[1];
+  while (done < max_steps && t_cur < t_end) {
+    if (dt_cur > 0.0 && (t_end - t_cur) / dt_cur < 1e9) {
+      long left = (long)((t_end - t_cur) / dt_cur) + 2;
+      chunk = left < 64 ? left : 64;
+    }
     long n = max_steps - done < chunk ? max_steps - done : chunk;
     for (long q = 0; q < n; ++q) {
       if (ctx->prof) {
@@ -557,7 +572,8 @@ lr_status lr_run(lr_ctx* ctx, double t_end, long max_steps, long* steps_done, do
     CK(cudaMemcpyAsync(sc, ctx->w.scal, sizeof(sc), cudaMemcpyDeviceToHost, ctx->stream), "read scalars");
     lr_status s = check_sticky(ctx);
     if (s != LR_OK) return s;
-    if (!(sc[0] < t_end)) break;
+    t_cur = sc[0];
+    dt_cur = ctx->g.dt_fixed > 0.0 ? ctx->g.dt_fixed : sc[1];
   }
   double sc[5];
   CK(cudaMemcpyAsync(sc, ctx->w.scal, sizeof(sc), cudaMemcpyDeviceToHost, ctx->stream), "read scalars");

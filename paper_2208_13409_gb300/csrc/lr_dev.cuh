@@ -21,6 +21,7 @@ struct LrGrid {
   int perx, pery;          // periodic flags (else reflective walls)
   int nxu, nyu;            // canonical node counts: nx (periodic) or nx+1
   double dx, dy, V, L, hmin, D;  // D = sqrt(dx^2+dy^2)
+  double inv2dx, inv2dy, inv8dx, inv8dy, invV, invD;  // reciprocals of the constant divisors
   double cfl, a1, a2, dt_fixed;
   double gam[LR_MAXM], pin[LR_MAXM];
   int face_o2, corner_o2, presc;
@@ -39,13 +40,16 @@ struct LrState {
 
 struct LrWork {
   double* scal;            // [0] t, [1] dt from the CFL rule, [2] dt of the last step, [3] t_end,
-                           // [4] steps taken
-  unsigned long long* red; // [0] max(c+|u|) bits, [1] block counter
+                           // [4] steps taken, [5] dt of the step in flight (written by lr_cell_pre)
+  unsigned long long* red; // [0] max(c+|u|) bits, [1] block counter, [2] mixed-cell count
+  int* mixed;              // work list of mixed cells (cell indices), red[2] entries
   int* err;                // [0] error bits, [1] first failing index
   double* pux; double* puy;                  // prescribed velocity (nodes)
   // cells
   double* mc; double* Q; double* Pi; double* cc;
-  double* Ph[LR_MAXM]; double* elag[LR_MAXM]; double* rcf[LR_MAXM];
+  double* elc[LR_MAXM];    // (P_a^{n+1/2} + Q) / (rho_a dx dy): e_a^{lag} = e_a - elc (Vol^{lag} - dx dy)
+  double* elag[LR_MAXM]; double* rcf[LR_MAXM];
+  unsigned char* mask;     // bit a set when material a is present in the cell at t^n
   double* ox; double* oy; double* wx; double* wy; double* vcf;
   double* cut[6];          // interface lines of mixed cells (n0x, n0y, d0, n1x, n1y, d1)
   // nodes
@@ -67,7 +71,7 @@ struct LrWork {
 
 // Host-side launchers (lr_kernels.cu).  Each enqueues one kernel on `s`.
 enum LrKernelId {
-  LRK_CELL_PRE = 0, LRK_NODE_HALF, LRK_CELL_LAG, LRK_CELL_CF, LRK_MAT_FLUX,
+  LRK_CELL_PRE = 0, LRK_NODE_HALF, LRK_CELL_LAG, LRK_CELL_CF, LRK_MIXED, LRK_MAT_FLUX,
   LRK_CELL_UPDATE, LRK_DUAL_FLUX, LRK_NODE_UPDATE, LRK_COUNT
 };
 extern const char* const lr_kernel_names[LRK_COUNT];

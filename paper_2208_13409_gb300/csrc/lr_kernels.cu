@@ -19,7 +19,7 @@
 #include <math.h>
 
 const char* const lr_kernel_names[LRK_COUNT] = {
-  "lr_cell_pre", "lr_node_half", "lr_cell_lag", "lr_cell_cf", "lr_mat_flux",
+  "lr_cell_pre", "lr_node_half", "lr_cell_lag", "lr_cell_cf", "lr_mixed", "lr_mat_flux",
   "lr_cell_update", "lr_dual_flux", "lr_node_update"};
 
 namespace {
@@ -103,13 +103,15 @@ __device__ __forceinline__ void set_err(const LrWork& w, int bit, int idx) {
   atomicCAS(&w.err[1], -1, idx);
 }
 
-// dt of the current step: CFL rule (or fixed), capped at t_end.
-__device__ __forceinline__ double step_dt(const LrGrid& g, const double* scal) {
+// dt of the current step: CFL rule (or fixed), capped at t_end.  Evaluated
+// by lr_cell_pre, which publishes it in scal[5] for the step's later kernels.
+__device__ __forceinline__ double step_dt_eval(const LrGrid& g, const double* scal) {
   double t = scal[0], te = scal[3];
   double dt = g.dt_fixed > 0.0 ? g.dt_fixed : scal[1];
   if (te - t < dt) dt = te - t;
   return dt;
 }
+__device__ __forceinline__ double step_dt(const LrGrid&, const double* scal) { return scal[5]; }
 
 // ---------------------------------------------------------------- EOS
 // Stiffened gas of section 5.2: p = (gamma-1) rho e - pi; c^2 = (gamma p + pi)/rho.
@@ -258,8 +260,8 @@ __device__ void youngs(const LrGrid& g, const double* K, int i, int j, double& n
   double kpp = cellS(g, K, i + 1, j + 1), kp0 = cellS(g, K, i + 1, j), kpm = cellS(g, K, i + 1, j - 1);
   double kmp = cellS(g, K, i - 1, j + 1), km0 = cellS(g, K, i - 1, j), kmm = cellS(g, K, i - 1, j - 1);
   double k0p = cellS(g, K, i, j + 1), k0m = cellS(g, K, i, j - 1);
-  double gx = ((kpp + 2.0 * kp0 + kpm) - (kmp + 2.0 * km0 + kmm)) / (8.0 * g.dx);
-  double gy = ((kpp + 2.0 * k0p + kmp) - (kpm + 2.0 * k0m + kmm)) / (8.0 * g.dy);
+  double gx = ((kpp + 2.0 * kp0 + kpm) - (kmp + 2.0 * km0 + kmm)) * g.inv8dx;
+  double gy = ((kpp + 2.0 * k0p + kmp) - (kpm + 2.0 * k0m + kmm)) * g.inv8dy;
   double gn = sqrt(gx * gx + gy * gy);
   if (gn > 0.0) { nxv = -gx / gn; nyv = -gy / gn; } else { nxv = 1.0; nyv = 0.0; }
 }
@@ -283,8 +285,9 @@ __device__ __forceinline__ int corner_cells(double ddx, double ddy, int i, int j
 template <int M>
 __global__ void __launch_bounds__(256) lr_cell_pre(LrGrid g, LrState cur, LrWork w) {
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+  double dt = step_dt_eval(g, w.scal);
+  if (i == 0 && j == 0) w.scal[5] = dt > 0.0 ? dt : 0.0;
   if (i >= g.nx || j >= g.ny) return;
-  double dt = step_dt(g, w.scal);
   if (!(dt > 0.0)) return;
   int c = j * g.nx + i;
   int nn = g.nx + 1;
@@ -293,47 +296,58 @@ __global__ void __launch_bounds__(256) lr_cell_pre(LrGrid g, LrState cur, LrWork
   int ll = j * nn + i, lr = j * nn + i1, ul = j1 * nn + i, ur = j1 * nn + i1;
   double uxll = cur.ux[ll], uxlr = cur.ux[lr], uxul = cur.ux[ul], uxur = cur.ux[ur];
   double uyll = cur.uy[ll], uylr = cur.uy[lr], uyul = cur.uy[ul], uyur = cur.uy[ur];
-  double kk[M], rr[M], ee[M], pa[M];
+  double kk[M], rr[M], ee[M], pa[M], ir[M];
   double m = 0.0, cmax = 0.0;
+  unsigned msk = 0u;
 #pragma unroll
   for (int a = 0; a < M; ++a) {
     kk[a] = cur.k[a][c];
-    rr[a] = cur.r[a][c];
-    ee[a] = cur.e[a][c];
-    pa[a] = 0.0;
+    rr[a] = 0.0; ee[a] = 0.0; pa[a] = 0.0; ir[a] = 0.0;
     if (kk[a] > 0.0) {
+      msk |= 1u << a;
+      rr[a] = cur.r[a][c];
+      ee[a] = cur.e[a][c];
+      ir[a] = 1.0 / rr[a];
       pa[a] = eos_p(g.gam[a], g.pin[a], rr[a], ee[a]);
-      double c2 = eos_c2(g.gam[a], g.pin[a], rr[a], pa[a]);
-      double wgt = kk[a] / EPS_C < 1.0 ? kk[a] / EPS_C : 1.0;
+      double c2 = (g.gam[a] * pa[a] + g.pin[a]) * ir[a];
+      double wgt = kk[a] * (1.0 / EPS_C) < 1.0 ? kk[a] * (1.0 / EPS_C) : 1.0;
       if (wgt >= 1.0 && !(c2 > 0.0)) set_err(w, LR_DERR_SOUND, c);
       double ca = sqrt(c2 > 0.0 ? c2 : 0.0);
       if (wgt * ca > cmax) cmax = wgt * ca;
       m += rr[a] * kk[a] * g.V;
     }
   }
-  double div = ((uxlr + uxur) - (uxll + uxul)) / (2.0 * g.dx) + ((uyul + uyur) - (uyll + uylr)) / (2.0 * g.dy);
-  double rc = m / g.V;
+  double div = ((uxlr + uxur) - (uxll + uxul)) * g.inv2dx + ((uyul + uyur) - (uyll + uylr)) * g.inv2dy;
+  double rc = m * g.invV;
   double Q = div < 0.0 ? rc * (g.a1 * g.L * cmax * fabs(div) + g.a2 * g.L * g.L * div * div) : 0.0;
   double h = 0.5 * dt;
   double vol = cell_F(h * uxll, h * uyll, g.dx + h * uxlr, h * uylr, h * uxul, g.dy + h * uyul,
                       g.dx + h * uxur, g.dy + h * uyur);
   if (!(vol > 0.0)) set_err(w, LR_DERR_VOLUME, c);
   double dv = vol - g.V;
+  double vV = g.V / vol;
   double P = 0.0;
 #pragma unroll
   for (int a = 0; a < M; ++a) {
-    double ph = 0.0;
-    if (kk[a] > 0.0) {
-      double rh = rr[a] * g.V / vol;
-      double eh = ee[a] - (pa[a] + Q) * (dv / (rr[a] * g.V));
-      ph = eos_p(g.gam[a], g.pin[a], rh, eh);
+    double cl = 0.0;
+    if (msk & (1u << a)) {
+      double rh = rr[a] * vV;
+      double iv = ir[a] * g.invV;
+      double eh = ee[a] - (pa[a] + Q) * (dv * iv);
+      double ph = eos_p(g.gam[a], g.pin[a], rh, eh);
       P += kk[a] * ph;
+      cl = (ph + Q) * iv;
     }
-    w.Ph[a][c] = ph;
+    w.elc[a][c] = cl;
   }
   w.mc[c] = m;
   w.Q[c] = Q;
   w.Pi[c] = P + Q;
+  w.mask[c] = (unsigned char)msk;
+  if (msk & (msk - 1u)) {  // two or more materials: interface work list
+    unsigned long long slot = atomicAdd(&w.red[2], 1ull);
+    w.mixed[slot] = c;
+  }
 }
 
 // K2: node velocity at t^{n+1/2} (section 1.2): u^{n+1/2} = u^n - dt/2
@@ -352,14 +366,13 @@ __global__ void __launch_bounds__(256) lr_node_half(LrGrid g, LrState cur, LrWor
   } else {
     int A = cix(g, i - 1, j - 1).idx, B = cix(g, i, j - 1).idx;
     int C = cix(g, i - 1, j).idx, D = cix(g, i, j).idx;
-    double gx = ((w.Pi[B] + w.Pi[D]) - (w.Pi[A] + w.Pi[C])) / (2.0 * g.dx);
-    double gy = ((w.Pi[C] + w.Pi[D]) - (w.Pi[A] + w.Pi[B])) / (2.0 * g.dy);
+    double gx = ((w.Pi[B] + w.Pi[D]) - (w.Pi[A] + w.Pi[C])) * g.inv2dx;
+    double gy = ((w.Pi[C] + w.Pi[D]) - (w.Pi[A] + w.Pi[B])) * g.inv2dy;
     double mp = 0.25 * (w.mc[A] + w.mc[B] + w.mc[C] + w.mc[D]);
-    double rp = mp / g.V;
-    double h = 0.5 * dt;
+    double f = 0.5 * dt * g.V / mp;  // dt/2 / rho_p
     double u0x = cur.ux[n], u0y = cur.uy[n];
-    hx = u0x - h * gx / rp;
-    hy = u0y - h * gy / rp;
+    hx = u0x - f * gx;
+    hy = u0y - f * gy;
     if (!g.perx && (i == 0 || i == g.nx)) hx = 0.0;
     if (!g.pery && (j == 0 || j == g.ny)) hy = 0.0;
     lx = 2.0 * hx - u0x;
@@ -398,15 +411,11 @@ __global__ void __launch_bounds__(256) lr_cell_lag(LrGrid g, LrState cur, LrWork
     double vol = cell_F(dxll, dyll, g.dx + dxlr, dylr, dxul, g.dy + dyul, g.dx + dxur, g.dy + dyur);
     if (!(vol > 0.0)) set_err(w, LR_DERR_VOLUME, c);
     double dv = vol - g.V;
-    double Q = w.Q[c];
+    unsigned msk = w.mask[c];
 #pragma unroll
     for (int a = 0; a < M; ++a) {
-      double ka = cur.k[a][c];
       double el = 0.0;
-      if (ka > 0.0) {
-        double ra = cur.r[a][c];
-        el = cur.e[a][c] - (w.Ph[a][c] + Q) * (dv / (ra * g.V));
-      }
+      if (msk & (1u << a)) el = cur.e[a][c] - w.elc[a][c] * dv;
       w.elag[a][c] = el;
     }
     double xl = 0.5 * (dxll + dxul), xr = g.dx + 0.5 * (dxlr + dxur);
@@ -494,120 +503,149 @@ __global__ void __launch_bounds__(256) lr_cell_cf(LrGrid g, LrState cur, LrWork 
   int fb = yix(g, i, j).idx, ft = yix(g, i, j + 1).idx;
   double vL = w.fx[fl], vR = w.fx[fr], vB = w.fy[fb], vT = w.fy[ft];
   double v = g.V + vR - vL + vT - vB;
-  int nidx[4];
-  double cdx[4], cdy[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     int a = q & 1, b = q >> 1;
     int n = nix(g, i + a, j + b).idx;
-    nidx[q] = n;
-    cdx[q] = w.ddx[n];
-    cdy[q] = w.ddy[n];
+    double cx = w.ddx[n], cy = w.ddy[n];
     int di, dj, ri, rj;
-    if (!corner_cells(cdx[q], cdy[q], i + a, j + b, di, dj, ri, rj)) continue;
-    double f = fabs(cdx[q] * cdy[q]);
+    if (!corner_cells(cx, cy, i + a, j + b, di, dj, ri, rj)) continue;
+    double f = fabs(cx * cy);
     if (di == i && dj == j) v += f;
     if (ri == i && rj == j) v -= f;
   }
   if (!(v > 0.0)) set_err(w, LR_DERR_VOLUME, c);
   w.vcf[c] = v;
-  double kk[M];
-  int np = 0, order[LR_MAXM] = {0, 0, 0}, dom = 0;
+  unsigned msk = w.mask[c];
+  double vV = g.V / v;
 #pragma unroll
-  for (int a = 0; a < M; ++a) {
-    kk[a] = cur.k[a][c];
-    w.rcf[a][c] = kk[a] > 0.0 ? cur.r[a][c] * g.V / v : 0.0;
-    if (kk[a] > 0.0) order[np++] = a;
-    if (kk[a] > kk[dom]) dom = a;
-  }
-  if (np < 2) return;
-  // ---- mixed cell: interface lines in the rectangular Lagrangian cell
-  double wxc = w.wx[c], wyc = w.wy[c];
-  double xl = 0.5 * g.dx - 0.5 * wxc + w.ox[c], xr = xl + wxc;
-  double yb = 0.5 * g.dy - 0.5 * wyc + w.oy[c], yt = yb + wyc;
-  int ncut = np - 1;
-  double cut[2][3];
-  {
-    double nxv, nyv;
-    youngs(g, cur.k[order[0]], i, j, nxv, nyv);
-    cut[0][0] = nxv; cut[0][1] = nyv;
-    cut[0][2] = rect_plic(xl, xr, yb, yt, nxv, nyv, kk[order[0]]);
-  }
-  if (ncut == 2) {
-    double nxv, nyv;
-    youngs(g, cur.k[order[1]], i, j, nxv, nyv);
-    Poly rect, rest;
-    poly_rect(rect, xl, xr, yb, yt);
-    poly_clip(rect, cut[0][0], cut[0][1], cut[0][2], -1.0, rest);
-    double target = kk[order[1]] * (wxc * wyc);
-    double ra = poly_area(rest);
-    if (target > ra) target = ra;
-    cut[1][0] = nxv; cut[1][1] = nyv;
-    cut[1][2] = poly_plic(rest, nxv, nyv, target);
-  }
-  w.cut[0][c] = cut[0][0]; w.cut[1][c] = cut[0][1]; w.cut[2][c] = cut[0][2];
-  if (ncut == 2) { w.cut[3][c] = cut[1][0]; w.cut[4][c] = cut[1][1]; w.cut[5][c] = cut[1][2]; }
-  // ---- outgoing fluxes: 0 left, 1 right, 2 bottom, 3 top, 4..7 corners
-  double A[8][M];
-  int kind[8], fidx[8];
-  int nf = 0;
-  double r[4];
-  double out[M];
+  for (int a = 0; a < M; ++a) w.rcf[a][c] = (msk & (1u << a)) ? cur.r[a][c] * vV : 0.0;
+}
+
+// K4b: the interface work of mixed cells only (the list built by lr_cell_pre):
+// Youngs normals and PLIC lines in the rectangular Lagrangian cell (sections
+// 4.1 and 4.4; three materials by nested cuts in material order), the split
+// of every flux the cell donates, and the clipping of a material's outgoing
+// volume to what it holds (excess to the dominant material).
+template <int M>
+__global__ void __launch_bounds__(128) lr_mixed(LrGrid g, LrState cur, LrWork w) {
+  double dt = step_dt(g, w.scal);
+  if (!(dt > 0.0)) return;
+  int count = (int)w.red[2];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
+    int c = w.mixed[t];
+    int i = c % g.nx, j = c / g.nx;
+    double v = w.vcf[c];
+    int fl = xix(g, i, j).idx, fr = xix(g, i + 1, j).idx;
+    int fb = yix(g, i, j).idx, ft = yix(g, i, j + 1).idx;
+    double vL = w.fx[fl], vR = w.fx[fr], vB = w.fy[fb], vT = w.fy[ft];
+    int nidx[4];
+    double cdx[4], cdy[4];
 #pragma unroll
-  for (int a = 0; a < M; ++a) out[a] = 0.0;
-  if (vL < 0.0) {
-    r[0] = w.fxb[fl]; r[1] = 0.0; r[2] = w.fxlo[fl]; r[3] = w.fxhi[fl];
-    split_region<M>(ncut, order, cut, r, -vL, A[nf]); kind[nf] = 0; fidx[nf] = fl; ++nf;
-  }
-  if (vR > 0.0) {
-    r[0] = g.dx; r[1] = g.dx + w.fxb[fr]; r[2] = w.fxlo[fr]; r[3] = w.fxhi[fr];
-    split_region<M>(ncut, order, cut, r, vR, A[nf]); kind[nf] = 0; fidx[nf] = fr; ++nf;
-  }
-  if (vB < 0.0) {
-    r[0] = w.fylo[fb]; r[1] = w.fyhi[fb]; r[2] = w.fyb[fb]; r[3] = 0.0;
-    split_region<M>(ncut, order, cut, r, -vB, A[nf]); kind[nf] = 1; fidx[nf] = fb; ++nf;
-  }
-  if (vT > 0.0) {
-    r[0] = w.fylo[ft]; r[1] = w.fyhi[ft]; r[2] = g.dy; r[3] = g.dy + w.fyb[ft];
-    split_region<M>(ncut, order, cut, r, vT, A[nf]); kind[nf] = 1; fidx[nf] = ft; ++nf;
-  }
-  for (int q = 0; q < 4; ++q) {
-    int a = q & 1, b = q >> 1;
-    int di, dj, ri, rj;
-    if (!corner_cells(cdx[q], cdy[q], i + a, j + b, di, dj, ri, rj)) continue;
-    if (di != i || dj != j) continue;
-    corner_region(g, cdx[q], cdy[q], r);
-    split_region<M>(ncut, order, cut, r, fabs(cdx[q] * cdy[q]), A[nf]);
-    kind[nf] = 2; fidx[nf] = nidx[q]; ++nf;
-  }
-  for (int f = 0; f < nf; ++f)
-#pragma unroll
-    for (int a = 0; a < M; ++a) out[a] += A[f][a];
-  double sc[M];
-#pragma unroll
-  for (int a = 0; a < M; ++a) {
-    sc[a] = 1.0;
-    if (a == dom) continue;
-    double avail = kk[a] * v;
-    if (out[a] > avail) sc[a] = avail / out[a];
-  }
-  for (int f = 0; f < nf; ++f) {
-    double moved = 0.0;
-#pragma unroll
-    for (int a = 0; a < M; ++a) {
-      if (sc[a] < 1.0) { moved += (1.0 - sc[a]) * A[f][a]; A[f][a] *= sc[a]; }
+    for (int q = 0; q < 4; ++q) {
+      int n = nix(g, i + (q & 1), j + (q >> 1)).idx;
+      nidx[q] = n;
+      cdx[q] = w.ddx[n];
+      cdy[q] = w.ddy[n];
     }
-    A[f][dom] += moved;
+    double kk[M];
+    int np = 0, order[LR_MAXM] = {0, 0, 0}, dom = 0;
+    unsigned msk = w.mask[c];
 #pragma unroll
     for (int a = 0; a < M; ++a) {
-      double* dst = kind[f] == 0 ? w.xAm[a] : kind[f] == 1 ? w.yAm[a] : w.cAm[a];
-      dst[fidx[f]] = A[f][a];
+      kk[a] = (msk & (1u << a)) ? cur.k[a][c] : 0.0;
+      if (msk & (1u << a)) order[np++] = a;
+      if (kk[a] > kk[dom]) dom = a;
+    }
+    // ---- mixed cell: interface lines in the rectangular Lagrangian cell
+    double wxc = w.wx[c], wyc = w.wy[c];
+    double xl = 0.5 * g.dx - 0.5 * wxc + w.ox[c], xr = xl + wxc;
+    double yb = 0.5 * g.dy - 0.5 * wyc + w.oy[c], yt = yb + wyc;
+    int ncut = np - 1;
+    double cut[2][3];
+    {
+      double nxv, nyv;
+      youngs(g, cur.k[order[0]], i, j, nxv, nyv);
+      cut[0][0] = nxv; cut[0][1] = nyv;
+      cut[0][2] = rect_plic(xl, xr, yb, yt, nxv, nyv, kk[order[0]]);
+    }
+    if (ncut == 2) {
+      double nxv, nyv;
+      youngs(g, cur.k[order[1]], i, j, nxv, nyv);
+      Poly rect, rest;
+      poly_rect(rect, xl, xr, yb, yt);
+      poly_clip(rect, cut[0][0], cut[0][1], cut[0][2], -1.0, rest);
+      double target = kk[order[1]] * (wxc * wyc);
+      double ra = poly_area(rest);
+      if (target > ra) target = ra;
+      cut[1][0] = nxv; cut[1][1] = nyv;
+      cut[1][2] = poly_plic(rest, nxv, nyv, target);
+    }
+    w.cut[0][c] = cut[0][0]; w.cut[1][c] = cut[0][1]; w.cut[2][c] = cut[0][2];
+    if (ncut == 2) { w.cut[3][c] = cut[1][0]; w.cut[4][c] = cut[1][1]; w.cut[5][c] = cut[1][2]; }
+    // ---- outgoing fluxes: 0 left, 1 right, 2 bottom, 3 top, 4..7 corners
+    double A[8][M];
+    int kind[8], fidx[8];
+    int nf = 0;
+    double r[4];
+    double out[M];
+  #pragma unroll
+    for (int a = 0; a < M; ++a) out[a] = 0.0;
+    if (vL < 0.0) {
+      r[0] = w.fxb[fl]; r[1] = 0.0; r[2] = w.fxlo[fl]; r[3] = w.fxhi[fl];
+      split_region<M>(ncut, order, cut, r, -vL, A[nf]); kind[nf] = 0; fidx[nf] = fl; ++nf;
+    }
+    if (vR > 0.0) {
+      r[0] = g.dx; r[1] = g.dx + w.fxb[fr]; r[2] = w.fxlo[fr]; r[3] = w.fxhi[fr];
+      split_region<M>(ncut, order, cut, r, vR, A[nf]); kind[nf] = 0; fidx[nf] = fr; ++nf;
+    }
+    if (vB < 0.0) {
+      r[0] = w.fylo[fb]; r[1] = w.fyhi[fb]; r[2] = w.fyb[fb]; r[3] = 0.0;
+      split_region<M>(ncut, order, cut, r, -vB, A[nf]); kind[nf] = 1; fidx[nf] = fb; ++nf;
+    }
+    if (vT > 0.0) {
+      r[0] = w.fylo[ft]; r[1] = w.fyhi[ft]; r[2] = g.dy; r[3] = g.dy + w.fyb[ft];
+      split_region<M>(ncut, order, cut, r, vT, A[nf]); kind[nf] = 1; fidx[nf] = ft; ++nf;
+    }
+    for (int q = 0; q < 4; ++q) {
+      int a = q & 1, b = q >> 1;
+      int di, dj, ri, rj;
+      if (!corner_cells(cdx[q], cdy[q], i + a, j + b, di, dj, ri, rj)) continue;
+      if (di != i || dj != j) continue;
+      corner_region(g, cdx[q], cdy[q], r);
+      split_region<M>(ncut, order, cut, r, fabs(cdx[q] * cdy[q]), A[nf]);
+      kind[nf] = 2; fidx[nf] = nidx[q]; ++nf;
+    }
+    for (int f = 0; f < nf; ++f)
+  #pragma unroll
+      for (int a = 0; a < M; ++a) out[a] += A[f][a];
+    double sc[M];
+  #pragma unroll
+    for (int a = 0; a < M; ++a) {
+      sc[a] = 1.0;
+      if (a == dom) continue;
+      double avail = kk[a] * v;
+      if (out[a] > avail) sc[a] = avail / out[a];
+    }
+    for (int f = 0; f < nf; ++f) {
+      double moved = 0.0;
+  #pragma unroll
+      for (int a = 0; a < M; ++a) {
+        if (sc[a] < 1.0) { moved += (1.0 - sc[a]) * A[f][a]; A[f][a] *= sc[a]; }
+      }
+      A[f][dom] += moved;
+  #pragma unroll
+      for (int a = 0; a < M; ++a) {
+        double* dst = kind[f] == 0 ? w.xAm[a] : kind[f] == 1 ? w.yAm[a] : w.cAm[a];
+        dst[fidx[f]] = A[f][a];
+      }
     }
   }
 }
 
-__device__ __forceinline__ bool pure_in(const LrGrid& g, const double* K, int i, int j) {
-  return cellS(g, K, i, j) == 1.0;
+// Purity from the material bitmask: the cell holds material a only.
+__device__ __forceinline__ bool pure_in(const LrGrid& g, const unsigned char* mask, int i, int j, unsigned bit) {
+  return mask[cix(g, i, j).idx] == bit;
 }
 
 // Face value (section 2.1.1): a_d + slope/2 (sgn(dVol) wx_d - dt u_f).
@@ -643,11 +681,11 @@ __device__ __forceinline__ double recon_corner(const LrGrid& g, const double* q,
   double oxp = cellOX(g, w.ox, di + 1, dj + sj), oyp = cellOY(g, w.oy, di + 1, dj + sj);
   double oxm = cellOX(g, w.ox, di - 1, dj - sj), oym = cellOY(g, w.oy, di - 1, dj - sj);
   double sdy = sy * g.dy;
-  double hp = ((g.dx + oxp - ox0) * g.dx + (sdy + oyp - oy0) * sdy) / g.D;
-  double hm = ((g.dx + ox0 - oxm) * g.dx + (sdy + oy0 - oym) * sdy) / g.D;
+  double hp = ((g.dx + oxp - ox0) * g.dx + (sdy + oyp - oy0) * sdy) * g.invD;
+  double hm = ((g.dx + ox0 - oxm) * g.dx + (sdy + oy0 - oym) * sdy) * g.invD;
   double sl = vl_slope(a0 - am, ap - a0, hm, hp);
   double sgx = ddx > 0.0 ? 1.0 : -1.0;
-  double off = 0.5 * (sgx * (w.wx[c] * g.dx + w.wy[c] * g.dy) - (ddx * g.dx + sy * ddy * g.dy)) / g.D;
+  double off = 0.5 * (sgx * (w.wx[c] * g.dx + w.wy[c] * g.dy) - (ddx * g.dx + sy * ddy * g.dy)) * g.invD;
   return a0 + sl * off;
 }
 
@@ -671,37 +709,37 @@ __global__ void __launch_bounds__(256) lr_mat_flux(LrGrid g, LrState cur, LrWork
     int f = j * nn + i;
     double v = w.fx[f];
     double mt = 0.0;
+    unsigned dm = 0u;
+    int di = 0, dc = 0;
+    double sg = 1.0, fd = 0.0;
     if (v != 0.0) {
       bool left = v > 0.0;
-      double sg = left ? 1.0 : -1.0;
-      int di = left ? i - 1 : i;
-      int dc = cix(g, di, j).idx;
-      int np = 0, pm = 0;
+      sg = left ? 1.0 : -1.0;
+      di = left ? i - 1 : i;
+      dc = cix(g, di, j).idx;
+      dm = w.mask[dc];
+      fd = 0.5 * (w.ddx[j * nn + i] + w.ddx[j1 * nn + i]);
+    }
+    bool mixed = (dm & (dm - 1u)) != 0u;
 #pragma unroll
-      for (int a = 0; a < M; ++a) if (cur.k[a][dc] > 0.0) { ++np; pm = a; }
-      double fd = 0.5 * (w.ddx[j * nn + i] + w.ddx[j1 * nn + i]);
-#pragma unroll
-      for (int a = 0; a < M; ++a) {
-        double Aa = np > 1 ? w.xAm[a][f] : (a == pm ? fabs(v) : 0.0);
-        double Ma = 0.0, Ea = 0.0;
-        if (Aa > 0.0) {
-          double rf = w.rcf[a][dc], ef = w.elag[a][dc];
-          if (g.face_o2 && pure_in(g, cur.k[a], di - 1, j) && cur.k[a][dc] == 1.0 &&
-              pure_in(g, cur.k[a], di + 1, j)) {
-            rf = recon_face_x(g, w.rcf[a], w.ox, w.wx, di, j, sg, fd, true);
-            ef = recon_face_x(g, w.elag[a], w.ox, w.wx, di, j, sg, fd, true);
-          }
-          Ma = rf * Aa;
-          Ea = rf * ef * Aa;
-        } else {
-          Aa = 0.0;
+    for (int a = 0; a < M; ++a) {
+      unsigned bit = 1u << a;
+      if (!(dm & bit)) { w.xA[a][f] = 0.0; w.xMm[a][f] = 0.0; w.xE[a][f] = 0.0; continue; }
+      double Aa = mixed ? w.xAm[a][f] : fabs(v);
+      double Ma = 0.0, Ea = 0.0;
+      if (!mixed || Aa > 0.0) {
+        double rf = w.rcf[a][dc], ef = w.elag[a][dc];
+        if (!mixed && g.face_o2 && pure_in(g, w.mask, di - 1, j, bit) && pure_in(g, w.mask, di + 1, j, bit)) {
+          rf = recon_face_x(g, w.rcf[a], w.ox, w.wx, di, j, sg, fd, true);
+          ef = recon_face_x(g, w.elag[a], w.ox, w.wx, di, j, sg, fd, true);
         }
-        w.xA[a][f] = sg * Aa; w.xMm[a][f] = sg * Ma; w.xE[a][f] = sg * Ea;
-        mt += sg * Ma;
+        Ma = rf * Aa;
+        Ea = Ma * ef;
+      } else {
+        Aa = 0.0;
       }
-    } else {
-#pragma unroll
-      for (int a = 0; a < M; ++a) { w.xA[a][f] = 0.0; w.xMm[a][f] = 0.0; w.xE[a][f] = 0.0; }
+      w.xA[a][f] = sg * Aa; w.xMm[a][f] = sg * Ma; w.xE[a][f] = sg * Ea;
+      mt += sg * Ma;
     }
     w.MX[f] = mt;
   }
@@ -710,37 +748,37 @@ __global__ void __launch_bounds__(256) lr_mat_flux(LrGrid g, LrState cur, LrWork
     int f = j * g.nx + i;
     double v = w.fy[f];
     double mt = 0.0;
+    unsigned dm = 0u;
+    int dj = 0, dc = 0;
+    double sg = 1.0, fd = 0.0;
     if (v != 0.0) {
       bool below = v > 0.0;
-      double sg = below ? 1.0 : -1.0;
-      int dj = below ? j - 1 : j;
-      int dc = cix(g, i, dj).idx;
-      int np = 0, pm = 0;
+      sg = below ? 1.0 : -1.0;
+      dj = below ? j - 1 : j;
+      dc = cix(g, i, dj).idx;
+      dm = w.mask[dc];
+      fd = 0.5 * (w.ddy[j * nn + i] + w.ddy[j * nn + i1]);
+    }
+    bool mixed = (dm & (dm - 1u)) != 0u;
 #pragma unroll
-      for (int a = 0; a < M; ++a) if (cur.k[a][dc] > 0.0) { ++np; pm = a; }
-      double fd = 0.5 * (w.ddy[j * nn + i] + w.ddy[j * nn + i1]);
-#pragma unroll
-      for (int a = 0; a < M; ++a) {
-        double Aa = np > 1 ? w.yAm[a][f] : (a == pm ? fabs(v) : 0.0);
-        double Ma = 0.0, Ea = 0.0;
-        if (Aa > 0.0) {
-          double rf = w.rcf[a][dc], ef = w.elag[a][dc];
-          if (g.face_o2 && pure_in(g, cur.k[a], i, dj - 1) && cur.k[a][dc] == 1.0 &&
-              pure_in(g, cur.k[a], i, dj + 1)) {
-            rf = recon_face_x(g, w.rcf[a], w.oy, w.wy, i, dj, sg, fd, false);
-            ef = recon_face_x(g, w.elag[a], w.oy, w.wy, i, dj, sg, fd, false);
-          }
-          Ma = rf * Aa;
-          Ea = rf * ef * Aa;
-        } else {
-          Aa = 0.0;
+    for (int a = 0; a < M; ++a) {
+      unsigned bit = 1u << a;
+      if (!(dm & bit)) { w.yA[a][f] = 0.0; w.yMm[a][f] = 0.0; w.yE[a][f] = 0.0; continue; }
+      double Aa = mixed ? w.yAm[a][f] : fabs(v);
+      double Ma = 0.0, Ea = 0.0;
+      if (!mixed || Aa > 0.0) {
+        double rf = w.rcf[a][dc], ef = w.elag[a][dc];
+        if (!mixed && g.face_o2 && pure_in(g, w.mask, i, dj - 1, bit) && pure_in(g, w.mask, i, dj + 1, bit)) {
+          rf = recon_face_x(g, w.rcf[a], w.oy, w.wy, i, dj, sg, fd, false);
+          ef = recon_face_x(g, w.elag[a], w.oy, w.wy, i, dj, sg, fd, false);
         }
-        w.yA[a][f] = sg * Aa; w.yMm[a][f] = sg * Ma; w.yE[a][f] = sg * Ea;
-        mt += sg * Ma;
+        Ma = rf * Aa;
+        Ea = Ma * ef;
+      } else {
+        Aa = 0.0;
       }
-    } else {
-#pragma unroll
-      for (int a = 0; a < M; ++a) { w.yA[a][f] = 0.0; w.yMm[a][f] = 0.0; w.yE[a][f] = 0.0; }
+      w.yA[a][f] = sg * Aa; w.yMm[a][f] = sg * Ma; w.yE[a][f] = sg * Ea;
+      mt += sg * Ma;
     }
     w.MY[f] = mt;
   }
@@ -749,40 +787,41 @@ __global__ void __launch_bounds__(256) lr_mat_flux(LrGrid g, LrState cur, LrWork
     int n = j * nn + i;
     double ddx = w.ddx[n], ddy = w.ddy[n];
     double mt = 0.0;
-    int di, dj, ri, rj;
+    int di = 0, dj = 0, ri, rj, dc = 0, sj = 1;
+    unsigned dm = 0u;
+    double fv = 0.0;
     if (corner_cells(ddx, ddy, i, j, di, dj, ri, rj)) {
-      double fv = fabs(ddx * ddy);
-      int dc = cix(g, di, dj).idx;
-      int np = 0, pm = 0;
+      fv = fabs(ddx * ddy);
+      dc = cix(g, di, dj).idx;
+      dm = w.mask[dc];
+      sj = ddx * ddy > 0.0 ? 1 : -1;
+    }
+    bool mixed = (dm & (dm - 1u)) != 0u;
 #pragma unroll
-      for (int a = 0; a < M; ++a) if (cur.k[a][dc] > 0.0) { ++np; pm = a; }
-      int sj = ddx * ddy > 0.0 ? 1 : -1;
-#pragma unroll
-      for (int a = 0; a < M; ++a) {
-        double Aa = np > 1 ? w.cAm[a][n] : (a == pm ? fv : 0.0);
-        double Ma = 0.0, Ea = 0.0;
-        if (Aa > 0.0) {
-          double rf = w.rcf[a][dc], ef = w.elag[a][dc];
-          if (g.corner_o2 && pure_in(g, cur.k[a], di - 1, dj - sj) && cur.k[a][dc] == 1.0 &&
-              pure_in(g, cur.k[a], di + 1, dj + sj)) {
-            rf = recon_corner(g, w.rcf[a], w, di, dj, ddx, ddy);
-            ef = recon_corner(g, w.elag[a], w, di, dj, ddx, ddy);
-          }
-          Ma = rf * Aa;
-          Ea = rf * ef * Aa;
-        } else {
-          Aa = 0.0;
+    for (int a = 0; a < M; ++a) {
+      unsigned bit = 1u << a;
+      if (!(dm & bit)) { w.cA[a][n] = 0.0; w.cMm[a][n] = 0.0; w.cE[a][n] = 0.0; continue; }
+      double Aa = mixed ? w.cAm[a][n] : fv;
+      double Ma = 0.0, Ea = 0.0;
+      if (!mixed || Aa > 0.0) {
+        double rf = w.rcf[a][dc], ef = w.elag[a][dc];
+        if (!mixed && g.corner_o2 && pure_in(g, w.mask, di - 1, dj - sj, bit) &&
+            pure_in(g, w.mask, di + 1, dj + sj, bit)) {
+          rf = recon_corner(g, w.rcf[a], w, di, dj, ddx, ddy);
+          ef = recon_corner(g, w.elag[a], w, di, dj, ddx, ddy);
         }
-        w.cA[a][n] = Aa; w.cMm[a][n] = Ma; w.cE[a][n] = Ea;
-        mt += Ma;
+        Ma = rf * Aa;
+        Ea = Ma * ef;
+      } else {
+        Aa = 0.0;
       }
-    } else {
-#pragma unroll
-      for (int a = 0; a < M; ++a) { w.cA[a][n] = 0.0; w.cMm[a][n] = 0.0; w.cE[a][n] = 0.0; }
+      w.cA[a][n] = Aa; w.cMm[a][n] = Ma; w.cE[a][n] = Ea;
+      mt += Ma;
     }
     double sgm = ddx > 0.0 ? mt : -mt;  // signed along +x
-    w.Mpp[n] = ddx * ddy > 0.0 ? sgm : 0.0;
-    w.Mpm[n] = ddx * ddy < 0.0 ? sgm : 0.0;
+    bool pp = ddx * ddy > 0.0;
+    w.Mpp[n] = pp ? sgm : 0.0;
+    w.Mpm[n] = (!pp && dm) ? sgm : 0.0;
   }
 }
 
@@ -801,6 +840,14 @@ __global__ void __launch_bounds__(256) lr_cell_update(LrGrid g, LrState cur, LrS
 #pragma unroll
     for (int a = 0; a < M; ++a) { nxt.k[a][c] = cur.k[a][c]; nxt.r[a][c] = cur.r[a][c]; nxt.e[a][c] = cur.e[a][c]; }
     return;
+  }
+  // materials that can be in this cell after the remap: its own and those of
+  // every cell that can donate to it (the 3x3 neighbourhood)
+  unsigned own = w.mask[c], nb = own;
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    if (q == 4) continue;
+    nb |= w.mask[cix(g, i + q % 3 - 1, j + q / 3 - 1).idx];
   }
   int fl = xix(g, i, j).idx, fr = xix(g, i + 1, j).idx;
   int fb = yix(g, i, j).idx, ft = yix(g, i, j + 1).idx;
@@ -821,9 +868,15 @@ __global__ void __launch_bounds__(256) lr_cell_update(LrGrid g, LrState cur, LrS
   double vol[M], mas[M], ene[M];
 #pragma unroll
   for (int a = 0; a < M; ++a) {
-    double ka = cur.k[a][c];
-    double m = cur.r[a][c] * ka * g.V;
-    double vv = ka * vcf, mm = m, ee = m * w.elag[a][c];
+    vol[a] = 0.0; mas[a] = 0.0; ene[a] = 0.0;
+    if (!(nb & (1u << a))) continue;
+    double vv = 0.0, mm = 0.0, ee = 0.0;
+    if (own & (1u << a)) {
+      double ka = cur.k[a][c];
+      mm = cur.r[a][c] * ka * g.V;
+      vv = ka * vcf;
+      ee = mm * w.elag[a][c];
+    }
     vv += w.xA[a][fl] - w.xA[a][fr] + w.yA[a][fb] - w.yA[a][ft];
     mm += w.xMm[a][fl] - w.xMm[a][fr] + w.yMm[a][fb] - w.yMm[a][ft];
     ee += w.xE[a][fl] - w.xE[a][fr] + w.yE[a][fb] - w.yE[a][ft];
@@ -835,31 +888,33 @@ __global__ void __launch_bounds__(256) lr_cell_update(LrGrid g, LrState cur, LrS
     vol[a] = vv; mas[a] = mm; ene[a] = ee;
   }
   bool keep[M];
-  int big = -1;
+  int big = -1, nkeep = 0;
   double tot = 0.0, lm = 0.0, le = 0.0;
 #pragma unroll
   for (int a = 0; a < M; ++a) {
-    keep[a] = vol[a] > EPS_K * g.V;
-    if (keep[a]) { tot += vol[a]; if (big < 0 || vol[a] > vol[big]) big = a; }
+    keep[a] = (nb & (1u << a)) && vol[a] > EPS_K * g.V;
+    if (keep[a]) { tot += vol[a]; ++nkeep; if (big < 0 || vol[a] > vol[big]) big = a; }
     else { lm += mas[a]; le += ene[a]; }
   }
   if (big < 0) { set_err(w, LR_DERR_VOLUME, c); big = 0; tot = 1.0; }
-  double cmax = 0.0;
 #pragma unroll
   for (int a = 0; a < M; ++a) {
     if (a == big) { mas[a] += lm; ene[a] += le; }
   }
+  double cmax = 0.0;
 #pragma unroll
   for (int a = 0; a < M; ++a) {
     double ka = 0.0, ra = 0.0, ea = 0.0;
     if (keep[a]) {
-      ka = vol[a] / tot;
+      ka = nkeep == 1 ? 1.0 : vol[a] / tot;
       if (!(mas[a] > 0.0)) set_err(w, LR_DERR_MASS, c);
-      ra = mas[a] / (ka * g.V);
-      ea = ene[a] / mas[a];
+      double im = 1.0 / mas[a];
+      double kV = ka * g.V;
+      ra = nkeep == 1 ? mas[a] * g.invV : mas[a] / kV;
+      ea = ene[a] * im;
       double pa = eos_p(g.gam[a], g.pin[a], ra, ea);
-      double c2 = eos_c2(g.gam[a], g.pin[a], ra, pa);
-      double wgt = ka / EPS_C < 1.0 ? ka / EPS_C : 1.0;
+      double c2 = (g.gam[a] * pa + g.pin[a]) * (kV * im);
+      double wgt = ka * (1.0 / EPS_C) < 1.0 ? ka * (1.0 / EPS_C) : 1.0;
       if (wgt >= 1.0 && !(c2 > 0.0)) set_err(w, LR_DERR_SOUND, c);
       double ca = sqrt(c2 > 0.0 ? c2 : 0.0);
       if (wgt * ca > cmax) cmax = wgt * ca;
@@ -905,7 +960,6 @@ __global__ void __launch_bounds__(256) lr_dual_flux(LrGrid g, LrWork w) {
   bool xnode = i >= 0 && i < g.nxu;                     // canonical node in x
   bool ynode = j >= 0 && j < g.nyu;
   int o = (j + 1) * (g.nx + 2) + (i + 1);
-  const double D = g.D;
   auto MXr = [&](int a, int b) { Ix q = xix(g, a, b); double v = w.MX[q.idx]; return q.fx ? -v : v; };
   auto MYr = [&](int a, int b) { Ix q = yix(g, a, b); double v = w.MY[q.idx]; return q.fy ? -v : v; };
   auto CPr = [&](int a, int b, double& pp, double& pm) {
@@ -974,11 +1028,11 @@ __global__ void __launch_bounds__(256) lr_dual_flux(LrGrid g, LrWork w) {
           double dx0 = nodeX(g, w.ddx, qi, qj), dy0 = nodeY(g, w.ddy, qi, qj);
           double dxp = nodeX(g, w.ddx, qi + 1, qj + sj), dyp = nodeY(g, w.ddy, qi + 1, qj + sj);
           double dxm = nodeX(g, w.ddx, qi - 1, qj - sj), dym = nodeY(g, w.ddy, qi - 1, qj - sj);
-          double hp = ((g.dx + dxp - dx0) * g.dx + (sdy + dyp - dy0) * sdy) / D;
-          double hm = ((g.dx + dx0 - dxm) * g.dx + (sdy + dy0 - dym) * sdy) / D;
+          double hp = ((g.dx + dxp - dx0) * g.dx + (sdy + dyp - dy0) * sdy) * g.invD;
+          double hm = ((g.dx + dx0 - dxm) * g.dx + (sdy + dy0 - dym) * sdy) * g.invD;
           double wxq = g.dx + 0.5 * (nodeX(g, w.ddx, qi + 1, qj) - nodeX(g, w.ddx, qi - 1, qj));
           double wyq = g.dy + 0.5 * (nodeY(g, w.ddy, qi, qj + 1) - nodeY(g, w.ddy, qi, qj - 1));
-          double off = 0.5 * (sg * (wxq * g.dx + wyq * g.dy) - (cdx * g.dx + sy * cdy * g.dy)) / D;
+          double off = 0.5 * (sg * (wxq * g.dx + wyq * g.dy) - (cdx * g.dx + sy * cdy * g.dy)) * g.invD;
           double uxp = nodeX(g, w.ulx, qi + 1, qj + sj), uxm = nodeX(g, w.ulx, qi - 1, qj - sj);
           double uyp = nodeY(g, w.uly, qi + 1, qj + sj), uym = nodeY(g, w.uly, qi - 1, qj - sj);
           vx = vx + vl_slope(vx - uxm, uxp - vx, hm, hp) * off;
@@ -1024,6 +1078,7 @@ __device__ void cfl_finalize(const LrGrid& g, const LrWork& w, double v, bool ad
     w.scal[1] = g.cfl * best;
     w.red[0] = 0ull;
     w.red[1] = 0ull;
+    w.red[2] = 0ull;
   }
 }
 
@@ -1061,8 +1116,9 @@ __global__ void __launch_bounds__(256) lr_node_update(LrGrid g, LrState cur, LrS
       px += -w.dPP[1][c0] + w.dPP[1][c1] - w.dPM[1][c2] + w.dPM[1][c3];
       py += -w.dPP[2][c0] + w.dPP[2][c1] - w.dPM[2][c2] + w.dPM[2][c3];
       if (!(mnew > 0.0)) set_err(w, LR_DERR_MASS, n);
-      ux1 = px / mnew;
-      uy1 = py / mnew;
+      double im = 1.0 / mnew;
+      ux1 = px * im;
+      uy1 = py * im;
       if (!isfinite(ux1) || !isfinite(uy1)) set_err(w, LR_DERR_NAN, n);
     }
     if (!g.perx && (i == 0 || i == g.nx)) ux1 = 0.0;
@@ -1138,7 +1194,7 @@ __global__ void __launch_bounds__(256) lr_prepare(LrGrid g, LrState st, LrWork w
 
 __global__ void lr_set_scalar_k(double* p, double v) { *p = v; }
 __global__ void lr_reset_k(LrWork w) {
-  w.red[0] = 0ull; w.red[1] = 0ull; w.err[0] = 0; w.err[1] = -1;
+  w.red[0] = 0ull; w.red[1] = 0ull; w.red[2] = 0ull; w.err[0] = 0; w.err[1] = -1;
   w.scal[0] = 0.0; w.scal[1] = 0.0; w.scal[2] = 0.0; w.scal[3] = 0.0; w.scal[4] = 0.0;
 }
 
@@ -1177,6 +1233,14 @@ cudaError_t lr_launch(int kid, const LrGrid& g, const LrState& cur, const LrStat
     case LRK_NODE_HALF: lr_node_half<<<grid_for(g.nxu, g.nyu), dim3(BX, BY), 0, s>>>(g, cur, w); break;
     case LRK_CELL_LAG: LR_DISPATCH_M(lr_cell_lag, grid_for(g.nxu, g.nyu), g, cur, w); break;
     case LRK_CELL_CF: LR_DISPATCH_M(lr_cell_cf, grid_for(g.nx, g.ny), g, cur, w); break;
+    case LRK_MIXED: {
+      int nb = (g.nx * g.ny + 127) / 128;
+      if (nb > 152 * 8) nb = 152 * 8;
+      if (g.M == 1) break;  // one material: no interfaces
+      if (g.M == 2) lr_mixed<2><<<nb, 128, 0, s>>>(g, cur, w);
+      else lr_mixed<3><<<nb, 128, 0, s>>>(g, cur, w);
+      break;
+    }
     case LRK_MAT_FLUX: LR_DISPATCH_M(lr_mat_flux, grid_for(g.nxu, g.nyu), g, cur, w); break;
     case LRK_CELL_UPDATE: LR_DISPATCH_M(lr_cell_update, grid_for(g.nx, g.ny), g, cur, nxt, w); break;
     case LRK_DUAL_FLUX: lr_dual_flux<<<grid_for(g.nx + 2, g.ny + 2), dim3(BX, BY), 0, s>>>(g, w); break;
