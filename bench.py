@@ -38,6 +38,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="lr", choices=["lr", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "df64", "fp32"],
+                    help="arithmetic of the timed step (fp64: native double, the headline)")
+    ap.add_argument("--other-modes", type=int, default=1,
+                    help="also time the other arithmetic modes (short runs) and report them")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-baseline-steps", type=int, default=20)
     ap.add_argument("--t-start", type=float, default=2.0,
@@ -199,6 +203,52 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+MODES = {"fp64": 0, "df64": 1, "fp32": 2}
+DTYPES = {"fp64": "f64", "df64": "df64 (float pair)", "fp32": "f32"}
+
+
+def field_set(sim, lr):
+    k = sim.get(lr.F_K)
+    return {"k": k, "k_rho": k * sim.get(lr.F_RHO_MAT), "p": sim.get(lr.F_P),
+            "u": __import__("numpy").stack([sim.get(lr.F_UX), sim.get(lr.F_UY)])}
+
+
+def l1_rel(g, o):
+    import numpy as np
+    s = np.abs(o).sum()
+    return float(np.abs(g - o).sum() / s) if s > 0 else float(np.abs(g).sum())
+
+
+def timed_steps(sim, K, flush, torch):
+    """K steps, each bracketed by CUDA events on the library's stream, with an
+    untimed L2 flush before each; returns summed milliseconds."""
+    stream = sim.stream
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    with torch.cuda.stream(stream):
+        for q in range(K):
+            flush.fill_(float(q))
+            ev[q][0].record(stream)
+            sim.step(sync=False)
+            ev[q][1].record(stream)
+    torch.cuda.synchronize()
+    sim.sync()
+    return sum(a.elapsed_time(b) for a, b in ev)
+
+
+def kernel_profile(sim, K, flush, torch):
+    """Per-kernel mean durations from events the library records around each
+    launch on its stream."""
+    sim.set_profiling(True)
+    with torch.cuda.stream(sim.stream):
+        for q in range(K):
+            flush.fill_(float(q))
+            sim.step(sync=False)
+    sim.sync()
+    kt = sim.kernel_times()
+    sim.set_profiling(False)
+    return {k: v[1] / max(v[0], 1) for k, v in kt.items() if v[0] > 0}
+
+
 def run_lr(args, world, rank, local):
     import numpy as np
     import torch
@@ -211,18 +261,17 @@ def run_lr(args, world, rank, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     pr = P.triple_point()
     cells = pr.cells
-    sim = lr.Sim(pr)
-    stream = sim.stream
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 512 MB > L2
+    sim = lr.Sim(pr, precision=MODES[args.precision])
+    launches_per_step = sim.launches_per_step()
+    pre_steps = 0
     if args.t_start > 0:
         pre_steps, _ = sim.run(1 << 30, args.t_start)  # developed flow, mid-run
-    else:
-        pre_steps = 0
+    ref_fields = field_set(sim, lr) if rank == 0 else None
     for _ in range(args.warmup):
         sim.step(sync=False)
     sim.sync()
-    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 512 MB > L2
     K = args.steps
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     gpu_id = None
     try:
         gpu_id = str(torch.cuda.get_device_properties(local).uuid)
@@ -237,47 +286,31 @@ def run_lr(args, world, rank, local):
     sampler.start()
     time.sleep(0.3)
     wall0 = time.perf_counter()
-    with torch.cuda.stream(stream):
-        for q in range(K):
-            flush.fill_(float(q))
-            ev[q][0].record(stream)
-            sim.step(sync=False)
-            ev[q][1].record(stream)
-    torch.cuda.synchronize()
+    ms = timed_steps(sim, K, flush, torch)
     wall = time.perf_counter() - wall0
     if dist:
         dist.barrier()
     clocks = sampler.stop()
-    sim.sync()
-    ms = sum(a.elapsed_time(b) for a, b in ev)
     tmax = torch.tensor([ms], dtype=torch.float64, device="cuda")
     if dist:
         dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
     ms_max = float(tmax.item())
     value = world * cells * K / (ms_max * 1e-3)
+    step_ms = ms_max / K
 
-    # ---- per-kernel durations (separate profiled pass, events on the library stream)
-    sim.set_profiling(True)
-    with torch.cuda.stream(stream):
-        for q in range(K):
-            flush.fill_(float(q))
-            sim.step(sync=False)
-    sim.sync()
-    kt = sim.kernel_times()
-    sim.set_profiling(False)
-    dom = max(kt, key=lambda k: kt[k][1])
-    dom_ms = kt[dom][1] / max(kt[dom][0], 1)
+    # ---- per-kernel durations (separate pass, events on the library stream)
+    kms = kernel_profile(sim, K, flush, torch)
+    dom = max(kms, key=lambda k: kms[k])
+    dom_ms = kms[dom]
     flops = FLOPS_PER_UNIT.get(dom, 0.0) * units_per_launch(dom, pr.nx, pr.ny)
     achieved = flops / (dom_ms * 1e-3) / 1e12
     peak = fp64_peak_flops() / 1e12
-    traffic = kernel_traffic(dom)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": dom,
+                "frac": achieved / peak, "traffic": kernel_traffic(dom), "kernel": dom,
                 "kernel_ms": dom_ms, "peak_source": "FP64: 152 SMs x 4 flop/clk x 2.07 GHz (unit counts)"}
     peaks = load_peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
-    alg_bytes = 16 * (3 * pr.nmat + 2)  # read + write the state once per cell-step
-    step_ms = ms_max / K
+    alg_bytes = 16 * (3 * pr.nmat + 2)  # read + write the FP64 state once per cell-step
     hbm_frac = cells * alg_bytes / (step_ms * 1e-3) / (hbm * 1e9)
 
     # ---- end to end through the C ABI with pinned host buffers
@@ -287,10 +320,10 @@ def run_lr(args, world, rank, local):
     h2d = sum(a.nbytes for a in (hp.k, hp.rho, hp.p, hp.ux, hp.uy))
     d2h = sum(a.nbytes for a in outs.values())
     n_e2e = max(3, min(K, 30))
+    import ctypes
+    L = lr.load()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    L = lr.load()
-    import ctypes
     for q in range(n_e2e):
         sim.init(hp)
         sim.step(sync=False)
@@ -300,6 +333,29 @@ def run_lr(args, world, rank, local):
                 raise RuntimeError("lr_get_fields failed")
     e2e_s = (time.perf_counter() - t0) / n_e2e
     e2e_val = world * cells / e2e_s
+    sim.close()
+
+    # ---- the other arithmetic modes: same workload, short timed runs, and
+    # their L1 difference per field from this run at the same time t_start
+    modes = {}
+    if args.other_modes and rank == 0:
+        for name, mode in MODES.items():
+            if name == args.precision:
+                continue
+            s2 = lr.Sim(pr, precision=mode)
+            if args.t_start > 0:
+                s2.run(1 << 30, args.t_start)
+            diff = {k: l1_rel(v, ref_fields[k]) for k, v in field_set(s2, lr).items()}
+            for _ in range(args.warmup):
+                s2.step(sync=False)
+            s2.sync()
+            K2 = min(K, 500)
+            ms2 = timed_steps(s2, K2, flush, torch)
+            k2 = kernel_profile(s2, min(K2, 200), flush, torch)
+            modes[name] = {"value": cells * K2 / (ms2 * 1e-3), "ms_per_step": ms2 / K2, "steps": K2,
+                           "dtype": DTYPES[name], "kernels_ms": k2,
+                           "l1_vs_" + args.precision + "_at_t_start": diff}
+            s2.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -307,18 +363,21 @@ def run_lr(args, world, rank, local):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
                 "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "vs_baseline": None, "dtype": DTYPES[args.precision].split(" ")[0], "data": "synthetic",
                 "config": {"workload": WORKLOAD, "nx": pr.nx, "ny": pr.ny, "nmat": pr.nmat,
+                           "precision": args.precision,
                            "t_start": args.t_start, "steps_before_timing": pre_steps + args.warmup,
                            "l2": "flushed between timed steps (512 MB write, untimed)",
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-                "gpu_launches": K * (sim.launches_per_step() + 1),
+                "gpu_launches": K * launches_per_step,
                 "roofline": roofline,
                 "hbm_alg_frac": {"achieved_gbs": cells * alg_bytes / (step_ms * 1e-3) / 1e9, "peak_gbs": hbm,
                                  "frac": hbm_frac, "bytes_per_cell": alg_bytes},
-                "kernels_ms": {k: v[1] / max(v[0], 1) for k, v in kt.items()},
+                "kernels_ms": kms,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "clocks": clocks, "wall_s": wall}
+        if modes:
+            line["modes"] = modes
         if cpu:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
@@ -331,7 +390,7 @@ def run_kernels_only(args):
     import torch
     from paper_2208_13409_gb300 import lr, problems as P
 
-    sim = lr.Sim(P.triple_point())
+    sim = lr.Sim(P.triple_point(), precision=MODES[args.precision])
     if args.t_start > 0:
         sim.run(1 << 30, args.t_start)
     for _ in range(args.warmup + args.steps):

@@ -53,7 +53,17 @@ typedef enum {
 enum { LR_BC_REFLECT = 0, LR_BC_PERIODIC = 1 };
 enum { LR_EOS_IDEAL = 0, LR_EOS_STIFFENED = 1 };
 enum { LR_CORNER_UPWIND = 0, LR_CORNER_DIAG = 1 };
-enum { LR_FP64 = 0 };
+/* Arithmetic of the step (lr_config.precision):
+ *   LR_FP64  native IEEE double (GB300 runs FP64 at 1/64 of its FP32 rate);
+ *   LR_DF64  double-float: each value is an unevaluated sum of two floats
+ *            (about 48 significand bits) computed on the FP32 pipe with
+ *            error-free transformations; interface geometry stays in FP64;
+ *   LR_FP32  single precision bulk (Lagrange phase and remap in float,
+ *            interface geometry, flux clipping and conservation sums in
+ *            FP64): the accuracy/throughput trade-off mode.
+ * The state is stored in the step's type; lr_init and lr_get_fields
+ * convert from and to double. */
+enum { LR_FP64 = 0, LR_DF64 = 1, LR_FP32 = 2 };
 
 /* Material EOS, section 5.2: p = (gamma - 1) rho e - pi; pi = 0 is the
  * perfect gas p = (gamma - 1) rho e of section 5.1.  gamma > 1, pi >= 0. */
@@ -71,7 +81,7 @@ typedef struct {
   double a1, a2;          /* Wilkins linear / quadratic coefficients (0.5, 1.0) */
   int bc[4];              /* xlo, xhi, ylo, yhi: LR_BC_REFLECT | LR_BC_PERIODIC;
                              xlo == xhi and ylo == yhi */
-  int precision;          /* LR_FP64 */
+  int precision;          /* LR_FP64 (default), LR_DF64 or LR_FP32 */
   int face_order;         /* 1 upwind or 2 Van Leer limited linear (default 2) */
   int corner_recon;       /* LR_CORNER_UPWIND or LR_CORNER_DIAG (default) */
   double dt_fixed;        /* > 0: use this dt instead of the CFL rule */
@@ -178,7 +188,8 @@ lr_status lr_get_fields_device(lr_ctx* ctx, int field, double* dev_out, size_t n
 /* Current simulation time and the CFL time step of the next step (synchronises). */
 lr_status lr_time(lr_ctx* ctx, double* t, double* dt_next);
 
-/* Kernel launches one lr_step issues (constant per configuration). */
+/* Kernel launches one lr_step issues (constant per configuration; lr_run
+ * issues one fewer per step plus one per call). */
 int lr_launches_per_step(const lr_ctx* ctx);
 
 /* Per-kernel timing with CUDA events recorded on the context's stream around

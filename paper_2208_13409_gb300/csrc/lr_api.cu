@@ -83,50 +83,57 @@ bool config_ok(const lr_config* c, char* why, size_t nwhy) {
   if (c->a1 < 0.0 || c->a2 < 0.0) { snprintf(why, nwhy, "negative viscosity coefficient"); return false; }
   if (c->face_order != 1 && c->face_order != 2) { snprintf(why, nwhy, "face_order must be 1 or 2"); return false; }
   if (c->corner_recon != LR_CORNER_UPWIND && c->corner_recon != LR_CORNER_DIAG) { snprintf(why, nwhy, "bad corner_recon"); return false; }
-  if (c->precision != LR_FP64) { snprintf(why, nwhy, "only LR_FP64 is available"); return false; }
+  if (c->precision != LR_FP64 && c->precision != LR_DF64 && c->precision != LR_FP32) {
+    snprintf(why, nwhy, "precision must be LR_FP64, LR_DF64 or LR_FP32");
+    return false;
+  }
   if (c->dt_fixed < 0.0) { snprintf(why, nwhy, "dt_fixed < 0"); return false; }
   return true;
 }
 
-// Lay out every device array; returns the arena size.
+// Lay out every device array; returns the arena size.  Real arrays have the
+// element size of the step's arithmetic (8 bytes for double and double-float,
+// 4 for float).
 size_t layout(const lr_config* cfg, char* base, LrState* st, LrWork* w, double** tmp, size_t* tmp_elems,
               double** rows) {
   Bump b{base, 0};
   size_t nx = cfg->nx, ny = cfg->ny, M = cfg->nmat;
   size_t nc = nx * ny, nn = (nx + 1) * (ny + 1), nfx = (nx + 1) * ny, nfy = nx * (ny + 1);
   size_t nd = (nx + 2) * (ny + 2);
+  size_t es = lr_real_size(cfg->precision == LR_DF64 ? LR_MODE_DF64 : cfg->precision == LR_FP32 ? LR_MODE_FP32 : LR_MODE_FP64);
+  auto R = [&](size_t n) { return static_cast<void*>(b.take<char>(n * es)); };
   LrState s[2];
   LrWork W;
   memset(s, 0, sizeof(s));
   memset(&W, 0, sizeof(W));
   for (int q = 0; q < 2; ++q) {
-    for (size_t a = 0; a < M; ++a) { s[q].k[a] = b.take<double>(nc); s[q].r[a] = b.take<double>(nc); s[q].e[a] = b.take<double>(nc); }
-    s[q].ux = b.take<double>(nn); s[q].uy = b.take<double>(nn);
+    for (size_t a = 0; a < M; ++a) { s[q].k[a] = R(nc); s[q].r[a] = R(nc); s[q].e[a] = R(nc); }
+    s[q].ux = R(nn); s[q].uy = R(nn);
   }
   W.scal = b.take<double>(8);
   W.red = b.take<unsigned long long>(4);
-  W.mixed = b.take<int>(nc);
   W.err = b.take<int>(2);
-  W.pux = b.take<double>(nn); W.puy = b.take<double>(nn);
-  W.mc = b.take<double>(nc); W.Q = b.take<double>(nc); W.Pi = b.take<double>(nc); W.cc = b.take<double>(nc);
-  for (size_t a = 0; a < M; ++a) { W.elc[a] = b.take<double>(nc); W.elag[a] = b.take<double>(nc); W.rcf[a] = b.take<double>(nc); }
+  W.mixed = b.take<int>(nc);
   W.mask = b.take<unsigned char>(nc);
-  W.ox = b.take<double>(nc); W.oy = b.take<double>(nc); W.wx = b.take<double>(nc); W.wy = b.take<double>(nc);
-  W.vcf = b.take<double>(nc);
   for (int q = 0; q < 6; ++q) W.cut[q] = b.take<double>(nc);
-  W.uhx = b.take<double>(nn); W.uhy = b.take<double>(nn); W.ddx = b.take<double>(nn); W.ddy = b.take<double>(nn);
-  W.ulx = b.take<double>(nn); W.uly = b.take<double>(nn);
-  W.fx = b.take<double>(nfx); W.fxb = b.take<double>(nfx); W.fxlo = b.take<double>(nfx); W.fxhi = b.take<double>(nfx);
-  W.fy = b.take<double>(nfy); W.fyb = b.take<double>(nfy); W.fylo = b.take<double>(nfy); W.fyhi = b.take<double>(nfy);
+  W.stage = b.take<double>(3 * M * nc + 2 * nn);
+  W.dtR = R(1);
+  W.pux = R(nn); W.puy = R(nn);
+  W.mc = R(nc); W.Q = R(nc); W.Pi = R(nc); W.cc = R(nc);
+  for (size_t a = 0; a < M; ++a) { W.elc[a] = R(nc); W.elag[a] = R(nc); W.rcf[a] = R(nc); }
+  W.ox = R(nc); W.oy = R(nc); W.wx = R(nc); W.wy = R(nc); W.vcf = R(nc);
+  W.uhx = R(nn); W.uhy = R(nn); W.ddx = R(nn); W.ddy = R(nn); W.ulx = R(nn); W.uly = R(nn);
+  W.fx = R(nfx); W.fxb = R(nfx); W.fxlo = R(nfx); W.fxhi = R(nfx);
+  W.fy = R(nfy); W.fyb = R(nfy); W.fylo = R(nfy); W.fyhi = R(nfy);
   if (M > 1)
-    for (size_t a = 0; a < M; ++a) { W.xAm[a] = b.take<double>(nfx); W.yAm[a] = b.take<double>(nfy); W.cAm[a] = b.take<double>(nn); }
+    for (size_t a = 0; a < M; ++a) { W.xAm[a] = R(nfx); W.yAm[a] = R(nfy); W.cAm[a] = R(nn); }
   for (size_t a = 0; a < M; ++a) {
-    W.xA[a] = b.take<double>(nfx); W.xMm[a] = b.take<double>(nfx); W.xE[a] = b.take<double>(nfx);
-    W.yA[a] = b.take<double>(nfy); W.yMm[a] = b.take<double>(nfy); W.yE[a] = b.take<double>(nfy);
-    W.cA[a] = b.take<double>(nn); W.cMm[a] = b.take<double>(nn); W.cE[a] = b.take<double>(nn);
+    W.xA[a] = R(nfx); W.xMm[a] = R(nfx); W.xE[a] = R(nfx);
+    W.yA[a] = R(nfy); W.yMm[a] = R(nfy); W.yE[a] = R(nfy);
+    W.cA[a] = R(nn); W.cMm[a] = R(nn); W.cE[a] = R(nn);
   }
-  W.MX = b.take<double>(nfx); W.MY = b.take<double>(nfy); W.Mpp = b.take<double>(nn); W.Mpm = b.take<double>(nn);
-  for (int q = 0; q < 3; ++q) { W.dX[q] = b.take<double>(nd); W.dY[q] = b.take<double>(nd); W.dPP[q] = b.take<double>(nd); W.dPM[q] = b.take<double>(nd); }
+  W.MX = R(nfx); W.MY = R(nfy); W.Mpp = R(nn); W.Mpm = R(nn);
+  for (int q = 0; q < 3; ++q) { W.dX[q] = R(nd); W.dY[q] = R(nd); W.dPP[q] = R(nd); W.dPM[q] = R(nd); }
   size_t te = M * nc > nn ? M * nc : nn;
   if (6 * nc > te) te = 6 * nc;
   if (M * nn > te) te = M * nn;
@@ -164,6 +171,7 @@ void fill_grid(lr_ctx* c) {
   g.cfl = f.cfl; g.a1 = f.a1; g.a2 = f.a2; g.dt_fixed = f.dt_fixed;
   g.face_o2 = f.face_order == 2;
   g.corner_o2 = f.corner_recon == LR_CORNER_DIAG;
+  g.mode = f.precision == LR_DF64 ? LR_MODE_DF64 : f.precision == LR_FP32 ? LR_MODE_FP32 : LR_MODE_FP64;
 }
 
 void drop_graphs(lr_ctx* c) {
@@ -257,8 +265,8 @@ lr_status create_common(const lr_config* cfg, void* mem, size_t bytes, bool own,
   }
   ctx->sticky = LR_OK;
   if (lr_launch_reset(ctx->w, ctx->stream) != cudaSuccess ||
-      cudaMemsetAsync(ctx->w.pux, 0, sizeof(double) * (cfg->nx + 1) * (cfg->ny + 1), ctx->stream) != cudaSuccess ||
-      cudaMemsetAsync(ctx->w.puy, 0, sizeof(double) * (cfg->nx + 1) * (cfg->ny + 1), ctx->stream) != cudaSuccess ||
+      cudaMemsetAsync(ctx->w.pux, 0, lr_real_size(ctx->g.mode) * (cfg->nx + 1) * (cfg->ny + 1), ctx->stream) != cudaSuccess ||
+      cudaMemsetAsync(ctx->w.puy, 0, lr_real_size(ctx->g.mode) * (cfg->nx + 1) * (cfg->ny + 1), ctx->stream) != cudaSuccess ||
       cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     if (own) cudaFree(mem);
@@ -270,163 +278,60 @@ lr_status create_common(const lr_config* cfg, void* mem, size_t bytes, bool own,
 }
 
 // ------------------------------------------------ field views (device)
-__global__ void gather_node(const double* src, double* dst, int nx, int ny, int perx, int pery) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
-  if (i > nx || j > ny) return;
-  int mi = perx ? i % nx : i, mj = pery ? j % ny : j;
-  dst[j * (nx + 1) + i] = src[mj * (nx + 1) + mi];
-}
-// Interface lines of the last step, masked to the cells that were mixed
-// (the pre-step state is still in the other half of the double buffer).
-__global__ void gather_cuts(LrGrid g, LrState prev, LrWork w, double* dst) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
-  if (i >= g.nx || j >= g.ny) return;
-  int c = j * g.nx + i, np = 0;
-  for (int a = 0; a < g.M; ++a) np += prev.k[a][c] > 0.0;
-  size_t nc = (size_t)g.nx * g.ny;
-  for (int z = 0; z < 6; ++z) dst[z * nc + c] = (np >= 2 + z / 3) ? w.cut[z][c] : 0.0;
-}
-__global__ void gather_xface(const double* src, double* dst, int nx, int ny, int perx) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
-  if (i > nx || j >= ny) return;
-  int mi = perx ? i % nx : i;
-  dst[j * (nx + 1) + i] = src[j * (nx + 1) + mi];
-}
-__global__ void gather_yface(const double* src, double* dst, int nx, int ny, int pery) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
-  if (i >= nx || j > ny) return;
-  int mj = pery ? j % ny : j;
-  dst[j * nx + i] = src[mj * nx + i];
-}
-// Mixture fields from the state: P = sum k P_a, rho = sum k rho_a, e = sum(m e)/m.
-__global__ void mixture(LrGrid g, LrState s, double* out, int which) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
-  if (i >= g.nx || j >= g.ny) return;
-  int c = j * g.nx + i;
-  double P = 0.0, R = 0.0, me = 0.0;
-  for (int a = 0; a < g.M; ++a) {
-    double ka = s.k[a][c];
-    if (!(ka > 0.0)) continue;
-    double ra = s.r[a][c], ea = s.e[a][c];
-    P += ka * ((g.gam[a] - 1.0) * ra * ea - g.pin[a]);
-    R += ka * ra;
-    me += ka * ra * ea;
-  }
-  out[c] = which == 0 ? P : which == 1 ? R : me / R;
-}
-// Conservation sums, one thread per row (deterministic order), then rows
-// summed in order by one thread.
-__global__ void cons_rows(LrGrid g, LrState s, double* rows) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  int nyu = g.pery ? g.ny : g.ny + 1, nxu = g.perx ? g.nx : g.nx + 1;
-  if (j >= nyu) return;
-  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  if (j < g.ny)
-    for (int i = 0; i < g.nx; ++i) {
-      int c = j * g.nx + i;
-      for (int a = 0; a < g.M; ++a) {
-        double m = s.r[a][c] * s.k[a][c] * g.V;
-        acc[a] += m; acc[3] += m; acc[6] += m * s.e[a][c];
-      }
-    }
-  for (int i = 0; i < nxu; ++i) {
-    double mp = 0.0;
-    for (int b = -1; b <= 0; ++b)
-      for (int a2 = -1; a2 <= 0; ++a2) {
-        int ci = i + a2, cj = j + b;
-        if (ci < 0) ci = g.perx ? ci + g.nx : -1 - ci;
-        if (ci >= g.nx) ci = g.perx ? ci - g.nx : 2 * g.nx - 1 - ci;
-        if (cj < 0) cj = g.pery ? cj + g.ny : -1 - cj;
-        if (cj >= g.ny) cj = g.pery ? cj - g.ny : 2 * g.ny - 1 - cj;
-        int c = cj * g.nx + ci;
-        for (int a = 0; a < g.M; ++a) mp += 0.25 * s.r[a][c] * s.k[a][c] * g.V;
-      }
-    double wgt = 1.0;
-    if (!g.perx && (i == 0 || i == g.nx)) wgt *= 0.5;
-    if (!g.pery && (j == 0 || j == g.ny)) wgt *= 0.5;
-    int n = j * (g.nx + 1) + i;
-    double u = s.ux[n], v = s.uy[n];
-    acc[4] += wgt * mp * u; acc[5] += wgt * mp * v;
-    acc[7] += 0.5 * wgt * mp * (u * u + v * v);
-  }
-  for (int q = 0; q < 8; ++q) rows[8 * j + q] = acc[q];
-}
-__global__ void cons_sum(const double* rows, int nrows, double* out) {
-  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int j = 0; j < nrows; ++j)
-    for (int q = 0; q < 8; ++q) acc[q] += rows[8 * j + q];
-  for (int q = 0; q < 7; ++q) out[q] = acc[q];
-  out[7] = acc[6] + acc[7];
-}
-
 lr_status field_to_device(lr_ctx* ctx, int field, double* dst) {
   const LrGrid& g = ctx->g;
   const LrState& s = ctx->st[ctx->cur];
+  const LrWork& w = ctx->w;
   size_t nc = (size_t)g.nx * g.ny;
   cudaStream_t st = ctx->stream;
-  dim3 b(128);
-  dim3 gn((g.nx + 1 + 127) / 128, g.ny + 1), gc((g.nx + 127) / 128, g.ny);
   switch (field) {
     case LR_F_K: case LR_F_RHO_MAT: case LR_F_E_MAT: case LR_F_E_LAG:
       for (int a = 0; a < g.M; ++a) {
-        const double* src = field == LR_F_K ? s.k[a] : field == LR_F_RHO_MAT ? s.r[a]
-                          : field == LR_F_E_MAT ? s.e[a] : ctx->w.elag[a];
-        CK(cudaMemcpyAsync(dst + a * nc, src, nc * sizeof(double), cudaMemcpyDeviceToDevice, st), "copy field");
+        const void* src = field == LR_F_K ? s.k[a] : field == LR_F_RHO_MAT ? s.r[a]
+                        : field == LR_F_E_MAT ? s.e[a] : w.elag[a];
+        CK(lr_launch_view(g, src, dst + a * nc, nc, 0, st), "view");
       }
       return LR_OK;
     case LR_F_P: case LR_F_RHO: case LR_F_E:
-      mixture<<<gc, b, 0, st>>>(g, s, dst, field == LR_F_P ? 0 : field == LR_F_RHO ? 1 : 2);
-      CK(cudaGetLastError(), "mixture");
+      CK(lr_launch_mixture(g, s, dst, field == LR_F_P ? 0 : field == LR_F_RHO ? 1 : 2, st), "mixture");
       return LR_OK;
-    case LR_F_C: case LR_F_VOL_LAGCF: case LR_F_Q: {
-      const double* src = field == LR_F_C ? ctx->w.cc : field == LR_F_Q ? ctx->w.Q : ctx->w.vcf;
-      CK(cudaMemcpyAsync(dst, src, nc * sizeof(double), cudaMemcpyDeviceToDevice, st), "copy field");
+    case LR_F_C: case LR_F_VOL_LAGCF: case LR_F_Q:
+      CK(lr_launch_view(g, field == LR_F_C ? w.cc : field == LR_F_Q ? w.Q : w.vcf, dst, nc, 0, st), "view");
       return LR_OK;
-    }
     case LR_F_UX: case LR_F_UY: case LR_F_UHX: case LR_F_UHY: {
-      const double* src = field == LR_F_UX ? s.ux : field == LR_F_UY ? s.uy
-                        : field == LR_F_UHX ? ctx->w.uhx : ctx->w.uhy;
-      gather_node<<<gn, b, 0, st>>>(src, dst, g.nx, g.ny, g.perx, g.pery);
-      CK(cudaGetLastError(), "gather_node");
+      const void* src = field == LR_F_UX ? s.ux : field == LR_F_UY ? s.uy : field == LR_F_UHX ? w.uhx : w.uhy;
+      CK(lr_launch_view(g, src, dst, 0, 1, st), "view");
       return LR_OK;
     }
     case LR_F_FX: case LR_F_MX:
-      gather_xface<<<gn, b, 0, st>>>(field == LR_F_FX ? ctx->w.fx : ctx->w.MX, dst, g.nx, g.ny, g.perx);
-      CK(cudaGetLastError(), "gather_xface");
+      CK(lr_launch_view(g, field == LR_F_FX ? w.fx : w.MX, dst, 0, 2, st), "view");
       return LR_OK;
     case LR_F_FY: case LR_F_MY:
-      gather_yface<<<gn, b, 0, st>>>(field == LR_F_FY ? ctx->w.fy : ctx->w.MY, dst, g.nx, g.ny, g.pery);
-      CK(cudaGetLastError(), "gather_yface");
+      CK(lr_launch_view(g, field == LR_F_FY ? w.fy : w.MY, dst, 0, 3, st), "view");
       return LR_OK;
     case LR_F_FC: case LR_F_MC:
-      CK(lr_launch_corner_debug(g, ctx->w, field == LR_F_FC ? dst : nullptr, field == LR_F_MC ? dst : nullptr, st),
+      CK(lr_launch_corner_debug(g, w, field == LR_F_FC ? dst : nullptr, field == LR_F_MC ? dst : nullptr, st),
          "corner view");
       return LR_OK;
     case LR_F_DT:
-      CK(cudaMemcpyAsync(dst, ctx->w.scal + 2, sizeof(double), cudaMemcpyDeviceToDevice, st), "dt");
+      CK(cudaMemcpyAsync(dst, w.scal + 2, sizeof(double), cudaMemcpyDeviceToDevice, st), "dt");
+      return LR_OK;
+    case LR_F_CONS:
+      CK(lr_launch_cons(g, s, ctx->rows, dst, st), "cons");
       return LR_OK;
     case LR_F_CUTS:
-      gather_cuts<<<gc, b, 0, st>>>(g, ctx->st[1 - ctx->cur], ctx->w, dst);
-      CK(cudaGetLastError(), "gather_cuts");
+      CK(lr_launch_cuts(g, ctx->st[1 - ctx->cur], w, dst, st), "cuts");
       return LR_OK;
     case LR_F_XA: case LR_F_YA: case LR_F_CA:
       for (int a = 0; a < g.M; ++a) {
         if (field == LR_F_XA)
-          gather_xface<<<gn, b, 0, st>>>(ctx->w.xA[a], dst + (size_t)a * (g.nx + 1) * g.ny, g.nx, g.ny, g.perx);
+          CK(lr_launch_view(g, w.xA[a], dst + (size_t)a * (g.nx + 1) * g.ny, 0, 2, st), "view");
         else if (field == LR_F_YA)
-          gather_yface<<<gn, b, 0, st>>>(ctx->w.yA[a], dst + (size_t)a * g.nx * (g.ny + 1), g.nx, g.ny, g.pery);
+          CK(lr_launch_view(g, w.yA[a], dst + (size_t)a * g.nx * (g.ny + 1), 0, 3, st), "view");
         else
-          gather_node<<<gn, b, 0, st>>>(ctx->w.cA[a], dst + (size_t)a * (g.nx + 1) * (g.ny + 1), g.nx, g.ny, g.perx, g.pery);
+          CK(lr_launch_view(g, w.cA[a], dst + (size_t)a * (g.nx + 1) * (g.ny + 1), 0, 1, st), "view");
       }
-      CK(cudaGetLastError(), "gather per-material flux");
       return LR_OK;
-    case LR_F_CONS: {
-      int nrows = g.pery ? g.ny : g.ny + 1;
-      cons_rows<<<(nrows + 63) / 64, 64, 0, st>>>(g, s, ctx->rows);
-      cons_sum<<<1, 1, 0, st>>>(ctx->rows, nrows, dst);
-      CK(cudaGetLastError(), "cons");
-      return LR_OK;
-    }
   }
   setmsg(ctx, "unknown field %d", field);
   return LR_ERR_ARG;
@@ -484,17 +389,15 @@ lr_status lr_init(lr_ctx* ctx, const double* k, const double* rho, const double*
   size_t nc = (size_t)g.nx * g.ny, nn = (size_t)(g.nx + 1) * (g.ny + 1);
   ctx->cur = 0;
   LrState& s = ctx->st[0];
+  double* sk = ctx->w.stage;
   CK(cudaStreamSynchronize(ctx->stream), "sync");
-  for (int a = 0; a < g.M; ++a) {
-    CK(cudaMemcpyAsync(s.k[a], k + a * nc, nc * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload k");
-    CK(cudaMemcpyAsync(s.r[a], rho + a * nc, nc * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload rho");
-    CK(cudaMemcpyAsync(s.e[a], p + a * nc, nc * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload p");
-  }
-  CK(cudaMemcpyAsync(s.ux, ux, nn * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload ux");
-  CK(cudaMemcpyAsync(s.uy, uy, nn * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload uy");
+  CK(cudaMemcpyAsync(sk, k, g.M * nc * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload k");
+  CK(cudaMemcpyAsync(sk + g.M * nc, rho, g.M * nc * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload rho");
+  CK(cudaMemcpyAsync(sk + 2 * g.M * nc, p, g.M * nc * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload p");
+  CK(cudaMemcpyAsync(sk + 3 * g.M * nc, ux, nn * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload ux");
+  CK(cudaMemcpyAsync(sk + 3 * g.M * nc + nn, uy, nn * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload uy");
   CK(lr_launch_reset(ctx->w, ctx->stream), "reset");
-  CK(lr_launch_prepare_init(g, s, ctx->w, ctx->stream), "prepare");
-  CK(lr_launch_init_cfl(g, s, ctx->w, ctx->stream), "initial cfl");
+  CK(lr_launch_init(g, s, ctx->w, ctx->stream), "prepare");
   ctx->sticky = LR_OK;
   ctx->inited = false;
   lr_status st = check_sticky(ctx);
@@ -513,8 +416,11 @@ lr_status lr_set_prescribed_velocity(lr_ctx* ctx, const double* ux, const double
   if (!ux || !uy) {
     ctx->g.presc = 0;
   } else {
-    CK(cudaMemcpyAsync(ctx->w.pux, ux, nn * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload pu");
-    CK(cudaMemcpyAsync(ctx->w.puy, uy, nn * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload pu");
+    double* sk = ctx->tmp;  // staging of one node field at a time
+    CK(cudaMemcpyAsync(sk, ux, nn * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload pu");
+    CK(lr_launch_from_double(ctx->g, sk, ctx->w.pux, nn, ctx->stream), "convert pu");
+    CK(cudaMemcpyAsync(sk, uy, nn * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload pu");
+    CK(lr_launch_from_double(ctx->g, sk, ctx->w.puy, nn, ctx->stream), "convert pu");
     CK(cudaStreamSynchronize(ctx->stream), "sync");
     ctx->g.presc = 1;
   }
@@ -526,7 +432,7 @@ lr_status lr_step(lr_ctx* ctx, double t_end, double* dt_taken) {
   if (!ctx) return LR_ERR_ARG;
   if (!ctx->inited) { setmsg(ctx, "lr_step before lr_init"); return LR_ERR_STATE; }
   if (ctx->sticky != LR_OK) return (lr_status)ctx->sticky;
-  CK(lr_launch_set_scalar(ctx->w.scal + 3, t_end, ctx->stream), "set t_end");
+  CK(lr_launch_set_tend(ctx->g, ctx->w, t_end, ctx->stream), "set t_end");
   CK(enqueue_step(ctx, ctx->cur), "step launch");
   ctx->cur = 1 - ctx->cur;
   if (dt_taken) {
@@ -545,7 +451,7 @@ lr_status lr_run(lr_ctx* ctx, double t_end, long max_steps, long* steps_done, do
   double s0[5];
   CK(cudaMemcpyAsync(s0, ctx->w.scal, sizeof(s0), cudaMemcpyDeviceToHost, ctx->stream), "read scalars");
   CK(cudaStreamSynchronize(ctx->stream), "sync");
-  CK(lr_launch_set_scalar(ctx->w.scal + 3, t_end, ctx->stream), "set t_end");
+  CK(lr_launch_set_tend(ctx->g, ctx->w, t_end, ctx->stream), "set t_end");
   // Steps are enqueued in chunks; after each chunk t and the next CFL dt are
   // read back and the next chunk is sized from the time left, so few no-op
   // steps (t already at t_end) are enqueued.
@@ -637,7 +543,10 @@ lr_status lr_time(lr_ctx* ctx, double* t, double* dt_next) {
   return LR_OK;
 }
 
-int lr_launches_per_step(const lr_ctx* ctx) { return ctx ? (int)LRK_COUNT : 0; }
+int lr_launches_per_step(const lr_ctx* ctx) {
+  // the t_end/dt kernel, then the step's kernels (no interface kernel with one material)
+  return ctx ? 1 + (int)LRK_COUNT - (ctx->g.M == 1 ? 1 : 0) : 0;
+}
 
 lr_status lr_set_profiling(lr_ctx* ctx, int on) {
   if (!ctx) return LR_ERR_ARG;

@@ -15,11 +15,16 @@ enum {
   LR_DERR_GEOM = 16        // face flux trapezoid with negative height
 };
 
-// Constants of one simulation (passed by value to every kernel).
+// Arithmetic of the step kernels (lr_config.precision).
+enum { LR_MODE_FP64 = 0, LR_MODE_DF64 = 1, LR_MODE_FP32 = 2 };
+
+// Constants of one simulation (host doubles; the kernels get them converted
+// to their arithmetic type).
 struct LrGrid {
   int nx, ny, M;
   int perx, pery;          // periodic flags (else reflective walls)
   int nxu, nyu;            // canonical node counts: nx (periodic) or nx+1
+  int mode;                // LR_MODE_*
   double dx, dy, V, L, hmin, D;  // D = sqrt(dx^2+dy^2)
   double inv2dx, inv2dy, inv8dx, inv8dy, invV, invD;  // reciprocals of the constant divisors
   double cfl, a1, a2, dt_fixed;
@@ -27,49 +32,86 @@ struct LrGrid {
   int face_o2, corner_o2, presc;
 };
 
-// Device arrays.  Cell arrays have nx*ny entries ([j][i]); node arrays
+// Real-valued device arrays, listed once so the generic (void*) and typed
+// views stay in step.  Cell arrays have nx*ny entries ([j][i]); node arrays
 // (nx+1)*(ny+1); X-face arrays (nx+1)*ny; Y-face arrays nx*(ny+1); dual
 // arrays (nx+2)*(ny+2) indexed (i+1, j+1) for i in [-1, nx], j in [-1, ny].
-struct LrState {
-  double* k[LR_MAXM];
-  double* r[LR_MAXM];
-  double* e[LR_MAXM];
-  double* ux;
-  double* uy;
+#define LR_WORK_REALS(X)                                                      \
+  X(pux) X(puy)                       /* prescribed velocity (nodes) */        \
+  X(mc) X(Q) X(Pi) X(cc)              /* cell mass, Q, P+Q, sound speed */     \
+  X(ox) X(oy) X(wx) X(wy) X(vcf)      /* Lagrangian rectangle, Vol^{lagCF} */  \
+  X(uhx) X(uhy) X(ddx) X(ddy) X(ulx) X(uly)  /* node u^{n+1/2}, d, u^{lag} */  \
+  X(fx) X(fxb) X(fxlo) X(fxhi)        /* X faces: flux and its rectangle */    \
+  X(fy) X(fyb) X(fylo) X(fyhi)        /* Y faces */                            \
+  X(MX) X(MY) X(Mpp) X(Mpm)           /* total mass fluxes */                  \
+  X(dtR)                              /* [1] dt of the step in flight */
+#define LR_WORK_MAT_REALS(X)                                                  \
+  X(elc)   /* (P_a^{n+1/2} + Q)/(rho_a dx dy): e^{lag} = e - elc (Vol^{lag} - V) */ \
+  X(elag) X(rcf)                      /* e^{lag}, rho^{lagCF} */               \
+  X(xAm) X(yAm) X(cAm)                /* material volumes of mixed donors */   \
+  X(xA) X(xMm) X(xE) X(yA) X(yMm) X(yE) X(cA) X(cMm) X(cE)  /* final fluxes */
+
+template <class R>
+struct LrStateT {
+  R* k[LR_MAXM];
+  R* r[LR_MAXM];
+  R* e[LR_MAXM];
+  R* ux;
+  R* uy;
 };
 
-struct LrWork {
+template <class R>
+struct LrWorkT {
   double* scal;            // [0] t, [1] dt from the CFL rule, [2] dt of the last step, [3] t_end,
-                           // [4] steps taken, [5] dt of the step in flight (written by lr_cell_pre)
-  unsigned long long* red; // [0] max(c+|u|) bits, [1] block counter, [2] mixed-cell count
-  int* mixed;              // work list of mixed cells (cell indices), red[2] entries
+                           // [4] steps taken, [5] dt of the step in flight
+  unsigned long long* red; // [0] max(c+|u|) key, [1] block counter, [2] mixed-cell count
   int* err;                // [0] error bits, [1] first failing index
-  double* pux; double* puy;                  // prescribed velocity (nodes)
-  // cells
-  double* mc; double* Q; double* Pi; double* cc;
-  double* elc[LR_MAXM];    // (P_a^{n+1/2} + Q) / (rho_a dx dy): e_a^{lag} = e_a - elc (Vol^{lag} - dx dy)
-  double* elag[LR_MAXM]; double* rcf[LR_MAXM];
+  int* mixed;              // work list of mixed cells (cell indices), red[2] entries
   unsigned char* mask;     // bit a set when material a is present in the cell at t^n
-  double* ox; double* oy; double* wx; double* wy; double* vcf;
   double* cut[6];          // interface lines of mixed cells (n0x, n0y, d0, n1x, n1y, d1)
-  // nodes
-  double* uhx; double* uhy; double* ddx; double* ddy; double* ulx; double* uly;
-  // X faces / Y faces: signed volume flux, rectangle (bar, lo, hi)
-  double* fx; double* fxb; double* fxlo; double* fxhi;
-  double* fy; double* fyb; double* fylo; double* fyhi;
-  // per-material volumes of fluxes given by mixed donors
-  double* xAm[LR_MAXM]; double* yAm[LR_MAXM]; double* cAm[LR_MAXM];
-  // per-material final volume / mass / energy fluxes
-  double* xA[LR_MAXM]; double* xMm[LR_MAXM]; double* xE[LR_MAXM];
-  double* yA[LR_MAXM]; double* yMm[LR_MAXM]; double* yE[LR_MAXM];
-  double* cA[LR_MAXM]; double* cMm[LR_MAXM]; double* cE[LR_MAXM];
-  // total mass fluxes
-  double* MX; double* MY; double* Mpp; double* Mpm;
-  // dual objects: [0] mass, [1] x-momentum, [2] y-momentum
-  double* dX[3]; double* dY[3]; double* dPP[3]; double* dPM[3];
+  double* stage;           // init staging: k, rho, p [3][nmat][nc] then ux, uy [2][nn]
+#define LR_F1(n) R* n;
+  LR_WORK_REALS(LR_F1)
+#undef LR_F1
+#define LR_F1(n) R* n[LR_MAXM];
+  LR_WORK_MAT_REALS(LR_F1)
+#undef LR_F1
+  R* dX[3]; R* dY[3]; R* dPP[3]; R* dPM[3];  // dual objects: mass, x- and y-momentum
 };
 
-// Host-side launchers (lr_kernels.cu).  Each enqueues one kernel on `s`.
+using LrState = LrStateT<void>;
+using LrWork = LrWorkT<void>;
+
+template <class R>
+inline LrStateT<R> typed(const LrState& s) {
+  LrStateT<R> t;
+  for (int a = 0; a < LR_MAXM; ++a) {
+    t.k[a] = static_cast<R*>(s.k[a]); t.r[a] = static_cast<R*>(s.r[a]); t.e[a] = static_cast<R*>(s.e[a]);
+  }
+  t.ux = static_cast<R*>(s.ux);
+  t.uy = static_cast<R*>(s.uy);
+  return t;
+}
+template <class R>
+inline LrWorkT<R> typed(const LrWork& w) {
+  LrWorkT<R> t;
+  t.scal = w.scal; t.red = w.red; t.err = w.err; t.mixed = w.mixed; t.mask = w.mask; t.stage = w.stage;
+  for (int q = 0; q < 6; ++q) t.cut[q] = w.cut[q];
+#define LR_F1(n) t.n = static_cast<R*>(w.n);
+  LR_WORK_REALS(LR_F1)
+#undef LR_F1
+#define LR_F1(n) for (int a = 0; a < LR_MAXM; ++a) t.n[a] = static_cast<R*>(w.n[a]);
+  LR_WORK_MAT_REALS(LR_F1)
+#undef LR_F1
+  for (int q = 0; q < 3; ++q) {
+    t.dX[q] = static_cast<R*>(w.dX[q]); t.dY[q] = static_cast<R*>(w.dY[q]);
+    t.dPP[q] = static_cast<R*>(w.dPP[q]); t.dPM[q] = static_cast<R*>(w.dPM[q]);
+  }
+  return t;
+}
+
+// Host-side launchers (lr_kernels.cu).  Each enqueues one kernel on `s`;
+// the arithmetic follows g.mode.
 enum LrKernelId {
   LRK_CELL_PRE = 0, LRK_NODE_HALF, LRK_CELL_LAG, LRK_CELL_CF, LRK_MIXED, LRK_MAT_FLUX,
   LRK_CELL_UPDATE, LRK_DUAL_FLUX, LRK_NODE_UPDATE, LRK_COUNT
@@ -78,9 +120,17 @@ extern const char* const lr_kernel_names[LRK_COUNT];
 
 cudaError_t lr_launch(int kid, const LrGrid& g, const LrState& cur, const LrState& nxt,
                       const LrWork& w, cudaStream_t s);
-cudaError_t lr_launch_init_cfl(const LrGrid& g, const LrState& cur, const LrWork& w, cudaStream_t s);
-cudaError_t lr_launch_set_scalar(double* p, double v, cudaStream_t s);
+cudaError_t lr_launch_init(const LrGrid& g, const LrState& st, const LrWork& w, cudaStream_t s);
+cudaError_t lr_launch_set_tend(const LrGrid& g, const LrWork& w, double t_end, cudaStream_t s);
 cudaError_t lr_launch_reset(const LrWork& w, cudaStream_t s);
-cudaError_t lr_launch_prepare_init(const LrGrid& g, const LrState& st, const LrWork& w, cudaStream_t s);
+// Field views: convert a real array (element type from g.mode) to double,
+// gathering with the boundary mapping: kind 0 plain copy of n values, 1 node
+// array, 2 X-face array, 3 Y-face array.
+cudaError_t lr_launch_view(const LrGrid& g, const void* src, double* dst, size_t n, int kind, cudaStream_t s);
+cudaError_t lr_launch_mixture(const LrGrid& g, const LrState& st, double* dst, int which, cudaStream_t s);
+cudaError_t lr_launch_cons(const LrGrid& g, const LrState& st, double* rows, double* dst, cudaStream_t s);
 cudaError_t lr_launch_corner_debug(const LrGrid& g, const LrWork& w, double* fc_out, double* mc_out,
                                    cudaStream_t s);
+cudaError_t lr_launch_cuts(const LrGrid& g, const LrState& prev, const LrWork& w, double* dst, cudaStream_t s);
+cudaError_t lr_launch_from_double(const LrGrid& g, const double* src, void* dst, size_t n, cudaStream_t s);
+size_t lr_real_size(int mode);

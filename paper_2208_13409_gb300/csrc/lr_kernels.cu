@@ -5,17 +5,18 @@
 // reconstructions (sections 2.1.1 and 3.3), cell remap, dual-mesh momentum
 // remap and the CFL minimum.
 //
-// Design: the step is FP64-pipe bound on GB300 (about 0.6e12 DFMA/s against
-// ~7 TB/s of HBM), so every flux object -- X face, Y face, corner, dual face,
-// dual corner -- is evaluated by exactly one thread and its result kept in HBM
-// for the cells and nodes that share it; nothing is recomputed in halos.
-// Boundary conditions are applied on read: an index outside the domain maps
-// to its mirror image (reflective wall, with the sign of the mirrored vector
-// component or flux flipped) or wraps (periodic).  Pure cells never enter
-// the interface geometry; mixed cells do their PLIC work in the donor-owned
-// kernel lr_cell_cf, which also writes the final material split of every
-// flux they donate.
+// Design: every flux object -- X face, Y face, corner, dual face, dual corner
+// -- is evaluated by exactly one thread and kept in HBM for the cells and
+// nodes that share it; nothing is recomputed in halos, because the step is
+// arithmetic-bound on GB300 (FP64: ~0.6e12 DFMA/s against ~7 TB/s of HBM).
+// The kernels are templates over the arithmetic type R: native double, float
+// (the FP32 bulk mode) or df64 (double-float on the FP32 pipe, see
+// lr_real.cuh).  Interface geometry of mixed cells (lr_mixed) always runs in
+// double.  Boundary conditions are applied on read: an index outside the
+// domain maps to its mirror image (reflective wall, with the sign of the
+// mirrored vector component or flux flipped) or wraps (periodic).
 #include "lr_dev.cuh"
+#include "lr_real.cuh"
 #include <math.h>
 
 const char* const lr_kernel_names[LRK_COUNT] = {
@@ -25,18 +26,43 @@ const char* const lr_kernel_names[LRK_COUNT] = {
 namespace {
 
 constexpr double EPS_K = 1e-12;  // material dropped when its volume <= EPS_K dx dy
+constexpr double EPS_K_FP32 = 1e-6;  // the same in the FP32 bulk mode (above float round-off)
 constexpr double EPS_C = 1e-3;   // sound-speed weight min(1, k / EPS_C)
 constexpr int BX = 32, BY = 8;
 
+// Constants of the scheme in the kernels' arithmetic type (converted on the
+// host, so no kernel converts from double).
+template <class R>
+struct KC {
+  R dx, dy, V, invV, inv2dx, inv2dy, invD, a1L, a2LL, epsKV, cfl, hmin, invEpsC;
+  R gm1[LR_MAXM], gam[LR_MAXM], pin[LR_MAXM];
+};
+template <class R>
+KC<R> make_kc(const LrGrid& g) {
+  KC<R> k;
+  k.dx = from_double<R>(g.dx); k.dy = from_double<R>(g.dy); k.V = from_double<R>(g.V);
+  k.invV = from_double<R>(g.invV); k.inv2dx = from_double<R>(g.inv2dx); k.inv2dy = from_double<R>(g.inv2dy);
+  k.invD = from_double<R>(g.invD);
+  k.a1L = from_double<R>(g.a1 * g.L); k.a2LL = from_double<R>(g.a2 * g.L * g.L);
+  k.epsKV = from_double<R>((g.mode == LR_MODE_FP32 ? EPS_K_FP32 : EPS_K) * g.V);
+  k.cfl = from_double<R>(g.cfl); k.hmin = from_double<R>(g.hmin);
+  k.invEpsC = from_double<R>(1.0 / EPS_C);
+  for (int a = 0; a < LR_MAXM; ++a) {
+    double ga = a < g.M ? g.gam[a] : 1.4, pa = a < g.M ? g.pin[a] : 0.0;
+    k.gm1[a] = from_double<R>(ga - 1.0); k.gam[a] = from_double<R>(ga); k.pin[a] = from_double<R>(pa);
+  }
+  return k;
+}
+
 // ------------------------------------------------------------ index maps
-__device__ __forceinline__ int map_cell(int i, int n, int per, int& flip) {
+__host__ __device__ __forceinline__ int map_cell(int i, int n, int per, int& flip) {
   flip = 0;
   if (i >= 0 && i < n) return i;
   if (per) return (i + n) % n;
   flip = 1;
   return i < 0 ? -1 - i : 2 * n - 1 - i;
 }
-__device__ __forceinline__ int map_node(int i, int n, int per, int& flip) {
+__host__ __device__ __forceinline__ int map_node(int i, int n, int per, int& flip) {
   flip = 0;
   if (per) return (i + n) % n;
   if (i >= 0 && i <= n) return i;
@@ -75,68 +101,62 @@ __device__ __forceinline__ int dix(const LrGrid& g, int i, int j) {
   if (g.pery) j = (j + g.ny) % g.ny;
   return (j + 1) * (g.nx + 2) + (i + 1);
 }
-// mirrored node-vector reads
-__device__ __forceinline__ double nodeX(const LrGrid& g, const double* a, int i, int j) {
+// mirrored reads: node vector components, cell scalars, centre offsets
+template <class R> __device__ __forceinline__ R nodeX(const LrGrid& g, const R* a, int i, int j) {
   Ix q = nix(g, i, j);
-  double v = a[q.idx];
+  R v = a[q.idx];
   return q.fx ? -v : v;
 }
-__device__ __forceinline__ double nodeY(const LrGrid& g, const double* a, int i, int j) {
+template <class R> __device__ __forceinline__ R nodeY(const LrGrid& g, const R* a, int i, int j) {
   Ix q = nix(g, i, j);
-  double v = a[q.idx];
+  R v = a[q.idx];
   return q.fy ? -v : v;
 }
-__device__ __forceinline__ double cellS(const LrGrid& g, const double* a, int i, int j) {
+template <class R> __device__ __forceinline__ R cellS(const LrGrid& g, const R* a, int i, int j) {
   return a[cix(g, i, j).idx];
 }
-__device__ __forceinline__ double cellOX(const LrGrid& g, const double* a, int i, int j) {
+template <class R> __device__ __forceinline__ R cellOX(const LrGrid& g, const R* a, int i, int j) {
   Ix q = cix(g, i, j);
-  return q.fx ? -a[q.idx] : a[q.idx];
+  R v = a[q.idx];
+  return q.fx ? -v : v;
 }
-__device__ __forceinline__ double cellOY(const LrGrid& g, const double* a, int i, int j) {
+template <class R> __device__ __forceinline__ R cellOY(const LrGrid& g, const R* a, int i, int j) {
   Ix q = cix(g, i, j);
-  return q.fy ? -a[q.idx] : a[q.idx];
+  R v = a[q.idx];
+  return q.fy ? -v : v;
 }
 
-__device__ __forceinline__ void set_err(const LrWork& w, int bit, int idx) {
-  atomicOr(&w.err[0], bit);
-  atomicCAS(&w.err[1], -1, idx);
+__device__ __forceinline__ void set_err(int* err, int bit, int idx) {
+  atomicOr(&err[0], bit);
+  atomicCAS(&err[1], -1, idx);
 }
 
-// dt of the current step: CFL rule (or fixed), capped at t_end.  Evaluated
-// by lr_cell_pre, which publishes it in scal[5] for the step's later kernels.
-__device__ __forceinline__ double step_dt_eval(const LrGrid& g, const double* scal) {
-  double t = scal[0], te = scal[3];
-  double dt = g.dt_fixed > 0.0 ? g.dt_fixed : scal[1];
-  if (te - t < dt) dt = te - t;
-  return dt;
-}
-__device__ __forceinline__ double step_dt(const LrGrid&, const double* scal) { return scal[5]; }
+// dt of the step in flight (scal[5], and dtR in the kernels' type), set by
+// lr_set_tend at each call and by the previous step's finalize.
+__device__ __forceinline__ bool step_live(const double* scal) { return scal[5] > 0.0; }
 
 // ---------------------------------------------------------------- EOS
 // Stiffened gas of section 5.2: p = (gamma-1) rho e - pi; c^2 = (gamma p + pi)/rho.
-__host__ __device__ __forceinline__ double eos_p(double ga, double pi, double rho, double e) {
-  return (ga - 1.0) * rho * e - pi;
-}
-__host__ __device__ __forceinline__ double eos_c2(double ga, double pi, double rho, double p) {
-  return (ga * p + pi) / rho;
-}
+template <class R> __device__ __forceinline__ R eos_p(R gm1, R pi, R rho, R e) { return gm1 * rho * e - pi; }
 
 // Cell volume F of section 1.2 (two triangles split along lr-ul), in
 // coordinates local to the cell.
-__host__ __device__ __forceinline__ double cell_F(double llx, double lly, double lrx, double lry,
-                                         double ulx, double uly, double urx, double ury) {
-  double lx = ulx - llx, ly = uly - lly, bx = lrx - llx, by = lry - lly;
-  double rx = urx - lrx, ry = ury - lry, tx = urx - ulx, ty = ury - uly;
-  return 0.5 * fabs(lx * by - ly * bx) + 0.5 * fabs(rx * ty - ry * tx);
+template <class R>
+__device__ __forceinline__ R cell_F(R llx, R lly, R lrx, R lry, R ulx, R uly, R urx, R ury) {
+  using O = RealOps<R>;
+  R lx = ulx - llx, ly = uly - lly, bx = lrx - llx, by = lry - lly;
+  R rx = urx - lrx, ry = ury - lry, tx = urx - ulx, ty = ury - uly;
+  return O::c(0.5f) * (O::abs(lx * by - ly * bx) + O::abs(rx * ty - ry * tx));
 }
 
 // Van Leer limited slope (section 2.1.1) from the two one-sided differences
 // dm = a_d - a_{d-1}, dp = a_{d+1} - a_d over the Lagrangian centre spacings
 // hm, hp: the harmonic mean of dm/hm and dp/hp, written with one division.
-__host__ __device__ __forceinline__ double vl_slope(double dm, double dp, double hm, double hp) {
-  double pr = dm * dp;
-  return pr > 0.0 ? 2.0 * pr / (dp * hm + dm * hp) : 0.0;
+template <class R>
+__device__ __forceinline__ R vl_slope(R dm, R dp, R hm, R hp) {
+  using O = RealOps<R>;
+  R pr = dm * dp;
+  return O::pos(pr) ? O::c(2.0f) * pr / (dp * hm + dm * hp) : O::c(0.0f);
 }
 
 // --------------------------------------------------- half-plane geometry
@@ -256,10 +276,12 @@ __host__ __device__ __noinline__ double poly_plic(const Poly& p, double nx, doub
 
 // Youngs normal n = -grad k / |grad k| (outward from the material), 9-point
 // weights (1,2,1)/(8 dx), (1,2,1)/(8 dy) (section 4.1); n = (1,0) if grad k = 0.
-__device__ void youngs(const LrGrid& g, const double* K, int i, int j, double& nxv, double& nyv) {
-  double kpp = cellS(g, K, i + 1, j + 1), kp0 = cellS(g, K, i + 1, j), kpm = cellS(g, K, i + 1, j - 1);
-  double kmp = cellS(g, K, i - 1, j + 1), km0 = cellS(g, K, i - 1, j), kmm = cellS(g, K, i - 1, j - 1);
-  double k0p = cellS(g, K, i, j + 1), k0m = cellS(g, K, i, j - 1);
+template <class R>
+__device__ void youngs(const LrGrid& g, const R* K, int i, int j, double& nxv, double& nyv) {
+  using O = RealOps<R>;
+  auto k = [&](int a, int b) { return O::todouble(cellS(g, K, i + a, j + b)); };
+  double kpp = k(1, 1), kp0 = k(1, 0), kpm = k(1, -1), kmp = k(-1, 1), km0 = k(-1, 0), kmm = k(-1, -1);
+  double k0p = k(0, 1), k0m = k(0, -1);
   double gx = ((kpp + 2.0 * kp0 + kpm) - (kmp + 2.0 * km0 + kmm)) * g.inv8dx;
   double gy = ((kpp + 2.0 * k0p + kmp) - (kpm + 2.0 * k0m + kmm)) * g.inv8dy;
   double gn = sqrt(gx * gx + gy * gy);
@@ -267,12 +289,14 @@ __device__ void youngs(const LrGrid& g, const double* K, int i, int j, double& n
 }
 
 // Corner donor table (section 3.3): returns 0 when the corner carries no flux.
-__device__ __forceinline__ int corner_cells(double ddx, double ddy, int i, int j, int& di, int& dj,
-                                            int& ri, int& rj) {
-  if (ddx > 0.0 && ddy > 0.0) { di = i - 1; dj = j - 1; ri = i; rj = j; return 1; }
-  if (ddx < 0.0 && ddy < 0.0) { di = i; dj = j; ri = i - 1; rj = j - 1; return 1; }
-  if (ddx > 0.0 && ddy < 0.0) { di = i - 1; dj = j; ri = i; rj = j - 1; return 1; }
-  if (ddx < 0.0 && ddy > 0.0) { di = i; dj = j - 1; ri = i - 1; rj = j; return 1; }
+template <class R>
+__device__ __forceinline__ int corner_cells(R ddx, R ddy, int i, int j, int& di, int& dj, int& ri, int& rj) {
+  using O = RealOps<R>;
+  bool xp = O::pos(ddx), xn = O::neg(ddx), yp = O::pos(ddy), yn = O::neg(ddy);
+  if (xp && yp) { di = i - 1; dj = j - 1; ri = i; rj = j; return 1; }
+  if (xn && yn) { di = i; dj = j; ri = i - 1; rj = j - 1; return 1; }
+  if (xp && yn) { di = i - 1; dj = j; ri = i; rj = j - 1; return 1; }
+  if (xn && yp) { di = i; dj = j - 1; ri = i - 1; rj = j; return 1; }
   return 0;
 }
 
@@ -282,59 +306,67 @@ __device__ __forceinline__ int corner_cells(double ddx, double ddy, int i, int j
 // rho_a V / Vol^{n+1/2}; e_a^{n+1/2} = e_a - (P_a + Q)(1/rho_a^{n+1/2} -
 // 1/rho_a); P^{n+1/2} = sum_a k_a EOS_a.  Q = rho (a1 L c |div u| + a2 L^2
 // div u^2) for div u < 0 (quadratic term read with rho so Q is a pressure).
-template <int M>
-__global__ void __launch_bounds__(256) lr_cell_pre(LrGrid g, LrState cur, LrWork w) {
+// Also the material bitmask and the mixed-cell work list.
+template <class R, int M>
+__global__ void __launch_bounds__(256) lr_cell_pre(LrGrid g, KC<R> kc, LrStateT<R> cur, LrWorkT<R> w) {
+  using O = RealOps<R>;
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-  double dt = step_dt_eval(g, w.scal);
-  if (i == 0 && j == 0) w.scal[5] = dt > 0.0 ? dt : 0.0;
   if (i >= g.nx || j >= g.ny) return;
-  if (!(dt > 0.0)) return;
+  if (!step_live(w.scal)) return;
+  const R Z = O::c(0.0f), ONE = O::c(1.0f);
+  R dt = w.dtR[0];
   int c = j * g.nx + i;
   int nn = g.nx + 1;
   int i1 = (g.perx && i + 1 == g.nx) ? 0 : i + 1;
   int j1 = (g.pery && j + 1 == g.ny) ? 0 : j + 1;
   int ll = j * nn + i, lr = j * nn + i1, ul = j1 * nn + i, ur = j1 * nn + i1;
-  double uxll = cur.ux[ll], uxlr = cur.ux[lr], uxul = cur.ux[ul], uxur = cur.ux[ur];
-  double uyll = cur.uy[ll], uylr = cur.uy[lr], uyul = cur.uy[ul], uyur = cur.uy[ur];
-  double kk[M], rr[M], ee[M], pa[M], ir[M];
-  double m = 0.0, cmax = 0.0;
+  R uxll = cur.ux[ll], uxlr = cur.ux[lr], uxul = cur.ux[ul], uxur = cur.ux[ur];
+  R uyll = cur.uy[ll], uylr = cur.uy[lr], uyul = cur.uy[ul], uyur = cur.uy[ur];
+  R kk[M], rr[M], ee[M], pa[M], ir[M];
+  R m = Z, cmax = Z;
   unsigned msk = 0u;
 #pragma unroll
   for (int a = 0; a < M; ++a) {
     kk[a] = cur.k[a][c];
-    rr[a] = 0.0; ee[a] = 0.0; pa[a] = 0.0; ir[a] = 0.0;
-    if (kk[a] > 0.0) {
+    rr[a] = Z; ee[a] = Z; pa[a] = Z; ir[a] = Z;
+    if (O::pos(kk[a])) {
       msk |= 1u << a;
       rr[a] = cur.r[a][c];
       ee[a] = cur.e[a][c];
-      ir[a] = 1.0 / rr[a];
-      pa[a] = eos_p(g.gam[a], g.pin[a], rr[a], ee[a]);
-      double c2 = (g.gam[a] * pa[a] + g.pin[a]) * ir[a];
-      double wgt = kk[a] * (1.0 / EPS_C) < 1.0 ? kk[a] * (1.0 / EPS_C) : 1.0;
-      if (wgt >= 1.0 && !(c2 > 0.0)) set_err(w, LR_DERR_SOUND, c);
-      double ca = sqrt(c2 > 0.0 ? c2 : 0.0);
-      if (wgt * ca > cmax) cmax = wgt * ca;
-      m += rr[a] * kk[a] * g.V;
+      ir[a] = O::rcp(rr[a]);
+      pa[a] = eos_p(kc.gm1[a], kc.pin[a], rr[a], ee[a]);
+      R c2 = (kc.gam[a] * pa[a] + kc.pin[a]) * ir[a];
+      R wk = kk[a] * kc.invEpsC;
+      R wgt = wk < ONE ? wk : ONE;
+      if (!(wk < ONE) && !O::pos(c2)) set_err(w.err, LR_DERR_SOUND, c);
+      R ca = O::pos(c2) ? O::sqrt(c2) : Z;
+      R wc = wgt * ca;
+      if (cmax < wc) cmax = wc;
+      m += rr[a] * kk[a] * kc.V;
     }
   }
-  double div = ((uxlr + uxur) - (uxll + uxul)) * g.inv2dx + ((uyul + uyur) - (uyll + uylr)) * g.inv2dy;
-  double rc = m * g.invV;
-  double Q = div < 0.0 ? rc * (g.a1 * g.L * cmax * fabs(div) + g.a2 * g.L * g.L * div * div) : 0.0;
-  double h = 0.5 * dt;
-  double vol = cell_F(h * uxll, h * uyll, g.dx + h * uxlr, h * uylr, h * uxul, g.dy + h * uyul,
-                      g.dx + h * uxur, g.dy + h * uyur);
-  if (!(vol > 0.0)) set_err(w, LR_DERR_VOLUME, c);
-  double dv = vol - g.V;
-  double vV = g.V / vol;
-  double P = 0.0;
+  R div = ((uxlr + uxur) - (uxll + uxul)) * kc.inv2dx + ((uyul + uyur) - (uyll + uylr)) * kc.inv2dy;
+  R rc = m * kc.invV;
+  R Q = Z;
+  if (O::neg(div)) {
+    R ad = O::abs(div);
+    Q = rc * (kc.a1L * cmax * ad + kc.a2LL * div * div);
+  }
+  R h = O::c(0.5f) * dt;
+  R vol = cell_F(h * uxll, h * uyll, kc.dx + h * uxlr, h * uylr, h * uxul, kc.dy + h * uyul,
+                 kc.dx + h * uxur, kc.dy + h * uyur);
+  if (!O::pos(vol)) set_err(w.err, LR_DERR_VOLUME, c);
+  R dv = vol - kc.V;
+  R vV = kc.V / vol;
+  R P = Z;
 #pragma unroll
   for (int a = 0; a < M; ++a) {
-    double cl = 0.0;
+    R cl = Z;
     if (msk & (1u << a)) {
-      double rh = rr[a] * vV;
-      double iv = ir[a] * g.invV;
-      double eh = ee[a] - (pa[a] + Q) * (dv * iv);
-      double ph = eos_p(g.gam[a], g.pin[a], rh, eh);
+      R rh = rr[a] * vV;
+      R iv = ir[a] * kc.invV;
+      R eh = ee[a] - (pa[a] + Q) * (dv * iv);
+      R ph = eos_p(kc.gm1[a], kc.pin[a], rh, eh);
       P += kk[a] * ph;
       cl = (ph + Q) * iv;
     }
@@ -354,32 +386,35 @@ __global__ void __launch_bounds__(256) lr_cell_pre(LrGrid g, LrState cur, LrWork
 // grad(P+Q)_p / rho_p with the four-cell gradient over 2dx, 2dy and
 // rho_p = (1/4 sum m_c)/(dx dy); u^{lag} = 2 u^{n+1/2} - u^n; node
 // displacement d = dt u^{n+1/2}.  Wall-normal components vanish.
-__global__ void __launch_bounds__(256) lr_node_half(LrGrid g, LrState cur, LrWork w) {
+template <class R>
+__global__ void __launch_bounds__(256) lr_node_half(LrGrid g, KC<R> kc, LrStateT<R> cur, LrWorkT<R> w) {
+  using O = RealOps<R>;
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
   if (i >= g.nxu || j >= g.nyu) return;
-  double dt = step_dt(g, w.scal);
-  if (!(dt > 0.0)) return;
+  if (!step_live(w.scal)) return;
+  const R Z = O::c(0.0f);
+  R dt = w.dtR[0];
   int n = j * (g.nx + 1) + i;
-  double hx, hy, lx, ly;
+  R hx, hy, lx, ly;
   if (g.presc) {
     hx = w.pux[n]; hy = w.puy[n]; lx = hx; ly = hy;
   } else {
     int A = cix(g, i - 1, j - 1).idx, B = cix(g, i, j - 1).idx;
     int C = cix(g, i - 1, j).idx, D = cix(g, i, j).idx;
-    double gx = ((w.Pi[B] + w.Pi[D]) - (w.Pi[A] + w.Pi[C])) * g.inv2dx;
-    double gy = ((w.Pi[C] + w.Pi[D]) - (w.Pi[A] + w.Pi[B])) * g.inv2dy;
-    double mp = 0.25 * (w.mc[A] + w.mc[B] + w.mc[C] + w.mc[D]);
-    double f = 0.5 * dt * g.V / mp;  // dt/2 / rho_p
-    double u0x = cur.ux[n], u0y = cur.uy[n];
+    R gx = ((w.Pi[B] + w.Pi[D]) - (w.Pi[A] + w.Pi[C])) * kc.inv2dx;
+    R gy = ((w.Pi[C] + w.Pi[D]) - (w.Pi[A] + w.Pi[B])) * kc.inv2dy;
+    R mp = O::c(0.25f) * (w.mc[A] + w.mc[B] + w.mc[C] + w.mc[D]);
+    R f = O::c(0.5f) * dt * kc.V / mp;  // dt/2 / rho_p
+    R u0x = cur.ux[n], u0y = cur.uy[n];
     hx = u0x - f * gx;
     hy = u0y - f * gy;
-    if (!g.perx && (i == 0 || i == g.nx)) hx = 0.0;
-    if (!g.pery && (j == 0 || j == g.ny)) hy = 0.0;
-    lx = 2.0 * hx - u0x;
-    ly = 2.0 * hy - u0y;
+    if (!g.perx && (i == 0 || i == g.nx)) hx = Z;
+    if (!g.pery && (j == 0 || j == g.ny)) hy = Z;
+    lx = O::c(2.0f) * hx - u0x;
+    ly = O::c(2.0f) * hy - u0y;
   }
-  if (!g.perx && (i == 0 || i == g.nx)) { hx = 0.0; lx = 0.0; }
-  if (!g.pery && (j == 0 || j == g.ny)) { hy = 0.0; ly = 0.0; }
+  if (!g.perx && (i == 0 || i == g.nx)) { hx = Z; lx = Z; }
+  if (!g.pery && (j == 0 || j == g.ny)) { hy = Z; ly = Z; }
   w.uhx[n] = hx; w.uhy[n] = hy;
   w.ulx[n] = lx; w.uly[n] = ly;
   w.ddx[n] = dt * hx; w.ddy[n] = dt * hy;
@@ -394,65 +429,96 @@ __global__ void __launch_bounds__(256) lr_node_half(LrGrid g, LrState cur, LrWor
 // straight Lagrangian face line x(y) through (dx_{p-}, dy_{p-}) and
 // (dx_{p+}, Dy + dy_{p+}), dVol = 1/2 (x(y-) + x(y+)) (y+ - y-); the flux
 // region is the rectangle [0, xbar] x [y-, y+].  Y faces swap the axes.
-template <int M>
-__global__ void __launch_bounds__(256) lr_cell_lag(LrGrid g, LrState cur, LrWork w) {
+template <class R, int M>
+__global__ void __launch_bounds__(256) lr_cell_lag(LrGrid g, KC<R> kc, LrStateT<R> cur, LrWorkT<R> w) {
+  using O = RealOps<R>;
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
   if (i >= g.nxu || j >= g.nyu) return;
-  double dt = step_dt(g, w.scal);
-  if (!(dt > 0.0)) return;
+  if (!step_live(w.scal)) return;
+  const R Z = O::c(0.0f), H = O::c(0.5f);
   int nn = g.nx + 1;
   int i1 = (g.perx && i + 1 == g.nx) ? 0 : i + 1;
   int j1 = (g.pery && j + 1 == g.ny) ? 0 : j + 1;
   if (i < g.nx && j < g.ny) {
     int c = j * g.nx + i;
     int ll = j * nn + i, lr = j * nn + i1, ul = j1 * nn + i, ur = j1 * nn + i1;
-    double dxll = w.ddx[ll], dxlr = w.ddx[lr], dxul = w.ddx[ul], dxur = w.ddx[ur];
-    double dyll = w.ddy[ll], dylr = w.ddy[lr], dyul = w.ddy[ul], dyur = w.ddy[ur];
-    double vol = cell_F(dxll, dyll, g.dx + dxlr, dylr, dxul, g.dy + dyul, g.dx + dxur, g.dy + dyur);
-    if (!(vol > 0.0)) set_err(w, LR_DERR_VOLUME, c);
-    double dv = vol - g.V;
+    R dxll = w.ddx[ll], dxlr = w.ddx[lr], dxul = w.ddx[ul], dxur = w.ddx[ur];
+    R dyll = w.ddy[ll], dylr = w.ddy[lr], dyul = w.ddy[ul], dyur = w.ddy[ur];
+    R vol = cell_F(dxll, dyll, kc.dx + dxlr, dylr, dxul, kc.dy + dyul, kc.dx + dxur, kc.dy + dyur);
+    if (!O::pos(vol)) set_err(w.err, LR_DERR_VOLUME, c);
+    R dv = vol - kc.V;
     unsigned msk = w.mask[c];
 #pragma unroll
     for (int a = 0; a < M; ++a) {
-      double el = 0.0;
+      R el = Z;
       if (msk & (1u << a)) el = cur.e[a][c] - w.elc[a][c] * dv;
       w.elag[a][c] = el;
     }
-    double xl = 0.5 * (dxll + dxul), xr = g.dx + 0.5 * (dxlr + dxur);
-    double yb = 0.5 * (dyll + dylr), yt = g.dy + 0.5 * (dyul + dyur);
-    w.ox[c] = 0.5 * (xl + xr) - 0.5 * g.dx;
-    w.oy[c] = 0.5 * (yb + yt) - 0.5 * g.dy;
+    R xl = H * (dxll + dxul), xr = kc.dx + H * (dxlr + dxur);
+    R yb = H * (dyll + dylr), yt = kc.dy + H * (dyul + dyur);
+    w.ox[c] = H * (xl + xr) - H * kc.dx;
+    w.oy[c] = H * (yb + yt) - H * kc.dy;
     w.wx[c] = xr - xl;
     w.wy[c] = yt - yb;
   }
   if (j < g.ny) {  // X face (i, j), canonical i
     int pm = j * nn + i, pp = j1 * nn + i;
-    double ax = w.ddx[pm], ay = w.ddy[pm], bx = w.ddx[pp], by = g.dy + w.ddy[pp];
-    double ylo = ay > 0.0 ? ay : 0.0;
-    double dyp = w.ddy[pp];
-    double yhi = g.dy + (dyp < 0.0 ? dyp : 0.0);
-    if (!(yhi > ylo)) set_err(w, LR_DERR_GEOM, pm);
-    double sl = (bx - ax) / (by - ay);
-    double xlo = ax + sl * (ylo - ay), xhi = ax + sl * (yhi - ay);
-    double xb = 0.5 * (xlo + xhi);
+    R ax = w.ddx[pm], ay = w.ddy[pm], bx = w.ddx[pp], dyp = w.ddy[pp], by = kc.dy + dyp;
+    R ylo = O::pos(ay) ? ay : Z;
+    R yhi = kc.dy + (O::neg(dyp) ? dyp : Z);
+    if (!(ylo < yhi)) set_err(w.err, LR_DERR_GEOM, pm);
+    R sl = (bx - ax) / (by - ay);
+    R xlo = ax + sl * (ylo - ay), xhi = ax + sl * (yhi - ay);
+    R xb = H * (xlo + xhi);
     int f = j * nn + i;
     w.fx[f] = xb * (yhi - ylo);
     w.fxb[f] = xb; w.fxlo[f] = ylo; w.fxhi[f] = yhi;
   }
   if (i < g.nx) {  // Y face (i, j), canonical j
     int pm = j * nn + i, pp = j * nn + i1;
-    double ax = w.ddx[pm], ay = w.ddy[pm], bx = g.dx + w.ddx[pp], by = w.ddy[pp];
-    double xlo = ax > 0.0 ? ax : 0.0;
-    double dxp = w.ddx[pp];
-    double xhi = g.dx + (dxp < 0.0 ? dxp : 0.0);
-    if (!(xhi > xlo)) set_err(w, LR_DERR_GEOM, pm);
-    double sl = (by - ay) / (bx - ax);
-    double ylo = ay + sl * (xlo - ax), yhi = ay + sl * (xhi - ax);
-    double yb = 0.5 * (ylo + yhi);
+    R ax = w.ddx[pm], ay = w.ddy[pm], dxp = w.ddx[pp], bx = kc.dx + dxp, by = w.ddy[pp];
+    R xlo = O::pos(ax) ? ax : Z;
+    R xhi = kc.dx + (O::neg(dxp) ? dxp : Z);
+    if (!(xlo < xhi)) set_err(w.err, LR_DERR_GEOM, pm);
+    R sl = (by - ay) / (bx - ax);
+    R ylo = ay + sl * (xlo - ax), yhi = ay + sl * (xhi - ax);
+    R yb = H * (ylo + yhi);
     int f = j * g.nx + i;
     w.fy[f] = yb * (xhi - xlo);
     w.fyb[f] = yb; w.fylo[f] = xlo; w.fyhi[f] = xhi;
   }
+}
+
+// K4: flux-consistent Lagrangian volume (section 2.3; each flux has one donor
+// and one receiver, Vol^{lagCF} = dx dy - received + donated) and
+// rho_a^{lagCF} = rho_a V / Vol^{lagCF} for every cell.
+template <class R, int M>
+__global__ void __launch_bounds__(256) lr_cell_cf(LrGrid g, KC<R> kc, LrStateT<R> cur, LrWorkT<R> w) {
+  using O = RealOps<R>;
+  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+  if (i >= g.nx || j >= g.ny) return;
+  if (!step_live(w.scal)) return;
+  int c = j * g.nx + i;
+  int fl = xix(g, i, j).idx, fr = xix(g, i + 1, j).idx;
+  int fb = yix(g, i, j).idx, ft = yix(g, i, j + 1).idx;
+  R v = kc.V + w.fx[fr] - w.fx[fl] + w.fy[ft] - w.fy[fb];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    int a = q & 1, b = q >> 1;
+    int n = nix(g, i + a, j + b).idx;
+    R cx = w.ddx[n], cy = w.ddy[n];
+    int di, dj, ri, rj;
+    if (!corner_cells(cx, cy, i + a, j + b, di, dj, ri, rj)) continue;
+    R f = O::abs(cx * cy);
+    if (di == i && dj == j) v += f;
+    if (ri == i && rj == j) v -= f;
+  }
+  if (!O::pos(v)) set_err(w.err, LR_DERR_VOLUME, c);
+  w.vcf[c] = v;
+  unsigned msk = w.mask[c];
+  R vV = kc.V / v;
+#pragma unroll
+  for (int a = 0; a < M; ++a) w.rcf[a][c] = (msk & (1u << a)) ? cur.r[a][c] * vV : O::c(0.0f);
 }
 
 // Flux regions in the donor's frame (origin at its Eulerian lower-left node).
@@ -485,82 +551,47 @@ __device__ void split_region(int ncut, const int* order, const double (*cut)[3],
   A[order[ncut]] = left > 0.0 ? left : 0.0;
 }
 
-// K4: flux-consistent Lagrangian volume (section 2.3; each flux has one donor
-// and one receiver, Vol^{lagCF} = dx dy - received + donated), rho_a^{lagCF}
-// = rho_a V / Vol^{lagCF}, and for mixed cells the interface (section 4.1
-// Youngs normal, PLIC on the rectangular Lagrangian cell of section 4.4;
-// three materials by nested cuts in material order), the split of every flux
-// this cell donates, and the clipping of a material's outgoing volume to
-// what it holds (excess to the dominant material).
-template <int M>
-__global__ void __launch_bounds__(256) lr_cell_cf(LrGrid g, LrState cur, LrWork w) {
-  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-  if (i >= g.nx || j >= g.ny) return;
-  double dt = step_dt(g, w.scal);
-  if (!(dt > 0.0)) return;
-  int c = j * g.nx + i;
-  int fl = xix(g, i, j).idx, fr = xix(g, i + 1, j).idx;
-  int fb = yix(g, i, j).idx, ft = yix(g, i, j + 1).idx;
-  double vL = w.fx[fl], vR = w.fx[fr], vB = w.fy[fb], vT = w.fy[ft];
-  double v = g.V + vR - vL + vT - vB;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    int a = q & 1, b = q >> 1;
-    int n = nix(g, i + a, j + b).idx;
-    double cx = w.ddx[n], cy = w.ddy[n];
-    int di, dj, ri, rj;
-    if (!corner_cells(cx, cy, i + a, j + b, di, dj, ri, rj)) continue;
-    double f = fabs(cx * cy);
-    if (di == i && dj == j) v += f;
-    if (ri == i && rj == j) v -= f;
-  }
-  if (!(v > 0.0)) set_err(w, LR_DERR_VOLUME, c);
-  w.vcf[c] = v;
-  unsigned msk = w.mask[c];
-  double vV = g.V / v;
-#pragma unroll
-  for (int a = 0; a < M; ++a) w.rcf[a][c] = (msk & (1u << a)) ? cur.r[a][c] * vV : 0.0;
-}
-
-// K4b: the interface work of mixed cells only (the list built by lr_cell_pre):
-// Youngs normals and PLIC lines in the rectangular Lagrangian cell (sections
-// 4.1 and 4.4; three materials by nested cuts in material order), the split
-// of every flux the cell donates, and the clipping of a material's outgoing
-// volume to what it holds (excess to the dominant material).
-template <int M>
-__global__ void __launch_bounds__(128) lr_mixed(LrGrid g, LrState cur, LrWork w) {
-  double dt = step_dt(g, w.scal);
-  if (!(dt > 0.0)) return;
+// K4b: the interface work of mixed cells only (the list built by lr_cell_pre),
+// in double whatever the step's arithmetic: Youngs normals and PLIC lines in
+// the rectangular Lagrangian cell (sections 4.1 and 4.4; three materials by
+// nested cuts in material order), the split of every flux the cell donates,
+// and the clipping of a material's outgoing volume to what it holds (excess
+// to the dominant material).
+template <class R, int M>
+__global__ void __launch_bounds__(128) lr_mixed(LrGrid g, LrStateT<R> cur, LrWorkT<R> w) {
+  using O = RealOps<R>;
+  if (!step_live(w.scal)) return;
   int count = (int)w.red[2];
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
     int c = w.mixed[t];
     int i = c % g.nx, j = c / g.nx;
-    double v = w.vcf[c];
+    double v = O::todouble(w.vcf[c]);
     int fl = xix(g, i, j).idx, fr = xix(g, i + 1, j).idx;
     int fb = yix(g, i, j).idx, ft = yix(g, i, j + 1).idx;
-    double vL = w.fx[fl], vR = w.fx[fr], vB = w.fy[fb], vT = w.fy[ft];
+    double vL = O::todouble(w.fx[fl]), vR = O::todouble(w.fx[fr]);
+    double vB = O::todouble(w.fy[fb]), vT = O::todouble(w.fy[ft]);
     int nidx[4];
     double cdx[4], cdy[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       int n = nix(g, i + (q & 1), j + (q >> 1)).idx;
       nidx[q] = n;
-      cdx[q] = w.ddx[n];
-      cdy[q] = w.ddy[n];
+      cdx[q] = O::todouble(w.ddx[n]);
+      cdy[q] = O::todouble(w.ddy[n]);
     }
     double kk[M];
     int np = 0, order[LR_MAXM] = {0, 0, 0}, dom = 0;
     unsigned msk = w.mask[c];
 #pragma unroll
     for (int a = 0; a < M; ++a) {
-      kk[a] = (msk & (1u << a)) ? cur.k[a][c] : 0.0;
+      kk[a] = (msk & (1u << a)) ? O::todouble(cur.k[a][c]) : 0.0;
       if (msk & (1u << a)) order[np++] = a;
       if (kk[a] > kk[dom]) dom = a;
     }
-    // ---- mixed cell: interface lines in the rectangular Lagrangian cell
-    double wxc = w.wx[c], wyc = w.wy[c];
-    double xl = 0.5 * g.dx - 0.5 * wxc + w.ox[c], xr = xl + wxc;
-    double yb = 0.5 * g.dy - 0.5 * wyc + w.oy[c], yt = yb + wyc;
+    // ---- interface lines in the rectangular Lagrangian cell
+    double wxc = O::todouble(w.wx[c]), wyc = O::todouble(w.wy[c]);
+    double xl = 0.5 * g.dx - 0.5 * wxc + O::todouble(w.ox[c]), xr = xl + wxc;
+    double yb = 0.5 * g.dy - 0.5 * wyc + O::todouble(w.oy[c]), yt = yb + wyc;
     int ncut = np - 1;
     double cut[2][3];
     {
@@ -583,28 +614,25 @@ __global__ void __launch_bounds__(128) lr_mixed(LrGrid g, LrState cur, LrWork w)
     }
     w.cut[0][c] = cut[0][0]; w.cut[1][c] = cut[0][1]; w.cut[2][c] = cut[0][2];
     if (ncut == 2) { w.cut[3][c] = cut[1][0]; w.cut[4][c] = cut[1][1]; w.cut[5][c] = cut[1][2]; }
-    // ---- outgoing fluxes: 0 left, 1 right, 2 bottom, 3 top, 4..7 corners
+    // ---- outgoing fluxes: left, right, bottom, top, then corners
     double A[8][M];
     int kind[8], fidx[8];
     int nf = 0;
     double r[4];
-    double out[M];
-  #pragma unroll
-    for (int a = 0; a < M; ++a) out[a] = 0.0;
     if (vL < 0.0) {
-      r[0] = w.fxb[fl]; r[1] = 0.0; r[2] = w.fxlo[fl]; r[3] = w.fxhi[fl];
+      r[0] = O::todouble(w.fxb[fl]); r[1] = 0.0; r[2] = O::todouble(w.fxlo[fl]); r[3] = O::todouble(w.fxhi[fl]);
       split_region<M>(ncut, order, cut, r, -vL, A[nf]); kind[nf] = 0; fidx[nf] = fl; ++nf;
     }
     if (vR > 0.0) {
-      r[0] = g.dx; r[1] = g.dx + w.fxb[fr]; r[2] = w.fxlo[fr]; r[3] = w.fxhi[fr];
+      r[0] = g.dx; r[1] = g.dx + O::todouble(w.fxb[fr]); r[2] = O::todouble(w.fxlo[fr]); r[3] = O::todouble(w.fxhi[fr]);
       split_region<M>(ncut, order, cut, r, vR, A[nf]); kind[nf] = 0; fidx[nf] = fr; ++nf;
     }
     if (vB < 0.0) {
-      r[0] = w.fylo[fb]; r[1] = w.fyhi[fb]; r[2] = w.fyb[fb]; r[3] = 0.0;
+      r[0] = O::todouble(w.fylo[fb]); r[1] = O::todouble(w.fyhi[fb]); r[2] = O::todouble(w.fyb[fb]); r[3] = 0.0;
       split_region<M>(ncut, order, cut, r, -vB, A[nf]); kind[nf] = 1; fidx[nf] = fb; ++nf;
     }
     if (vT > 0.0) {
-      r[0] = w.fylo[ft]; r[1] = w.fyhi[ft]; r[2] = g.dy; r[3] = g.dy + w.fyb[ft];
+      r[0] = O::todouble(w.fylo[ft]); r[1] = O::todouble(w.fyhi[ft]); r[2] = g.dy; r[3] = g.dy + O::todouble(w.fyb[ft]);
       split_region<M>(ncut, order, cut, r, vT, A[nf]); kind[nf] = 1; fidx[nf] = ft; ++nf;
     }
     for (int q = 0; q < 4; ++q) {
@@ -616,11 +644,14 @@ __global__ void __launch_bounds__(128) lr_mixed(LrGrid g, LrState cur, LrWork w)
       split_region<M>(ncut, order, cut, r, fabs(cdx[q] * cdy[q]), A[nf]);
       kind[nf] = 2; fidx[nf] = nidx[q]; ++nf;
     }
+    double out[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) out[a] = 0.0;
     for (int f = 0; f < nf; ++f)
-  #pragma unroll
+#pragma unroll
       for (int a = 0; a < M; ++a) out[a] += A[f][a];
     double sc[M];
-  #pragma unroll
+#pragma unroll
     for (int a = 0; a < M; ++a) {
       sc[a] = 1.0;
       if (a == dom) continue;
@@ -629,19 +660,39 @@ __global__ void __launch_bounds__(128) lr_mixed(LrGrid g, LrState cur, LrWork w)
     }
     for (int f = 0; f < nf; ++f) {
       double moved = 0.0;
-  #pragma unroll
+#pragma unroll
       for (int a = 0; a < M; ++a) {
         if (sc[a] < 1.0) { moved += (1.0 - sc[a]) * A[f][a]; A[f][a] *= sc[a]; }
       }
       A[f][dom] += moved;
-  #pragma unroll
+#pragma unroll
       for (int a = 0; a < M; ++a) {
-        double* dst = kind[f] == 0 ? w.xAm[a] : kind[f] == 1 ? w.yAm[a] : w.cAm[a];
-        dst[fidx[f]] = A[f][a];
+        R* dst = kind[f] == 0 ? w.xAm[a] : kind[f] == 1 ? w.yAm[a] : w.cAm[a];
+        dst[fidx[f]] = from_double<R>(A[f][a]);
       }
     }
   }
 }
+
+// Flux accumulation: compensated (Kahan) summation in the FP32 bulk mode,
+// plain sums in double and double-float (which carry their own extra bits).
+template <class R> struct Acc {
+  R s;
+  __device__ void init(R v) { s = v; }
+  __device__ void add(R x) { s += x; }
+  __device__ R get() const { return s; }
+};
+template <> struct Acc<float> {
+  float s, c;
+  __device__ void init(float v) { s = v; c = 0.0f; }
+  __device__ void add(float x) {
+    float y = __fsub_rn(x, c);
+    float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+  }
+  __device__ float get() const { return s; }
+};
 
 // Purity from the material bitmask: the cell holds material a only.
 __device__ __forceinline__ bool pure_in(const LrGrid& g, const unsigned char* mask, int i, int j, unsigned bit) {
@@ -649,12 +700,13 @@ __device__ __forceinline__ bool pure_in(const LrGrid& g, const unsigned char* ma
 }
 
 // Face value (section 2.1.1): a_d + slope/2 (sgn(dVol) wx_d - dt u_f).
-__device__ __forceinline__ double recon_face_x(const LrGrid& g, const double* q, const double* ox,
-                                               const double* wx, int di, int dj, double sg,
-                                               double fdisp, bool xdir) {
+template <class R>
+__device__ __forceinline__ R recon_face(const LrGrid& g, const KC<R>& kc, const R* q, const R* ox, const R* wx,
+                                       int di, int dj, R sg, R fdisp, bool xdir) {
+  using O = RealOps<R>;
   int c = cix(g, di, dj).idx;
-  double a0 = q[c];
-  double am, ap, om, op;
+  R a0 = q[c];
+  R am, ap, om, op;
   if (xdir) {
     am = cellS(g, q, di - 1, dj); ap = cellS(g, q, di + 1, dj);
     om = cellOX(g, ox, di - 1, dj); op = cellOX(g, ox, di + 1, dj);
@@ -662,166 +714,170 @@ __device__ __forceinline__ double recon_face_x(const LrGrid& g, const double* q,
     am = cellS(g, q, di, dj - 1); ap = cellS(g, q, di, dj + 1);
     om = cellOY(g, ox, di, dj - 1); op = cellOY(g, ox, di, dj + 1);
   }
-  double o0 = ox[c];
-  double h = xdir ? g.dx : g.dy;
-  double sl = vl_slope(a0 - am, ap - a0, h + o0 - om, h + op - o0);
-  return a0 + 0.5 * sl * (sg * wx[c] - fdisp);
+  R o0 = ox[c];
+  R h = xdir ? kc.dx : kc.dy;
+  R sl = vl_slope(a0 - am, ap - a0, h + o0 - om, h + op - o0);
+  return a0 + O::c(0.5f) * sl * (sg * wx[c] - fdisp);
 }
 // Corner value, diagonal limited reconstruction (section 3.3): along v (or
 // v_perp when dx dy < 0), slope over the diagonal neighbours' Lagrangian
 // centres, evaluated at 1/2 (sgn(dx) (wx, +-wy) - (dx, dy)) . v from the
 // donor's centre.
-__device__ __forceinline__ double recon_corner(const LrGrid& g, const double* q, const LrWork& w,
-                                               int di, int dj, double ddx, double ddy) {
-  double sy = (ddx * ddy > 0.0) ? 1.0 : -1.0;
-  int sj = sy > 0.0 ? 1 : -1;
+template <class R>
+__device__ __forceinline__ R recon_corner(const LrGrid& g, const KC<R>& kc, const R* q, const LrWorkT<R>& w,
+                                         int di, int dj, R ddx, R ddy, int sj) {
+  using O = RealOps<R>;
   int c = cix(g, di, dj).idx;
-  double a0 = q[c], ox0 = w.ox[c], oy0 = w.oy[c];
-  double ap = cellS(g, q, di + 1, dj + sj), am = cellS(g, q, di - 1, dj - sj);
-  double oxp = cellOX(g, w.ox, di + 1, dj + sj), oyp = cellOY(g, w.oy, di + 1, dj + sj);
-  double oxm = cellOX(g, w.ox, di - 1, dj - sj), oym = cellOY(g, w.oy, di - 1, dj - sj);
-  double sdy = sy * g.dy;
-  double hp = ((g.dx + oxp - ox0) * g.dx + (sdy + oyp - oy0) * sdy) * g.invD;
-  double hm = ((g.dx + ox0 - oxm) * g.dx + (sdy + oy0 - oym) * sdy) * g.invD;
-  double sl = vl_slope(a0 - am, ap - a0, hm, hp);
-  double sgx = ddx > 0.0 ? 1.0 : -1.0;
-  double off = 0.5 * (sgx * (w.wx[c] * g.dx + w.wy[c] * g.dy) - (ddx * g.dx + sy * ddy * g.dy)) * g.invD;
+  R a0 = q[c], ox0 = w.ox[c], oy0 = w.oy[c];
+  R ap = cellS(g, q, di + 1, dj + sj), am = cellS(g, q, di - 1, dj - sj);
+  R oxp = cellOX(g, w.ox, di + 1, dj + sj), oyp = cellOY(g, w.oy, di + 1, dj + sj);
+  R oxm = cellOX(g, w.ox, di - 1, dj - sj), oym = cellOY(g, w.oy, di - 1, dj - sj);
+  R sdy = sj > 0 ? kc.dy : -kc.dy;
+  R hp = ((kc.dx + oxp - ox0) * kc.dx + (sdy + oyp - oy0) * sdy) * kc.invD;
+  R hm = ((kc.dx + ox0 - oxm) * kc.dx + (sdy + oy0 - oym) * sdy) * kc.invD;
+  R sl = vl_slope(a0 - am, ap - a0, hm, hp);
+  R wsum = w.wx[c] * kc.dx + w.wy[c] * kc.dy;
+  R dsum = ddx * kc.dx + ddy * sdy;
+  R off = O::c(0.5f) * ((O::pos(ddx) ? wsum : -wsum) - dsum) * kc.invD;
   return a0 + sl * off;
 }
 
-// K5: per flux object (X face, Y face, corner): final material volumes (the
-// pure donor gives its single material the whole flux; mixed donors' splits
-// come from K4), reconstructed rho_a^{lagCF} and e_a^{lag} (order 2 only
-// where the donor and its two neighbours along the direction are pure in
-// that material -- section 4.2 remark), mass and energy fluxes, and the
-// total mass fluxes the dual remap needs.
-template <int M>
-__global__ void __launch_bounds__(256) lr_mat_flux(LrGrid g, LrState cur, LrWork w) {
+// K5: per flux object (X face, Y face, corner): final material volumes (a
+// pure donor gives its material the whole flux; mixed donors' splits come
+// from lr_mixed), reconstructed rho_a^{lagCF} and e_a^{lag} (order 2 only
+// where the donor and its two neighbours along the direction hold that
+// material alone -- section 4.2 remark), mass and energy fluxes, and the
+// total mass fluxes the dual remap needs.  Materials absent from the donor
+// get stored zeros, no arithmetic.
+template <class R, int M>
+__global__ void __launch_bounds__(256) lr_mat_flux(LrGrid g, KC<R> kc, LrStateT<R> cur, LrWorkT<R> w) {
+  using O = RealOps<R>;
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
   if (i >= g.nxu || j >= g.nyu) return;
-  double dt = step_dt(g, w.scal);
-  if (!(dt > 0.0)) return;
+  if (!step_live(w.scal)) return;
+  const R Z = O::c(0.0f), H = O::c(0.5f), ONE = O::c(1.0f);
   int nn = g.nx + 1;
   int j1 = (g.pery && j + 1 == g.ny) ? 0 : j + 1;
   int i1 = (g.perx && i + 1 == g.nx) ? 0 : i + 1;
   // ---- X face (i, j)
   if (j < g.ny) {
     int f = j * nn + i;
-    double v = w.fx[f];
-    double mt = 0.0;
+    R v = w.fx[f];
+    R mt = Z;
     unsigned dm = 0u;
     int di = 0, dc = 0;
-    double sg = 1.0, fd = 0.0;
-    if (v != 0.0) {
-      bool left = v > 0.0;
-      sg = left ? 1.0 : -1.0;
+    bool left = O::pos(v);
+    R sg = left ? ONE : -ONE, fd = Z;
+    if (!O::zero(v)) {
       di = left ? i - 1 : i;
       dc = cix(g, di, j).idx;
       dm = w.mask[dc];
-      fd = 0.5 * (w.ddx[j * nn + i] + w.ddx[j1 * nn + i]);
+      fd = H * (w.ddx[j * nn + i] + w.ddx[j1 * nn + i]);
     }
     bool mixed = (dm & (dm - 1u)) != 0u;
 #pragma unroll
     for (int a = 0; a < M; ++a) {
       unsigned bit = 1u << a;
-      if (!(dm & bit)) { w.xA[a][f] = 0.0; w.xMm[a][f] = 0.0; w.xE[a][f] = 0.0; continue; }
-      double Aa = mixed ? w.xAm[a][f] : fabs(v);
-      double Ma = 0.0, Ea = 0.0;
-      if (!mixed || Aa > 0.0) {
-        double rf = w.rcf[a][dc], ef = w.elag[a][dc];
+      if (!(dm & bit)) { w.xA[a][f] = Z; w.xMm[a][f] = Z; w.xE[a][f] = Z; continue; }
+      R Aa = mixed ? w.xAm[a][f] : O::abs(v);
+      R Ma = Z, Ea = Z;
+      if (!mixed || O::pos(Aa)) {
+        R rf = w.rcf[a][dc], ef = w.elag[a][dc];
         if (!mixed && g.face_o2 && pure_in(g, w.mask, di - 1, j, bit) && pure_in(g, w.mask, di + 1, j, bit)) {
-          rf = recon_face_x(g, w.rcf[a], w.ox, w.wx, di, j, sg, fd, true);
-          ef = recon_face_x(g, w.elag[a], w.ox, w.wx, di, j, sg, fd, true);
+          rf = recon_face(g, kc, w.rcf[a], w.ox, w.wx, di, j, sg, fd, true);
+          ef = recon_face(g, kc, w.elag[a], w.ox, w.wx, di, j, sg, fd, true);
         }
         Ma = rf * Aa;
         Ea = Ma * ef;
       } else {
-        Aa = 0.0;
+        Aa = Z;
       }
-      w.xA[a][f] = sg * Aa; w.xMm[a][f] = sg * Ma; w.xE[a][f] = sg * Ea;
-      mt += sg * Ma;
+      R sMa = left ? Ma : -Ma;
+      w.xA[a][f] = left ? Aa : -Aa; w.xMm[a][f] = sMa; w.xE[a][f] = left ? Ea : -Ea;
+      mt += sMa;
     }
     w.MX[f] = mt;
   }
   // ---- Y face (i, j)
   if (i < g.nx) {
     int f = j * g.nx + i;
-    double v = w.fy[f];
-    double mt = 0.0;
+    R v = w.fy[f];
+    R mt = Z;
     unsigned dm = 0u;
     int dj = 0, dc = 0;
-    double sg = 1.0, fd = 0.0;
-    if (v != 0.0) {
-      bool below = v > 0.0;
-      sg = below ? 1.0 : -1.0;
+    bool below = O::pos(v);
+    R sg = below ? ONE : -ONE, fd = Z;
+    if (!O::zero(v)) {
       dj = below ? j - 1 : j;
       dc = cix(g, i, dj).idx;
       dm = w.mask[dc];
-      fd = 0.5 * (w.ddy[j * nn + i] + w.ddy[j * nn + i1]);
+      fd = H * (w.ddy[j * nn + i] + w.ddy[j * nn + i1]);
     }
     bool mixed = (dm & (dm - 1u)) != 0u;
 #pragma unroll
     for (int a = 0; a < M; ++a) {
       unsigned bit = 1u << a;
-      if (!(dm & bit)) { w.yA[a][f] = 0.0; w.yMm[a][f] = 0.0; w.yE[a][f] = 0.0; continue; }
-      double Aa = mixed ? w.yAm[a][f] : fabs(v);
-      double Ma = 0.0, Ea = 0.0;
-      if (!mixed || Aa > 0.0) {
-        double rf = w.rcf[a][dc], ef = w.elag[a][dc];
+      if (!(dm & bit)) { w.yA[a][f] = Z; w.yMm[a][f] = Z; w.yE[a][f] = Z; continue; }
+      R Aa = mixed ? w.yAm[a][f] : O::abs(v);
+      R Ma = Z, Ea = Z;
+      if (!mixed || O::pos(Aa)) {
+        R rf = w.rcf[a][dc], ef = w.elag[a][dc];
         if (!mixed && g.face_o2 && pure_in(g, w.mask, i, dj - 1, bit) && pure_in(g, w.mask, i, dj + 1, bit)) {
-          rf = recon_face_x(g, w.rcf[a], w.oy, w.wy, i, dj, sg, fd, false);
-          ef = recon_face_x(g, w.elag[a], w.oy, w.wy, i, dj, sg, fd, false);
+          rf = recon_face(g, kc, w.rcf[a], w.oy, w.wy, i, dj, sg, fd, false);
+          ef = recon_face(g, kc, w.elag[a], w.oy, w.wy, i, dj, sg, fd, false);
         }
         Ma = rf * Aa;
         Ea = Ma * ef;
       } else {
-        Aa = 0.0;
+        Aa = Z;
       }
-      w.yA[a][f] = sg * Aa; w.yMm[a][f] = sg * Ma; w.yE[a][f] = sg * Ea;
-      mt += sg * Ma;
+      R sMa = below ? Ma : -Ma;
+      w.yA[a][f] = below ? Aa : -Aa; w.yMm[a][f] = sMa; w.yE[a][f] = below ? Ea : -Ea;
+      mt += sMa;
     }
     w.MY[f] = mt;
   }
   // ---- corner at node (i, j)
   {
     int n = j * nn + i;
-    double ddx = w.ddx[n], ddy = w.ddy[n];
-    double mt = 0.0;
+    R ddx = w.ddx[n], ddy = w.ddy[n];
+    R mt = Z;
     int di = 0, dj = 0, ri, rj, dc = 0, sj = 1;
     unsigned dm = 0u;
-    double fv = 0.0;
+    R fv = Z;
+    bool pp = false;
     if (corner_cells(ddx, ddy, i, j, di, dj, ri, rj)) {
-      fv = fabs(ddx * ddy);
+      fv = O::abs(ddx * ddy);
       dc = cix(g, di, dj).idx;
       dm = w.mask[dc];
-      sj = ddx * ddy > 0.0 ? 1 : -1;
+      pp = O::pos(ddx) == O::pos(ddy);
+      sj = pp ? 1 : -1;
     }
     bool mixed = (dm & (dm - 1u)) != 0u;
 #pragma unroll
     for (int a = 0; a < M; ++a) {
       unsigned bit = 1u << a;
-      if (!(dm & bit)) { w.cA[a][n] = 0.0; w.cMm[a][n] = 0.0; w.cE[a][n] = 0.0; continue; }
-      double Aa = mixed ? w.cAm[a][n] : fv;
-      double Ma = 0.0, Ea = 0.0;
-      if (!mixed || Aa > 0.0) {
-        double rf = w.rcf[a][dc], ef = w.elag[a][dc];
+      if (!(dm & bit)) { w.cA[a][n] = Z; w.cMm[a][n] = Z; w.cE[a][n] = Z; continue; }
+      R Aa = mixed ? w.cAm[a][n] : fv;
+      R Ma = Z, Ea = Z;
+      if (!mixed || O::pos(Aa)) {
+        R rf = w.rcf[a][dc], ef = w.elag[a][dc];
         if (!mixed && g.corner_o2 && pure_in(g, w.mask, di - 1, dj - sj, bit) &&
             pure_in(g, w.mask, di + 1, dj + sj, bit)) {
-          rf = recon_corner(g, w.rcf[a], w, di, dj, ddx, ddy);
-          ef = recon_corner(g, w.elag[a], w, di, dj, ddx, ddy);
+          rf = recon_corner(g, kc, w.rcf[a], w, di, dj, ddx, ddy, sj);
+          ef = recon_corner(g, kc, w.elag[a], w, di, dj, ddx, ddy, sj);
         }
         Ma = rf * Aa;
         Ea = Ma * ef;
       } else {
-        Aa = 0.0;
+        Aa = Z;
       }
       w.cA[a][n] = Aa; w.cMm[a][n] = Ma; w.cE[a][n] = Ea;
       mt += Ma;
     }
-    double sgm = ddx > 0.0 ? mt : -mt;  // signed along +x
-    bool pp = ddx * ddy > 0.0;
-    w.Mpp[n] = pp ? sgm : 0.0;
-    w.Mpm[n] = (!pp && dm) ? sgm : 0.0;
+    R sgm = O::pos(ddx) ? mt : -mt;  // signed along +x
+    w.Mpp[n] = (dm && pp) ? sgm : Z;
+    w.Mpm[n] = (dm && !pp) ? sgm : Z;
   }
 }
 
@@ -829,20 +885,21 @@ __global__ void __launch_bounds__(256) lr_mat_flux(LrGrid g, LrState cur, LrWork
 // faces and four corners; materials with Vol_a <= EPS_K dx dy are dropped
 // (mass and energy to the largest remaining material); k_a = Vol_a / sum
 // Vol; rho_a = m_a/(k_a dx dy); e_a = (m e)_a / m_a; the sound speed for the
-// CFL rule of the next step.
-template <int M>
-__global__ void __launch_bounds__(256) lr_cell_update(LrGrid g, LrState cur, LrState nxt, LrWork w) {
+// CFL rule of the next step.  Only materials present in the cell's 3x3
+// neighbourhood (its possible donors) are accumulated.
+template <class R, int M>
+__global__ void __launch_bounds__(256) lr_cell_update(LrGrid g, KC<R> kc, LrStateT<R> cur, LrStateT<R> nxt,
+                                                      LrWorkT<R> w) {
+  using O = RealOps<R>;
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
   if (i >= g.nx || j >= g.ny) return;
   int c = j * g.nx + i;
-  double dt = step_dt(g, w.scal);
-  if (!(dt > 0.0)) {
+  if (!step_live(w.scal)) {
 #pragma unroll
     for (int a = 0; a < M; ++a) { nxt.k[a][c] = cur.k[a][c]; nxt.r[a][c] = cur.r[a][c]; nxt.e[a][c] = cur.e[a][c]; }
     return;
   }
-  // materials that can be in this cell after the remap: its own and those of
-  // every cell that can donate to it (the 3x3 neighbourhood)
+  const R Z = O::c(0.0f), ONE = O::c(1.0f);
   unsigned own = w.mask[c], nb = own;
 #pragma unroll
   for (int q = 0; q < 9; ++q) {
@@ -864,82 +921,94 @@ __global__ void __launch_bounds__(256) lr_cell_update(LrGrid g, LrState cur, LrS
       if (di == i && dj == j) cs[q] = -1;
     }
   }
-  double vcf = w.vcf[c];
-  double vol[M], mas[M], ene[M];
+  R vcf = w.vcf[c];
+  R vol[M], mas[M], ene[M];
 #pragma unroll
   for (int a = 0; a < M; ++a) {
-    vol[a] = 0.0; mas[a] = 0.0; ene[a] = 0.0;
+    vol[a] = Z; mas[a] = Z; ene[a] = Z;
     if (!(nb & (1u << a))) continue;
-    double vv = 0.0, mm = 0.0, ee = 0.0;
+    Acc<R> vv, mm, ee;
+    vv.init(Z); mm.init(Z); ee.init(Z);
     if (own & (1u << a)) {
-      double ka = cur.k[a][c];
-      mm = cur.r[a][c] * ka * g.V;
-      vv = ka * vcf;
-      ee = mm * w.elag[a][c];
+      R ka = cur.k[a][c];
+      R m0 = cur.r[a][c] * ka * kc.V;
+      mm.init(m0);
+      vv.init(ka * vcf);
+      ee.init(m0 * w.elag[a][c]);
     }
-    vv += w.xA[a][fl] - w.xA[a][fr] + w.yA[a][fb] - w.yA[a][ft];
-    mm += w.xMm[a][fl] - w.xMm[a][fr] + w.yMm[a][fb] - w.yMm[a][ft];
-    ee += w.xE[a][fl] - w.xE[a][fr] + w.yE[a][fb] - w.yE[a][ft];
+    vv.add(w.xA[a][fl] - w.xA[a][fr]); vv.add(w.yA[a][fb] - w.yA[a][ft]);
+    mm.add(w.xMm[a][fl] - w.xMm[a][fr]); mm.add(w.yMm[a][fb] - w.yMm[a][ft]);
+    ee.add(w.xE[a][fl] - w.xE[a][fr]); ee.add(w.yE[a][fb] - w.yE[a][ft]);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      if (cs[q] == 1) { vv += w.cA[a][cn[q]]; mm += w.cMm[a][cn[q]]; ee += w.cE[a][cn[q]]; }
-      if (cs[q] == -1) { vv -= w.cA[a][cn[q]]; mm -= w.cMm[a][cn[q]]; ee -= w.cE[a][cn[q]]; }
+      if (cs[q] == 1) { vv.add(w.cA[a][cn[q]]); mm.add(w.cMm[a][cn[q]]); ee.add(w.cE[a][cn[q]]); }
+      if (cs[q] == -1) { vv.add(-w.cA[a][cn[q]]); mm.add(-w.cMm[a][cn[q]]); ee.add(-w.cE[a][cn[q]]); }
     }
-    vol[a] = vv; mas[a] = mm; ene[a] = ee;
+    vol[a] = vv.get(); mas[a] = mm.get(); ene[a] = ee.get();
   }
   bool keep[M];
   int big = -1, nkeep = 0;
-  double tot = 0.0, lm = 0.0, le = 0.0;
+  R tot = Z, lm = Z, le = Z;
 #pragma unroll
   for (int a = 0; a < M; ++a) {
-    keep[a] = (nb & (1u << a)) && vol[a] > EPS_K * g.V;
-    if (keep[a]) { tot += vol[a]; ++nkeep; if (big < 0 || vol[a] > vol[big]) big = a; }
-    else { lm += mas[a]; le += ene[a]; }
+    keep[a] = (nb & (1u << a)) && kc.epsKV < vol[a];
+    if (keep[a]) {
+      tot += vol[a];
+      ++nkeep;
+      if (big < 0) big = a;
+      else if (vol[big] < vol[a]) big = a;
+    } else {
+      lm += mas[a];
+      le += ene[a];
+    }
   }
-  if (big < 0) { set_err(w, LR_DERR_VOLUME, c); big = 0; tot = 1.0; }
+  if (big < 0) { set_err(w.err, LR_DERR_VOLUME, c); big = 0; tot = ONE; }
 #pragma unroll
   for (int a = 0; a < M; ++a) {
     if (a == big) { mas[a] += lm; ene[a] += le; }
   }
-  double cmax = 0.0;
+  R cmax = Z;
 #pragma unroll
   for (int a = 0; a < M; ++a) {
-    double ka = 0.0, ra = 0.0, ea = 0.0;
+    R ka = Z, ra = Z, ea = Z;
     if (keep[a]) {
-      ka = nkeep == 1 ? 1.0 : vol[a] / tot;
-      if (!(mas[a] > 0.0)) set_err(w, LR_DERR_MASS, c);
-      double im = 1.0 / mas[a];
-      double kV = ka * g.V;
-      ra = nkeep == 1 ? mas[a] * g.invV : mas[a] / kV;
+      ka = nkeep == 1 ? ONE : vol[a] / tot;
+      if (!O::pos(mas[a])) set_err(w.err, LR_DERR_MASS, c);
+      R im = O::rcp(mas[a]);
+      R kV = ka * kc.V;
+      ra = nkeep == 1 ? mas[a] * kc.invV : mas[a] / kV;
       ea = ene[a] * im;
-      double pa = eos_p(g.gam[a], g.pin[a], ra, ea);
-      double c2 = (g.gam[a] * pa + g.pin[a]) * (kV * im);
-      double wgt = ka * (1.0 / EPS_C) < 1.0 ? ka * (1.0 / EPS_C) : 1.0;
-      if (wgt >= 1.0 && !(c2 > 0.0)) set_err(w, LR_DERR_SOUND, c);
-      double ca = sqrt(c2 > 0.0 ? c2 : 0.0);
-      if (wgt * ca > cmax) cmax = wgt * ca;
-      if (!isfinite(ra) || !isfinite(ea)) set_err(w, LR_DERR_NAN, c);
+      R pa = eos_p(kc.gm1[a], kc.pin[a], ra, ea);
+      R c2 = (kc.gam[a] * pa + kc.pin[a]) * (kV * im);
+      R wk = ka * kc.invEpsC;
+      R wgt = wk < ONE ? wk : ONE;
+      if (!(wk < ONE) && !O::pos(c2)) set_err(w.err, LR_DERR_SOUND, c);
+      R ca = O::pos(c2) ? O::sqrt(c2) : Z;
+      R wc = wgt * ca;
+      if (cmax < wc) cmax = wc;
+      if (!O::finite(ra) || !O::finite(ea)) set_err(w.err, LR_DERR_NAN, c);
     }
     nxt.k[a][c] = ka; nxt.r[a][c] = ra; nxt.e[a][c] = ea;
   }
   w.cc[c] = cmax;
 }
 
-// Dual-object reconstruction of a node velocity component along x or y:
-// the primary formula with nodes as centres (Lagrangian positions x + d,
-// dual width dx + (d_{q+1} - d_{q-1})/2, face displacement fdisp).
-__device__ __forceinline__ double recon_dual_face(const LrGrid& g, const double* u, bool ucomp_x,
-                                                  const double* dd, int qi, int qj, bool xdir,
-                                                  double sg, double fdisp) {
+// Dual reconstruction of a node velocity component along x or y: the
+// primary formula with nodes as centres (Lagrangian positions x + d, dual
+// width dx + (d_{q+1} - d_{q-1})/2, face displacement fdisp).
+template <class R>
+__device__ __forceinline__ R recon_dual_face(const LrGrid& g, const KC<R>& kc, const R* u, bool ucomp_x,
+                                            const R* dd, int qi, int qj, bool xdir, R sg, R fdisp) {
+  using O = RealOps<R>;
   auto U = [&](int a, int b) { return ucomp_x ? nodeX(g, u, a, b) : nodeY(g, u, a, b); };
   auto Dd = [&](int a, int b) { return xdir ? nodeX(g, dd, a, b) : nodeY(g, dd, a, b); };
   int mi = xdir ? 1 : 0, mj = xdir ? 0 : 1;
-  double u0 = U(qi, qj), up = U(qi + mi, qj + mj), um = U(qi - mi, qj - mj);
-  double d0 = Dd(qi, qj), dp = Dd(qi + mi, qj + mj), dm = Dd(qi - mi, qj - mj);
-  double h = xdir ? g.dx : g.dy;
-  double sl = vl_slope(u0 - um, up - u0, h + d0 - dm, h + dp - d0);
-  double wd = h + 0.5 * (dp - dm);
-  return u0 + 0.5 * sl * (sg * wd - fdisp);
+  R u0 = U(qi, qj), up = U(qi + mi, qj + mj), um = U(qi - mi, qj - mj);
+  R d0 = Dd(qi, qj), dp = Dd(qi + mi, qj + mj), dm = Dd(qi - mi, qj - mj);
+  R h = xdir ? kc.dx : kc.dy;
+  R sl = vl_slope(u0 - um, up - u0, h + d0 - dm, h + dp - d0);
+  R wd = h + O::c(0.5f) * (dp - dm);
+  return u0 + O::c(0.5f) * sl * (sg * wd - fdisp);
 }
 
 // K7a: dual-mesh fluxes (sections 2.1.1 and 2.3).  Dual X face between nodes
@@ -950,36 +1019,39 @@ __device__ __forceinline__ double recon_dual_face(const LrGrid& g, const double*
 // and the momentum flux with the upwind-node velocity u^{lag} reconstructed
 // on the dual mesh.  Objects just outside reflective walls are evaluated from
 // the mirrored data, so every boundary node sees a full dual cell.
-__global__ void __launch_bounds__(256) lr_dual_flux(LrGrid g, LrWork w) {
+template <class R>
+__global__ void __launch_bounds__(256) lr_dual_flux(LrGrid g, KC<R> kc, LrWorkT<R> w) {
+  using O = RealOps<R>;
   int i = (int)(blockIdx.x * BX + threadIdx.x) - 1, j = (int)(blockIdx.y * BY + threadIdx.y) - 1;
   if (i > g.nx || j > g.ny) return;
-  double dt = step_dt(g, w.scal);
-  if (!(dt > 0.0)) return;
+  if (!step_live(w.scal)) return;
+  const R Z = O::c(0.0f), H = O::c(0.5f), Q4 = O::c(0.25f), ONE = O::c(1.0f);
   bool xdual = g.perx ? (i >= 0 && i < g.nx) : true;   // dual index range in x
   bool ydual = g.pery ? (j >= 0 && j < g.ny) : true;
   bool xnode = i >= 0 && i < g.nxu;                     // canonical node in x
   bool ynode = j >= 0 && j < g.nyu;
   int o = (j + 1) * (g.nx + 2) + (i + 1);
-  auto MXr = [&](int a, int b) { Ix q = xix(g, a, b); double v = w.MX[q.idx]; return q.fx ? -v : v; };
-  auto MYr = [&](int a, int b) { Ix q = yix(g, a, b); double v = w.MY[q.idx]; return q.fy ? -v : v; };
-  auto CPr = [&](int a, int b, double& pp, double& pm) {
+  auto MXr = [&](int a, int b) { Ix q = xix(g, a, b); R v = w.MX[q.idx]; return q.fx ? -v : v; };
+  auto MYr = [&](int a, int b) { Ix q = yix(g, a, b); R v = w.MY[q.idx]; return q.fy ? -v : v; };
+  auto CPr = [&](int a, int b, R& pp, R& pm) {
     Ix q = nix(g, a, b);
-    double x = w.Mpp[q.idx], y = w.Mpm[q.idx];
-    if (q.fx) { double t = -y; y = -x; x = t; }
-    if (q.fy) { double t = y; y = x; x = t; }
+    R x = w.Mpp[q.idx], y = w.Mpm[q.idx];
+    if (q.fx) { R t = -y; y = -x; x = t; }
+    if (q.fy) { R t = y; y = x; x = t; }
     pp = x; pm = y;
   };
   if (xdual && ynode) {  // dual X face between nodes (i,j), (i+1,j)
-    double Dm = 0.25 * (MXr(i, j - 1) + MXr(i + 1, j - 1) + MXr(i, j) + MXr(i + 1, j));
-    double px = 0.0, py = 0.0;
-    if (Dm != 0.0) {
-      int qi = Dm > 0.0 ? i : i + 1;
-      double sg = Dm > 0.0 ? 1.0 : -1.0;
-      double fd = 0.5 * (nodeX(g, w.ddx, i, j) + nodeX(g, w.ddx, i + 1, j));
-      double vx, vy;
+    R Dm = Q4 * (MXr(i, j - 1) + MXr(i + 1, j - 1) + MXr(i, j) + MXr(i + 1, j));
+    R px = Z, py = Z;
+    if (!O::zero(Dm)) {
+      bool fwd = O::pos(Dm);
+      int qi = fwd ? i : i + 1;
+      R sg = fwd ? ONE : -ONE;
+      R fd = H * (nodeX(g, w.ddx, i, j) + nodeX(g, w.ddx, i + 1, j));
+      R vx, vy;
       if (g.face_o2) {
-        vx = recon_dual_face(g, w.ulx, true, w.ddx, qi, j, true, sg, fd);
-        vy = recon_dual_face(g, w.uly, false, w.ddx, qi, j, true, sg, fd);
+        vx = recon_dual_face(g, kc, w.ulx, true, w.ddx, qi, j, true, sg, fd);
+        vy = recon_dual_face(g, kc, w.uly, false, w.ddx, qi, j, true, sg, fd);
       } else {
         vx = nodeX(g, w.ulx, qi, j); vy = nodeY(g, w.uly, qi, j);
       }
@@ -988,16 +1060,17 @@ __global__ void __launch_bounds__(256) lr_dual_flux(LrGrid g, LrWork w) {
     w.dX[0][o] = Dm; w.dX[1][o] = px; w.dX[2][o] = py;
   }
   if (xnode && ydual) {  // dual Y face between nodes (i,j), (i,j+1)
-    double Dm = 0.25 * (MYr(i - 1, j) + MYr(i - 1, j + 1) + MYr(i, j) + MYr(i, j + 1));
-    double px = 0.0, py = 0.0;
-    if (Dm != 0.0) {
-      int qj = Dm > 0.0 ? j : j + 1;
-      double sg = Dm > 0.0 ? 1.0 : -1.0;
-      double fd = 0.5 * (nodeY(g, w.ddy, i, j) + nodeY(g, w.ddy, i, j + 1));
-      double vx, vy;
+    R Dm = Q4 * (MYr(i - 1, j) + MYr(i - 1, j + 1) + MYr(i, j) + MYr(i, j + 1));
+    R px = Z, py = Z;
+    if (!O::zero(Dm)) {
+      bool fwd = O::pos(Dm);
+      int qj = fwd ? j : j + 1;
+      R sg = fwd ? ONE : -ONE;
+      R fd = H * (nodeY(g, w.ddy, i, j) + nodeY(g, w.ddy, i, j + 1));
+      R vx, vy;
       if (g.face_o2) {
-        vx = recon_dual_face(g, w.ulx, true, w.ddy, i, qj, false, sg, fd);
-        vy = recon_dual_face(g, w.uly, false, w.ddy, i, qj, false, sg, fd);
+        vx = recon_dual_face(g, kc, w.ulx, true, w.ddy, i, qj, false, sg, fd);
+        vy = recon_dual_face(g, kc, w.uly, false, w.ddy, i, qj, false, sg, fd);
       } else {
         vx = nodeX(g, w.ulx, i, qj); vy = nodeY(g, w.uly, i, qj);
       }
@@ -1006,35 +1079,35 @@ __global__ void __launch_bounds__(256) lr_dual_flux(LrGrid g, LrWork w) {
     w.dY[0][o] = Dm; w.dY[1][o] = px; w.dY[2][o] = py;
   }
   if (xdual && ydual) {  // dual corners at the centre of cell (i,j)
-    double p0, m0, p1, m1, p2, m2, p3, m3;
+    R p0, m0, p1, m1, p2, m2, p3, m3;
     CPr(i, j, p0, m0); CPr(i + 1, j, p1, m1); CPr(i, j + 1, p2, m2); CPr(i + 1, j + 1, p3, m3);
-    double cdx = 0.25 * (nodeX(g, w.ddx, i, j) + nodeX(g, w.ddx, i + 1, j) + nodeX(g, w.ddx, i, j + 1) +
-                         nodeX(g, w.ddx, i + 1, j + 1));
-    double cdy = 0.25 * (nodeY(g, w.ddy, i, j) + nodeY(g, w.ddy, i + 1, j) + nodeY(g, w.ddy, i, j + 1) +
-                         nodeY(g, w.ddy, i + 1, j + 1));
+    R cdx = Q4 * (nodeX(g, w.ddx, i, j) + nodeX(g, w.ddx, i + 1, j) + nodeX(g, w.ddx, i, j + 1) +
+                  nodeX(g, w.ddx, i + 1, j + 1));
+    R cdy = Q4 * (nodeY(g, w.ddy, i, j) + nodeY(g, w.ddy, i + 1, j) + nodeY(g, w.ddy, i, j + 1) +
+                  nodeY(g, w.ddy, i + 1, j + 1));
     for (int kind = 0; kind < 2; ++kind) {
       bool pp = kind == 0;
-      double Dm = pp ? 0.25 * (p0 + p1 + p2 + p3) : 0.25 * (m0 + m1 + m2 + m3);
-      double px = 0.0, py = 0.0;
-      if (Dm != 0.0) {
+      R Dm = pp ? Q4 * (p0 + p1 + p2 + p3) : Q4 * (m0 + m1 + m2 + m3);
+      R px = Z, py = Z;
+      if (!O::zero(Dm)) {
+        bool fwd = O::pos(Dm);
         int ai = i, aj = pp ? j : j + 1, bi = i + 1, bj = pp ? j + 1 : j;
-        int qi = Dm > 0.0 ? ai : bi, qj = Dm > 0.0 ? aj : bj;
-        double sg = Dm > 0.0 ? 1.0 : -1.0;
-        double vx = nodeX(g, w.ulx, qi, qj), vy = nodeY(g, w.uly, qi, qj);
+        int qi = fwd ? ai : bi, qj = fwd ? aj : bj;
+        R vx = nodeX(g, w.ulx, qi, qj), vy = nodeY(g, w.uly, qi, qj);
         if (g.corner_o2) {
-          double sy = pp ? 1.0 : -1.0;
           int sj = pp ? 1 : -1;
-          double sdy = sy * g.dy;
-          double dx0 = nodeX(g, w.ddx, qi, qj), dy0 = nodeY(g, w.ddy, qi, qj);
-          double dxp = nodeX(g, w.ddx, qi + 1, qj + sj), dyp = nodeY(g, w.ddy, qi + 1, qj + sj);
-          double dxm = nodeX(g, w.ddx, qi - 1, qj - sj), dym = nodeY(g, w.ddy, qi - 1, qj - sj);
-          double hp = ((g.dx + dxp - dx0) * g.dx + (sdy + dyp - dy0) * sdy) * g.invD;
-          double hm = ((g.dx + dx0 - dxm) * g.dx + (sdy + dy0 - dym) * sdy) * g.invD;
-          double wxq = g.dx + 0.5 * (nodeX(g, w.ddx, qi + 1, qj) - nodeX(g, w.ddx, qi - 1, qj));
-          double wyq = g.dy + 0.5 * (nodeY(g, w.ddy, qi, qj + 1) - nodeY(g, w.ddy, qi, qj - 1));
-          double off = 0.5 * (sg * (wxq * g.dx + wyq * g.dy) - (cdx * g.dx + sy * cdy * g.dy)) * g.invD;
-          double uxp = nodeX(g, w.ulx, qi + 1, qj + sj), uxm = nodeX(g, w.ulx, qi - 1, qj - sj);
-          double uyp = nodeY(g, w.uly, qi + 1, qj + sj), uym = nodeY(g, w.uly, qi - 1, qj - sj);
+          R sdy = pp ? kc.dy : -kc.dy;
+          R dx0 = nodeX(g, w.ddx, qi, qj), dy0 = nodeY(g, w.ddy, qi, qj);
+          R dxp = nodeX(g, w.ddx, qi + 1, qj + sj), dyp = nodeY(g, w.ddy, qi + 1, qj + sj);
+          R dxm = nodeX(g, w.ddx, qi - 1, qj - sj), dym = nodeY(g, w.ddy, qi - 1, qj - sj);
+          R hp = ((kc.dx + dxp - dx0) * kc.dx + (sdy + dyp - dy0) * sdy) * kc.invD;
+          R hm = ((kc.dx + dx0 - dxm) * kc.dx + (sdy + dy0 - dym) * sdy) * kc.invD;
+          R wxq = kc.dx + H * (nodeX(g, w.ddx, qi + 1, qj) - nodeX(g, w.ddx, qi - 1, qj));
+          R wyq = kc.dy + H * (nodeY(g, w.ddy, qi, qj + 1) - nodeY(g, w.ddy, qi, qj - 1));
+          R wsum = wxq * kc.dx + wyq * kc.dy;
+          R off = H * ((fwd ? wsum : -wsum) - (cdx * kc.dx + cdy * sdy)) * kc.invD;
+          R uxp = nodeX(g, w.ulx, qi + 1, qj + sj), uxm = nodeX(g, w.ulx, qi - 1, qj - sj);
+          R uyp = nodeY(g, w.uly, qi + 1, qj + sj), uym = nodeY(g, w.uly, qi - 1, qj - sj);
           vx = vx + vl_slope(vx - uxm, uxp - vx, hm, hp) * off;
           vy = vy + vl_slope(vy - uym, uyp - vy, hm, hp) * off;
         }
@@ -1046,21 +1119,55 @@ __global__ void __launch_bounds__(256) lr_dual_flux(LrGrid g, LrWork w) {
   }
 }
 
-// Block-wide max of v >= 0 folded into red[0]; the last block of the grid
-// turns it into the next CFL time step (and advances t when `advance`).
-__device__ void cfl_finalize(const LrGrid& g, const LrWork& w, double v, bool advance, double dt) {
-  __shared__ double sm[32];
+// Order-preserving 64-bit keys of non-negative values for the CFL max.
+template <class R> struct Key;
+template <> struct Key<double> {
+  __device__ static unsigned long long enc(double v) { return (unsigned long long)__double_as_longlong(v); }
+  __device__ static double dec(unsigned long long k) { return __longlong_as_double((long long)k); }
+};
+template <> struct Key<float> {
+  __device__ static unsigned long long enc(float v) { return (unsigned long long)__float_as_uint(v); }
+  __device__ static float dec(unsigned long long k) { return __uint_as_float((unsigned)k); }
+};
+template <> struct Key<df64> {
+  __device__ static unsigned ord(float f) {
+    unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+  }
+  __device__ static float unord(unsigned u) { return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u); }
+  __device__ static unsigned long long enc(df64 v) {
+    return ((unsigned long long)__float_as_uint(v.hi) << 32) | ord(v.lo);
+  }
+  __device__ static df64 dec(unsigned long long k) { return df64(__uint_as_float((unsigned)(k >> 32)), unord((unsigned)k)); }
+};
+template <class R>
+__device__ __forceinline__ R key_max(R a, R b) { return a < b ? b : a; }
+
+// Block-wide max of v >= 0 folded into red[0]; the last block turns it into
+// the CFL time step (dt = cfl min(dx,dy) / max), advances t by the step just
+// taken when `advance`, and publishes the next step's dt capped at t_end.
+template <class R>
+__device__ void cfl_finalize(const LrGrid& g, const KC<R>& kc, const LrWorkT<R>& w, R v, bool advance) {
+  using O = RealOps<R>;
+  __shared__ unsigned long long sm[32];
   __shared__ int last;
   int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
-  if ((tid & 31) == 0) sm[tid >> 5] = v;
+  unsigned long long key = Key<R>::enc(v);
+  for (int off = 16; off > 0; off >>= 1) {
+    unsigned long long o = __shfl_xor_sync(0xffffffffu, key, off);
+    key = o > key ? o : key;
+  }
+  if ((tid & 31) == 0) sm[tid >> 5] = key;
   __syncthreads();
   if (tid < 32) {
     int nw = (blockDim.x * blockDim.y) >> 5;
-    double x = tid < nw ? sm[tid] : 0.0;
-    for (int off = 16; off > 0; off >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, off));
+    unsigned long long x = tid < nw ? sm[tid] : 0ull;
+    for (int off = 16; off > 0; off >>= 1) {
+      unsigned long long o = __shfl_xor_sync(0xffffffffu, x, off);
+      x = o > x ? o : x;
+    }
     if (tid == 0) {
-      atomicMax(&w.red[0], (unsigned long long)__double_as_longlong(x));
+      atomicMax(&w.red[0], x);
       __threadfence();
       unsigned long long nb = (unsigned long long)gridDim.x * gridDim.y;
       unsigned long long prev = atomicAdd(&w.red[1], 1ull);
@@ -1070,12 +1177,17 @@ __device__ void cfl_finalize(const LrGrid& g, const LrWork& w, double v, bool ad
   __syncthreads();
   if (last && tid == 0) {
     __threadfence();
-    double mx = __longlong_as_double((long long)atomicAdd(&w.red[0], 0ull));
-    double best = mx > 0.0 ? g.hmin / mx : 1e300;
+    R mx = Key<R>::dec(atomicAdd(&w.red[0], 0ull));
+    double dtc = O::pos(mx) ? O::todouble(kc.cfl * (kc.hmin / mx)) : g.cfl * 1e300;
     double t = w.scal[0];
-    if (advance) { t = t + dt; w.scal[2] = dt; w.scal[4] += 1.0; }
+    if (advance) { t = t + w.scal[5]; w.scal[2] = w.scal[5]; w.scal[4] += 1.0; }
     w.scal[0] = t;
-    w.scal[1] = g.cfl * best;
+    w.scal[1] = dtc;
+    double dn = g.dt_fixed > 0.0 ? g.dt_fixed : dtc;
+    if (w.scal[3] - t < dn) dn = w.scal[3] - t;
+    dn = dn > 0.0 ? dn : 0.0;
+    w.scal[5] = dn;
+    w.dtR[0] = from_double<R>(dn);
     w.red[0] = 0ull;
     w.red[1] = 0ull;
     w.red[2] = 0ull;
@@ -1088,74 +1200,89 @@ __device__ void cfl_finalize(const LrGrid& g, const LrWork& w, double v, bool ad
 // CFL rule for the next step from max over nodes of (max over the node's
 // cells of c_c + |u_p|), which equals the per-cell form
 // min_c min(dx,dy)/(c_c + max_{p in c} |u_p|).
-__global__ void __launch_bounds__(256) lr_node_update(LrGrid g, LrState cur, LrState nxt, LrWork w) {
+template <class R>
+__global__ void __launch_bounds__(256) lr_node_update(LrGrid g, KC<R> kc, LrStateT<R> cur, LrStateT<R> nxt,
+                                                      LrWorkT<R> w) {
+  using O = RealOps<R>;
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
   bool act = i < g.nxu && j < g.nyu;
-  double dt = step_dt(g, w.scal);
-  if (!(dt > 0.0)) {
+  if (!step_live(w.scal)) {
     if (act) { int n = j * (g.nx + 1) + i; nxt.ux[n] = cur.ux[n]; nxt.uy[n] = cur.uy[n]; }
     if (i == 0 && j == 0) w.scal[2] = 0.0;
     return;
   }
-  double val = 0.0;
+  const R Z = O::c(0.0f);
+  R val = Z;
   if (act) {
     int n = j * (g.nx + 1) + i;
-    double ux1, uy1;
+    R ux1, uy1;
     if (g.presc) {
       ux1 = w.pux[n]; uy1 = w.puy[n];
     } else {
       int A = cix(g, i - 1, j - 1).idx, B = cix(g, i, j - 1).idx;
       int C = cix(g, i - 1, j).idx, Dd = cix(g, i, j).idx;
-      double mp = 0.25 * (w.mc[A] + w.mc[B] + w.mc[C] + w.mc[Dd]);
-      double mnew = mp, px = mp * w.ulx[n], py = mp * w.uly[n];
+      R mp = O::c(0.25f) * (w.mc[A] + w.mc[B] + w.mc[C] + w.mc[Dd]);
+      R mnew = mp, px = mp * w.ulx[n], py = mp * w.uly[n];
       int oR = dix(g, i, j), oL = dix(g, i - 1, j), oT = dix(g, i, j), oB = dix(g, i, j - 1);
-      mnew += -w.dX[0][oR] + w.dX[0][oL]; px += -w.dX[1][oR] + w.dX[1][oL]; py += -w.dX[2][oR] + w.dX[2][oL];
-      mnew += -w.dY[0][oT] + w.dY[0][oB]; px += -w.dY[1][oT] + w.dY[1][oB]; py += -w.dY[2][oT] + w.dY[2][oB];
+      mnew += w.dX[0][oL] - w.dX[0][oR]; px += w.dX[1][oL] - w.dX[1][oR]; py += w.dX[2][oL] - w.dX[2][oR];
+      mnew += w.dY[0][oB] - w.dY[0][oT]; px += w.dY[1][oB] - w.dY[1][oT]; py += w.dY[2][oB] - w.dY[2][oT];
       int c0 = dix(g, i, j), c1 = dix(g, i - 1, j - 1), c2 = dix(g, i, j - 1), c3 = dix(g, i - 1, j);
-      mnew += -w.dPP[0][c0] + w.dPP[0][c1] - w.dPM[0][c2] + w.dPM[0][c3];
-      px += -w.dPP[1][c0] + w.dPP[1][c1] - w.dPM[1][c2] + w.dPM[1][c3];
-      py += -w.dPP[2][c0] + w.dPP[2][c1] - w.dPM[2][c2] + w.dPM[2][c3];
-      if (!(mnew > 0.0)) set_err(w, LR_DERR_MASS, n);
-      double im = 1.0 / mnew;
+      mnew += (w.dPP[0][c1] - w.dPP[0][c0]) + (w.dPM[0][c3] - w.dPM[0][c2]);
+      px += (w.dPP[1][c1] - w.dPP[1][c0]) + (w.dPM[1][c3] - w.dPM[1][c2]);
+      py += (w.dPP[2][c1] - w.dPP[2][c0]) + (w.dPM[2][c3] - w.dPM[2][c2]);
+      if (!O::pos(mnew)) set_err(w.err, LR_DERR_MASS, n);
+      R im = O::rcp(mnew);
       ux1 = px * im;
       uy1 = py * im;
-      if (!isfinite(ux1) || !isfinite(uy1)) set_err(w, LR_DERR_NAN, n);
+      if (!O::finite(ux1) || !O::finite(uy1)) set_err(w.err, LR_DERR_NAN, n);
     }
-    if (!g.perx && (i == 0 || i == g.nx)) ux1 = 0.0;
-    if (!g.pery && (j == 0 || j == g.ny)) uy1 = 0.0;
+    if (!g.perx && (i == 0 || i == g.nx)) ux1 = Z;
+    if (!g.pery && (j == 0 || j == g.ny)) uy1 = Z;
     nxt.ux[n] = ux1;
     nxt.uy[n] = uy1;
-    double cm = fmax(fmax(w.cc[cix(g, i - 1, j - 1).idx], w.cc[cix(g, i, j - 1).idx]),
-                     fmax(w.cc[cix(g, i - 1, j).idx], w.cc[cix(g, i, j).idx]));
-    val = cm + sqrt(ux1 * ux1 + uy1 * uy1);
+    R cm = rmax(rmax(w.cc[cix(g, i - 1, j - 1).idx], w.cc[cix(g, i, j - 1).idx]),
+                rmax(w.cc[cix(g, i - 1, j).idx], w.cc[cix(g, i, j).idx]));
+    val = cm + O::sqrt(ux1 * ux1 + uy1 * uy1);
   }
-  cfl_finalize(g, w, val, true, dt);
+  cfl_finalize(g, kc, w, val, true);
 }
 
 // CFL rule from the current state only (after lr_init).
-__global__ void __launch_bounds__(256) lr_cfl_only(LrGrid g, LrState cur, LrWork w) {
+template <class R>
+__global__ void __launch_bounds__(256) lr_cfl_only(LrGrid g, KC<R> kc, LrStateT<R> cur, LrWorkT<R> w) {
+  using O = RealOps<R>;
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-  double val = 0.0;
+  R val = O::c(0.0f);
   if (i < g.nxu && j < g.nyu) {
     int n = j * (g.nx + 1) + i;
-    double ux1 = cur.ux[n], uy1 = cur.uy[n];
-    double cm = fmax(fmax(w.cc[cix(g, i - 1, j - 1).idx], w.cc[cix(g, i, j - 1).idx]),
-                     fmax(w.cc[cix(g, i - 1, j).idx], w.cc[cix(g, i, j).idx]));
-    val = cm + sqrt(ux1 * ux1 + uy1 * uy1);
+    R ux1 = cur.ux[n], uy1 = cur.uy[n];
+    R cm = rmax(rmax(w.cc[cix(g, i - 1, j - 1).idx], w.cc[cix(g, i, j - 1).idx]),
+                rmax(w.cc[cix(g, i - 1, j).idx], w.cc[cix(g, i, j).idx]));
+    val = cm + O::sqrt(ux1 * ux1 + uy1 * uy1);
   }
-  cfl_finalize(g, w, val, false, 0.0);
+  cfl_finalize(g, kc, w, val, false);
 }
 
-// Initial state: the upload placed k, rho and p in the state arrays; drop
-// materials with k <= EPS_K, renormalise, e = (p + pi)/((gamma-1) rho),
-// sound speed; zero wall-normal node velocities.
-template <int M>
-__global__ void __launch_bounds__(256) lr_prepare(LrGrid g, LrState st, LrWork w) {
+// Initial state from the staging area (doubles k, rho, p, ux, uy): drop
+// materials with k <= EPS_K, renormalise, e = (p + pi)/((gamma-1) rho) in
+// double, store in the step's type, sound speed, zero wall-normal velocity.
+template <class R, int M>
+__global__ void __launch_bounds__(256) lr_prepare(LrGrid g, KC<R> kc, LrStateT<R> st, LrWorkT<R> w) {
+  using O = RealOps<R>;
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+  size_t nc = (size_t)g.nx * g.ny, nn = (size_t)(g.nx + 1) * (g.ny + 1);
+  const double* sk = w.stage;
+  const double* sr = w.stage + (size_t)M * nc;
+  const double* sp = w.stage + (size_t)2 * M * nc;
+  const double* sux = w.stage + (size_t)3 * M * nc;
+  const double* suy = sux + nn;
   if (i <= g.nx && j <= g.ny) {
     int n = j * (g.nx + 1) + i;
-    if (!g.perx && (i == 0 || i == g.nx)) st.ux[n] = 0.0;
-    if (!g.pery && (j == 0 || j == g.ny)) st.uy[n] = 0.0;
+    double ux = sux[n], uy = suy[n];
+    if (!g.perx && (i == 0 || i == g.nx)) ux = 0.0;
+    if (!g.pery && (j == 0 || j == g.ny)) uy = 0.0;
+    st.ux[n] = from_double<R>(ux);
+    st.uy[n] = from_double<R>(uy);
   }
   if (i >= g.nx || j >= g.ny) return;
   int c = j * g.nx + i;
@@ -1163,105 +1290,237 @@ __global__ void __launch_bounds__(256) lr_prepare(LrGrid g, LrState st, LrWork w
   bool bad = false;
 #pragma unroll
   for (int a = 0; a < M; ++a) {
-    double ka = st.k[a][c];
+    double ka = sk[a * nc + c];
     if (!(ka >= -1e-12 && ka <= 1.0 + 1e-12)) bad = true;
     sum += ka;
     if (ka > EPS_K) kept += ka;
   }
   if (!(fabs(sum - 1.0) <= 1e-9)) bad = true;
-  double cmax = 0.0;
+  R cmax = O::c(0.0f);
 #pragma unroll
   for (int a = 0; a < M; ++a) {
-    double ka = st.k[a][c];
+    double ka = sk[a * nc + c];
     if (ka > EPS_K && !bad) {
-      double ra = st.r[a][c], pa = st.e[a][c];
+      double ra = sr[a * nc + c], pa = sp[a * nc + c];
       if (!(ra > 0.0)) bad = true;
       double kn = ka / kept;
       double ea = (pa + g.pin[a]) / ((g.gam[a] - 1.0) * ra);
-      st.k[a][c] = kn; st.e[a][c] = ea;
-      double p2 = eos_p(g.gam[a], g.pin[a], ra, ea);
-      double c2 = eos_c2(g.gam[a], g.pin[a], ra, p2);
-      double wgt = kn / EPS_C < 1.0 ? kn / EPS_C : 1.0;
-      double ca = sqrt(c2 > 0.0 ? c2 : 0.0);
-      if (wgt * ca > cmax) cmax = wgt * ca;
+      R kR = from_double<R>(kn), rR = from_double<R>(ra), eR = from_double<R>(ea);
+      st.k[a][c] = kR; st.r[a][c] = rR; st.e[a][c] = eR;
+      R p2 = eos_p(kc.gm1[a], kc.pin[a], rR, eR);
+      R c2 = (kc.gam[a] * p2 + kc.pin[a]) / rR;
+      R wk = kR * kc.invEpsC;
+      R wgt = wk < O::c(1.0f) ? wk : O::c(1.0f);
+      R ca = O::pos(c2) ? O::sqrt(c2) : O::c(0.0f);
+      R wc = wgt * ca;
+      if (cmax < wc) cmax = wc;
     } else {
-      st.k[a][c] = 0.0; st.r[a][c] = 0.0; st.e[a][c] = 0.0;
+      st.k[a][c] = O::c(0.0f); st.r[a][c] = O::c(0.0f); st.e[a][c] = O::c(0.0f);
     }
   }
-  if (bad) set_err(w, LR_DERR_MASS, c);
+  if (bad) set_err(w.err, LR_DERR_MASS, c);
   w.cc[c] = cmax;
 }
 
-__global__ void lr_set_scalar_k(double* p, double v) { *p = v; }
+// t_end of this call and the dt of the next step (one thread).
+template <class R>
+__global__ void lr_set_tend_k(LrGrid g, LrWorkT<R> w, double t_end) {
+  w.scal[3] = t_end;
+  double t = w.scal[0];
+  double dn = g.dt_fixed > 0.0 ? g.dt_fixed : w.scal[1];
+  if (t_end - t < dn) dn = t_end - t;
+  dn = dn > 0.0 ? dn : 0.0;
+  w.scal[5] = dn;
+  w.dtR[0] = from_double<R>(dn);
+}
 __global__ void lr_reset_k(LrWork w) {
   w.red[0] = 0ull; w.red[1] = 0ull; w.red[2] = 0ull; w.err[0] = 0; w.err[1] = -1;
-  w.scal[0] = 0.0; w.scal[1] = 0.0; w.scal[2] = 0.0; w.scal[3] = 0.0; w.scal[4] = 0.0;
+  for (int q = 0; q < 8; ++q) w.scal[q] = 0.0;
 }
 
+// Field views (to double, with the boundary mapping for canonical storage).
+template <class R>
+__global__ void lr_view_k(LrGrid g, const R* src, double* dst, size_t n, int kind) {
+  using O = RealOps<R>;
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (kind == 0) {
+    if (t < n) dst[t] = O::todouble(src[t]);
+    return;
+  }
+  int nx = g.nx, ny = g.ny;
+  if (kind == 1) {  // nodes
+    if (t >= (size_t)(nx + 1) * (ny + 1)) return;
+    int i = (int)(t % (nx + 1)), j = (int)(t / (nx + 1));
+    int mi = g.perx ? i % nx : i, mj = g.pery ? j % ny : j;
+    dst[t] = O::todouble(src[mj * (nx + 1) + mi]);
+  } else if (kind == 2) {  // X faces
+    if (t >= (size_t)(nx + 1) * ny) return;
+    int i = (int)(t % (nx + 1)), j = (int)(t / (nx + 1));
+    int mi = g.perx ? i % nx : i;
+    dst[t] = O::todouble(src[j * (nx + 1) + mi]);
+  } else {  // Y faces
+    if (t >= (size_t)nx * (ny + 1)) return;
+    int i = (int)(t % nx), j = (int)(t / nx);
+    int mj = g.pery ? j % ny : j;
+    dst[t] = O::todouble(src[mj * nx + i]);
+  }
+}
+// Mixture fields in double from the state: P = sum k P_a, rho = sum k rho_a,
+// e = sum(k rho e)/rho.
+template <class R>
+__global__ void lr_mixture_k(LrGrid g, LrStateT<R> s, double* out, int which) {
+  using O = RealOps<R>;
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.nx * g.ny) return;
+  double P = 0.0, Rm = 0.0, me = 0.0;
+  for (int a = 0; a < g.M; ++a) {
+    double ka = O::todouble(s.k[a][c]);
+    if (!(ka > 0.0)) continue;
+    double ra = O::todouble(s.r[a][c]), ea = O::todouble(s.e[a][c]);
+    P += ka * ((g.gam[a] - 1.0) * ra * ea - g.pin[a]);
+    Rm += ka * ra;
+    me += ka * ra * ea;
+  }
+  out[c] = which == 0 ? P : which == 1 ? Rm : me / Rm;
+}
+// Conservation sums in double: one thread per row (fixed order), then the
+// rows in order by one thread.
+template <class R>
+__global__ void lr_cons_rows(LrGrid g, LrStateT<R> s, double* rows) {
+  using O = RealOps<R>;
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  int nyu = g.pery ? g.ny : g.ny + 1, nxu = g.perx ? g.nx : g.nx + 1;
+  if (j >= nyu) return;
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (j < g.ny)
+    for (int i = 0; i < g.nx; ++i) {
+      int c = j * g.nx + i;
+      for (int a = 0; a < g.M; ++a) {
+        double m = O::todouble(s.r[a][c]) * O::todouble(s.k[a][c]) * g.V;
+        acc[a] += m; acc[3] += m; acc[6] += m * O::todouble(s.e[a][c]);
+      }
+    }
+  for (int i = 0; i < nxu; ++i) {
+    double mp = 0.0;
+    for (int b = -1; b <= 0; ++b)
+      for (int a2 = -1; a2 <= 0; ++a2) {
+        int f1, f2;
+        int ci = map_cell(i + a2, g.nx, g.perx, f1), cj = map_cell(j + b, g.ny, g.pery, f2);
+        int c = cj * g.nx + ci;
+        for (int a = 0; a < g.M; ++a) mp += 0.25 * O::todouble(s.r[a][c]) * O::todouble(s.k[a][c]) * g.V;
+      }
+    double wgt = 1.0;
+    if (!g.perx && (i == 0 || i == g.nx)) wgt *= 0.5;
+    if (!g.pery && (j == 0 || j == g.ny)) wgt *= 0.5;
+    int n = j * (g.nx + 1) + i;
+    double u = O::todouble(s.ux[n]), v = O::todouble(s.uy[n]);
+    acc[4] += wgt * mp * u; acc[5] += wgt * mp * v;
+    acc[7] += 0.5 * wgt * mp * (u * u + v * v);
+  }
+  for (int q = 0; q < 8; ++q) rows[8 * j + q] = acc[q];
+}
+__global__ void lr_cons_sum(const double* rows, int nrows, double* out) {
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int j = 0; j < nrows; ++j)
+    for (int q = 0; q < 8; ++q) acc[q] += rows[8 * j + q];
+  for (int q = 0; q < 7; ++q) out[q] = acc[q];
+  out[7] = acc[6] + acc[7];
+}
 // Debug view of the last step's corner fluxes: |dx dy| and total mass.
-template <int M>
-__global__ void lr_corner_dbg(LrGrid g, LrWork w, double* fc, double* mcn) {
+template <class R>
+__global__ void lr_corner_dbg(LrGrid g, LrWorkT<R> w, double* fc, double* mcn) {
+  using O = RealOps<R>;
   int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
   if (i > g.nx || j > g.ny) return;
   int o = j * (g.nx + 1) + i;
   int n = nix(g, i, j).idx;
-  double ddx = w.ddx[n], ddy = w.ddy[n];
-  if (fc) fc[o] = fabs(ddx * ddy);
+  if (fc) fc[o] = fabs(O::todouble(w.ddx[n]) * O::todouble(w.ddy[n]));
   if (mcn) {
     double m = 0.0;
-#pragma unroll
-    for (int a = 0; a < M; ++a) m += w.cMm[a][n];
+    for (int a = 0; a < g.M; ++a) m += O::todouble(w.cMm[a][n]);
     mcn[o] = m;
   }
+}
+// Interface lines of the last step, masked to the cells that were mixed
+// (the pre-step state is still in the other half of the double buffer).
+template <class R>
+__global__ void lr_cuts_k(LrGrid g, LrStateT<R> prev, LrWork w, double* dst) {
+  using O = RealOps<R>;
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= g.nx * g.ny) return;
+  int np = 0;
+  for (int a = 0; a < g.M; ++a) np += O::pos(prev.k[a][c]) ? 1 : 0;
+  size_t nc = (size_t)g.nx * g.ny;
+  for (int z = 0; z < 6; ++z) dst[z * nc + c] = (np >= 2 + z / 3) ? w.cut[z][c] : 0.0;
+}
+
+template <class R>
+__global__ void lr_from_double_k(const double* src, R* dst, size_t n) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) dst[t] = from_double<R>(src[t]);
 }
 
 inline dim3 grid_for(int nxr, int nyr) { return dim3((nxr + BX - 1) / BX, (nyr + BY - 1) / BY); }
 
-}  // namespace
-
-#define LR_DISPATCH_M(KERNEL, GRID, ...)                                        \
-  do {                                                                          \
-    if (g.M == 1) KERNEL<1><<<GRID, dim3(BX, BY), 0, s>>>(__VA_ARGS__);         \
-    else if (g.M == 2) KERNEL<2><<<GRID, dim3(BX, BY), 0, s>>>(__VA_ARGS__);    \
-    else KERNEL<3><<<GRID, dim3(BX, BY), 0, s>>>(__VA_ARGS__);                  \
+template <class R>
+cudaError_t launch_t(int kid, const LrGrid& g, const LrState& cur0, const LrState& nxt0, const LrWork& w0,
+                     cudaStream_t s) {
+  KC<R> kc = make_kc<R>(g);
+  LrStateT<R> cur = typed<R>(cur0), nxt = typed<R>(nxt0);
+  LrWorkT<R> w = typed<R>(w0);
+  dim3 b(BX, BY);
+#define LR_M(K, GRID, ...)                                                   \
+  do {                                                                       \
+    if (g.M == 1) K<R, 1><<<GRID, b, 0, s>>>(__VA_ARGS__);                   \
+    else if (g.M == 2) K<R, 2><<<GRID, b, 0, s>>>(__VA_ARGS__);              \
+    else K<R, 3><<<GRID, b, 0, s>>>(__VA_ARGS__);                            \
   } while (0)
-
-cudaError_t lr_launch(int kid, const LrGrid& g, const LrState& cur, const LrState& nxt,
-                      const LrWork& w, cudaStream_t s) {
   switch (kid) {
-    case LRK_CELL_PRE: LR_DISPATCH_M(lr_cell_pre, grid_for(g.nx, g.ny), g, cur, w); break;
-    case LRK_NODE_HALF: lr_node_half<<<grid_for(g.nxu, g.nyu), dim3(BX, BY), 0, s>>>(g, cur, w); break;
-    case LRK_CELL_LAG: LR_DISPATCH_M(lr_cell_lag, grid_for(g.nxu, g.nyu), g, cur, w); break;
-    case LRK_CELL_CF: LR_DISPATCH_M(lr_cell_cf, grid_for(g.nx, g.ny), g, cur, w); break;
+    case LRK_CELL_PRE: LR_M(lr_cell_pre, grid_for(g.nx, g.ny), g, kc, cur, w); break;
+    case LRK_NODE_HALF: lr_node_half<R><<<grid_for(g.nxu, g.nyu), b, 0, s>>>(g, kc, cur, w); break;
+    case LRK_CELL_LAG: LR_M(lr_cell_lag, grid_for(g.nxu, g.nyu), g, kc, cur, w); break;
+    case LRK_CELL_CF: LR_M(lr_cell_cf, grid_for(g.nx, g.ny), g, kc, cur, w); break;
     case LRK_MIXED: {
+      if (g.M == 1) break;  // one material: no interfaces
       int nb = (g.nx * g.ny + 127) / 128;
       if (nb > 152 * 8) nb = 152 * 8;
-      if (g.M == 1) break;  // one material: no interfaces
-      if (g.M == 2) lr_mixed<2><<<nb, 128, 0, s>>>(g, cur, w);
-      else lr_mixed<3><<<nb, 128, 0, s>>>(g, cur, w);
+      if (g.M == 2) lr_mixed<R, 2><<<nb, 128, 0, s>>>(g, cur, w);
+      else lr_mixed<R, 3><<<nb, 128, 0, s>>>(g, cur, w);
       break;
     }
-    case LRK_MAT_FLUX: LR_DISPATCH_M(lr_mat_flux, grid_for(g.nxu, g.nyu), g, cur, w); break;
-    case LRK_CELL_UPDATE: LR_DISPATCH_M(lr_cell_update, grid_for(g.nx, g.ny), g, cur, nxt, w); break;
-    case LRK_DUAL_FLUX: lr_dual_flux<<<grid_for(g.nx + 2, g.ny + 2), dim3(BX, BY), 0, s>>>(g, w); break;
-    case LRK_NODE_UPDATE: lr_node_update<<<grid_for(g.nxu, g.nyu), dim3(BX, BY), 0, s>>>(g, cur, nxt, w); break;
+    case LRK_MAT_FLUX: LR_M(lr_mat_flux, grid_for(g.nxu, g.nyu), g, kc, cur, w); break;
+    case LRK_CELL_UPDATE: LR_M(lr_cell_update, grid_for(g.nx, g.ny), g, kc, cur, nxt, w); break;
+    case LRK_DUAL_FLUX: lr_dual_flux<R><<<grid_for(g.nx + 2, g.ny + 2), b, 0, s>>>(g, kc, w); break;
+    case LRK_NODE_UPDATE: lr_node_update<R><<<grid_for(g.nxu, g.nyu), b, 0, s>>>(g, kc, cur, nxt, w); break;
+    case 100: LR_M(lr_prepare, grid_for(g.nx + 1, g.ny + 1), g, kc, cur, w);
+              lr_cfl_only<R><<<grid_for(g.nxu, g.nyu), b, 0, s>>>(g, kc, cur, w); break;
     default: return cudaErrorInvalidValue;
   }
+#undef LR_M
   return cudaGetLastError();
 }
 
-cudaError_t lr_launch_init_cfl(const LrGrid& g, const LrState& cur, const LrWork& w, cudaStream_t s) {
-  lr_cfl_only<<<grid_for(g.nxu, g.nyu), dim3(BX, BY), 0, s>>>(g, cur, w);
-  return cudaGetLastError();
+}  // namespace
+
+size_t lr_real_size(int mode) { return mode == LR_MODE_FP32 ? sizeof(float) : mode == LR_MODE_DF64 ? sizeof(df64) : sizeof(double); }
+
+#define LR_BY_MODE(CALL_D, CALL_F, CALL_DF) \
+  (g.mode == LR_MODE_FP32 ? (CALL_F) : g.mode == LR_MODE_DF64 ? (CALL_DF) : (CALL_D))
+
+cudaError_t lr_launch(int kid, const LrGrid& g, const LrState& cur, const LrState& nxt, const LrWork& w,
+                      cudaStream_t s) {
+  return LR_BY_MODE(launch_t<double>(kid, g, cur, nxt, w, s), launch_t<float>(kid, g, cur, nxt, w, s),
+                    launch_t<df64>(kid, g, cur, nxt, w, s));
 }
 
-cudaError_t lr_launch_prepare_init(const LrGrid& g, const LrState& st, const LrWork& w, cudaStream_t s) {
-  LR_DISPATCH_M(lr_prepare, grid_for(g.nx + 1, g.ny + 1), g, st, w);
-  return cudaGetLastError();
+cudaError_t lr_launch_init(const LrGrid& g, const LrState& st, const LrWork& w, cudaStream_t s) {
+  return lr_launch(100, g, st, st, w, s);
 }
 
-cudaError_t lr_launch_set_scalar(double* p, double v, cudaStream_t s) {
-  lr_set_scalar_k<<<1, 1, 0, s>>>(p, v);
+cudaError_t lr_launch_set_tend(const LrGrid& g, const LrWork& w, double t_end, cudaStream_t s) {
+  if (g.mode == LR_MODE_FP32) lr_set_tend_k<float><<<1, 1, 0, s>>>(g, typed<float>(w), t_end);
+  else if (g.mode == LR_MODE_DF64) lr_set_tend_k<df64><<<1, 1, 0, s>>>(g, typed<df64>(w), t_end);
+  else lr_set_tend_k<double><<<1, 1, 0, s>>>(g, typed<double>(w), t_end);
   return cudaGetLastError();
 }
 
@@ -1270,8 +1529,55 @@ cudaError_t lr_launch_reset(const LrWork& w, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t lr_launch_view(const LrGrid& g, const void* src, double* dst, size_t n, int kind, cudaStream_t s) {
+  size_t tot = kind == 0 ? n : kind == 1 ? (size_t)(g.nx + 1) * (g.ny + 1)
+             : kind == 2 ? (size_t)(g.nx + 1) * g.ny : (size_t)g.nx * (g.ny + 1);
+  unsigned nb = (unsigned)((tot + 255) / 256);
+  if (g.mode == LR_MODE_FP32) lr_view_k<float><<<nb, 256, 0, s>>>(g, static_cast<const float*>(src), dst, n, kind);
+  else if (g.mode == LR_MODE_DF64) lr_view_k<df64><<<nb, 256, 0, s>>>(g, static_cast<const df64*>(src), dst, n, kind);
+  else lr_view_k<double><<<nb, 256, 0, s>>>(g, static_cast<const double*>(src), dst, n, kind);
+  return cudaGetLastError();
+}
+
+cudaError_t lr_launch_mixture(const LrGrid& g, const LrState& st, double* dst, int which, cudaStream_t s) {
+  unsigned nb = (unsigned)((g.nx * g.ny + 255) / 256);
+  if (g.mode == LR_MODE_FP32) lr_mixture_k<float><<<nb, 256, 0, s>>>(g, typed<float>(st), dst, which);
+  else if (g.mode == LR_MODE_DF64) lr_mixture_k<df64><<<nb, 256, 0, s>>>(g, typed<df64>(st), dst, which);
+  else lr_mixture_k<double><<<nb, 256, 0, s>>>(g, typed<double>(st), dst, which);
+  return cudaGetLastError();
+}
+
+cudaError_t lr_launch_cons(const LrGrid& g, const LrState& st, double* rows, double* dst, cudaStream_t s) {
+  int nrows = g.pery ? g.ny : g.ny + 1;
+  unsigned nb = (unsigned)((nrows + 63) / 64);
+  if (g.mode == LR_MODE_FP32) lr_cons_rows<float><<<nb, 64, 0, s>>>(g, typed<float>(st), rows);
+  else if (g.mode == LR_MODE_DF64) lr_cons_rows<df64><<<nb, 64, 0, s>>>(g, typed<df64>(st), rows);
+  else lr_cons_rows<double><<<nb, 64, 0, s>>>(g, typed<double>(st), rows);
+  lr_cons_sum<<<1, 1, 0, s>>>(rows, nrows, dst);
+  return cudaGetLastError();
+}
+
 cudaError_t lr_launch_corner_debug(const LrGrid& g, const LrWork& w, double* fc_out, double* mc_out,
                                    cudaStream_t s) {
-  LR_DISPATCH_M(lr_corner_dbg, grid_for(g.nx + 1, g.ny + 1), g, w, fc_out, mc_out);
+  dim3 gr = grid_for(g.nx + 1, g.ny + 1), b(BX, BY);
+  if (g.mode == LR_MODE_FP32) lr_corner_dbg<float><<<gr, b, 0, s>>>(g, typed<float>(w), fc_out, mc_out);
+  else if (g.mode == LR_MODE_DF64) lr_corner_dbg<df64><<<gr, b, 0, s>>>(g, typed<df64>(w), fc_out, mc_out);
+  else lr_corner_dbg<double><<<gr, b, 0, s>>>(g, typed<double>(w), fc_out, mc_out);
+  return cudaGetLastError();
+}
+
+cudaError_t lr_launch_cuts(const LrGrid& g, const LrState& prev, const LrWork& w, double* dst, cudaStream_t s) {
+  unsigned nb = (unsigned)((g.nx * g.ny + 255) / 256);
+  if (g.mode == LR_MODE_FP32) lr_cuts_k<float><<<nb, 256, 0, s>>>(g, typed<float>(prev), w, dst);
+  else if (g.mode == LR_MODE_DF64) lr_cuts_k<df64><<<nb, 256, 0, s>>>(g, typed<df64>(prev), w, dst);
+  else lr_cuts_k<double><<<nb, 256, 0, s>>>(g, typed<double>(prev), w, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t lr_launch_from_double(const LrGrid& g, const double* src, void* dst, size_t n, cudaStream_t s) {
+  unsigned nb = (unsigned)((n + 255) / 256);
+  if (g.mode == LR_MODE_FP32) lr_from_double_k<float><<<nb, 256, 0, s>>>(src, static_cast<float*>(dst), n);
+  else if (g.mode == LR_MODE_DF64) lr_from_double_k<df64><<<nb, 256, 0, s>>>(src, static_cast<df64*>(dst), n);
+  else lr_from_double_k<double><<<nb, 256, 0, s>>>(src, static_cast<double*>(dst), n);
   return cudaGetLastError();
 }

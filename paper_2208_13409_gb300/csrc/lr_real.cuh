@@ -1,0 +1,147 @@
+// lr_real.cuh -- arithmetic types of the step kernels.
+//
+// GB300 executes FP64 at 1/64 of its FP32 rate (304 DFMA against 19456 FFMA
+// lanes per clock), so besides native double the kernels can run on a
+// double-float type: a value is the unevaluated sum hi + lo of two floats
+// with |lo| <= ulp(hi)/2, about 48 significand bits, carried entirely by the
+// FP32 pipe.  The error-free transformations are the classical ones:
+//   two-sum (Knuth, TAOCP vol. 2, 4.2.2): s = a+b, e = (a-(s-bb)) + (b-bb);
+//   fast two-sum (Dekker 1971) when |a| >= |b|: s = a+b, e = b-(s-a);
+//   two-product with a fused multiply-add: p = a*b, e = fma(a, b, -p);
+// and the double-length operations built from them follow Dekker 1971 and
+// the double-double algorithms of Hida, Li and Bailey (2001), here on floats.
+// Every rounding step uses __fadd_rn/__fmul_rn/__fmaf_rn so the compiler
+// cannot contract or reorder them.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+struct __align__(8) df64 {
+  float hi, lo;
+  __host__ __device__ df64() {}
+  __host__ __device__ constexpr df64(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ explicit df64(float h) : hi(h), lo(0.0f) {}
+};
+
+namespace dfops {
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+__device__ __forceinline__ df64 add(df64 x, df64 y) {
+  float s, e;
+  two_sum(x.hi, y.hi, s, e);
+  e = __fadd_rn(e, __fadd_rn(x.lo, y.lo));
+  df64 r;
+  fast_two_sum(s, e, r.hi, r.lo);
+  return r;
+}
+__device__ __forceinline__ df64 neg(df64 x) { return df64(-x.hi, -x.lo); }
+__device__ __forceinline__ df64 mul(df64 x, df64 y) {
+  float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  df64 r;
+  fast_two_sum(p, e, r.hi, r.lo);
+  return r;
+}
+// x / y: three quotient digits from an approximate reciprocal of y.hi, each
+// removing the remainder of the previous ones (long division in base 2^24).
+__device__ __forceinline__ df64 div(df64 x, df64 y) {
+  float r0 = __frcp_rn(y.hi);
+  float q1 = __fmul_rn(x.hi, r0);
+  df64 rem = add(x, neg(mul(y, df64(q1))));
+  float q2 = __fmul_rn(rem.hi, r0);
+  rem = add(rem, neg(mul(y, df64(q2))));
+  float q3 = __fmul_rn(rem.hi, r0);
+  df64 q;
+  fast_two_sum(q1, q2, q.hi, q.lo);
+  return add(q, df64(q3));
+}
+// sqrt(x): float square root, then one Newton correction in double length:
+// s' = s + (x - s^2) / (2 s).
+__device__ __forceinline__ df64 sqrt_(df64 x) {
+  if (!(x.hi > 0.0f)) return df64(0.0f, 0.0f);
+  float s = __fsqrt_rn(x.hi);
+  df64 ss = mul(df64(s), df64(s));
+  df64 d = add(x, neg(ss));
+  float c = __fmul_rn(d.hi, __frcp_rn(__fmul_rn(2.0f, s)));
+  df64 r;
+  fast_two_sum(s, c, r.hi, r.lo);
+  return r;
+}
+
+}  // namespace dfops
+
+__device__ __forceinline__ df64 operator+(df64 a, df64 b) { return dfops::add(a, b); }
+__device__ __forceinline__ df64 operator-(df64 a, df64 b) { return dfops::add(a, dfops::neg(b)); }
+__device__ __forceinline__ df64 operator-(df64 a) { return dfops::neg(a); }
+__device__ __forceinline__ df64 operator*(df64 a, df64 b) { return dfops::mul(a, b); }
+__device__ __forceinline__ df64 operator/(df64 a, df64 b) { return dfops::div(a, b); }
+__device__ __forceinline__ df64& operator+=(df64& a, df64 b) { a = a + b; return a; }
+__device__ __forceinline__ df64& operator-=(df64& a, df64 b) { a = a - b; return a; }
+__device__ __forceinline__ df64& operator*=(df64& a, df64 b) { a = a * b; return a; }
+// Comparisons of normalised pairs: hi decides unless the his are equal.
+__device__ __forceinline__ bool operator<(df64 a, df64 b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+__device__ __forceinline__ bool operator>(df64 a, df64 b) { return b < a; }
+__device__ __forceinline__ bool operator<=(df64 a, df64 b) { return !(b < a); }
+__device__ __forceinline__ bool operator>=(df64 a, df64 b) { return !(a < b); }
+__device__ __forceinline__ bool operator==(df64 a, df64 b) { return a.hi == b.hi && a.lo == b.lo; }
+__device__ __forceinline__ bool operator!=(df64 a, df64 b) { return !(a == b); }
+
+// ---- uniform helpers over double, float and df64
+template <class R> struct RealOps;
+template <> struct RealOps<double> {
+  __device__ static __forceinline__ double c(float v) { return (double)v; }
+  __device__ static __forceinline__ double abs(double x) { return fabs(x); }
+  __device__ static __forceinline__ double sqrt(double x) { return ::sqrt(x); }
+  __device__ static __forceinline__ double rcp(double x) { return 1.0 / x; }
+  __device__ static __forceinline__ bool finite(double x) { return isfinite(x); }
+  __device__ static __forceinline__ bool pos(double x) { return x > 0.0; }
+  __device__ static __forceinline__ bool neg(double x) { return x < 0.0; }
+  __device__ static __forceinline__ bool zero(double x) { return x == 0.0; }
+  __host__ __device__ static __forceinline__ double todouble(double x) { return x; }
+};
+template <> struct RealOps<float> {
+  __device__ static __forceinline__ float c(float v) { return v; }
+  __device__ static __forceinline__ float abs(float x) { return fabsf(x); }
+  __device__ static __forceinline__ float sqrt(float x) { return sqrtf(x); }
+  __device__ static __forceinline__ float rcp(float x) { return 1.0f / x; }
+  __device__ static __forceinline__ bool finite(float x) { return isfinite(x); }
+  __device__ static __forceinline__ bool pos(float x) { return x > 0.0f; }
+  __device__ static __forceinline__ bool neg(float x) { return x < 0.0f; }
+  __device__ static __forceinline__ bool zero(float x) { return x == 0.0f; }
+  __host__ __device__ static __forceinline__ double todouble(float x) { return (double)x; }
+};
+template <> struct RealOps<df64> {
+  __device__ static __forceinline__ df64 c(float v) { return df64(v, 0.0f); }
+  __device__ static __forceinline__ df64 abs(df64 x) { return x.hi < 0.0f ? dfops::neg(x) : x; }
+  __device__ static __forceinline__ df64 sqrt(df64 x) { return dfops::sqrt_(x); }
+  __device__ static __forceinline__ df64 rcp(df64 x) { return dfops::div(df64(1.0f, 0.0f), x); }
+  __device__ static __forceinline__ bool finite(df64 x) { return isfinite(x.hi) && isfinite(x.lo); }
+  __device__ static __forceinline__ bool pos(df64 x) { return x.hi > 0.0f; }
+  __device__ static __forceinline__ bool neg(df64 x) { return x.hi < 0.0f; }
+  __device__ static __forceinline__ bool zero(df64 x) { return x.hi == 0.0f; }
+  __host__ __device__ static __forceinline__ double todouble(df64 x) { return (double)x.hi + (double)x.lo; }
+};
+
+// Conversions from double (host: exact splitting, used for constants and at
+// the API boundary).
+template <class R> __host__ __device__ inline R from_double(double v);
+template <> __host__ __device__ inline double from_double<double>(double v) { return v; }
+template <> __host__ __device__ inline float from_double<float>(double v) { return (float)v; }
+template <> __host__ __device__ inline df64 from_double<df64>(double v) {
+  float h = (float)v;
+  float l = (float)(v - (double)h);
+  return df64(h, l);
+}
+
+template <class R> __device__ __forceinline__ R rmin(R a, R b) { return b < a ? b : a; }
+template <class R> __device__ __forceinline__ R rmax(R a, R b) { return a < b ? b : a; }

@@ -22,7 +22,7 @@ HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))
 OK, ERR_ARG, ERR_OOM, ERR_NUMERIC, ERR_TIMEOUT, ERR_STATE, ERR_CUDA = 0, -1, -2, -3, -4, -5, -6
 BC_REFLECT, BC_PERIODIC = 0, 1
 CORNER_UPWIND, CORNER_DIAG = 0, 1
-FP64 = 0
+FP64, DF64, FP32 = 0, 1, 2
 F_K, F_RHO_MAT, F_E_MAT, F_P, F_RHO, F_E, F_UX, F_UY, F_CONS, F_C = range(10)
 F_UHX, F_UHY, F_VOL_LAGCF, F_E_LAG, F_FX, F_FY, F_FC, F_MX, F_MY, F_MC, F_Q, F_DT = range(20, 32)
 F_CUTS, F_XA, F_YA, F_CA = range(32, 36)
@@ -117,7 +117,7 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(_dp)
 
 
-def make_config(problem, stream: Optional[int] = None) -> Config:
+def make_config(problem, stream: Optional[int] = None, precision: int = FP64) -> Config:
     c = Config()
     load().lr_config_default(ctypes.byref(c))
     c.nx, c.ny = problem.nx, problem.ny
@@ -126,7 +126,7 @@ def make_config(problem, stream: Optional[int] = None) -> Config:
     c.cfl, c.a1, c.a2 = problem.cfl, problem.a1, problem.a2
     for q in range(4):
         c.bc[q] = problem.bc[q]
-    c.precision = FP64
+    c.precision = precision
     c.face_order = problem.face_order
     c.corner_recon = problem.corner_recon
     c.dt_fixed = problem.dt_fixed
@@ -137,7 +137,7 @@ def make_config(problem, stream: Optional[int] = None) -> Config:
 class Sim:
     """One simulation on the GPU behind the C ABI."""
 
-    def __init__(self, problem, use_torch: bool = True):
+    def __init__(self, problem, use_torch: bool = True, precision: int = FP64):
         L = load()
         self.p = problem
         self._arena = None
@@ -152,7 +152,8 @@ class Sim:
             # recorded on it; the legacy default stream gets a private one
             self.stream = cs if cs.cuda_stream != 0 else torch.cuda.Stream()
             stream = self.stream.cuda_stream
-        self.cfg = make_config(problem, stream)
+        self.cfg = make_config(problem, stream, precision)
+        self.precision = precision
         h = ctypes.c_void_p()
         if use_torch:
             import torch

@@ -19,8 +19,8 @@ TOL_1 = 1e-11
 TOL_100 = 1e-9
 
 
-def _pair(pr):
-    return lr.Sim(pr), oracle.Oracle(pr)
+def _pair(pr, precision=lr.FP64):
+    return lr.Sim(pr, precision=precision), oracle.Oracle(pr)
 
 
 def _steps(sim, orc, n, t_end=1e300):
@@ -54,10 +54,14 @@ CASES_1 = {
 }
 
 
+PRECISIONS = {"fp64": lr.FP64, "df64": lr.DF64}
+
+
+@pytest.mark.parametrize("prec", sorted(PRECISIONS))
 @pytest.mark.parametrize("name", sorted(CASES_1))
-def test_parity_one_and_five_steps(name):
+def test_parity_one_and_five_steps(name, prec):
     pr = CASES_1[name]()
-    sim, orc = _pair(pr)
+    sim, orc = _pair(pr, PRECISIONS[prec])
     # init: e from p through the EOS; stiffened-gas p = (g-1) rho e - pi
     # cancels (pi = 2.6e9 against p = 1e5), so allow a few ulps of pi
     _assert_close(compare(sim, orc), 1e-13, f"{name} init")
@@ -82,14 +86,15 @@ def test_intermediates_after_one_step():
     _assert_close(res, TOL_1, "intermediates")
 
 
+@pytest.mark.parametrize("prec", sorted(PRECISIONS))
 @pytest.mark.parametrize("name,make", [
     ("sod_256x4", lambda: P.sod()),
     ("triple_point_140x60", lambda: P.triple_point(140, 60)),
     ("shock_bubble_256x64", lambda: P.shock_bubble(256, 64)),
 ])
-def test_parity_100_steps_l1(name, make):
+def test_parity_100_steps_l1(name, make, prec):
     pr = make()
-    sim, orc = _pair(pr)
+    sim, orc = _pair(pr, PRECISIONS[prec])
     for _ in range(100):
         sim.step(pr.t_end, sync=False)
         orc.step(pr.t_end)
@@ -143,11 +148,12 @@ def test_prescribed_one_node_displacement():
     _assert_close(compare(sim, orc), TOL_1, "prescribed")
 
 
-def test_full_size_one_step_triple_point():
+@pytest.mark.parametrize("prec", sorted(PRECISIONS))
+def test_full_size_one_step_triple_point(prec):
     """The bench workload (1400 x 600, three materials) after warm-up steps:
     every field against the oracle."""
     pr = P.triple_point()
-    sim, orc = _pair(pr)
+    sim, orc = _pair(pr, PRECISIONS[prec])
     _steps(sim, orc, 3)
     _assert_close(compare(sim, orc), TOL_1, "triple point 1400x600")
 
