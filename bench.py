@@ -358,8 +358,10 @@ def run_lr(args, world, rank, local):
             s2.close()
 
     cpu = None
+    accuracy = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_baseline_steps)
+        accuracy = sod_accuracy()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
                 "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
@@ -378,11 +380,44 @@ def run_lr(args, world, rank, local):
                 "clocks": clocks, "wall_s": wall}
         if modes:
             line["modes"] = modes
+        if accuracy:
+            line["sod_l1_t0.2"] = accuracy
         if cpu:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def sod_accuracy():
+    """Per-field L1 error of each arithmetic mode on the Sod tube at t = 0.2:
+    against the exact Riemann solution and against the FP64 oracle."""
+    import numpy as np
+    import oracle
+    from paper_2208_13409_gb300 import lr, problems as P
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import riemann_exact
+
+    pr = P.sod()
+    xc = (np.arange(pr.nx) + 0.5) / pr.nx
+    ex = np.array([riemann_exact.sample((x - 0.5) / 0.2, 1.0, 0.0, 1.0, 0.125, 0.0, 0.1, 1.4) for x in xc])
+
+    def fields(get):
+        ux = get(lr.F_UX)[1]
+        return {"rho": get(lr.F_RHO)[1], "u": 0.5 * (ux[:-1] + ux[1:]), "p": get(lr.F_P)[1]}
+
+    o = oracle.Oracle(pr)
+    o.run(10000, pr.t_end)
+    fo = fields(o.get)
+    out = {"oracle_vs_exact": {k: float(np.mean(np.abs(v - ex[:, q]))) for q, (k, v) in enumerate(fo.items())}}
+    for name, mode in MODES.items():
+        s = lr.Sim(pr, precision=mode)
+        s.run(10000, pr.t_end)
+        fs = fields(s.get)
+        out[name] = {"vs_exact": {k: float(np.mean(np.abs(v - ex[:, q]))) for q, (k, v) in enumerate(fs.items())},
+                     "vs_oracle": {k: l1_rel(v, fo[k]) for k, v in fs.items()}}
+        s.close()
+    return out
 
 
 def run_kernels_only(args):

@@ -85,6 +85,8 @@ typedef struct {
   int face_order;         /* 1 upwind or 2 Van Leer limited linear (default 2) */
   int corner_recon;       /* LR_CORNER_UPWIND or LR_CORNER_DIAG (default) */
   double dt_fixed;        /* > 0: use this dt instead of the CFL rule */
+  int mixed_lanes;        /* threads per mixed cell in the interface kernel:
+                             1, 2, 4 or 8; 0 (default) picks per precision */
   void* cuda_stream;      /* cudaStream_t to run on; NULL = library-owned stream */
 } lr_config;
 
@@ -171,7 +173,8 @@ enum {
                         (n0x, n0y, d0, n1x, n1y, d1 in the cell's frame; 0 elsewhere) */
   LR_F_XA = 33,      /* [nmat][ny][nx+1] per-material X-face volume flux, signed */
   LR_F_YA = 34,      /* [nmat][ny+1][nx] per-material Y-face volume flux, signed */
-  LR_F_CA = 35       /* [nmat][(ny+1)][(nx+1)] per-material corner volume flux */
+  LR_F_CA = 35,      /* [nmat][(ny+1)][(nx+1)] per-material corner volume flux */
+  LR_F_NMIXED = 36   /* [1] number of mixed cells (two or more materials) in the last step */
 };
 
 /* Number of doubles of a field, or 0 for an unknown field. */

@@ -22,6 +22,7 @@ CORNER_UPWIND, CORNER_DIAG = 0, 1
 F_K, F_RHO_MAT, F_E_MAT, F_P, F_RHO, F_E, F_UX, F_UY, F_CONS, F_C = range(10)
 F_UHX, F_UHY, F_VOL_LAGCF, F_E_LAG, F_FX, F_FY, F_FC, F_MX, F_MY, F_MC, F_Q, F_DT = range(20, 32)
 F_CUTS, F_XA, F_YA, F_CA = range(32, 36)
+F_SCLIP = 37
 
 
 class Config(ctypes.Structure):
@@ -159,7 +160,7 @@ class Oracle:
         if rc != 0:
             raise ValueError(f"orc_get({field}) failed")
         nx, ny, M = self.p.nx, self.p.ny, self.p.nmat
-        if field in (F_K, F_RHO_MAT, F_E_MAT, F_E_LAG):
+        if field in (F_K, F_RHO_MAT, F_E_MAT, F_E_LAG, F_SCLIP):
             return out.reshape(M, ny, nx)
         if field in (F_P, F_RHO, F_E, F_C, F_VOL_LAGCF, F_Q):
             return out.reshape(ny, nx)

@@ -1234,7 +1234,7 @@ int orc_step(orc* s, double t_end, double* dt_out) {
 long orc_size(const orc* s, int field) {
   long c = (long)s->nx * s->ny, n = (long)(s->nx + 1) * (s->ny + 1);
   switch (field) {
-    case ORC_F_K: case ORC_F_RHO_MAT: case ORC_F_E_MAT: case ORC_F_E_LAG: return c * s->M;
+    case ORC_F_K: case ORC_F_RHO_MAT: case ORC_F_E_MAT: case ORC_F_E_LAG: case ORC_F_SCLIP: return c * s->M;
     case ORC_F_P: case ORC_F_RHO: case ORC_F_E: case ORC_F_C: case ORC_F_VOL_LAGCF: case ORC_F_Q: return c;
     case ORC_F_UX: case ORC_F_UY: case ORC_F_UHX: case ORC_F_UHY: case ORC_F_FC: case ORC_F_MC: return n;
     case ORC_F_FX: case ORC_F_MX: return (long)s->ny * (s->nx + 1);
@@ -1264,13 +1264,14 @@ int orc_get(orc* s, int field, double* out, long n) {
   int nx = s->nx, ny = s->ny, M = s->M;
   long cc = (long)nx * ny;
   switch (field) {
-    case ORC_F_K: case ORC_F_RHO_MAT: case ORC_F_E_MAT: case ORC_F_E_LAG:
+    case ORC_F_K: case ORC_F_RHO_MAT: case ORC_F_E_MAT: case ORC_F_E_LAG: case ORC_F_SCLIP:
       for (int a = 0; a < M; ++a)
         for (int j = 0; j < ny; ++j)
           for (int i = 0; i < nx; ++i) {
             int c = CI(s, i, j);
             double v = field == ORC_F_K ? s->k[a][c] : field == ORC_F_RHO_MAT ? s->r[a][c]
-                     : field == ORC_F_E_MAT ? s->e[a][c] : s->elag[a][c];
+                     : field == ORC_F_E_MAT ? s->e[a][c] : field == ORC_F_SCLIP ? s->sclip[a][c]
+                     : s->elag[a][c];
             out[a * cc + (long)j * nx + i] = v;
           }
       return 0;

@@ -63,7 +63,9 @@ enum {
   ORC_F_CUTS = 32,    /* [6][ny][nx] interface lines of mixed cells: n0x, n0y, d0, n1x, n1y, d1 */
   ORC_F_XA = 33,      /* [nmat][ny][nx+1] per-material X-face volume flux, signed */
   ORC_F_YA = 34,      /* [nmat][ny+1][nx] per-material Y-face volume flux, signed */
-  ORC_F_CA = 35       /* [nmat][(ny+1)][(nx+1)] per-material corner volume flux */
+  ORC_F_CA = 35,      /* [nmat][(ny+1)][(nx+1)] per-material corner volume flux */
+  ORC_F_SCLIP = 37    /* [nmat][ny][nx] factor on material a's outgoing volume
+                         in the last step (1 unless clipped to what it holds) */
 };
 
 orc* orc_create(const orc_config* cfg, const double* gamma, const double* pinf);

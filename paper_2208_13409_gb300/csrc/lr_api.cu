@@ -88,6 +88,11 @@ bool config_ok(const lr_config* c, char* why, size_t nwhy) {
     return false;
   }
   if (c->dt_fixed < 0.0) { snprintf(why, nwhy, "dt_fixed < 0"); return false; }
+  if (c->mixed_lanes != 0 && c->mixed_lanes != 1 && c->mixed_lanes != 2 && c->mixed_lanes != 4 &&
+      c->mixed_lanes != 8) {
+    snprintf(why, nwhy, "mixed_lanes must be 0, 1, 2, 4 or 8");
+    return false;
+  }
   return true;
 }
 
@@ -172,6 +177,7 @@ void fill_grid(lr_ctx* c) {
   g.face_o2 = f.face_order == 2;
   g.corner_o2 = f.corner_recon == LR_CORNER_DIAG;
   g.mode = f.precision == LR_DF64 ? LR_MODE_DF64 : f.precision == LR_FP32 ? LR_MODE_FP32 : LR_MODE_FP64;
+  g.mixed_lanes = f.mixed_lanes ? f.mixed_lanes : lr_default_mixed_lanes(g.mode);
 }
 
 void drop_graphs(lr_ctx* c) {
@@ -315,6 +321,9 @@ lr_status field_to_device(lr_ctx* ctx, int field, double* dst) {
       return LR_OK;
     case LR_F_DT:
       CK(cudaMemcpyAsync(dst, w.scal + 2, sizeof(double), cudaMemcpyDeviceToDevice, st), "dt");
+      return LR_OK;
+    case LR_F_NMIXED:
+      CK(cudaMemcpyAsync(dst, w.scal + 6, sizeof(double), cudaMemcpyDeviceToDevice, st), "mixed count");
       return LR_OK;
     case LR_F_CONS:
       CK(lr_launch_cons(g, s, ctx->rows, dst, st), "cons");
@@ -505,6 +514,7 @@ size_t lr_field_size(const lr_ctx* ctx, int field) {
     case LR_F_FY: case LR_F_MY: return nx * (ny + 1);
     case LR_F_CONS: return 8;
     case LR_F_DT: return 1;
+    case LR_F_NMIXED: return 1;
     case LR_F_CUTS: return 6 * nx * ny;
     case LR_F_XA: return M * (nx + 1) * ny;
     case LR_F_YA: return M * nx * (ny + 1);

@@ -30,6 +30,7 @@ struct LrGrid {
   double cfl, a1, a2, dt_fixed;
   double gam[LR_MAXM], pin[LR_MAXM];
   int face_o2, corner_o2, presc;
+  int mixed_lanes;         // lanes per mixed cell in lr_mixed: 1, 2, 4 or 8
 };
 
 // Real-valued device arrays, listed once so the generic (void*) and typed
@@ -134,3 +135,5 @@ cudaError_t lr_launch_corner_debug(const LrGrid& g, const LrWork& w, double* fc_
 cudaError_t lr_launch_cuts(const LrGrid& g, const LrState& prev, const LrWork& w, double* dst, cudaStream_t s);
 cudaError_t lr_launch_from_double(const LrGrid& g, const double* src, void* dst, size_t n, cudaStream_t s);
 size_t lr_real_size(int mode);
+// Lanes per mixed cell in lr_mixed when the configuration leaves it open.
+int lr_default_mixed_lanes(int mode);

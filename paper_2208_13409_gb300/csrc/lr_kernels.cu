@@ -551,34 +551,75 @@ __device__ void split_region(int ncut, const int* order, const double (*cut)[3],
   A[order[ncut]] = left > 0.0 ? left : 0.0;
 }
 
+// Flux l of a mixed cell (0 left, 1 right, 2 bottom, 3 top, 4..7 the corners
+// at nodes ll, lr, ul, ur) when the cell donates it: its region r in the
+// cell's frame, its volume and index; returns the kind (0 X face, 1 Y face,
+// 2 corner) or -1 when the flux enters the cell.
+template <class R>
+__device__ __forceinline__ int donated_flux(const LrGrid& g, const LrWorkT<R>& w, int i, int j, int l,
+                                            double* r, double& vol, int& fidx) {
+  using O = RealOps<R>;
+  if (l < 2) {
+    int f = xix(g, i + l, j).idx;
+    double vf = O::todouble(w.fx[f]);
+    if (!(l == 0 ? vf < 0.0 : vf > 0.0)) return -1;
+    double xb = O::todouble(w.fxb[f]);
+    r[0] = l == 0 ? xb : g.dx; r[1] = l == 0 ? 0.0 : g.dx + xb;
+    r[2] = O::todouble(w.fxlo[f]); r[3] = O::todouble(w.fxhi[f]);
+    vol = fabs(vf); fidx = f;
+    return 0;
+  }
+  if (l < 4) {
+    int up = l - 2;
+    int f = yix(g, i, j + up).idx;
+    double vf = O::todouble(w.fy[f]);
+    if (!(up == 0 ? vf < 0.0 : vf > 0.0)) return -1;
+    double ybf = O::todouble(w.fyb[f]);
+    r[0] = O::todouble(w.fylo[f]); r[1] = O::todouble(w.fyhi[f]);
+    r[2] = up == 0 ? ybf : g.dy; r[3] = up == 0 ? 0.0 : g.dy + ybf;
+    vol = fabs(vf); fidx = f;
+    return 1;
+  }
+  int q = l - 4, qa = q & 1, qb = q >> 1;
+  int n = nix(g, i + qa, j + qb).idx;
+  double cx = O::todouble(w.ddx[n]), cy = O::todouble(w.ddy[n]);
+  int di, dj, ri, rj;
+  if (!corner_cells(cx, cy, i + qa, j + qb, di, dj, ri, rj) || di != i || dj != j) return -1;
+  corner_region(g, cx, cy, r);
+  vol = fabs(cx * cy); fidx = n;
+  return 2;
+}
+
 // K4b: the interface work of mixed cells only (the list built by lr_cell_pre),
 // in double whatever the step's arithmetic: Youngs normals and PLIC lines in
 // the rectangular Lagrangian cell (sections 4.1 and 4.4; three materials by
 // nested cuts in material order), the split of every flux the cell donates,
 // and the clipping of a material's outgoing volume to what it holds (excess
-// to the dominant material).
+// to the dominant material).  g.mixed_lanes = L lanes (1, 2, 4 or 8) work on
+// one cell: all place the interface, lane l splits fluxes l, l+L, ...; the
+// outgoing volumes per material are summed across the L lanes with shuffles.
+// More lanes hide more latency (the list is short) but repeat the interface
+// placement L times per warp instruction, so L is chosen per arithmetic.
+// Splits are stored unclipped; the rare cell whose material runs short
+// rescales its own stored splits in a second pass.
 template <class R, int M>
 __global__ void __launch_bounds__(128) lr_mixed(LrGrid g, LrStateT<R> cur, LrWorkT<R> w) {
   using O = RealOps<R>;
   if (!step_live(w.scal)) return;
   int count = (int)w.red[2];
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
-    int c = w.mixed[t];
+  const int L = g.mixed_lanes, lg = __ffs(L) - 1;
+  int lane = threadIdx.x & (L - 1);
+  int group = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> lg);
+  int ngroups = (int)((gridDim.x * blockDim.x) >> lg);
+  int wmask = (32 >> lg) - 1;   // groups per warp - 1
+  for (int k = 0;; ++k) {
+    int tw = (group & ~wmask) + k * ngroups;   // first group of this warp: the warp iterates together
+    if (tw >= count) break;
+    int t = group + k * ngroups;
+    bool valid = t < count;
+    int c = w.mixed[valid ? t : 0];
     int i = c % g.nx, j = c / g.nx;
     double v = O::todouble(w.vcf[c]);
-    int fl = xix(g, i, j).idx, fr = xix(g, i + 1, j).idx;
-    int fb = yix(g, i, j).idx, ft = yix(g, i, j + 1).idx;
-    double vL = O::todouble(w.fx[fl]), vR = O::todouble(w.fx[fr]);
-    double vB = O::todouble(w.fy[fb]), vT = O::todouble(w.fy[ft]);
-    int nidx[4];
-    double cdx[4], cdy[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      int n = nix(g, i + (q & 1), j + (q >> 1)).idx;
-      nidx[q] = n;
-      cdx[q] = O::todouble(w.ddx[n]);
-      cdy[q] = O::todouble(w.ddy[n]);
-    }
     double kk[M];
     int np = 0, order[LR_MAXM] = {0, 0, 0}, dom = 0;
     unsigned msk = w.mask[c];
@@ -612,63 +653,57 @@ __global__ void __launch_bounds__(128) lr_mixed(LrGrid g, LrStateT<R> cur, LrWor
       cut[1][0] = nxv; cut[1][1] = nyv;
       cut[1][2] = poly_plic(rest, nxv, nyv, target);
     }
-    w.cut[0][c] = cut[0][0]; w.cut[1][c] = cut[0][1]; w.cut[2][c] = cut[0][2];
-    if (ncut == 2) { w.cut[3][c] = cut[1][0]; w.cut[4][c] = cut[1][1]; w.cut[5][c] = cut[1][2]; }
-    // ---- outgoing fluxes: left, right, bottom, top, then corners
-    double A[8][M];
-    int kind[8], fidx[8];
-    int nf = 0;
-    double r[4];
-    if (vL < 0.0) {
-      r[0] = O::todouble(w.fxb[fl]); r[1] = 0.0; r[2] = O::todouble(w.fxlo[fl]); r[3] = O::todouble(w.fxhi[fl]);
-      split_region<M>(ncut, order, cut, r, -vL, A[nf]); kind[nf] = 0; fidx[nf] = fl; ++nf;
+    if (valid && lane == 0) {
+      w.cut[0][c] = cut[0][0]; w.cut[1][c] = cut[0][1]; w.cut[2][c] = cut[0][2];
+      if (ncut == 2) { w.cut[3][c] = cut[1][0]; w.cut[4][c] = cut[1][1]; w.cut[5][c] = cut[1][2]; }
     }
-    if (vR > 0.0) {
-      r[0] = g.dx; r[1] = g.dx + O::todouble(w.fxb[fr]); r[2] = O::todouble(w.fxlo[fr]); r[3] = O::todouble(w.fxhi[fr]);
-      split_region<M>(ncut, order, cut, r, vR, A[nf]); kind[nf] = 0; fidx[nf] = fr; ++nf;
-    }
-    if (vB < 0.0) {
-      r[0] = O::todouble(w.fylo[fb]); r[1] = O::todouble(w.fyhi[fb]); r[2] = O::todouble(w.fyb[fb]); r[3] = 0.0;
-      split_region<M>(ncut, order, cut, r, -vB, A[nf]); kind[nf] = 1; fidx[nf] = fb; ++nf;
-    }
-    if (vT > 0.0) {
-      r[0] = O::todouble(w.fylo[ft]); r[1] = O::todouble(w.fyhi[ft]); r[2] = g.dy; r[3] = g.dy + O::todouble(w.fyb[ft]);
-      split_region<M>(ncut, order, cut, r, vT, A[nf]); kind[nf] = 1; fidx[nf] = ft; ++nf;
-    }
-    for (int q = 0; q < 4; ++q) {
-      int a = q & 1, b = q >> 1;
-      int di, dj, ri, rj;
-      if (!corner_cells(cdx[q], cdy[q], i + a, j + b, di, dj, ri, rj)) continue;
-      if (di != i || dj != j) continue;
-      corner_region(g, cdx[q], cdy[q], r);
-      split_region<M>(ncut, order, cut, r, fabs(cdx[q] * cdy[q]), A[nf]);
-      kind[nf] = 2; fidx[nf] = nidx[q]; ++nf;
-    }
-    double out[M];
+    // ---- this lane's fluxes: split and store, summing the outgoing volumes
+    double o[M];
 #pragma unroll
-    for (int a = 0; a < M; ++a) out[a] = 0.0;
-    for (int f = 0; f < nf; ++f)
+    for (int a = 0; a < M; ++a) o[a] = 0.0;
+    for (int l = lane; l < 8; l += L) {
+      double r[4], vol;
+      int fidx = 0;
+      int kind = valid ? donated_flux(g, w, i, j, l, r, vol, fidx) : -1;
+      if (kind < 0) continue;
+      double A[M];
+      split_region<M>(ncut, order, cut, r, vol, A);
 #pragma unroll
-      for (int a = 0; a < M; ++a) out[a] += A[f][a];
+      for (int a = 0; a < M; ++a) {
+        o[a] += A[a];
+        R* dst = kind == 0 ? w.xAm[a] : kind == 1 ? w.yAm[a] : w.cAm[a];
+        dst[fidx] = from_double<R>(A[a]);
+      }
+    }
+    // ---- clipping: outgoing volume per material over the L lanes
     double sc[M];
+    bool clip = false;
 #pragma unroll
     for (int a = 0; a < M; ++a) {
+      for (int off = 1; off < L; off <<= 1) o[a] += __shfl_xor_sync(0xffffffffu, o[a], off);
       sc[a] = 1.0;
       if (a == dom) continue;
       double avail = kk[a] * v;
-      if (out[a] > avail) sc[a] = avail / out[a];
+      if (o[a] > avail) { sc[a] = avail / o[a]; clip = true; }
     }
-    for (int f = 0; f < nf; ++f) {
-      double moved = 0.0;
+    if (!(valid && clip)) continue;
+    for (int l = lane; l < 8; l += L) {
+      double r[4], vol;
+      int fidx = 0;
+      int kind = donated_flux(g, w, i, j, l, r, vol, fidx);
+      if (kind < 0) continue;
+      double A[M], moved = 0.0;
 #pragma unroll
       for (int a = 0; a < M; ++a) {
-        if (sc[a] < 1.0) { moved += (1.0 - sc[a]) * A[f][a]; A[f][a] *= sc[a]; }
+        const R* src = kind == 0 ? w.xAm[a] : kind == 1 ? w.yAm[a] : w.cAm[a];
+        A[a] = O::todouble(src[fidx]);
+        if (sc[a] < 1.0) { moved += (1.0 - sc[a]) * A[a]; A[a] *= sc[a]; }
       }
-      A[f][dom] += moved;
 #pragma unroll
       for (int a = 0; a < M; ++a) {
-        R* dst = kind[f] == 0 ? w.xAm[a] : kind[f] == 1 ? w.yAm[a] : w.cAm[a];
-        dst[fidx[f]] = from_double<R>(A[f][a]);
+        if (a == dom) A[a] += moved;
+        R* dst = kind == 0 ? w.xAm[a] : kind == 1 ? w.yAm[a] : w.cAm[a];
+        dst[fidx] = from_double<R>(A[a]);
       }
     }
   }
@@ -1188,6 +1223,7 @@ __device__ void cfl_finalize(const LrGrid& g, const KC<R>& kc, const LrWorkT<R>&
     dn = dn > 0.0 ? dn : 0.0;
     w.scal[5] = dn;
     w.dtR[0] = from_double<R>(dn);
+    if (advance) w.scal[6] = (double)w.red[2];
     w.red[0] = 0ull;
     w.red[1] = 0ull;
     w.red[2] = 0ull;
@@ -1482,8 +1518,9 @@ cudaError_t launch_t(int kid, const LrGrid& g, const LrState& cur0, const LrStat
     case LRK_CELL_CF: LR_M(lr_cell_cf, grid_for(g.nx, g.ny), g, kc, cur, w); break;
     case LRK_MIXED: {
       if (g.M == 1) break;  // one material: no interfaces
-      int nb = (g.nx * g.ny + 127) / 128;
-      if (nb > 152 * 8) nb = 152 * 8;
+      long long lanes = (long long)g.mixed_lanes * g.nx * g.ny;
+      int nb = (int)((lanes + 127) / 128);
+      if (nb > 152 * 16) nb = 152 * 16;
       if (g.M == 2) lr_mixed<R, 2><<<nb, 128, 0, s>>>(g, cur, w);
       else lr_mixed<R, 3><<<nb, 128, 0, s>>>(g, cur, w);
       break;
@@ -1501,6 +1538,8 @@ cudaError_t launch_t(int kid, const LrGrid& g, const LrState& cur0, const LrStat
 }
 
 }  // namespace
+
+int lr_default_mixed_lanes(int mode) { return mode == LR_MODE_FP32 ? 8 : 4; }
 
 size_t lr_real_size(int mode) { return mode == LR_MODE_FP32 ? sizeof(float) : mode == LR_MODE_DF64 ? sizeof(df64) : sizeof(double); }
 

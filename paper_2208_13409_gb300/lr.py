@@ -25,7 +25,7 @@ CORNER_UPWIND, CORNER_DIAG = 0, 1
 FP64, DF64, FP32 = 0, 1, 2
 F_K, F_RHO_MAT, F_E_MAT, F_P, F_RHO, F_E, F_UX, F_UY, F_CONS, F_C = range(10)
 F_UHX, F_UHY, F_VOL_LAGCF, F_E_LAG, F_FX, F_FY, F_FC, F_MX, F_MY, F_MC, F_Q, F_DT = range(20, 32)
-F_CUTS, F_XA, F_YA, F_CA = range(32, 36)
+F_CUTS, F_XA, F_YA, F_CA, F_NMIXED = range(32, 37)
 
 
 class LrError(RuntimeError):
@@ -44,6 +44,7 @@ class Config(ctypes.Structure):
         ("bc", ctypes.c_int * 4),
         ("precision", ctypes.c_int), ("face_order", ctypes.c_int), ("corner_recon", ctypes.c_int),
         ("dt_fixed", ctypes.c_double),
+        ("mixed_lanes", ctypes.c_int),
         ("cuda_stream", ctypes.c_void_p),
     ]
 
@@ -117,7 +118,7 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(_dp)
 
 
-def make_config(problem, stream: Optional[int] = None, precision: int = FP64) -> Config:
+def make_config(problem, stream: Optional[int] = None, precision: int = FP64, mixed_lanes: int = 0) -> Config:
     c = Config()
     load().lr_config_default(ctypes.byref(c))
     c.nx, c.ny = problem.nx, problem.ny
@@ -130,6 +131,7 @@ def make_config(problem, stream: Optional[int] = None, precision: int = FP64) ->
     c.face_order = problem.face_order
     c.corner_recon = problem.corner_recon
     c.dt_fixed = problem.dt_fixed
+    c.mixed_lanes = mixed_lanes
     c.cuda_stream = stream
     return c
 
@@ -137,7 +139,7 @@ def make_config(problem, stream: Optional[int] = None, precision: int = FP64) ->
 class Sim:
     """One simulation on the GPU behind the C ABI."""
 
-    def __init__(self, problem, use_torch: bool = True, precision: int = FP64):
+    def __init__(self, problem, use_torch: bool = True, precision: int = FP64, mixed_lanes: int = 0):
         L = load()
         self.p = problem
         self._arena = None
@@ -152,7 +154,7 @@ class Sim:
             # recorded on it; the legacy default stream gets a private one
             self.stream = cs if cs.cuda_stream != 0 else torch.cuda.Stream()
             stream = self.stream.cuda_stream
-        self.cfg = make_config(problem, stream, precision)
+        self.cfg = make_config(problem, stream, precision, mixed_lanes)
         self.precision = precision
         h = ctypes.c_void_p()
         if use_torch:

@@ -36,4 +36,8 @@ def test_host_side_validation_without_gpu():
     bad = lr.make_config(P.sod(nx=16))
     bad.bc[0] = lr.BC_PERIODIC  # xlo != xhi
     assert L.lr_workspace_bytes(ctypes.byref(bad), ctypes.byref(nbytes)) == lr.ERR_ARG
+    for lanes, ok in ((0, True), (1, True), (4, True), (8, True), (3, False), (16, False), (-1, False)):
+        cfg = lr.make_config(P.sod(nx=16), mixed_lanes=lanes)
+        rc = L.lr_workspace_bytes(ctypes.byref(cfg), ctypes.byref(nbytes))
+        assert rc == (lr.OK if ok else lr.ERR_ARG), lanes
     assert L.lr_last_error(None) == b"null context"

@@ -103,6 +103,27 @@ def test_parity_100_steps_l1(name, make, prec):
     _assert_close(compare(sim, orc, l1_rel), TOL_100, f"{name} 100 steps")
 
 
+@pytest.mark.parametrize("prec", sorted(PRECISIONS))
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8])
+@pytest.mark.parametrize("name,make", [
+    ("random2_walls_velocity", lambda: P.random_box(21, nx=77, ny=45, nmat=2, velocity=0.3)),
+    ("random3_walls_velocity", lambda: P.random_box(22, nx=53, ny=70, nmat=3, velocity=0.3)),
+])
+def test_mixed_lanes_and_clipping(name, make, lanes, prec):
+    """Every lanes-per-mixed-cell setting of the interface kernel against the
+    oracle, over steps where the oracle clips some material's outgoing volume
+    (so the rescaling pass of the kernel runs)."""
+    pr = make()
+    sim = lr.Sim(pr, precision=PRECISIONS[prec], mixed_lanes=lanes)
+    orc = oracle.Oracle(pr)
+    clipped = 0
+    for q in range(16):
+        _steps(sim, orc, 1)
+        clipped += int((orc.get(oracle.F_SCLIP) < 1.0).sum())
+        _assert_close(compare(sim, orc), TOL_1 if q == 0 else 1e-10, f"{name} L={lanes} step {q + 1}")
+    assert clipped > 0
+
+
 def test_lr_run_matches_stepwise_and_oracle():
     """lr_run (CUDA graphs, dt kept on the device) against the oracle."""
     pr = P.triple_point(140, 60)
