@@ -1,6 +1,6 @@
 """Build the CUDA library liblr.so in-tree for sm_103a (nvcc, no cmake).
 
-The two translation units compile in parallel; the result goes to
+The translation units compile in parallel; the result goes to
 paper_2208_13409_gb300/_build/liblr.so (git-ignored).
 """
 from __future__ import annotations
@@ -13,8 +13,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblr.so")
-SOURCES = ["lr_kernels.cu", "lr_api.cu", "lr_noalloc.cu"]
-HEADERS = ["lr_dev.cuh", os.path.join("..", "..", "include", "lr.h")]
+SOURCES = ["lr_kernels.cu", "lr_api.cu", "lr_batch.cu", "lr_noalloc.cu"]
+HEADERS = ["lr_dev.cuh", "lr_real.cuh", "lr_host.h", os.path.join("..", "..", "include", "lr.h"),
+           os.path.join("..", "..", "include", "lr_batch.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 

@@ -2,6 +2,7 @@
 // CUDA graphs for lr_run, field read-back and kernel timing.
 #include "../../include/lr.h"
 #include "lr_dev.cuh"
+#include "lr_host.h"
 
 #include <math.h>
 #include <stdarg.h>
@@ -35,6 +36,146 @@ struct lr_ctx {
   size_t tmp_elems;
   double* rows;     // device scratch for conservation partial sums
 };
+
+// ---------------------------------------- shared with the batch API (lr_host.h)
+bool lr_config_ok(const lr_config* c, char* why, size_t nwhy) {
+  if (!c) { snprintf(why, nwhy, "null config"); return false; }
+  if (c->nx < 2 || c->ny < 2) { snprintf(why, nwhy, "nx, ny must be >= 2"); return false; }
+  if ((double)c->nx * (double)c->ny > (double)(1 << 28)) { snprintf(why, nwhy, "nx*ny above 2^28"); return false; }
+  if (c->nmat < 1 || c->nmat > LR_MAXM) { snprintf(why, nwhy, "nmat must be 1..3"); return false; }
+  if (!(c->x1 > c->x0) || !(c->y1 > c->y0)) { snprintf(why, nwhy, "empty domain"); return false; }
+  if (c->bc[0] != c->bc[1] || c->bc[2] != c->bc[3]) { snprintf(why, nwhy, "bc[0]==bc[1] and bc[2]==bc[3] required"); return false; }
+  for (int q = 0; q < 4; ++q)
+    if (c->bc[q] != LR_BC_REFLECT && c->bc[q] != LR_BC_PERIODIC) { snprintf(why, nwhy, "bad bc"); return false; }
+  if (!(c->cfl > 0.0) || c->cfl > 1.0) { snprintf(why, nwhy, "cfl must be in (0,1]"); return false; }
+  if (c->a1 < 0.0 || c->a2 < 0.0) { snprintf(why, nwhy, "negative viscosity coefficient"); return false; }
+  if (c->face_order != 1 && c->face_order != 2) { snprintf(why, nwhy, "face_order must be 1 or 2"); return false; }
+  if (c->corner_recon != LR_CORNER_UPWIND && c->corner_recon != LR_CORNER_DIAG) { snprintf(why, nwhy, "bad corner_recon"); return false; }
+  if (c->precision != LR_FP64 && c->precision != LR_DF64 && c->precision != LR_FP32) {
+    snprintf(why, nwhy, "precision must be LR_FP64, LR_DF64 or LR_FP32");
+    return false;
+  }
+  if (c->dt_fixed < 0.0) { snprintf(why, nwhy, "dt_fixed < 0"); return false; }
+  if (c->mixed_lanes != 0 && c->mixed_lanes != 1 && c->mixed_lanes != 2 && c->mixed_lanes != 4 &&
+      c->mixed_lanes != 8) {
+    snprintf(why, nwhy, "mixed_lanes must be 0, 1, 2, 4 or 8");
+    return false;
+  }
+  return true;
+}
+
+void lr_fill_grid(const lr_config& f, LrGrid& g) {
+  g.nx = f.nx; g.ny = f.ny; g.M = f.nmat;
+  g.perx = f.bc[0] == LR_BC_PERIODIC;
+  g.pery = f.bc[2] == LR_BC_PERIODIC;
+  g.nxu = g.perx ? g.nx : g.nx + 1;
+  g.nyu = g.pery ? g.ny : g.ny + 1;
+  g.dx = (f.x1 - f.x0) / f.nx;
+  g.dy = (f.y1 - f.y0) / f.ny;
+  g.V = g.dx * g.dy;
+  g.L = sqrt(g.dx * g.dy);
+  g.hmin = g.dx < g.dy ? g.dx : g.dy;
+  g.D = sqrt(g.dx * g.dx + g.dy * g.dy);
+  g.inv2dx = 1.0 / (2.0 * g.dx);
+  g.inv2dy = 1.0 / (2.0 * g.dy);
+  g.inv8dx = 1.0 / (8.0 * g.dx);
+  g.inv8dy = 1.0 / (8.0 * g.dy);
+  g.invV = 1.0 / g.V;
+  g.invD = 1.0 / g.D;
+  g.cfl = f.cfl; g.a1 = f.a1; g.a2 = f.a2; g.dt_fixed = f.dt_fixed;
+  g.face_o2 = f.face_order == 2;
+  g.corner_o2 = f.corner_recon == LR_CORNER_DIAG;
+  g.mode = f.precision == LR_DF64 ? LR_MODE_DF64 : f.precision == LR_FP32 ? LR_MODE_FP32 : LR_MODE_FP64;
+  g.mixed_lanes = f.mixed_lanes ? f.mixed_lanes : lr_default_mixed_lanes(g.mode);
+}
+
+// Field `field` of one simulation as doubles in dst (device); s is its
+// current state, prev the other half of its double buffer.
+cudaError_t lr_field_view(const LrGrid& g, const LrState& s, const LrState& prev, const LrWork& w, double* rows,
+                          int field, double* dst, cudaStream_t st, bool* unknown) {
+  size_t nc = (size_t)g.nx * g.ny;
+  *unknown = false;
+#define CK(call, where)                          \
+  do {                                           \
+    cudaError_t _e = (call);                     \
+    if (_e != cudaSuccess) return _e;            \
+  } while (0)
+  switch (field) {
+    case LR_F_K: case LR_F_RHO_MAT: case LR_F_E_MAT: case LR_F_E_LAG:
+      for (int a = 0; a < g.M; ++a) {
+        const void* src = field == LR_F_K ? s.k[a] : field == LR_F_RHO_MAT ? s.r[a]
+                        : field == LR_F_E_MAT ? s.e[a] : w.elag[a];
+        CK(lr_launch_view(g, src, dst + a * nc, nc, 0, st), "view");
+      }
+      return cudaSuccess;
+    case LR_F_P: case LR_F_RHO: case LR_F_E:
+      CK(lr_launch_mixture(g, s, dst, field == LR_F_P ? 0 : field == LR_F_RHO ? 1 : 2, st), "mixture");
+      return cudaSuccess;
+    case LR_F_C: case LR_F_VOL_LAGCF: case LR_F_Q:
+      CK(lr_launch_view(g, field == LR_F_C ? w.cc : field == LR_F_Q ? w.Q : w.vcf, dst, nc, 0, st), "view");
+      return cudaSuccess;
+    case LR_F_UX: case LR_F_UY: case LR_F_UHX: case LR_F_UHY: {
+      const void* src = field == LR_F_UX ? s.ux : field == LR_F_UY ? s.uy : field == LR_F_UHX ? w.uhx : w.uhy;
+      CK(lr_launch_view(g, src, dst, 0, 1, st), "view");
+      return cudaSuccess;
+    }
+    case LR_F_FX: case LR_F_MX:
+      CK(lr_launch_view(g, field == LR_F_FX ? w.fx : w.MX, dst, 0, 2, st), "view");
+      return cudaSuccess;
+    case LR_F_FY: case LR_F_MY:
+      CK(lr_launch_view(g, field == LR_F_FY ? w.fy : w.MY, dst, 0, 3, st), "view");
+      return cudaSuccess;
+    case LR_F_FC: case LR_F_MC:
+      CK(lr_launch_corner_debug(g, w, field == LR_F_FC ? dst : nullptr, field == LR_F_MC ? dst : nullptr, st),
+         "corner view");
+      return cudaSuccess;
+    case LR_F_DT:
+      CK(cudaMemcpyAsync(dst, w.scal + 2, sizeof(double), cudaMemcpyDeviceToDevice, st), "dt");
+      return cudaSuccess;
+    case LR_F_NMIXED:
+      CK(cudaMemcpyAsync(dst, w.scal + 6, sizeof(double), cudaMemcpyDeviceToDevice, st), "mixed count");
+      return cudaSuccess;
+    case LR_F_CONS:
+      CK(lr_launch_cons(g, s, rows, dst, st), "cons");
+      return cudaSuccess;
+    case LR_F_CUTS:
+      CK(lr_launch_cuts(g, prev, w, dst, st), "cuts");
+      return cudaSuccess;
+    case LR_F_XA: case LR_F_YA: case LR_F_CA:
+      for (int a = 0; a < g.M; ++a) {
+        if (field == LR_F_XA)
+          CK(lr_launch_view(g, w.xA[a], dst + (size_t)a * (g.nx + 1) * g.ny, 0, 2, st), "view");
+        else if (field == LR_F_YA)
+          CK(lr_launch_view(g, w.yA[a], dst + (size_t)a * g.nx * (g.ny + 1), 0, 3, st), "view");
+        else
+          CK(lr_launch_view(g, w.cA[a], dst + (size_t)a * (g.nx + 1) * (g.ny + 1), 0, 1, st), "view");
+      }
+      return cudaSuccess;
+  }
+#undef CK
+  *unknown = true;
+  return cudaSuccess;
+}
+
+
+size_t lr_field_count(const LrGrid& g, int field) {
+  size_t nx = g.nx, ny = g.ny, M = g.M;
+  switch (field) {
+    case LR_F_K: case LR_F_RHO_MAT: case LR_F_E_MAT: case LR_F_E_LAG: return M * nx * ny;
+    case LR_F_P: case LR_F_RHO: case LR_F_E: case LR_F_C: case LR_F_VOL_LAGCF: case LR_F_Q: return nx * ny;
+    case LR_F_UX: case LR_F_UY: case LR_F_UHX: case LR_F_UHY: case LR_F_FC: case LR_F_MC: return (nx + 1) * (ny + 1);
+    case LR_F_FX: case LR_F_MX: return (nx + 1) * ny;
+    case LR_F_FY: case LR_F_MY: return nx * (ny + 1);
+    case LR_F_CONS: return 8;
+    case LR_F_DT: return 1;
+    case LR_F_NMIXED: return 1;
+    case LR_F_CUTS: return 6 * nx * ny;
+    case LR_F_XA: return M * (nx + 1) * ny;
+    case LR_F_YA: return M * nx * (ny + 1);
+    case LR_F_CA: return M * (nx + 1) * (ny + 1);
+  }
+  return 0;
+}
 
 namespace {
 
@@ -70,31 +211,6 @@ struct Bump {
   }
 };
 
-bool config_ok(const lr_config* c, char* why, size_t nwhy) {
-  if (!c) { snprintf(why, nwhy, "null config"); return false; }
-  if (c->nx < 2 || c->ny < 2) { snprintf(why, nwhy, "nx, ny must be >= 2"); return false; }
-  if ((double)c->nx * (double)c->ny > (double)(1 << 28)) { snprintf(why, nwhy, "nx*ny above 2^28"); return false; }
-  if (c->nmat < 1 || c->nmat > LR_MAXM) { snprintf(why, nwhy, "nmat must be 1..3"); return false; }
-  if (!(c->x1 > c->x0) || !(c->y1 > c->y0)) { snprintf(why, nwhy, "empty domain"); return false; }
-  if (c->bc[0] != c->bc[1] || c->bc[2] != c->bc[3]) { snprintf(why, nwhy, "bc[0]==bc[1] and bc[2]==bc[3] required"); return false; }
-  for (int q = 0; q < 4; ++q)
-    if (c->bc[q] != LR_BC_REFLECT && c->bc[q] != LR_BC_PERIODIC) { snprintf(why, nwhy, "bad bc"); return false; }
-  if (!(c->cfl > 0.0) || c->cfl > 1.0) { snprintf(why, nwhy, "cfl must be in (0,1]"); return false; }
-  if (c->a1 < 0.0 || c->a2 < 0.0) { snprintf(why, nwhy, "negative viscosity coefficient"); return false; }
-  if (c->face_order != 1 && c->face_order != 2) { snprintf(why, nwhy, "face_order must be 1 or 2"); return false; }
-  if (c->corner_recon != LR_CORNER_UPWIND && c->corner_recon != LR_CORNER_DIAG) { snprintf(why, nwhy, "bad corner_recon"); return false; }
-  if (c->precision != LR_FP64 && c->precision != LR_DF64 && c->precision != LR_FP32) {
-    snprintf(why, nwhy, "precision must be LR_FP64, LR_DF64 or LR_FP32");
-    return false;
-  }
-  if (c->dt_fixed < 0.0) { snprintf(why, nwhy, "dt_fixed < 0"); return false; }
-  if (c->mixed_lanes != 0 && c->mixed_lanes != 1 && c->mixed_lanes != 2 && c->mixed_lanes != 4 &&
-      c->mixed_lanes != 8) {
-    snprintf(why, nwhy, "mixed_lanes must be 0, 1, 2, 4 or 8");
-    return false;
-  }
-  return true;
-}
 
 // Lay out every device array; returns the arena size.  Real arrays have the
 // element size of the step's arithmetic (8 bytes for double and double-float,
@@ -115,8 +231,8 @@ size_t layout(const lr_config* cfg, char* base, LrState* st, LrWork* w, double**
     for (size_t a = 0; a < M; ++a) { s[q].k[a] = R(nc); s[q].r[a] = R(nc); s[q].e[a] = R(nc); }
     s[q].ux = R(nn); s[q].uy = R(nn);
   }
-  W.scal = b.take<double>(8);
-  W.red = b.take<unsigned long long>(4);
+  W.scal = b.take<double>(LR_NSCAL);
+  W.red = b.take<unsigned long long>(LR_RED_INST + 2);
   W.err = b.take<int>(2);
   W.mixed = b.take<int>(nc);
   W.mask = b.take<unsigned char>(nc);
@@ -153,32 +269,7 @@ size_t layout(const lr_config* cfg, char* base, LrState* st, LrWork* w, double**
   return b.off + 256;
 }
 
-void fill_grid(lr_ctx* c) {
-  LrGrid& g = c->g;
-  const lr_config& f = c->cfg;
-  g.nx = f.nx; g.ny = f.ny; g.M = f.nmat;
-  g.perx = f.bc[0] == LR_BC_PERIODIC;
-  g.pery = f.bc[2] == LR_BC_PERIODIC;
-  g.nxu = g.perx ? g.nx : g.nx + 1;
-  g.nyu = g.pery ? g.ny : g.ny + 1;
-  g.dx = (f.x1 - f.x0) / f.nx;
-  g.dy = (f.y1 - f.y0) / f.ny;
-  g.V = g.dx * g.dy;
-  g.L = sqrt(g.dx * g.dy);
-  g.hmin = g.dx < g.dy ? g.dx : g.dy;
-  g.D = sqrt(g.dx * g.dx + g.dy * g.dy);
-  g.inv2dx = 1.0 / (2.0 * g.dx);
-  g.inv2dy = 1.0 / (2.0 * g.dy);
-  g.inv8dx = 1.0 / (8.0 * g.dx);
-  g.inv8dy = 1.0 / (8.0 * g.dy);
-  g.invV = 1.0 / g.V;
-  g.invD = 1.0 / g.D;
-  g.cfl = f.cfl; g.a1 = f.a1; g.a2 = f.a2; g.dt_fixed = f.dt_fixed;
-  g.face_o2 = f.face_order == 2;
-  g.corner_o2 = f.corner_recon == LR_CORNER_DIAG;
-  g.mode = f.precision == LR_DF64 ? LR_MODE_DF64 : f.precision == LR_FP32 ? LR_MODE_FP32 : LR_MODE_FP64;
-  g.mixed_lanes = f.mixed_lanes ? f.mixed_lanes : lr_default_mixed_lanes(g.mode);
-}
+void fill_grid(lr_ctx* c) { lr_fill_grid(c->cfg, c->g); }
 
 void drop_graphs(lr_ctx* c) {
   for (int q = 0; q < 2; ++q)
@@ -242,7 +333,7 @@ lr_status create_common(const lr_config* cfg, void* mem, size_t bytes, bool own,
   if (!out) return LR_ERR_ARG;
   *out = nullptr;
   char why[160];
-  if (!config_ok(cfg, why, sizeof(why))) return LR_ERR_ARG;
+  if (!lr_config_ok(cfg, why, sizeof(why))) return LR_ERR_ARG;
   lr_ctx* ctx = new lr_ctx();
   ctx->cfg = *cfg;
   fill_grid(ctx);
@@ -270,7 +361,7 @@ lr_status create_common(const lr_config* cfg, void* mem, size_t bytes, bool own,
     ctx->own_stream = true;
   }
   ctx->sticky = LR_OK;
-  if (lr_launch_reset(ctx->w, ctx->stream) != cudaSuccess ||
+  if (lr_launch_reset(ctx->g.mode, ctx->w, 1, ctx->stream) != cudaSuccess ||
       cudaMemsetAsync(ctx->w.pux, 0, lr_real_size(ctx->g.mode) * (cfg->nx + 1) * (cfg->ny + 1), ctx->stream) != cudaSuccess ||
       cudaMemsetAsync(ctx->w.puy, 0, lr_real_size(ctx->g.mode) * (cfg->nx + 1) * (cfg->ny + 1), ctx->stream) != cudaSuccess ||
       cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
@@ -285,65 +376,11 @@ lr_status create_common(const lr_config* cfg, void* mem, size_t bytes, bool own,
 
 // ------------------------------------------------ field views (device)
 lr_status field_to_device(lr_ctx* ctx, int field, double* dst) {
-  const LrGrid& g = ctx->g;
-  const LrState& s = ctx->st[ctx->cur];
-  const LrWork& w = ctx->w;
-  size_t nc = (size_t)g.nx * g.ny;
-  cudaStream_t st = ctx->stream;
-  switch (field) {
-    case LR_F_K: case LR_F_RHO_MAT: case LR_F_E_MAT: case LR_F_E_LAG:
-      for (int a = 0; a < g.M; ++a) {
-        const void* src = field == LR_F_K ? s.k[a] : field == LR_F_RHO_MAT ? s.r[a]
-                        : field == LR_F_E_MAT ? s.e[a] : w.elag[a];
-        CK(lr_launch_view(g, src, dst + a * nc, nc, 0, st), "view");
-      }
-      return LR_OK;
-    case LR_F_P: case LR_F_RHO: case LR_F_E:
-      CK(lr_launch_mixture(g, s, dst, field == LR_F_P ? 0 : field == LR_F_RHO ? 1 : 2, st), "mixture");
-      return LR_OK;
-    case LR_F_C: case LR_F_VOL_LAGCF: case LR_F_Q:
-      CK(lr_launch_view(g, field == LR_F_C ? w.cc : field == LR_F_Q ? w.Q : w.vcf, dst, nc, 0, st), "view");
-      return LR_OK;
-    case LR_F_UX: case LR_F_UY: case LR_F_UHX: case LR_F_UHY: {
-      const void* src = field == LR_F_UX ? s.ux : field == LR_F_UY ? s.uy : field == LR_F_UHX ? w.uhx : w.uhy;
-      CK(lr_launch_view(g, src, dst, 0, 1, st), "view");
-      return LR_OK;
-    }
-    case LR_F_FX: case LR_F_MX:
-      CK(lr_launch_view(g, field == LR_F_FX ? w.fx : w.MX, dst, 0, 2, st), "view");
-      return LR_OK;
-    case LR_F_FY: case LR_F_MY:
-      CK(lr_launch_view(g, field == LR_F_FY ? w.fy : w.MY, dst, 0, 3, st), "view");
-      return LR_OK;
-    case LR_F_FC: case LR_F_MC:
-      CK(lr_launch_corner_debug(g, w, field == LR_F_FC ? dst : nullptr, field == LR_F_MC ? dst : nullptr, st),
-         "corner view");
-      return LR_OK;
-    case LR_F_DT:
-      CK(cudaMemcpyAsync(dst, w.scal + 2, sizeof(double), cudaMemcpyDeviceToDevice, st), "dt");
-      return LR_OK;
-    case LR_F_NMIXED:
-      CK(cudaMemcpyAsync(dst, w.scal + 6, sizeof(double), cudaMemcpyDeviceToDevice, st), "mixed count");
-      return LR_OK;
-    case LR_F_CONS:
-      CK(lr_launch_cons(g, s, ctx->rows, dst, st), "cons");
-      return LR_OK;
-    case LR_F_CUTS:
-      CK(lr_launch_cuts(g, ctx->st[1 - ctx->cur], w, dst, st), "cuts");
-      return LR_OK;
-    case LR_F_XA: case LR_F_YA: case LR_F_CA:
-      for (int a = 0; a < g.M; ++a) {
-        if (field == LR_F_XA)
-          CK(lr_launch_view(g, w.xA[a], dst + (size_t)a * (g.nx + 1) * g.ny, 0, 2, st), "view");
-        else if (field == LR_F_YA)
-          CK(lr_launch_view(g, w.yA[a], dst + (size_t)a * g.nx * (g.ny + 1), 0, 3, st), "view");
-        else
-          CK(lr_launch_view(g, w.cA[a], dst + (size_t)a * (g.nx + 1) * (g.ny + 1), 0, 1, st), "view");
-      }
-      return LR_OK;
-  }
-  setmsg(ctx, "unknown field %d", field);
-  return LR_ERR_ARG;
+  bool unknown = false;
+  CK(lr_field_view(ctx->g, ctx->st[ctx->cur], ctx->st[1 - ctx->cur], ctx->w, ctx->rows, field, dst, ctx->stream,
+                   &unknown), "field view");
+  if (unknown) { setmsg(ctx, "unknown field %d", field); return LR_ERR_ARG; }
+  return LR_OK;
 }
 
 }  // namespace
@@ -366,7 +403,7 @@ void lr_config_default(lr_config* c) {
 
 lr_status lr_workspace_bytes(const lr_config* cfg, size_t* bytes) {
   char why[160];
-  if (!bytes || !config_ok(cfg, why, sizeof(why))) return LR_ERR_ARG;
+  if (!bytes || !lr_config_ok(cfg, why, sizeof(why))) return LR_ERR_ARG;
   *bytes = layout(cfg, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
   return LR_OK;
 }
@@ -405,7 +442,7 @@ lr_status lr_init(lr_ctx* ctx, const double* k, const double* rho, const double*
   CK(cudaMemcpyAsync(sk + 2 * g.M * nc, p, g.M * nc * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload p");
   CK(cudaMemcpyAsync(sk + 3 * g.M * nc, ux, nn * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload ux");
   CK(cudaMemcpyAsync(sk + 3 * g.M * nc + nn, uy, nn * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload uy");
-  CK(lr_launch_reset(ctx->w, ctx->stream), "reset");
+  CK(lr_launch_reset(g.mode, ctx->w, 1, ctx->stream), "reset");
   CK(lr_launch_init(g, s, ctx->w, ctx->stream), "prepare");
   ctx->sticky = LR_OK;
   ctx->inited = false;
@@ -503,25 +540,7 @@ lr_status lr_sync(lr_ctx* ctx) {
   return check_sticky(ctx);
 }
 
-size_t lr_field_size(const lr_ctx* ctx, int field) {
-  if (!ctx) return 0;
-  size_t nx = ctx->g.nx, ny = ctx->g.ny, M = ctx->g.M;
-  switch (field) {
-    case LR_F_K: case LR_F_RHO_MAT: case LR_F_E_MAT: case LR_F_E_LAG: return M * nx * ny;
-    case LR_F_P: case LR_F_RHO: case LR_F_E: case LR_F_C: case LR_F_VOL_LAGCF: case LR_F_Q: return nx * ny;
-    case LR_F_UX: case LR_F_UY: case LR_F_UHX: case LR_F_UHY: case LR_F_FC: case LR_F_MC: return (nx + 1) * (ny + 1);
-    case LR_F_FX: case LR_F_MX: return (nx + 1) * ny;
-    case LR_F_FY: case LR_F_MY: return nx * (ny + 1);
-    case LR_F_CONS: return 8;
-    case LR_F_DT: return 1;
-    case LR_F_NMIXED: return 1;
-    case LR_F_CUTS: return 6 * nx * ny;
-    case LR_F_XA: return M * (nx + 1) * ny;
-    case LR_F_YA: return M * nx * (ny + 1);
-    case LR_F_CA: return M * (nx + 1) * (ny + 1);
-  }
-  return 0;
-}
+size_t lr_field_size(const lr_ctx* ctx, int field) { return ctx ? lr_field_count(ctx->g, field) : 0; }
 
 lr_status lr_get_fields(lr_ctx* ctx, int field, double* host_out, size_t n_elems) {
   if (!ctx || !host_out) return LR_ERR_ARG;

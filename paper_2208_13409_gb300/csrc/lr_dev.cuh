@@ -31,7 +31,29 @@ struct LrGrid {
   double gam[LR_MAXM], pin[LR_MAXM];
   int face_o2, corner_o2, presc;
   int mixed_lanes;         // lanes per mixed cell in lr_mixed: 1, 2, 4 or 8
+  // Place of this simulation in arrays shared by a batch (all 0 for a lone
+  // simulation): first cell, node and dual-cell index (face arrays use the
+  // node offset, their per-instance slots being node-sized), its scalar
+  // slot (scal[LR_NSCAL inst ..], red[LR_RED_INST + 2 inst ..], err[2 inst ..],
+  // dtR[inst]), its mixed-cell counter red[mslot] with list start moff, and
+  // the start of its initial-state staging.
+  int coff, noff, doff, inst, mslot, moff;
+  long long stoff;
 };
+
+// Scalars per simulation: [0] t, [1] dt from the CFL rule, [2] dt of the last
+// step, [3] t_end, [4] steps taken, [5] dt of the step in flight (0: idle),
+// [6] mixed cells in the last step, [7] step limit (0: none).
+#define LR_NSCAL 8
+// red[0..2]: mixed-cell counters (one per material-count group of a batch);
+// red[LR_RED_INST + 2 s], red[LR_RED_INST + 2 s + 1]: CFL max key and tile
+// counter of simulation slot s.
+#define LR_RED_INST 4
+
+// One tile of a batched launch: simulation slot, origin of the tile in that
+// simulation's iteration domain, and the number of tiles the table holds for
+// that simulation (the CFL reduction's completion count).
+struct LrTile { int inst, i0, j0, n; };
 
 // Real-valued device arrays, listed once so the generic (void*) and typed
 // views stay in step.  Cell arrays have nx*ny entries ([j][i]); node arrays
@@ -45,7 +67,7 @@ struct LrGrid {
   X(fx) X(fxb) X(fxlo) X(fxhi)        /* X faces: flux and its rectangle */    \
   X(fy) X(fyb) X(fylo) X(fyhi)        /* Y faces */                            \
   X(MX) X(MY) X(Mpp) X(Mpm)           /* total mass fluxes */                  \
-  X(dtR)                              /* [1] dt of the step in flight */
+  X(dtR)                              /* [inst] dt of the step in flight */
 #define LR_WORK_MAT_REALS(X)                                                  \
   X(elc)   /* (P_a^{n+1/2} + Q)/(rho_a dx dy): e^{lag} = e - elc (Vol^{lag} - V) */ \
   X(elag) X(rcf)                      /* e^{lag}, rho^{lagCF} */               \
@@ -63,11 +85,11 @@ struct LrStateT {
 
 template <class R>
 struct LrWorkT {
-  double* scal;            // [0] t, [1] dt from the CFL rule, [2] dt of the last step, [3] t_end,
-                           // [4] steps taken, [5] dt of the step in flight
-  unsigned long long* red; // [0] max(c+|u|) key, [1] block counter, [2] mixed-cell count
-  int* err;                // [0] error bits, [1] first failing index
-  int* mixed;              // work list of mixed cells (cell indices), red[2] entries
+  double* scal;            // LR_NSCAL per simulation (see above)
+  unsigned long long* red; // mixed-cell counters, then CFL key and tile counter per simulation
+  int* err;                // per simulation: [0] error bits, [1] first failing index
+  int* mixed;              // work list of mixed cells (cell indices), red[mslot] entries
+  int* minst;              // batch only: simulation slot of each list entry (else null)
   unsigned char* mask;     // bit a set when material a is present in the cell at t^n
   double* cut[6];          // interface lines of mixed cells (n0x, n0y, d0, n1x, n1y, d1)
   double* stage;           // init staging: k, rho, p [3][nmat][nc] then ux, uy [2][nn]
@@ -96,7 +118,8 @@ inline LrStateT<R> typed(const LrState& s) {
 template <class R>
 inline LrWorkT<R> typed(const LrWork& w) {
   LrWorkT<R> t;
-  t.scal = w.scal; t.red = w.red; t.err = w.err; t.mixed = w.mixed; t.mask = w.mask; t.stage = w.stage;
+  t.scal = w.scal; t.red = w.red; t.err = w.err; t.mixed = w.mixed; t.minst = w.minst; t.mask = w.mask;
+  t.stage = w.stage;
   for (int q = 0; q < 6; ++q) t.cut[q] = w.cut[q];
 #define LR_F1(n) t.n = static_cast<R*>(w.n);
   LR_WORK_REALS(LR_F1)
@@ -115,15 +138,38 @@ inline LrWorkT<R> typed(const LrWork& w) {
 // the arithmetic follows g.mode.
 enum LrKernelId {
   LRK_CELL_PRE = 0, LRK_NODE_HALF, LRK_CELL_LAG, LRK_CELL_CF, LRK_MIXED, LRK_MAT_FLUX,
-  LRK_CELL_UPDATE, LRK_DUAL_FLUX, LRK_NODE_UPDATE, LRK_COUNT
+  LRK_CELL_UPDATE, LRK_DUAL_FLUX, LRK_NODE_UPDATE, LRK_COUNT,
+  LRK_PREPARE = 100,   // initial state from the staging area
+  LRK_CFL_ONLY = 101   // CFL rule from the current state
 };
+// Iteration domains of the kernels (tile tables of a batch are per domain).
+enum { LR_DOM_CELLS = 0, LR_DOM_NODES, LR_DOM_DUAL, LR_DOM_NODES_ALL, LR_NDOM };
+int lr_kernel_domain(int kid);
 extern const char* const lr_kernel_names[LRK_COUNT];
 
 cudaError_t lr_launch(int kid, const LrGrid& g, const LrState& cur, const LrState& nxt,
                       const LrWork& w, cudaStream_t s);
 cudaError_t lr_launch_init(const LrGrid& g, const LrState& st, const LrWork& w, cudaStream_t s);
 cudaError_t lr_launch_set_tend(const LrGrid& g, const LrWork& w, double t_end, cudaStream_t s);
-cudaError_t lr_launch_reset(const LrWork& w, cudaStream_t s);
+// Zero the scalars, reduction words and error words of nsim simulations.
+cudaError_t lr_launch_reset(int mode, const LrWork& w, int nsim, cudaStream_t s);
+
+// One kernel of the step over a batch's tile table (kernels named lb_*).
+struct LrBatchArgs {
+  int mode;                // LR_MODE_* of every simulation
+  int M;                   // material count of every simulation in the table
+  const LrGrid* gs;        // device: grids by simulation slot
+  const void* kcs;         // device: constants by slot, lr_kc_bytes(mode) each
+  const LrTile* tiles;     // device: the tiles of this launch
+  int ntiles;
+  int bx, by;              // block = tile shape, bx * by == 256
+  int grid;                // persistent blocks (lr_mixed: blocks of 128)
+  int lanes, mslot, moff;  // lr_mixed: lanes per cell, counter slot, list start
+};
+cudaError_t lr_launch_batch(int kid, const LrBatchArgs& a, const LrState& cur, const LrState& nxt,
+                            const LrWork& w, cudaStream_t s);
+size_t lr_kc_bytes(int mode);
+void lr_make_kc(const LrGrid& g, void* out);
 // Field views: convert a real array (element type from g.mode) to double,
 // gathering with the boundary mapping: kind 0 plain copy of n values, 1 node
 // array, 2 X-face array, 3 Y-face array.

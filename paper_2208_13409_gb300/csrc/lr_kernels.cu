@@ -73,33 +73,33 @@ struct Ix { int idx, fx, fy; };
 __device__ __forceinline__ Ix cix(const LrGrid& g, int i, int j) {
   Ix r;
   int mi = map_cell(i, g.nx, g.perx, r.fx), mj = map_cell(j, g.ny, g.pery, r.fy);
-  r.idx = mj * g.nx + mi;
+  r.idx = g.coff + mj * g.nx + mi;
   return r;
 }
 __device__ __forceinline__ Ix nix(const LrGrid& g, int i, int j) {
   Ix r;
   int mi = map_node(i, g.nx, g.perx, r.fx), mj = map_node(j, g.ny, g.pery, r.fy);
-  r.idx = mj * (g.nx + 1) + mi;
+  r.idx = g.noff + mj * (g.nx + 1) + mi;
   return r;
 }
 // X face (i node-like, j cell-like) and Y face (i cell-like, j node-like)
 __device__ __forceinline__ Ix xix(const LrGrid& g, int i, int j) {
   Ix r;
   int mi = map_node(i, g.nx, g.perx, r.fx), mj = map_cell(j, g.ny, g.pery, r.fy);
-  r.idx = mj * (g.nx + 1) + mi;
+  r.idx = g.noff + mj * (g.nx + 1) + mi;
   return r;
 }
 __device__ __forceinline__ Ix yix(const LrGrid& g, int i, int j) {
   Ix r;
   int mi = map_cell(i, g.nx, g.perx, r.fx), mj = map_node(j, g.ny, g.pery, r.fy);
-  r.idx = mj * g.nx + mi;
+  r.idx = g.noff + mj * g.nx + mi;
   return r;
 }
 // dual objects: i, j in [-1, n]; periodic directions wrap into [0, n)
 __device__ __forceinline__ int dix(const LrGrid& g, int i, int j) {
   if (g.perx) i = (i + g.nx) % g.nx;
   if (g.pery) j = (j + g.ny) % g.ny;
-  return (j + 1) * (g.nx + 2) + (i + 1);
+  return g.doff + (j + 1) * (g.nx + 2) + (i + 1);
 }
 // mirrored reads: node vector components, cell scalars, centre offsets
 template <class R> __device__ __forceinline__ R nodeX(const LrGrid& g, const R* a, int i, int j) {
@@ -131,9 +131,15 @@ __device__ __forceinline__ void set_err(int* err, int bit, int idx) {
   atomicCAS(&err[1], -1, idx);
 }
 
+// Per-simulation scalars and error word (slot g.inst).
+__device__ __forceinline__ double* scal_of(const LrGrid& g, double* scal) { return scal + LR_NSCAL * g.inst; }
+__device__ __forceinline__ int* err_of(const LrGrid& g, int* err) { return err + 2 * g.inst; }
 // dt of the step in flight (scal[5], and dtR in the kernels' type), set by
-// lr_set_tend at each call and by the previous step's finalize.
-__device__ __forceinline__ bool step_live(const double* scal) { return scal[5] > 0.0; }
+// lr_set_tend at each call and by the previous step's finalize; 0 when the
+// simulation is idle (t_end or its step limit reached).
+__device__ __forceinline__ bool step_live(const LrGrid& g, const double* scal) {
+  return scal[LR_NSCAL * g.inst + 5] > 0.0;
+}
 
 // ---------------------------------------------------------------- EOS
 // Stiffened gas of section 5.2: p = (gamma-1) rho e - pi; c^2 = (gamma p + pi)/rho.
@@ -308,18 +314,18 @@ __device__ __forceinline__ int corner_cells(R ddx, R ddy, int i, int j, int& di,
 // div u^2) for div u < 0 (quadratic term read with rho so Q is a pressure).
 // Also the material bitmask and the mixed-cell work list.
 template <class R, int M>
-__global__ void __launch_bounds__(256) lr_cell_pre(LrGrid g, KC<R> kc, LrStateT<R> cur, LrWorkT<R> w) {
+__device__ __forceinline__ void cell_pre_at(const LrGrid& g, const KC<R>& kc, const LrStateT<R>& cur,
+                                            const LrWorkT<R>& w, int i, int j) {
   using O = RealOps<R>;
-  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
   if (i >= g.nx || j >= g.ny) return;
-  if (!step_live(w.scal)) return;
+  if (!step_live(g, w.scal)) return;
   const R Z = O::c(0.0f), ONE = O::c(1.0f);
-  R dt = w.dtR[0];
-  int c = j * g.nx + i;
+  R dt = w.dtR[g.inst];
+  int c = g.coff + j * g.nx + i;
   int nn = g.nx + 1;
   int i1 = (g.perx && i + 1 == g.nx) ? 0 : i + 1;
   int j1 = (g.pery && j + 1 == g.ny) ? 0 : j + 1;
-  int ll = j * nn + i, lr = j * nn + i1, ul = j1 * nn + i, ur = j1 * nn + i1;
+  int ll = g.noff + j * nn + i, lr = g.noff + j * nn + i1, ul = g.noff + j1 * nn + i, ur = g.noff + j1 * nn + i1;
   R uxll = cur.ux[ll], uxlr = cur.ux[lr], uxul = cur.ux[ul], uxur = cur.ux[ur];
   R uyll = cur.uy[ll], uylr = cur.uy[lr], uyul = cur.uy[ul], uyur = cur.uy[ur];
   R kk[M], rr[M], ee[M], pa[M], ir[M];
@@ -338,7 +344,7 @@ __global__ void __launch_bounds__(256) lr_cell_pre(LrGrid g, KC<R> kc, LrStateT<
       R c2 = (kc.gam[a] * pa[a] + kc.pin[a]) * ir[a];
       R wk = kk[a] * kc.invEpsC;
       R wgt = wk < ONE ? wk : ONE;
-      if (!(wk < ONE) && !O::pos(c2)) set_err(w.err, LR_DERR_SOUND, c);
+      if (!(wk < ONE) && !O::pos(c2)) set_err(err_of(g, w.err), LR_DERR_SOUND, c);
       R ca = O::pos(c2) ? O::sqrt(c2) : Z;
       R wc = wgt * ca;
       if (cmax < wc) cmax = wc;
@@ -355,7 +361,7 @@ __global__ void __launch_bounds__(256) lr_cell_pre(LrGrid g, KC<R> kc, LrStateT<
   R h = O::c(0.5f) * dt;
   R vol = cell_F(h * uxll, h * uyll, kc.dx + h * uxlr, h * uylr, h * uxul, kc.dy + h * uyul,
                  kc.dx + h * uxur, kc.dy + h * uyur);
-  if (!O::pos(vol)) set_err(w.err, LR_DERR_VOLUME, c);
+  if (!O::pos(vol)) set_err(err_of(g, w.err), LR_DERR_VOLUME, c);
   R dv = vol - kc.V;
   R vV = kc.V / vol;
   R P = Z;
@@ -377,8 +383,9 @@ __global__ void __launch_bounds__(256) lr_cell_pre(LrGrid g, KC<R> kc, LrStateT<
   w.Pi[c] = P + Q;
   w.mask[c] = (unsigned char)msk;
   if (msk & (msk - 1u)) {  // two or more materials: interface work list
-    unsigned long long slot = atomicAdd(&w.red[2], 1ull);
+    int slot = g.moff + (int)atomicAdd(&w.red[g.mslot], 1ull);
     w.mixed[slot] = c;
+    if (w.minst) w.minst[slot] = g.inst;
   }
 }
 
@@ -387,14 +394,14 @@ __global__ void __launch_bounds__(256) lr_cell_pre(LrGrid g, KC<R> kc, LrStateT<
 // rho_p = (1/4 sum m_c)/(dx dy); u^{lag} = 2 u^{n+1/2} - u^n; node
 // displacement d = dt u^{n+1/2}.  Wall-normal components vanish.
 template <class R>
-__global__ void __launch_bounds__(256) lr_node_half(LrGrid g, KC<R> kc, LrStateT<R> cur, LrWorkT<R> w) {
+__device__ __forceinline__ void node_half_at(const LrGrid& g, const KC<R>& kc, const LrStateT<R>& cur,
+                                             const LrWorkT<R>& w, int i, int j) {
   using O = RealOps<R>;
-  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
   if (i >= g.nxu || j >= g.nyu) return;
-  if (!step_live(w.scal)) return;
+  if (!step_live(g, w.scal)) return;
   const R Z = O::c(0.0f);
-  R dt = w.dtR[0];
-  int n = j * (g.nx + 1) + i;
+  R dt = w.dtR[g.inst];
+  int n = g.noff + j * (g.nx + 1) + i;
   R hx, hy, lx, ly;
   if (g.presc) {
     hx = w.pux[n]; hy = w.puy[n]; lx = hx; ly = hy;
@@ -430,22 +437,23 @@ __global__ void __launch_bounds__(256) lr_node_half(LrGrid g, KC<R> kc, LrStateT
 // (dx_{p+}, Dy + dy_{p+}), dVol = 1/2 (x(y-) + x(y+)) (y+ - y-); the flux
 // region is the rectangle [0, xbar] x [y-, y+].  Y faces swap the axes.
 template <class R, int M>
-__global__ void __launch_bounds__(256) lr_cell_lag(LrGrid g, KC<R> kc, LrStateT<R> cur, LrWorkT<R> w) {
+__device__ __forceinline__ void cell_lag_at(const LrGrid& g, const KC<R>& kc, const LrStateT<R>& cur,
+                                            const LrWorkT<R>& w, int i, int j) {
   using O = RealOps<R>;
-  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
   if (i >= g.nxu || j >= g.nyu) return;
-  if (!step_live(w.scal)) return;
+  if (!step_live(g, w.scal)) return;
   const R Z = O::c(0.0f), H = O::c(0.5f);
   int nn = g.nx + 1;
   int i1 = (g.perx && i + 1 == g.nx) ? 0 : i + 1;
   int j1 = (g.pery && j + 1 == g.ny) ? 0 : j + 1;
+  int nb = g.noff;
   if (i < g.nx && j < g.ny) {
-    int c = j * g.nx + i;
-    int ll = j * nn + i, lr = j * nn + i1, ul = j1 * nn + i, ur = j1 * nn + i1;
+    int c = g.coff + j * g.nx + i;
+    int ll = nb + j * nn + i, lr = nb + j * nn + i1, ul = nb + j1 * nn + i, ur = nb + j1 * nn + i1;
     R dxll = w.ddx[ll], dxlr = w.ddx[lr], dxul = w.ddx[ul], dxur = w.ddx[ur];
     R dyll = w.ddy[ll], dylr = w.ddy[lr], dyul = w.ddy[ul], dyur = w.ddy[ur];
     R vol = cell_F(dxll, dyll, kc.dx + dxlr, dylr, dxul, kc.dy + dyul, kc.dx + dxur, kc.dy + dyur);
-    if (!O::pos(vol)) set_err(w.err, LR_DERR_VOLUME, c);
+    if (!O::pos(vol)) set_err(err_of(g, w.err), LR_DERR_VOLUME, c);
     R dv = vol - kc.V;
     unsigned msk = w.mask[c];
 #pragma unroll
@@ -462,28 +470,28 @@ __global__ void __launch_bounds__(256) lr_cell_lag(LrGrid g, KC<R> kc, LrStateT<
     w.wy[c] = yt - yb;
   }
   if (j < g.ny) {  // X face (i, j), canonical i
-    int pm = j * nn + i, pp = j1 * nn + i;
+    int pm = nb + j * nn + i, pp = nb + j1 * nn + i;
     R ax = w.ddx[pm], ay = w.ddy[pm], bx = w.ddx[pp], dyp = w.ddy[pp], by = kc.dy + dyp;
     R ylo = O::pos(ay) ? ay : Z;
     R yhi = kc.dy + (O::neg(dyp) ? dyp : Z);
-    if (!(ylo < yhi)) set_err(w.err, LR_DERR_GEOM, pm);
+    if (!(ylo < yhi)) set_err(err_of(g, w.err), LR_DERR_GEOM, pm);
     R sl = (bx - ax) / (by - ay);
     R xlo = ax + sl * (ylo - ay), xhi = ax + sl * (yhi - ay);
     R xb = H * (xlo + xhi);
-    int f = j * nn + i;
+    int f = nb + j * nn + i;
     w.fx[f] = xb * (yhi - ylo);
     w.fxb[f] = xb; w.fxlo[f] = ylo; w.fxhi[f] = yhi;
   }
   if (i < g.nx) {  // Y face (i, j), canonical j
-    int pm = j * nn + i, pp = j * nn + i1;
+    int pm = nb + j * nn + i, pp = nb + j * nn + i1;
     R ax = w.ddx[pm], ay = w.ddy[pm], dxp = w.ddx[pp], bx = kc.dx + dxp, by = w.ddy[pp];
     R xlo = O::pos(ax) ? ax : Z;
     R xhi = kc.dx + (O::neg(dxp) ? dxp : Z);
-    if (!(xlo < xhi)) set_err(w.err, LR_DERR_GEOM, pm);
+    if (!(xlo < xhi)) set_err(err_of(g, w.err), LR_DERR_GEOM, pm);
     R sl = (by - ay) / (bx - ax);
     R ylo = ay + sl * (xlo - ax), yhi = ay + sl * (xhi - ax);
     R yb = H * (ylo + yhi);
-    int f = j * g.nx + i;
+    int f = nb + j * g.nx + i;
     w.fy[f] = yb * (xhi - xlo);
     w.fyb[f] = yb; w.fylo[f] = xlo; w.fyhi[f] = xhi;
   }
@@ -493,12 +501,12 @@ __global__ void __launch_bounds__(256) lr_cell_lag(LrGrid g, KC<R> kc, LrStateT<
 // and one receiver, Vol^{lagCF} = dx dy - received + donated) and
 // rho_a^{lagCF} = rho_a V / Vol^{lagCF} for every cell.
 template <class R, int M>
-__global__ void __launch_bounds__(256) lr_cell_cf(LrGrid g, KC<R> kc, LrStateT<R> cur, LrWorkT<R> w) {
+__device__ __forceinline__ void cell_cf_at(const LrGrid& g, const KC<R>& kc, const LrStateT<R>& cur,
+                                           const LrWorkT<R>& w, int i, int j) {
   using O = RealOps<R>;
-  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
   if (i >= g.nx || j >= g.ny) return;
-  if (!step_live(w.scal)) return;
-  int c = j * g.nx + i;
+  if (!step_live(g, w.scal)) return;
+  int c = g.coff + j * g.nx + i;
   int fl = xix(g, i, j).idx, fr = xix(g, i + 1, j).idx;
   int fb = yix(g, i, j).idx, ft = yix(g, i, j + 1).idx;
   R v = kc.V + w.fx[fr] - w.fx[fl] + w.fy[ft] - w.fy[fb];
@@ -513,7 +521,7 @@ __global__ void __launch_bounds__(256) lr_cell_cf(LrGrid g, KC<R> kc, LrStateT<R
     if (di == i && dj == j) v += f;
     if (ri == i && rj == j) v -= f;
   }
-  if (!O::pos(v)) set_err(w.err, LR_DERR_VOLUME, c);
+  if (!O::pos(v)) set_err(err_of(g, w.err), LR_DERR_VOLUME, c);
   w.vcf[c] = v;
   unsigned msk = w.mask[c];
   R vV = kc.V / v;
@@ -595,30 +603,19 @@ __device__ __forceinline__ int donated_flux(const LrGrid& g, const LrWorkT<R>& w
 // the rectangular Lagrangian cell (sections 4.1 and 4.4; three materials by
 // nested cuts in material order), the split of every flux the cell donates,
 // and the clipping of a material's outgoing volume to what it holds (excess
-// to the dominant material).  g.mixed_lanes = L lanes (1, 2, 4 or 8) work on
-// one cell: all place the interface, lane l splits fluxes l, l+L, ...; the
+// to the dominant material).  L lanes (1, 2, 4 or 8) work on one cell: all
+// place the interface, lane l splits fluxes 8l/L .. 8(l+1)/L - 1; the
 // outgoing volumes per material are summed across the L lanes with shuffles.
 // More lanes hide more latency (the list is short) but repeat the interface
 // placement L times per warp instruction, so L is chosen per arithmetic.
 // Splits are stored unclipped; the rare cell whose material runs short
 // rescales its own stored splits in a second pass.
 template <class R, int M>
-__global__ void __launch_bounds__(128) lr_mixed(LrGrid g, LrStateT<R> cur, LrWorkT<R> w) {
+__device__ __forceinline__ void mixed_at(const LrGrid& g, const LrStateT<R>& cur, const LrWorkT<R>& w, int c,
+                                         bool valid, int lane, int L) {
   using O = RealOps<R>;
-  if (!step_live(w.scal)) return;
-  int count = (int)w.red[2];
-  const int L = g.mixed_lanes, lg = __ffs(L) - 1;
-  int lane = threadIdx.x & (L - 1);
-  int group = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> lg);
-  int ngroups = (int)((gridDim.x * blockDim.x) >> lg);
-  int wmask = (32 >> lg) - 1;   // groups per warp - 1
-  for (int k = 0;; ++k) {
-    int tw = (group & ~wmask) + k * ngroups;   // first group of this warp: the warp iterates together
-    if (tw >= count) break;
-    int t = group + k * ngroups;
-    bool valid = t < count;
-    int c = w.mixed[valid ? t : 0];
-    int i = c % g.nx, j = c / g.nx;
+  {
+    int i = (c - g.coff) % g.nx, j = (c - g.coff) / g.nx;
     double v = O::todouble(w.vcf[c]);
     double kk[M];
     int np = 0, order[LR_MAXM] = {0, 0, 0}, dom = 0;
@@ -657,24 +654,44 @@ __global__ void __launch_bounds__(128) lr_mixed(LrGrid g, LrStateT<R> cur, LrWor
       w.cut[0][c] = cut[0][0]; w.cut[1][c] = cut[0][1]; w.cut[2][c] = cut[0][2];
       if (ncut == 2) { w.cut[3][c] = cut[1][0]; w.cut[4][c] = cut[1][1]; w.cut[5][c] = cut[1][2]; }
     }
-    // ---- this lane's fluxes: split and store, summing the outgoing volumes
-    double o[M];
+    // ---- this lane's fluxes K lane .. K lane + K - 1 (K = 8 / L): split and
+    // store.  Their outgoing volumes are summed in the fixed pairwise order
+    // ((0+1)+(2+3))+((4+5)+(6+7)) of the eight fluxes -- the lane's block
+    // here, the blocks of the L lanes by the shuffles below -- so the sum and
+    // the clipping do not depend on L (absent fluxes count as +0).
+    const int K = 8 / L;
+    double p1[M], p2[M], p3[M], p4[M];
 #pragma unroll
-    for (int a = 0; a < M; ++a) o[a] = 0.0;
-    for (int l = lane; l < 8; l += L) {
-      double r[4], vol;
+    for (int a = 0; a < M; ++a) { p1[a] = 0.0; p2[a] = 0.0; p3[a] = 0.0; p4[a] = 0.0; }
+    for (int q = 0; q < K; ++q) {
+      double r[4], vol, A[M];
       int fidx = 0;
-      int kind = valid ? donated_flux(g, w, i, j, l, r, vol, fidx) : -1;
-      if (kind < 0) continue;
-      double A[M];
-      split_region<M>(ncut, order, cut, r, vol, A);
+      int kind = valid ? donated_flux(g, w, i, j, lane * K + q, r, vol, fidx) : -1;
+      if (kind >= 0) {
+        split_region<M>(ncut, order, cut, r, vol, A);
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+          R* dst = kind == 0 ? w.xAm[a] : kind == 1 ? w.yAm[a] : w.cAm[a];
+          dst[fidx] = from_double<R>(A[a]);
+        }
+      } else {
+#pragma unroll
+        for (int a = 0; a < M; ++a) A[a] = 0.0;
+      }
 #pragma unroll
       for (int a = 0; a < M; ++a) {
-        o[a] += A[a];
-        R* dst = kind == 0 ? w.xAm[a] : kind == 1 ? w.yAm[a] : w.cAm[a];
-        dst[fidx] = from_double<R>(A[a]);
+        double v = A[a];
+        if (!(q & 1)) { p1[a] = v; continue; }
+        v = p1[a] + v;
+        if (!(q & 2)) { p2[a] = v; continue; }
+        v = p2[a] + v;
+        if (!(q & 4)) { p3[a] = v; continue; }
+        p4[a] = p3[a] + v;
       }
     }
+    double o[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) o[a] = K == 1 ? p1[a] : K == 2 ? p2[a] : K == 4 ? p3[a] : p4[a];
     // ---- clipping: outgoing volume per material over the L lanes
     double sc[M];
     bool clip = false;
@@ -686,11 +703,11 @@ __global__ void __launch_bounds__(128) lr_mixed(LrGrid g, LrStateT<R> cur, LrWor
       double avail = kk[a] * v;
       if (o[a] > avail) { sc[a] = avail / o[a]; clip = true; }
     }
-    if (!(valid && clip)) continue;
-    for (int l = lane; l < 8; l += L) {
+    if (!(valid && clip)) return;
+    for (int q = 0; q < K; ++q) {
       double r[4], vol;
       int fidx = 0;
-      int kind = donated_flux(g, w, i, j, l, r, vol, fidx);
+      int kind = donated_flux(g, w, i, j, lane * K + q, r, vol, fidx);
       if (kind < 0) continue;
       double A[M], moved = 0.0;
 #pragma unroll
@@ -706,6 +723,29 @@ __global__ void __launch_bounds__(128) lr_mixed(LrGrid g, LrStateT<R> cur, LrWor
         dst[fidx] = from_double<R>(A[a]);
       }
     }
+  }
+}
+
+// Work distribution over a mixed-cell list (count in red[mslot], entries at
+// w.mixed[moff ..]): groups of L lanes take one entry each, a warp's groups
+// iterate together so the shuffles in mixed_at see the whole warp.  getg(e)
+// gives the grid of entry e.
+template <class R, int M, class G>
+__device__ __forceinline__ void mixed_loop(G getg, const LrStateT<R>& cur, const LrWorkT<R>& w, int L, int mslot,
+                                           int moff) {
+  int count = (int)w.red[mslot];
+  int lg = __ffs(L) - 1;
+  int lane = threadIdx.x & (L - 1);
+  int group = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> lg);
+  int ngroups = (int)((gridDim.x * blockDim.x) >> lg);
+  int wmask = (32 >> lg) - 1;   // groups per warp - 1
+  for (int k = 0;; ++k) {
+    int tw = (group & ~wmask) + k * ngroups;   // first group of this warp
+    if (tw >= count) break;
+    int t = group + k * ngroups;
+    bool valid = t < count;
+    int e = moff + (valid ? t : 0);
+    mixed_at<R, M>(getg(e), cur, w, w.mixed[e], valid, lane, L);
   }
 }
 
@@ -785,18 +825,18 @@ __device__ __forceinline__ R recon_corner(const LrGrid& g, const KC<R>& kc, cons
 // total mass fluxes the dual remap needs.  Materials absent from the donor
 // get stored zeros, no arithmetic.
 template <class R, int M>
-__global__ void __launch_bounds__(256) lr_mat_flux(LrGrid g, KC<R> kc, LrStateT<R> cur, LrWorkT<R> w) {
+__device__ __forceinline__ void mat_flux_at(const LrGrid& g, const KC<R>& kc, const LrStateT<R>& cur,
+                                            const LrWorkT<R>& w, int i, int j) {
   using O = RealOps<R>;
-  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
   if (i >= g.nxu || j >= g.nyu) return;
-  if (!step_live(w.scal)) return;
+  if (!step_live(g, w.scal)) return;
   const R Z = O::c(0.0f), H = O::c(0.5f), ONE = O::c(1.0f);
-  int nn = g.nx + 1;
+  int nn = g.nx + 1, nb = g.noff;
   int j1 = (g.pery && j + 1 == g.ny) ? 0 : j + 1;
   int i1 = (g.perx && i + 1 == g.nx) ? 0 : i + 1;
   // ---- X face (i, j)
   if (j < g.ny) {
-    int f = j * nn + i;
+    int f = nb + j * nn + i;
     R v = w.fx[f];
     R mt = Z;
     unsigned dm = 0u;
@@ -807,7 +847,7 @@ __global__ void __launch_bounds__(256) lr_mat_flux(LrGrid g, KC<R> kc, LrStateT<
       di = left ? i - 1 : i;
       dc = cix(g, di, j).idx;
       dm = w.mask[dc];
-      fd = H * (w.ddx[j * nn + i] + w.ddx[j1 * nn + i]);
+      fd = H * (w.ddx[nb + j * nn + i] + w.ddx[nb + j1 * nn + i]);
     }
     bool mixed = (dm & (dm - 1u)) != 0u;
 #pragma unroll
@@ -835,7 +875,7 @@ __global__ void __launch_bounds__(256) lr_mat_flux(LrGrid g, KC<R> kc, LrStateT<
   }
   // ---- Y face (i, j)
   if (i < g.nx) {
-    int f = j * g.nx + i;
+    int f = nb + j * g.nx + i;
     R v = w.fy[f];
     R mt = Z;
     unsigned dm = 0u;
@@ -846,7 +886,7 @@ __global__ void __launch_bounds__(256) lr_mat_flux(LrGrid g, KC<R> kc, LrStateT<
       dj = below ? j - 1 : j;
       dc = cix(g, i, dj).idx;
       dm = w.mask[dc];
-      fd = H * (w.ddy[j * nn + i] + w.ddy[j * nn + i1]);
+      fd = H * (w.ddy[nb + j * nn + i] + w.ddy[nb + j * nn + i1]);
     }
     bool mixed = (dm & (dm - 1u)) != 0u;
 #pragma unroll
@@ -874,7 +914,7 @@ __global__ void __launch_bounds__(256) lr_mat_flux(LrGrid g, KC<R> kc, LrStateT<
   }
   // ---- corner at node (i, j)
   {
-    int n = j * nn + i;
+    int n = nb + j * nn + i;
     R ddx = w.ddx[n], ddy = w.ddy[n];
     R mt = Z;
     int di = 0, dj = 0, ri, rj, dc = 0, sj = 1;
@@ -923,13 +963,12 @@ __global__ void __launch_bounds__(256) lr_mat_flux(LrGrid g, KC<R> kc, LrStateT<
 // CFL rule of the next step.  Only materials present in the cell's 3x3
 // neighbourhood (its possible donors) are accumulated.
 template <class R, int M>
-__global__ void __launch_bounds__(256) lr_cell_update(LrGrid g, KC<R> kc, LrStateT<R> cur, LrStateT<R> nxt,
-                                                      LrWorkT<R> w) {
+__device__ __forceinline__ void cell_update_at(const LrGrid& g, const KC<R>& kc, const LrStateT<R>& cur,
+                                               const LrStateT<R>& nxt, const LrWorkT<R>& w, int i, int j) {
   using O = RealOps<R>;
-  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
   if (i >= g.nx || j >= g.ny) return;
-  int c = j * g.nx + i;
-  if (!step_live(w.scal)) {
+  int c = g.coff + j * g.nx + i;
+  if (!step_live(g, w.scal)) {
 #pragma unroll
     for (int a = 0; a < M; ++a) { nxt.k[a][c] = cur.k[a][c]; nxt.r[a][c] = cur.r[a][c]; nxt.e[a][c] = cur.e[a][c]; }
     return;
@@ -997,7 +1036,7 @@ __global__ void __launch_bounds__(256) lr_cell_update(LrGrid g, KC<R> kc, LrStat
       le += ene[a];
     }
   }
-  if (big < 0) { set_err(w.err, LR_DERR_VOLUME, c); big = 0; tot = ONE; }
+  if (big < 0) { set_err(err_of(g, w.err), LR_DERR_VOLUME, c); big = 0; tot = ONE; }
 #pragma unroll
   for (int a = 0; a < M; ++a) {
     if (a == big) { mas[a] += lm; ene[a] += le; }
@@ -1008,7 +1047,7 @@ __global__ void __launch_bounds__(256) lr_cell_update(LrGrid g, KC<R> kc, LrStat
     R ka = Z, ra = Z, ea = Z;
     if (keep[a]) {
       ka = nkeep == 1 ? ONE : vol[a] / tot;
-      if (!O::pos(mas[a])) set_err(w.err, LR_DERR_MASS, c);
+      if (!O::pos(mas[a])) set_err(err_of(g, w.err), LR_DERR_MASS, c);
       R im = O::rcp(mas[a]);
       R kV = ka * kc.V;
       ra = nkeep == 1 ? mas[a] * kc.invV : mas[a] / kV;
@@ -1017,11 +1056,11 @@ __global__ void __launch_bounds__(256) lr_cell_update(LrGrid g, KC<R> kc, LrStat
       R c2 = (kc.gam[a] * pa + kc.pin[a]) * (kV * im);
       R wk = ka * kc.invEpsC;
       R wgt = wk < ONE ? wk : ONE;
-      if (!(wk < ONE) && !O::pos(c2)) set_err(w.err, LR_DERR_SOUND, c);
+      if (!(wk < ONE) && !O::pos(c2)) set_err(err_of(g, w.err), LR_DERR_SOUND, c);
       R ca = O::pos(c2) ? O::sqrt(c2) : Z;
       R wc = wgt * ca;
       if (cmax < wc) cmax = wc;
-      if (!O::finite(ra) || !O::finite(ea)) set_err(w.err, LR_DERR_NAN, c);
+      if (!O::finite(ra) || !O::finite(ea)) set_err(err_of(g, w.err), LR_DERR_NAN, c);
     }
     nxt.k[a][c] = ka; nxt.r[a][c] = ra; nxt.e[a][c] = ea;
   }
@@ -1055,17 +1094,16 @@ __device__ __forceinline__ R recon_dual_face(const LrGrid& g, const KC<R>& kc, c
 // on the dual mesh.  Objects just outside reflective walls are evaluated from
 // the mirrored data, so every boundary node sees a full dual cell.
 template <class R>
-__global__ void __launch_bounds__(256) lr_dual_flux(LrGrid g, KC<R> kc, LrWorkT<R> w) {
+__device__ __forceinline__ void dual_flux_at(const LrGrid& g, const KC<R>& kc, const LrWorkT<R>& w, int i, int j) {
   using O = RealOps<R>;
-  int i = (int)(blockIdx.x * BX + threadIdx.x) - 1, j = (int)(blockIdx.y * BY + threadIdx.y) - 1;
   if (i > g.nx || j > g.ny) return;
-  if (!step_live(w.scal)) return;
+  if (!step_live(g, w.scal)) return;
   const R Z = O::c(0.0f), H = O::c(0.5f), Q4 = O::c(0.25f), ONE = O::c(1.0f);
   bool xdual = g.perx ? (i >= 0 && i < g.nx) : true;   // dual index range in x
   bool ydual = g.pery ? (j >= 0 && j < g.ny) : true;
   bool xnode = i >= 0 && i < g.nxu;                     // canonical node in x
   bool ynode = j >= 0 && j < g.nyu;
-  int o = (j + 1) * (g.nx + 2) + (i + 1);
+  int o = g.doff + (j + 1) * (g.nx + 2) + (i + 1);
   auto MXr = [&](int a, int b) { Ix q = xix(g, a, b); R v = w.MX[q.idx]; return q.fx ? -v : v; };
   auto MYr = [&](int a, int b) { Ix q = yix(g, a, b); R v = w.MY[q.idx]; return q.fy ? -v : v; };
   auto CPr = [&](int a, int b, R& pp, R& pm) {
@@ -1178,15 +1216,19 @@ template <> struct Key<df64> {
 template <class R>
 __device__ __forceinline__ R key_max(R a, R b) { return a < b ? b : a; }
 
-// Block-wide max of v >= 0 folded into red[0]; the last block turns it into
-// the CFL time step (dt = cfl min(dx,dy) / max), advances t by the step just
-// taken when `advance`, and publishes the next step's dt capped at t_end.
+// Block-wide max of v >= 0 folded into the simulation's CFL key; the last of
+// its `ntiles` blocks (tiles) turns it into the CFL time step (dt = cfl
+// min(dx,dy) / max), advances t by the step just taken when `advance`, and
+// publishes the next step's dt, capped at t_end and 0 once the step limit
+// is reached.
 template <class R>
-__device__ void cfl_finalize(const LrGrid& g, const KC<R>& kc, const LrWorkT<R>& w, R v, bool advance) {
+__device__ void cfl_finalize(const LrGrid& g, const KC<R>& kc, const LrWorkT<R>& w, R v, bool advance,
+                             unsigned long long ntiles) {
   using O = RealOps<R>;
   __shared__ unsigned long long sm[32];
   __shared__ int last;
   int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  unsigned long long* red = w.red + LR_RED_INST + 2 * g.inst;
   unsigned long long key = Key<R>::enc(v);
   for (int off = 16; off > 0; off >>= 1) {
     unsigned long long o = __shfl_xor_sync(0xffffffffu, key, off);
@@ -1202,31 +1244,34 @@ __device__ void cfl_finalize(const LrGrid& g, const KC<R>& kc, const LrWorkT<R>&
       x = o > x ? o : x;
     }
     if (tid == 0) {
-      atomicMax(&w.red[0], x);
+      atomicMax(&red[0], x);
       __threadfence();
-      unsigned long long nb = (unsigned long long)gridDim.x * gridDim.y;
-      unsigned long long prev = atomicAdd(&w.red[1], 1ull);
-      last = prev == nb - 1;
+      unsigned long long prev = atomicAdd(&red[1], 1ull);
+      last = prev == ntiles - 1;
     }
   }
   __syncthreads();
   if (last && tid == 0) {
     __threadfence();
-    R mx = Key<R>::dec(atomicAdd(&w.red[0], 0ull));
+    double* sc = scal_of(g, w.scal);
+    R mx = Key<R>::dec(atomicAdd(&red[0], 0ull));
     double dtc = O::pos(mx) ? O::todouble(kc.cfl * (kc.hmin / mx)) : g.cfl * 1e300;
-    double t = w.scal[0];
-    if (advance) { t = t + w.scal[5]; w.scal[2] = w.scal[5]; w.scal[4] += 1.0; }
-    w.scal[0] = t;
-    w.scal[1] = dtc;
+    double t = sc[0];
+    if (advance) { t = t + sc[5]; sc[2] = sc[5]; sc[4] += 1.0; }
+    sc[0] = t;
+    sc[1] = dtc;
     double dn = g.dt_fixed > 0.0 ? g.dt_fixed : dtc;
-    if (w.scal[3] - t < dn) dn = w.scal[3] - t;
+    if (sc[3] - t < dn) dn = sc[3] - t;
+    if (sc[7] > 0.0 && sc[4] >= sc[7]) dn = 0.0;
     dn = dn > 0.0 ? dn : 0.0;
-    w.scal[5] = dn;
-    w.dtR[0] = from_double<R>(dn);
-    if (advance) w.scal[6] = (double)w.red[2];
-    w.red[0] = 0ull;
-    w.red[1] = 0ull;
-    w.red[2] = 0ull;
+    sc[5] = dn;
+    w.dtR[g.inst] = from_double<R>(dn);
+    if (advance) sc[6] = (double)w.red[g.mslot];
+    red[0] = 0ull;
+    red[1] = 0ull;
+    // the list is consumed (lr_mixed ran before this kernel); every
+    // simulation of a group clears it, the next step's lr_cell_pre refills it
+    w.red[g.mslot] = 0ull;
   }
 }
 
@@ -1237,20 +1282,20 @@ __device__ void cfl_finalize(const LrGrid& g, const KC<R>& kc, const LrWorkT<R>&
 // cells of c_c + |u_p|), which equals the per-cell form
 // min_c min(dx,dy)/(c_c + max_{p in c} |u_p|).
 template <class R>
-__global__ void __launch_bounds__(256) lr_node_update(LrGrid g, KC<R> kc, LrStateT<R> cur, LrStateT<R> nxt,
-                                                      LrWorkT<R> w) {
+__device__ __forceinline__ void node_update_at(const LrGrid& g, const KC<R>& kc, const LrStateT<R>& cur,
+                                               const LrStateT<R>& nxt, const LrWorkT<R>& w, int i, int j,
+                                               unsigned long long ntiles) {
   using O = RealOps<R>;
-  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
   bool act = i < g.nxu && j < g.nyu;
-  if (!step_live(w.scal)) {
-    if (act) { int n = j * (g.nx + 1) + i; nxt.ux[n] = cur.ux[n]; nxt.uy[n] = cur.uy[n]; }
-    if (i == 0 && j == 0) w.scal[2] = 0.0;
+  if (!step_live(g, w.scal)) {  // uniform over the block: one simulation per tile
+    if (act) { int n = g.noff + j * (g.nx + 1) + i; nxt.ux[n] = cur.ux[n]; nxt.uy[n] = cur.uy[n]; }
+    if (i == 0 && j == 0) scal_of(g, w.scal)[2] = 0.0;
     return;
   }
   const R Z = O::c(0.0f);
   R val = Z;
   if (act) {
-    int n = j * (g.nx + 1) + i;
+    int n = g.noff + j * (g.nx + 1) + i;
     R ux1, uy1;
     if (g.presc) {
       ux1 = w.pux[n]; uy1 = w.puy[n];
@@ -1266,11 +1311,11 @@ __global__ void __launch_bounds__(256) lr_node_update(LrGrid g, KC<R> kc, LrStat
       mnew += (w.dPP[0][c1] - w.dPP[0][c0]) + (w.dPM[0][c3] - w.dPM[0][c2]);
       px += (w.dPP[1][c1] - w.dPP[1][c0]) + (w.dPM[1][c3] - w.dPM[1][c2]);
       py += (w.dPP[2][c1] - w.dPP[2][c0]) + (w.dPM[2][c3] - w.dPM[2][c2]);
-      if (!O::pos(mnew)) set_err(w.err, LR_DERR_MASS, n);
+      if (!O::pos(mnew)) set_err(err_of(g, w.err), LR_DERR_MASS, n);
       R im = O::rcp(mnew);
       ux1 = px * im;
       uy1 = py * im;
-      if (!O::finite(ux1) || !O::finite(uy1)) set_err(w.err, LR_DERR_NAN, n);
+      if (!O::finite(ux1) || !O::finite(uy1)) set_err(err_of(g, w.err), LR_DERR_NAN, n);
     }
     if (!g.perx && (i == 0 || i == g.nx)) ux1 = Z;
     if (!g.pery && (j == 0 || j == g.ny)) uy1 = Z;
@@ -1280,53 +1325,53 @@ __global__ void __launch_bounds__(256) lr_node_update(LrGrid g, KC<R> kc, LrStat
                 rmax(w.cc[cix(g, i - 1, j).idx], w.cc[cix(g, i, j).idx]));
     val = cm + O::sqrt(ux1 * ux1 + uy1 * uy1);
   }
-  cfl_finalize(g, kc, w, val, true);
+  cfl_finalize(g, kc, w, val, true, ntiles);
 }
 
 // CFL rule from the current state only (after lr_init).
 template <class R>
-__global__ void __launch_bounds__(256) lr_cfl_only(LrGrid g, KC<R> kc, LrStateT<R> cur, LrWorkT<R> w) {
+__device__ __forceinline__ void cfl_only_at(const LrGrid& g, const KC<R>& kc, const LrStateT<R>& cur,
+                                            const LrWorkT<R>& w, int i, int j, unsigned long long ntiles) {
   using O = RealOps<R>;
-  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
   R val = O::c(0.0f);
   if (i < g.nxu && j < g.nyu) {
-    int n = j * (g.nx + 1) + i;
+    int n = g.noff + j * (g.nx + 1) + i;
     R ux1 = cur.ux[n], uy1 = cur.uy[n];
     R cm = rmax(rmax(w.cc[cix(g, i - 1, j - 1).idx], w.cc[cix(g, i, j - 1).idx]),
                 rmax(w.cc[cix(g, i - 1, j).idx], w.cc[cix(g, i, j).idx]));
     val = cm + O::sqrt(ux1 * ux1 + uy1 * uy1);
   }
-  cfl_finalize(g, kc, w, val, false);
+  cfl_finalize(g, kc, w, val, false, ntiles);
 }
 
 // Initial state from the staging area (doubles k, rho, p, ux, uy): drop
 // materials with k <= EPS_K, renormalise, e = (p + pi)/((gamma-1) rho) in
 // double, store in the step's type, sound speed, zero wall-normal velocity.
 template <class R, int M>
-__global__ void __launch_bounds__(256) lr_prepare(LrGrid g, KC<R> kc, LrStateT<R> st, LrWorkT<R> w) {
+__device__ __forceinline__ void prepare_at(const LrGrid& g, const KC<R>& kc, const LrStateT<R>& st,
+                                           const LrWorkT<R>& w, int i, int j) {
   using O = RealOps<R>;
-  int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
   size_t nc = (size_t)g.nx * g.ny, nn = (size_t)(g.nx + 1) * (g.ny + 1);
-  const double* sk = w.stage;
-  const double* sr = w.stage + (size_t)M * nc;
-  const double* sp = w.stage + (size_t)2 * M * nc;
-  const double* sux = w.stage + (size_t)3 * M * nc;
+  const double* sk = w.stage + g.stoff;
+  const double* sr = sk + (size_t)M * nc;
+  const double* sp = sk + (size_t)2 * M * nc;
+  const double* sux = sk + (size_t)3 * M * nc;
   const double* suy = sux + nn;
   if (i <= g.nx && j <= g.ny) {
-    int n = j * (g.nx + 1) + i;
-    double ux = sux[n], uy = suy[n];
+    int ln = j * (g.nx + 1) + i, n = g.noff + ln;
+    double ux = sux[ln], uy = suy[ln];
     if (!g.perx && (i == 0 || i == g.nx)) ux = 0.0;
     if (!g.pery && (j == 0 || j == g.ny)) uy = 0.0;
     st.ux[n] = from_double<R>(ux);
     st.uy[n] = from_double<R>(uy);
   }
   if (i >= g.nx || j >= g.ny) return;
-  int c = j * g.nx + i;
+  int lc = j * g.nx + i, c = g.coff + lc;
   double sum = 0.0, kept = 0.0;
   bool bad = false;
 #pragma unroll
   for (int a = 0; a < M; ++a) {
-    double ka = sk[a * nc + c];
+    double ka = sk[a * nc + lc];
     if (!(ka >= -1e-12 && ka <= 1.0 + 1e-12)) bad = true;
     sum += ka;
     if (ka > EPS_K) kept += ka;
@@ -1335,9 +1380,9 @@ __global__ void __launch_bounds__(256) lr_prepare(LrGrid g, KC<R> kc, LrStateT<R
   R cmax = O::c(0.0f);
 #pragma unroll
   for (int a = 0; a < M; ++a) {
-    double ka = sk[a * nc + c];
+    double ka = sk[a * nc + lc];
     if (ka > EPS_K && !bad) {
-      double ra = sr[a * nc + c], pa = sp[a * nc + c];
+      double ra = sr[a * nc + lc], pa = sp[a * nc + lc];
       if (!(ra > 0.0)) bad = true;
       double kn = ka / kept;
       double ea = (pa + g.pin[a]) / ((g.gam[a] - 1.0) * ra);
@@ -1354,24 +1399,22 @@ __global__ void __launch_bounds__(256) lr_prepare(LrGrid g, KC<R> kc, LrStateT<R
       st.k[a][c] = O::c(0.0f); st.r[a][c] = O::c(0.0f); st.e[a][c] = O::c(0.0f);
     }
   }
-  if (bad) set_err(w.err, LR_DERR_MASS, c);
+  if (bad) set_err(err_of(g, w.err), LR_DERR_MASS, c);
   w.cc[c] = cmax;
 }
 
 // t_end of this call and the dt of the next step (one thread).
 template <class R>
 __global__ void lr_set_tend_k(LrGrid g, LrWorkT<R> w, double t_end) {
-  w.scal[3] = t_end;
-  double t = w.scal[0];
-  double dn = g.dt_fixed > 0.0 ? g.dt_fixed : w.scal[1];
+  double* sc = scal_of(g, w.scal);
+  sc[3] = t_end;
+  double t = sc[0];
+  double dn = g.dt_fixed > 0.0 ? g.dt_fixed : sc[1];
   if (t_end - t < dn) dn = t_end - t;
+  if (sc[7] > 0.0 && sc[4] >= sc[7]) dn = 0.0;
   dn = dn > 0.0 ? dn : 0.0;
-  w.scal[5] = dn;
-  w.dtR[0] = from_double<R>(dn);
-}
-__global__ void lr_reset_k(LrWork w) {
-  w.red[0] = 0ull; w.red[1] = 0ull; w.red[2] = 0ull; w.err[0] = 0; w.err[1] = -1;
-  for (int q = 0; q < 8; ++q) w.scal[q] = 0.0;
+  sc[5] = dn;
+  w.dtR[g.inst] = from_double<R>(dn);
 }
 
 // Field views (to double, with the boundary mapping for canonical storage).
@@ -1496,6 +1539,109 @@ __global__ void lr_from_double_k(const double* src, R* dst, size_t n) {
   if (t < n) dst[t] = from_double<R>(src[t]);
 }
 
+// ============================================================ launch forms
+// Every body above works on one point (i, j) of its kernel's iteration
+// domain.  A lone simulation maps a 2D grid of BX x BY blocks onto that
+// domain; a batch runs a 1D grid whose blocks each walk a contiguous run of
+// a tile table (one block per tile, or persistent blocks with several
+// tiles; one simulation per tile, the block shape being the table's tile
+// shape), reading the simulation's grid and constants from device arrays.
+#define LR_OP(NAME, CALL)                                                                                 \
+  struct NAME {                                                                                           \
+    template <class R, int M>                                                                             \
+    __device__ static __forceinline__ void at(const LrGrid& g, const KC<R>& kc, const LrStateT<R>& cur,    \
+                                              const LrStateT<R>& nxt, const LrWorkT<R>& w, int i, int j,  \
+                                              unsigned long long nt) {                                    \
+      CALL;                                                                                               \
+    }                                                                                                     \
+  };
+LR_OP(OpCellPre, (cell_pre_at<R, M>(g, kc, cur, w, i, j)))
+LR_OP(OpNodeHalf, (node_half_at<R>(g, kc, cur, w, i, j)))
+LR_OP(OpCellLag, (cell_lag_at<R, M>(g, kc, cur, w, i, j)))
+LR_OP(OpCellCf, (cell_cf_at<R, M>(g, kc, cur, w, i, j)))
+LR_OP(OpMatFlux, (mat_flux_at<R, M>(g, kc, cur, w, i, j)))
+LR_OP(OpCellUpdate, (cell_update_at<R, M>(g, kc, cur, nxt, w, i, j)))
+LR_OP(OpDualFlux, (dual_flux_at<R>(g, kc, w, i - 1, j - 1)))
+LR_OP(OpNodeUpdate, (node_update_at<R>(g, kc, cur, nxt, w, i, j, nt)))
+LR_OP(OpCflOnly, (cfl_only_at<R>(g, kc, cur, w, i, j, nt)))
+LR_OP(OpPrepare, (prepare_at<R, M>(g, kc, cur, w, i, j)))
+#undef LR_OP
+
+// A batched block copies its tile's grid and constants into shared memory
+// (one coalesced load of a few hundred bytes, skipped while consecutive
+// tiles belong to the same simulation) and the body reads them from there,
+// instead of every thread loading each field it uses from global memory.
+template <class R>
+struct Staged {
+  static constexpr int NG = (int)(sizeof(LrGrid) / 4), NK = (int)(sizeof(KC<R>) / 4);
+  alignas(16) unsigned int gw[NG];   // 16-byte aligned: the descriptors hold doubles
+  alignas(16) unsigned int kw[NK];
+  __device__ __forceinline__ void load(const LrGrid* g, const KC<R>* kc) {
+    int tid = threadIdx.y * blockDim.x + threadIdx.x, nthr = blockDim.x * blockDim.y;
+    const unsigned int* ga = reinterpret_cast<const unsigned int*>(g);
+    const unsigned int* ka = reinterpret_cast<const unsigned int*>(kc);
+    for (int q = tid; q < NG + NK; q += nthr) {
+      if (q < NG) gw[q] = __ldg(ga + q);
+      else kw[q - NG] = __ldg(ka + (q - NG));
+    }
+    __syncthreads();
+  }
+  __device__ __forceinline__ const LrGrid& g() const { return *reinterpret_cast<const LrGrid*>(gw); }
+  __device__ __forceinline__ const KC<R>& kc() const { return *reinterpret_cast<const KC<R>*>(kw); }
+};
+static_assert(sizeof(LrGrid) % 8 == 0 && alignof(LrGrid) <= 16, "grid descriptor copied in words");
+static_assert(sizeof(KC<float>) % 4 == 0 && sizeof(KC<double>) % 8 == 0 && sizeof(KC<df64>) % 8 == 0 &&
+              alignof(KC<double>) <= 16 && alignof(KC<df64>) <= 16, "constants copied in words");
+
+#define LR_KERNEL_PAIR(NAME, OP)                                                                          \
+  template <class R, int M>                                                                               \
+  __global__ void __launch_bounds__(256) lr_##NAME(LrGrid g, KC<R> kc, LrStateT<R> cur, LrStateT<R> nxt,  \
+                                                   LrWorkT<R> w) {                                        \
+    OP::template at<R, M>(g, kc, cur, nxt, w, blockIdx.x * BX + threadIdx.x, blockIdx.y * BY + threadIdx.y, \
+                          (unsigned long long)gridDim.x * gridDim.y);                                     \
+  }                                                                                                       \
+  template <class R, int M>                                                                               \
+  __global__ void __launch_bounds__(256) lb_##NAME(const LrGrid* __restrict__ gs, const KC<R>* __restrict__ kcs, \
+                                                   const LrTile* __restrict__ tl, int nt, LrStateT<R> cur,   \
+                                                   LrStateT<R> nxt, LrWorkT<R> w) {                         \
+    __shared__ Staged<R> sd;                                                                              \
+    int staged = -1;                                                                                      \
+    int per = (nt + (int)gridDim.x - 1) / (int)gridDim.x;  /* a contiguous run of tiles per block */      \
+    int t1 = min(nt, ((int)blockIdx.x + 1) * per);                                                        \
+    for (int t = (int)blockIdx.x * per; t < t1; ++t) {                                                    \
+      LrTile T = tl[t];                                                                                   \
+      if (T.inst != staged) {  /* uniform: a tile belongs to one simulation */                            \
+        if (staged >= 0) __syncthreads();                                                                 \
+        sd.load(gs + T.inst, kcs + T.inst);                                                               \
+        staged = T.inst;                                                                                  \
+      }                                                                                                   \
+      OP::template at<R, M>(sd.g(), sd.kc(), cur, nxt, w, T.i0 + (int)threadIdx.x,                       \
+                            T.j0 + (int)threadIdx.y, (unsigned long long)T.n);                            \
+    }                                                                                                     \
+  }
+LR_KERNEL_PAIR(cell_pre, OpCellPre)
+LR_KERNEL_PAIR(node_half, OpNodeHalf)
+LR_KERNEL_PAIR(cell_lag, OpCellLag)
+LR_KERNEL_PAIR(cell_cf, OpCellCf)
+LR_KERNEL_PAIR(mat_flux, OpMatFlux)
+LR_KERNEL_PAIR(cell_update, OpCellUpdate)
+LR_KERNEL_PAIR(dual_flux, OpDualFlux)
+LR_KERNEL_PAIR(node_update, OpNodeUpdate)
+LR_KERNEL_PAIR(cfl_only, OpCflOnly)
+LR_KERNEL_PAIR(prepare, OpPrepare)
+#undef LR_KERNEL_PAIR
+
+template <class R, int M>
+__global__ void __launch_bounds__(128) lr_mixed(LrGrid g, LrStateT<R> cur, LrWorkT<R> w) {
+  if (!step_live(g, w.scal)) return;
+  mixed_loop<R, M>([&](int) -> const LrGrid& { return g; }, cur, w, g.mixed_lanes, g.mslot, g.moff);
+}
+template <class R, int M>
+__global__ void __launch_bounds__(128) lb_mixed(const LrGrid* __restrict__ gs, LrStateT<R> cur, LrWorkT<R> w,
+                                                int lanes, int mslot, int moff) {
+  mixed_loop<R, M>([&](int e) -> const LrGrid& { return gs[w.minst[e]]; }, cur, w, lanes, mslot, moff);
+}
+
 inline dim3 grid_for(int nxr, int nyr) { return dim3((nxr + BX - 1) / BX, (nyr + BY - 1) / BY); }
 
 template <class R>
@@ -1505,17 +1651,18 @@ cudaError_t launch_t(int kid, const LrGrid& g, const LrState& cur0, const LrStat
   LrStateT<R> cur = typed<R>(cur0), nxt = typed<R>(nxt0);
   LrWorkT<R> w = typed<R>(w0);
   dim3 b(BX, BY);
-#define LR_M(K, GRID, ...)                                                   \
-  do {                                                                       \
-    if (g.M == 1) K<R, 1><<<GRID, b, 0, s>>>(__VA_ARGS__);                   \
-    else if (g.M == 2) K<R, 2><<<GRID, b, 0, s>>>(__VA_ARGS__);              \
-    else K<R, 3><<<GRID, b, 0, s>>>(__VA_ARGS__);                            \
+#define LR_M(K, GRID)                                                                        \
+  do {                                                                                       \
+    if (g.M == 1) K<R, 1><<<GRID, b, 0, s>>>(g, kc, cur, nxt, w);                            \
+    else if (g.M == 2) K<R, 2><<<GRID, b, 0, s>>>(g, kc, cur, nxt, w);                       \
+    else K<R, 3><<<GRID, b, 0, s>>>(g, kc, cur, nxt, w);                                     \
   } while (0)
+#define LR_1(K, GRID) K<R, 1><<<GRID, b, 0, s>>>(g, kc, cur, nxt, w)
   switch (kid) {
-    case LRK_CELL_PRE: LR_M(lr_cell_pre, grid_for(g.nx, g.ny), g, kc, cur, w); break;
-    case LRK_NODE_HALF: lr_node_half<R><<<grid_for(g.nxu, g.nyu), b, 0, s>>>(g, kc, cur, w); break;
-    case LRK_CELL_LAG: LR_M(lr_cell_lag, grid_for(g.nxu, g.nyu), g, kc, cur, w); break;
-    case LRK_CELL_CF: LR_M(lr_cell_cf, grid_for(g.nx, g.ny), g, kc, cur, w); break;
+    case LRK_CELL_PRE: LR_M(lr_cell_pre, grid_for(g.nx, g.ny)); break;
+    case LRK_NODE_HALF: LR_1(lr_node_half, grid_for(g.nxu, g.nyu)); break;
+    case LRK_CELL_LAG: LR_M(lr_cell_lag, grid_for(g.nxu, g.nyu)); break;
+    case LRK_CELL_CF: LR_M(lr_cell_cf, grid_for(g.nx, g.ny)); break;
     case LRK_MIXED: {
       if (g.M == 1) break;  // one material: no interfaces
       long long lanes = (long long)g.mixed_lanes * g.nx * g.ny;
@@ -1525,16 +1672,66 @@ cudaError_t launch_t(int kid, const LrGrid& g, const LrState& cur0, const LrStat
       else lr_mixed<R, 3><<<nb, 128, 0, s>>>(g, cur, w);
       break;
     }
-    case LRK_MAT_FLUX: LR_M(lr_mat_flux, grid_for(g.nxu, g.nyu), g, kc, cur, w); break;
-    case LRK_CELL_UPDATE: LR_M(lr_cell_update, grid_for(g.nx, g.ny), g, kc, cur, nxt, w); break;
-    case LRK_DUAL_FLUX: lr_dual_flux<R><<<grid_for(g.nx + 2, g.ny + 2), b, 0, s>>>(g, kc, w); break;
-    case LRK_NODE_UPDATE: lr_node_update<R><<<grid_for(g.nxu, g.nyu), b, 0, s>>>(g, kc, cur, nxt, w); break;
-    case 100: LR_M(lr_prepare, grid_for(g.nx + 1, g.ny + 1), g, kc, cur, w);
-              lr_cfl_only<R><<<grid_for(g.nxu, g.nyu), b, 0, s>>>(g, kc, cur, w); break;
+    case LRK_MAT_FLUX: LR_M(lr_mat_flux, grid_for(g.nxu, g.nyu)); break;
+    case LRK_CELL_UPDATE: LR_M(lr_cell_update, grid_for(g.nx, g.ny)); break;
+    case LRK_DUAL_FLUX: LR_1(lr_dual_flux, grid_for(g.nx + 2, g.ny + 2)); break;
+    case LRK_NODE_UPDATE: LR_1(lr_node_update, grid_for(g.nxu, g.nyu)); break;
+    case LRK_PREPARE: LR_M(lr_prepare, grid_for(g.nx + 1, g.ny + 1)); break;
+    case LRK_CFL_ONLY: LR_1(lr_cfl_only, grid_for(g.nxu, g.nyu)); break;
     default: return cudaErrorInvalidValue;
   }
 #undef LR_M
+#undef LR_1
   return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_batch_t(int kid, const LrBatchArgs& a, const LrState& cur0, const LrState& nxt0,
+                           const LrWork& w0, cudaStream_t s) {
+  LrStateT<R> cur = typed<R>(cur0), nxt = typed<R>(nxt0);
+  LrWorkT<R> w = typed<R>(w0);
+  const KC<R>* kcs = static_cast<const KC<R>*>(a.kcs);
+  if (kid == LRK_MIXED) {
+    if (a.M == 1 || a.grid <= 0) return cudaSuccess;
+    if (a.M == 2) lb_mixed<R, 2><<<a.grid, 128, 0, s>>>(a.gs, cur, w, a.lanes, a.mslot, a.moff);
+    else lb_mixed<R, 3><<<a.grid, 128, 0, s>>>(a.gs, cur, w, a.lanes, a.mslot, a.moff);
+    return cudaGetLastError();
+  }
+  if (a.ntiles <= 0) return cudaSuccess;
+  if (a.bx * a.by != BX * BY || a.grid <= 0) return cudaErrorInvalidValue;
+  dim3 b(a.bx, a.by);
+#define LB_M(K)                                                                                    \
+  do {                                                                                             \
+    if (a.M == 1) K<R, 1><<<a.grid, b, 0, s>>>(a.gs, kcs, a.tiles, a.ntiles, cur, nxt, w);         \
+    else if (a.M == 2) K<R, 2><<<a.grid, b, 0, s>>>(a.gs, kcs, a.tiles, a.ntiles, cur, nxt, w);    \
+    else K<R, 3><<<a.grid, b, 0, s>>>(a.gs, kcs, a.tiles, a.ntiles, cur, nxt, w);                  \
+  } while (0)
+#define LB_1(K) K<R, 1><<<a.grid, b, 0, s>>>(a.gs, kcs, a.tiles, a.ntiles, cur, nxt, w)
+  switch (kid) {
+    case LRK_CELL_PRE: LB_M(lb_cell_pre); break;
+    case LRK_NODE_HALF: LB_1(lb_node_half); break;
+    case LRK_CELL_LAG: LB_M(lb_cell_lag); break;
+    case LRK_CELL_CF: LB_M(lb_cell_cf); break;
+    case LRK_MAT_FLUX: LB_M(lb_mat_flux); break;
+    case LRK_CELL_UPDATE: LB_M(lb_cell_update); break;
+    case LRK_DUAL_FLUX: LB_1(lb_dual_flux); break;
+    case LRK_NODE_UPDATE: LB_1(lb_node_update); break;
+    case LRK_PREPARE: LB_M(lb_prepare); break;
+    case LRK_CFL_ONLY: LB_1(lb_cfl_only); break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef LB_M
+#undef LB_1
+  return cudaGetLastError();
+}
+
+template <class R>
+__global__ void lr_reset_k(LrWorkT<R> w, int nsim) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < LR_RED_INST + 2 * nsim) w.red[t] = 0ull;
+  if (t < 2 * nsim) w.err[t] = (t & 1) ? -1 : 0;
+  if (t < LR_NSCAL * nsim) w.scal[t] = 0.0;
+  if (t < nsim) w.dtR[t] = from_double<R>(0.0);
 }
 
 }  // namespace
@@ -1553,7 +1750,34 @@ cudaError_t lr_launch(int kid, const LrGrid& g, const LrState& cur, const LrStat
 }
 
 cudaError_t lr_launch_init(const LrGrid& g, const LrState& st, const LrWork& w, cudaStream_t s) {
-  return lr_launch(100, g, st, st, w, s);
+  cudaError_t e = lr_launch(LRK_PREPARE, g, st, st, w, s);
+  return e != cudaSuccess ? e : lr_launch(LRK_CFL_ONLY, g, st, st, w, s);
+}
+
+cudaError_t lr_launch_batch(int kid, const LrBatchArgs& a, const LrState& cur, const LrState& nxt,
+                            const LrWork& w, cudaStream_t s) {
+  return a.mode == LR_MODE_FP32 ? launch_batch_t<float>(kid, a, cur, nxt, w, s)
+       : a.mode == LR_MODE_DF64 ? launch_batch_t<df64>(kid, a, cur, nxt, w, s)
+                                : launch_batch_t<double>(kid, a, cur, nxt, w, s);
+}
+
+int lr_kernel_domain(int kid) {
+  switch (kid) {
+    case LRK_CELL_PRE: case LRK_CELL_CF: case LRK_CELL_UPDATE: return LR_DOM_CELLS;
+    case LRK_DUAL_FLUX: return LR_DOM_DUAL;
+    case LRK_PREPARE: return LR_DOM_NODES_ALL;
+    default: return LR_DOM_NODES;
+  }
+}
+
+size_t lr_kc_bytes(int mode) {
+  return mode == LR_MODE_FP32 ? sizeof(KC<float>) : mode == LR_MODE_DF64 ? sizeof(KC<df64>) : sizeof(KC<double>);
+}
+
+void lr_make_kc(const LrGrid& g, void* out) {
+  if (g.mode == LR_MODE_FP32) *static_cast<KC<float>*>(out) = make_kc<float>(g);
+  else if (g.mode == LR_MODE_DF64) *static_cast<KC<df64>*>(out) = make_kc<df64>(g);
+  else *static_cast<KC<double>*>(out) = make_kc<double>(g);
 }
 
 cudaError_t lr_launch_set_tend(const LrGrid& g, const LrWork& w, double t_end, cudaStream_t s) {
@@ -1563,8 +1787,12 @@ cudaError_t lr_launch_set_tend(const LrGrid& g, const LrWork& w, double t_end, c
   return cudaGetLastError();
 }
 
-cudaError_t lr_launch_reset(const LrWork& w, cudaStream_t s) {
-  lr_reset_k<<<1, 1, 0, s>>>(w);
+cudaError_t lr_launch_reset(int mode, const LrWork& w, int nsim, cudaStream_t s) {
+  int n = LR_NSCAL * nsim > LR_RED_INST + 2 * nsim ? LR_NSCAL * nsim : LR_RED_INST + 2 * nsim;
+  unsigned nb = (unsigned)((n + 255) / 256);
+  if (mode == LR_MODE_FP32) lr_reset_k<float><<<nb, 256, 0, s>>>(typed<float>(w), nsim);
+  else if (mode == LR_MODE_DF64) lr_reset_k<df64><<<nb, 256, 0, s>>>(typed<df64>(w), nsim);
+  else lr_reset_k<double><<<nb, 256, 0, s>>>(typed<double>(w), nsim);
   return cudaGetLastError();
 }
 

@@ -18,6 +18,7 @@ import numpy as np
 from . import build as _build
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lr.h")
+BATCH_HEADER = os.path.join(os.path.dirname(HEADER), "lr_batch.h")
 
 OK, ERR_ARG, ERR_OOM, ERR_NUMERIC, ERR_TIMEOUT, ERR_STATE, ERR_CUDA = 0, -1, -2, -3, -4, -5, -6
 BC_REFLECT, BC_PERIODIC = 0, 1
@@ -49,6 +50,14 @@ class Config(ctypes.Structure):
     ]
 
 
+class BatchConfig(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int), ("nmat_max", ctypes.c_int),
+        ("capacity_units", ctypes.c_long), ("capacity_members", ctypes.c_int),
+        ("max_member_cells", ctypes.c_long), ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
 class Material(ctypes.Structure):
     _fields_ = [("eos", ctypes.c_int), ("gamma", ctypes.c_double), ("pi", ctypes.c_double)]
 
@@ -58,10 +67,13 @@ _dp = ctypes.POINTER(ctypes.c_double)
 
 
 def declared_symbols() -> list:
-    """Names of the functions declared in include/lr.h."""
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(lr_[a-z_]+)\s*\(", text)))
+    """Names of the functions declared in include/lr.h and include/lr_batch.h."""
+    names = set()
+    for h in (HEADER, BATCH_HEADER):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(lr_[a-z_]+)\s*\(", text))
+    return sorted(names)
 
 
 def load(build_if_missing: bool = True):
@@ -102,6 +114,40 @@ def load(build_if_missing: bool = True):
     L.lr_last_error.restype = ctypes.c_char_p
     L.lr_cfl_dt_noalloc.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(Material), vp, vp, vp, vp, vp, vp]
     L.lr_cfl_dt_noalloc.restype = ctypes.c_int
+    bp = ctypes.POINTER(BatchConfig)
+    L.lr_batch_config_default.argtypes = [bp]
+    L.lr_batch_config_default.restype = None
+    L.lr_batch_workspace_bytes.argtypes = [bp, ctypes.POINTER(ctypes.c_size_t)]
+    L.lr_batch_unit_bytes.argtypes = [bp, ctypes.POINTER(ctypes.c_size_t)]
+    L.lr_batch_create.argtypes = [bp, ctypes.POINTER(vp)]
+    L.lr_batch_destroy.argtypes = [vp]
+    L.lr_batch_destroy.restype = None
+    L.lr_batch_last_error.argtypes = [vp]
+    L.lr_batch_last_error.restype = ctypes.c_char_p
+    L.lr_batch_add.argtypes = [vp, ctypes.POINTER(Config), ctypes.POINTER(Material), _dp, _dp, _dp, _dp, _dp,
+                               ctypes.c_double, ctypes.c_long, ctypes.POINTER(ctypes.c_int)]
+    L.lr_batch_remove.argtypes = [vp, ctypes.c_int]
+    L.lr_batch_set_limits.argtypes = [vp, ctypes.c_int, ctypes.c_double, ctypes.c_long]
+    L.lr_batch_step.argtypes = [vp, ctypes.c_int]
+    L.lr_batch_sync.argtypes = [vp]
+    L.lr_batch_status.argtypes = [vp, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_int)]
+    L.lr_batch_status_all.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_long), ctypes.c_int]
+    L.lr_batch_field_size.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    L.lr_batch_field_size.restype = ctypes.c_size_t
+    L.lr_batch_get_fields.argtypes = [vp, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_size_t]
+    L.lr_batch_autotune.argtypes = [vp, ctypes.c_int]
+    L.lr_batch_schedule.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_int)]
+    L.lr_batch_launches_per_step.argtypes = [vp]
+    L.lr_batch_launches_per_step.restype = ctypes.c_int
+    L.lr_batch_set_profiling.argtypes = [vp, ctypes.c_int]
+    L.lr_batch_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_long),
+                                        _dp, ctypes.c_int]
+    L.lr_batch_kernel_times.restype = ctypes.c_int
+    for name in ("lr_batch_workspace_bytes", "lr_batch_unit_bytes", "lr_batch_create", "lr_batch_add",
+                 "lr_batch_remove", "lr_batch_set_limits", "lr_batch_step", "lr_batch_sync", "lr_batch_status", "lr_batch_status_all",
+                 "lr_batch_get_fields", "lr_batch_autotune", "lr_batch_schedule", "lr_batch_set_profiling"):
+        getattr(L, name).restype = ctypes.c_int
     for name in ("lr_workspace_bytes", "lr_create", "lr_create_in", "lr_set_materials", "lr_init",
                  "lr_set_prescribed_velocity", "lr_step", "lr_run", "lr_sync", "lr_get_fields",
                  "lr_get_fields_device", "lr_time", "lr_set_profiling"):
@@ -134,6 +180,38 @@ def make_config(problem, stream: Optional[int] = None, precision: int = FP64, mi
     c.mixed_lanes = mixed_lanes
     c.cuda_stream = stream
     return c
+
+
+def _shape_field(out: np.ndarray, field: int, problem) -> np.ndarray:
+    nx, ny, M = problem.nx, problem.ny, problem.nmat
+    if field in (F_K, F_RHO_MAT, F_E_MAT, F_E_LAG):
+        return out.reshape(M, ny, nx)
+    if field in (F_P, F_RHO, F_E, F_C, F_VOL_LAGCF, F_Q):
+        return out.reshape(ny, nx)
+    if field in (F_UX, F_UY, F_UHX, F_UHY, F_FC, F_MC):
+        return out.reshape(ny + 1, nx + 1)
+    if field in (F_FX, F_MX):
+        return out.reshape(ny, nx + 1)
+    if field in (F_FY, F_MY):
+        return out.reshape(ny + 1, nx)
+    if field == F_CUTS:
+        return out.reshape(6, ny, nx)
+    if field == F_XA:
+        return out.reshape(M, ny, nx + 1)
+    if field == F_YA:
+        return out.reshape(M, ny + 1, nx)
+    if field == F_CA:
+        return out.reshape(M, ny + 1, nx + 1)
+    return out
+
+
+def _materials(problem):
+    mats = (Material * problem.nmat)()
+    for a in range(problem.nmat):
+        mats[a].eos = 1 if problem.pinf[a] > 0 else 0
+        mats[a].gamma = float(problem.gamma[a])
+        mats[a].pi = float(problem.pinf[a])
+    return mats
 
 
 class Sim:
@@ -170,12 +248,7 @@ class Sim:
         if rc != OK or not h.value:
             raise LrError(rc, "lr_create failed")
         self._h = h
-        mats = (Material * problem.nmat)()
-        for a in range(problem.nmat):
-            mats[a].eos = 1 if problem.pinf[a] > 0 else 0
-            mats[a].gamma = float(problem.gamma[a])
-            mats[a].pi = float(problem.pinf[a])
-        self._check(L.lr_set_materials(self._h, problem.nmat, mats))
+        self._check(L.lr_set_materials(self._h, problem.nmat, _materials(problem)))
         self.init(problem)
 
     def _check(self, rc, h="self"):
@@ -225,26 +298,7 @@ class Sim:
         n = L.lr_field_size(self._h, field)
         out = np.empty(n, dtype=np.float64)
         self._check(L.lr_get_fields(self._h, field, _ptr(out), n))
-        nx, ny, M = self.p.nx, self.p.ny, self.p.nmat
-        if field in (F_K, F_RHO_MAT, F_E_MAT, F_E_LAG):
-            return out.reshape(M, ny, nx)
-        if field in (F_P, F_RHO, F_E, F_C, F_VOL_LAGCF, F_Q):
-            return out.reshape(ny, nx)
-        if field in (F_UX, F_UY, F_UHX, F_UHY, F_FC, F_MC):
-            return out.reshape(ny + 1, nx + 1)
-        if field in (F_FX, F_MX):
-            return out.reshape(ny, nx + 1)
-        if field in (F_FY, F_MY):
-            return out.reshape(ny + 1, nx)
-        if field == F_CUTS:
-            return out.reshape(6, ny, nx)
-        if field == F_XA:
-            return out.reshape(M, ny, nx + 1)
-        if field == F_YA:
-            return out.reshape(M, ny + 1, nx)
-        if field == F_CA:
-            return out.reshape(M, ny + 1, nx + 1)
-        return out
+        return _shape_field(out, field, self.p)
 
     def get_device(self, field: int, out_ptr: int, n: int):
         self._check(load().lr_get_fields_device(self._h, field, ctypes.c_void_p(out_ptr), n))
@@ -270,6 +324,153 @@ class Sim:
             load().lr_destroy(h)
             self._h = ctypes.c_void_p()
         self._arena = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+TILE_SHAPES = ((32, 8), (64, 4), (16, 16), (128, 2))
+RUNNING, DONE, FAILED, EMPTY = 0, 1, -1, -2
+
+
+def batch_units(problem) -> int:
+    """Units of a batch pool that one member on this grid occupies."""
+    return (problem.nx + 2) * (problem.ny + 2)
+
+
+class Batch:
+    """Many simulations advanced together behind the batch C ABI
+    (include/lr_batch.h): admission by pool units, one batched launch per
+    kernel of the step, per-member CFL time steps."""
+
+    def __init__(self, capacity_units: int, capacity_members: int, precision: int = FP64, nmat_max: int = 3,
+                 max_member_cells: int = 1 << 20, use_torch: bool = True):
+        L = load()
+        self.stream = None
+        cfg = BatchConfig()
+        L.lr_batch_config_default(ctypes.byref(cfg))
+        cfg.precision = precision
+        cfg.nmat_max = nmat_max
+        cfg.capacity_units = int(capacity_units)
+        cfg.capacity_members = int(capacity_members)
+        cfg.max_member_cells = int(max_member_cells)
+        if use_torch:
+            import torch
+            if not torch.cuda.is_available():
+                raise RuntimeError("CUDA device required")
+            self.stream = torch.cuda.Stream()
+            cfg.cuda_stream = self.stream.cuda_stream
+        self.cfg = cfg
+        self.precision = precision
+        self._h = ctypes.c_void_p()
+        rc = L.lr_batch_create(ctypes.byref(cfg), ctypes.byref(self._h))
+        if rc != OK or not self._h.value:
+            raise LrError(rc, "lr_batch_create failed")
+        self.problems = {}
+
+    @staticmethod
+    def unit_bytes(precision: int = FP64, nmat_max: int = 3) -> int:
+        cfg = BatchConfig()
+        load().lr_batch_config_default(ctypes.byref(cfg))
+        cfg.precision, cfg.nmat_max = precision, nmat_max
+        n = ctypes.c_size_t()
+        rc = load().lr_batch_unit_bytes(ctypes.byref(cfg), ctypes.byref(n))
+        if rc != OK:
+            raise LrError(rc, "lr_batch_unit_bytes")
+        return n.value
+
+    def _check(self, rc):
+        if rc != OK:
+            msg = load().lr_batch_last_error(self._h)
+            raise LrError(rc, msg.decode() if msg else "")
+
+    def add(self, problem, t_end: Optional[float] = None, max_steps: int = 0) -> Optional[int]:
+        """Admit a member; returns its id, or None when the pool or the
+        member slots are full right now."""
+        cfg = make_config(problem, None, self.precision)
+        k, r, p = _c64(problem.k), _c64(problem.rho), _c64(problem.p)
+        ux, uy = _c64(problem.ux), _c64(problem.uy)
+        m = ctypes.c_int(-1)
+        te = problem.t_end if t_end is None else t_end
+        rc = load().lr_batch_add(self._h, ctypes.byref(cfg), _materials(problem), _ptr(k), _ptr(r), _ptr(p),
+                                 _ptr(ux), _ptr(uy), float(te), int(max_steps), ctypes.byref(m))
+        if rc == ERR_OOM:
+            return None
+        if rc != OK and m.value >= 0:  # admitted but its initial state is invalid: release it
+            msg = load().lr_batch_last_error(self._h)
+            load().lr_batch_remove(self._h, m.value)
+            raise LrError(rc, msg.decode() if msg else "")
+        self._check(rc)
+        self.problems[m.value] = problem
+        return m.value
+
+    def set_limits(self, m: int, t_end: float = 1e300, max_steps: int = 0):
+        self._check(load().lr_batch_set_limits(self._h, m, float(t_end), int(max_steps)))
+
+    def remove(self, m: int):
+        self._check(load().lr_batch_remove(self._h, m))
+        self.problems.pop(m, None)
+
+    def step(self, nsteps: int = 1):
+        self._check(load().lr_batch_step(self._h, int(nsteps)))
+
+    def sync(self):
+        self._check(load().lr_batch_sync(self._h))
+
+    def status(self, m: int):
+        t = ctypes.c_double()
+        n = ctypes.c_long()
+        st = ctypes.c_int()
+        self._check(load().lr_batch_status(self._h, m, ctypes.byref(t), ctypes.byref(n), ctypes.byref(st)))
+        return t.value, n.value, st.value
+
+    def status_all(self):
+        S = self.cfg.capacity_members
+        st = (ctypes.c_int * S)()
+        n = (ctypes.c_long * S)()
+        self._check(load().lr_batch_status_all(self._h, st, n, S))
+        return list(st), list(n)
+
+    def get(self, m: int, field: int) -> np.ndarray:
+        L = load()
+        n = L.lr_batch_field_size(self._h, m, field)
+        out = np.empty(n, dtype=np.float64)
+        self._check(L.lr_batch_get_fields(self._h, m, field, _ptr(out), n))
+        return _shape_field(out, field, self.problems[m])
+
+    def autotune(self, trial_steps: int = 3):
+        self._check(load().lr_batch_autotune(self._h, int(trial_steps)))
+
+    def schedule(self):
+        sh = (ctypes.c_int * 9)()
+        bp = (ctypes.c_int * 9)()
+        ln = ctypes.c_int()
+        self._check(load().lr_batch_schedule(self._h, sh, bp, ctypes.byref(ln)))
+        return [TILE_SHAPES[q] for q in sh], list(bp), ln.value
+
+    def launches_per_step(self) -> int:
+        return load().lr_batch_launches_per_step(self._h)
+
+    def set_profiling(self, on: bool):
+        self._check(load().lr_batch_set_profiling(self._h, 1 if on else 0))
+
+    def kernel_times(self):
+        L = load()
+        n = 16
+        names = (ctypes.c_char_p * n)()
+        cnt = (ctypes.c_long * n)()
+        ms = (ctypes.c_double * n)()
+        k = L.lr_batch_kernel_times(self._h, names, cnt, ms, n)
+        return {names[q].decode(): (cnt[q], ms[q]) for q in range(min(k, n))}
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            load().lr_batch_destroy(h)
+            self._h = ctypes.c_void_p()
 
     def __del__(self):
         try:

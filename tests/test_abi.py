@@ -41,3 +41,27 @@ def test_host_side_validation_without_gpu():
         rc = L.lr_workspace_bytes(ctypes.byref(cfg), ctypes.byref(nbytes))
         assert rc == (lr.OK if ok else lr.ERR_ARG), lanes
     assert L.lr_last_error(None) == b"null context"
+
+
+def test_batch_host_side_validation_without_gpu():
+    L = lr.load()
+    cfg = lr.BatchConfig()
+    L.lr_batch_config_default(ctypes.byref(cfg))
+    assert (cfg.precision, cfg.nmat_max, cfg.capacity_members) == (lr.FP64, 3, 16)
+    n = ctypes.c_size_t()
+    assert L.lr_batch_workspace_bytes(ctypes.byref(cfg), ctypes.byref(n)) == lr.OK
+    u = ctypes.c_size_t()
+    assert L.lr_batch_unit_bytes(ctypes.byref(cfg), ctypes.byref(u)) == lr.OK
+    # the pool dominates: workspace ~ units x unit bytes (+ staging and scratch)
+    assert cfg.capacity_units * u.value <= n.value <= 2 * cfg.capacity_units * u.value + (64 << 20) * 8
+    # FP32 halves the real arrays; fewer material planes shrink the unit
+    f32 = lr.BatchConfig.from_buffer_copy(cfg)
+    f32.precision = lr.FP32
+    u32 = ctypes.c_size_t()
+    assert L.lr_batch_unit_bytes(ctypes.byref(f32), ctypes.byref(u32)) == lr.OK and u32.value < u.value
+    for field, bad in (("nmat_max", 4), ("nmat_max", 0), ("capacity_members", 0), ("capacity_units", 3),
+                       ("precision", 7), ("max_member_cells", 1)):
+        c = lr.BatchConfig.from_buffer_copy(cfg)
+        setattr(c, field, bad)
+        assert L.lr_batch_workspace_bytes(ctypes.byref(c), ctypes.byref(n)) == lr.ERR_ARG, field
+    assert L.lr_batch_last_error(None) == b"null batch"
