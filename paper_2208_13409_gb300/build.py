@@ -13,9 +13,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "liblr.so")
-SOURCES = ["lr_kernels.cu", "lr_api.cu", "lr_batch.cu", "lr_noalloc.cu"]
+SOURCES = ["lr_kernels.cu", "lr_api.cu", "lr_batch.cu", "lr_serve.cu", "lr_noalloc.cu"]
 HEADERS = ["lr_dev.cuh", "lr_real.cuh", "lr_host.h", os.path.join("..", "..", "include", "lr.h"),
-           os.path.join("..", "..", "include", "lr_batch.h")]
+           os.path.join("..", "..", "include", "lr_batch.h"), os.path.join("..", "..", "include", "lr_serve.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 
@@ -56,7 +56,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if p.returncode != 0:
             raise RuntimeError(f"nvcc failed on {src}:\n{out.decode(errors='replace')}")
     tmp = LIB + f".{os.getpid()}.tmp"
-    subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
+    subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"])
     os.replace(tmp, LIB)
     for o in objs:
         os.remove(o)

@@ -19,6 +19,7 @@ from . import build as _build
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lr.h")
 BATCH_HEADER = os.path.join(os.path.dirname(HEADER), "lr_batch.h")
+SERVE_HEADER = os.path.join(os.path.dirname(HEADER), "lr_serve.h")
 
 OK, ERR_ARG, ERR_OOM, ERR_NUMERIC, ERR_TIMEOUT, ERR_STATE, ERR_CUDA = 0, -1, -2, -3, -4, -5, -6
 BC_REFLECT, BC_PERIODIC = 0, 1
@@ -58,6 +59,18 @@ class BatchConfig(ctypes.Structure):
     ]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("batch", BatchConfig), ("max_chunk_steps", ctypes.c_int), ("max_bypass", ctypes.c_int),
+                ("device", ctypes.c_int)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_long), ("admitted", ctypes.c_long), ("completed", ctypes.c_long),
+                ("failed", ctypes.c_long), ("pending", ctypes.c_long), ("resident", ctypes.c_long),
+                ("cell_updates", ctypes.c_double), ("busy_s", ctypes.c_double),
+                ("steps_launched", ctypes.c_long)]
+
+
 class Material(ctypes.Structure):
     _fields_ = [("eos", ctypes.c_int), ("gamma", ctypes.c_double), ("pi", ctypes.c_double)]
 
@@ -67,9 +80,9 @@ _dp = ctypes.POINTER(ctypes.c_double)
 
 
 def declared_symbols() -> list:
-    """Names of the functions declared in include/lr.h and include/lr_batch.h."""
+    """Names of the functions declared in include/lr.h, lr_batch.h and lr_serve.h."""
     names = set()
-    for h in (HEADER, BATCH_HEADER):
+    for h in (HEADER, BATCH_HEADER, SERVE_HEADER):
         text = open(h).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
         names |= set(re.findall(r"\b(lr_[a-z_]+)\s*\(", text))
@@ -144,6 +157,29 @@ def load(build_if_missing: bool = True):
     L.lr_batch_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_long),
                                         _dp, ctypes.c_int]
     L.lr_batch_kernel_times.restype = ctypes.c_int
+    sp = ctypes.POINTER(ServerConfig)
+    L.lr_server_config_default.argtypes = [sp]
+    L.lr_server_config_default.restype = None
+    L.lr_server_create.argtypes = [sp, ctypes.POINTER(vp)]
+    L.lr_server_destroy.argtypes = [vp]
+    L.lr_server_destroy.restype = None
+    L.lr_server_last_error.argtypes = [vp]
+    L.lr_server_last_error.restype = ctypes.c_char_p
+    L.lr_server_submit.argtypes = [vp, ctypes.POINTER(Config), ctypes.POINTER(Material), _dp, _dp, _dp, _dp, _dp,
+                                   ctypes.c_double, ctypes.c_long, ctypes.POINTER(ctypes.c_long)]
+    L.lr_server_wait.argtypes = [vp, ctypes.c_long, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]
+    L.lr_server_drain.argtypes = [vp, ctypes.c_double]
+    L.lr_server_info.argtypes = [vp, ctypes.c_long, _dp, _dp, _dp, _dp, ctypes.POINTER(ctypes.c_long)]
+    L.lr_server_result_size.argtypes = [vp, ctypes.c_long, ctypes.c_int]
+    L.lr_server_result_size.restype = ctypes.c_size_t
+    L.lr_server_result.argtypes = [vp, ctypes.c_long, ctypes.c_int, _dp, ctypes.c_size_t]
+    L.lr_server_release.argtypes = [vp, ctypes.c_long]
+    L.lr_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+    L.lr_server_clock.argtypes = [vp]
+    L.lr_server_clock.restype = ctypes.c_double
+    for name in ("lr_server_create", "lr_server_submit", "lr_server_wait", "lr_server_drain", "lr_server_info",
+                 "lr_server_result", "lr_server_release", "lr_server_get_stats"):
+        getattr(L, name).restype = ctypes.c_int
     for name in ("lr_batch_workspace_bytes", "lr_batch_unit_bytes", "lr_batch_create", "lr_batch_add",
                  "lr_batch_remove", "lr_batch_set_limits", "lr_batch_step", "lr_batch_sync", "lr_batch_status", "lr_batch_status_all",
                  "lr_batch_get_fields", "lr_batch_autotune", "lr_batch_schedule", "lr_batch_set_profiling"):
@@ -470,6 +506,106 @@ class Batch:
         h = getattr(self, "_h", None)
         if h is not None and h.value:
             load().lr_batch_destroy(h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+SERVE_FIELDS = (F_K, F_RHO_MAT, F_E_MAT, F_P, F_UX, F_UY)
+
+
+class Server:
+    """Continuous-batching request loop behind include/lr_serve.h: requests
+    are admitted into a resident batch as pool units free up, advance
+    together, and are retired with their final fields on the host."""
+
+    def __init__(self, capacity_units: int, capacity_members: int, precision: int = FP64, nmat_max: int = 2,
+                 max_member_cells: int = 1 << 22, max_chunk_steps: int = 64, max_bypass: int = 8, device: int = 0):
+        L = load()
+        cfg = ServerConfig()
+        L.lr_server_config_default(ctypes.byref(cfg))
+        cfg.batch.precision = precision
+        cfg.batch.nmat_max = nmat_max
+        cfg.batch.capacity_units = int(capacity_units)
+        cfg.batch.capacity_members = int(capacity_members)
+        cfg.batch.max_member_cells = int(max_member_cells)
+        cfg.max_chunk_steps = int(max_chunk_steps)
+        cfg.max_bypass = int(max_bypass)
+        cfg.device = int(device)
+        self.cfg = cfg
+        self.precision = precision
+        self._h = ctypes.c_void_p()
+        rc = L.lr_server_create(ctypes.byref(cfg), ctypes.byref(self._h))
+        if rc != OK or not self._h.value:
+            raise LrError(rc, "lr_server_create failed")
+        self.problems = {}
+
+    def _check(self, rc):
+        if rc != OK:
+            msg = load().lr_server_last_error(self._h)
+            raise LrError(rc, msg.decode() if msg else "")
+
+    def submit(self, problem, t_end: Optional[float] = None, max_steps: int = 0) -> int:
+        cfg = make_config(problem, None, self.precision)
+        k, r, p = _c64(problem.k), _c64(problem.rho), _c64(problem.p)
+        ux, uy = _c64(problem.ux), _c64(problem.uy)
+        rid = ctypes.c_long(-1)
+        te = problem.t_end if t_end is None else t_end
+        self._check(load().lr_server_submit(self._h, ctypes.byref(cfg), _materials(problem), _ptr(k), _ptr(r),
+                                            _ptr(p), _ptr(ux), _ptr(uy), float(te), int(max_steps),
+                                            ctypes.byref(rid)))
+        self.problems[rid.value] = problem
+        return rid.value
+
+    def wait(self, rid: int, timeout: float = -1.0) -> int:
+        st = ctypes.c_int(0)
+        rc = load().lr_server_wait(self._h, rid, float(timeout), ctypes.byref(st))
+        if rc not in (OK, ERR_TIMEOUT):
+            self._check(rc)
+        return st.value
+
+    def drain(self, timeout: float = -1.0) -> bool:
+        rc = load().lr_server_drain(self._h, float(timeout))
+        if rc not in (OK, ERR_TIMEOUT):
+            self._check(rc)
+        return rc == OK
+
+    def info(self, rid: int) -> dict:
+        a, b, c, t = (ctypes.c_double() for _ in range(4))
+        n = ctypes.c_long()
+        self._check(load().lr_server_info(self._h, rid, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                          ctypes.byref(t), ctypes.byref(n)))
+        return {"submit": a.value, "admit": b.value, "done": c.value, "t": t.value, "steps": n.value}
+
+    def result(self, rid: int, field: int) -> np.ndarray:
+        L = load()
+        n = L.lr_server_result_size(self._h, rid, field)
+        if n == 0:
+            raise LrError(ERR_STATE, f"no result field {field} for request {rid}")
+        out = np.empty(n, dtype=np.float64)
+        self._check(L.lr_server_result(self._h, rid, field, _ptr(out), n))
+        return _shape_field(out, field, self.problems[rid])
+
+    def release(self, rid: int):
+        self._check(load().lr_server_release(self._h, rid))
+        self.problems.pop(rid, None)
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        self._check(load().lr_server_get_stats(self._h, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def clock(self) -> float:
+        return load().lr_server_clock(self._h)
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            load().lr_server_destroy(h)
             self._h = ctypes.c_void_p()
 
     def __del__(self):
