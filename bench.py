@@ -48,6 +48,14 @@ def parse():
                     help="advance the workload to this time before warm-up and timing (run ends at t=5)")
     ap.add_argument("--kernels-only", action="store_true",
                     help="init + warm-up + K steps of the workload and exit (for ncu captures)")
+    ap.add_argument("--extras", type=int, default=1,
+                    help="also measure the batched ensemble and the serving stream (rank 0, one GPU)")
+    ap.add_argument("--ensemble-steps", type=int, default=20)
+    ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--serve-load", type=float, default=0.8,
+                    help="offered load of the serving stream as a fraction of the measured capacity")
+    ap.add_argument("--reference-seconds", type=float, default=60.0,
+                    help="--impl reference: stop timing after this many seconds of oracle steps")
     return ap.parse_args()
 
 
@@ -186,19 +194,23 @@ def run_reference(args, world, rank):
 
     pr = P.triple_point()
     o = oracle.Oracle(pr)
-    for _ in range(args.warmup):
+    for _ in range(min(args.warmup, 3)):
         o.step()
+    # a bounded sample: the first steps of the K requested, up to the time cap
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    n = 0
+    while n < args.steps and (n == 0 or time.perf_counter() - t0 < args.reference_seconds):
         o.step()
+        n += 1
     el = time.perf_counter() - t0
-    val = pr.cells * args.steps / el
+    val = pr.cells * n / el
+    sample = (f"{n} of the {args.steps} requested steps of the 1400x600 triple point (time cap "
+              f"{args.reference_seconds:g} s) after {min(args.warmup, 3)} warm-up steps, single thread")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / n,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "nx": pr.nx, "ny": pr.ny, "nmat": 3},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} steps of the 1400x600 triple point after {args.warmup} warm-up steps, single thread"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -359,6 +371,12 @@ def run_lr(args, world, rank, local):
 
     cpu = None
     accuracy = None
+    extras = {}
+    if rank == 0 and world == 1 and args.extras:
+        del flush
+        torch.cuda.empty_cache()
+        extras["ensemble"] = ensemble_bench(args)
+        extras["serving"] = serving_bench(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_baseline_steps)
         accuracy = sod_accuracy()
@@ -380,6 +398,7 @@ def run_lr(args, world, rank, local):
                 "clocks": clocks, "wall_s": wall}
         if modes:
             line["modes"] = modes
+        line.update(extras)
         if accuracy:
             line["sod_l1_t0.2"] = accuracy
         if cpu:
@@ -387,6 +406,123 @@ def run_lr(args, world, rank, local):
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def ensemble_bench(args):
+    """The batched ensemble: 512 independent 2-3 material problems (grid sides
+    drawn from 64..512, seeded), one batched launch per kernel and material
+    group per step, per-member CFL dt; timed over a bounded number of steps
+    after the autotuner and warm-up, in FP64 and in the FP32 bulk mode."""
+    import torch
+    from paper_2208_13409_gb300 import lr, problems as P
+
+    probs = P.ensemble(512)
+    cells = sum(p.cells for p in probs)
+    units = sum(lr.batch_units(p) for p in probs)
+    out = {"workload": "ensemble_512_random_2-3mat_sides64-512", "members": len(probs), "cells": cells,
+           "steps_timed": args.ensemble_steps, "l2": "inputs far above L2 (no flush needed)"}
+    for name in ("fp64", "fp32"):
+        mode = MODES[name]
+        bt = lr.Batch(units, len(probs), precision=mode, max_member_cells=512 * 512)
+        t0 = time.perf_counter()
+        for p in probs:
+            bt.add(p, t_end=1e300, max_steps=500)
+        t_add = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        bt.autotune(2)
+        t_tune = time.perf_counter() - t0
+        bt.step(3)
+        bt.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(bt.stream)
+        bt.step(args.ensemble_steps)
+        e1.record(bt.stream)
+        bt.sync()
+        ms = e0.elapsed_time(e1) / args.ensemble_steps
+        shapes, bps, lanes = bt.schedule()
+        out[name] = {"value": cells / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                     "launches_per_step": bt.launches_per_step(), "admit_s": t_add, "autotune_s": t_tune,
+                     "pool_gb": units * lr.Batch.unit_bytes(mode) / 1e9,
+                     "schedule": {"tile": [f"{a}x{b}" for a, b in shapes], "blocks_per_sm": bps, "lanes": lanes}}
+        bt.close()
+        torch.cuda.empty_cache()
+    return out
+
+
+def serving_bench(args):
+    """Serving stream: Poisson arrivals of two-material air/water shock
+    problems (water column or droplet), grid sides log-uniform, each run to
+    its requested step count, admitted by pool footprint into one resident
+    batch; p50/p99 time-to-solution (submit to result on the host) and the
+    aggregate cell-updates/s.  Scaled to fit a few minutes: sides 128-1024
+    and 20-200 steps per request (the full stream draws 128-2048 and
+    200-2000)."""
+    import queue
+    import numpy as np
+    from paper_2208_13409_gb300 import lr, problems as P
+
+    n_req = args.serve_requests
+    side_lo, side_hi, st_lo, st_hi = 128, 1024, 20, 200
+    mean_cells = (side_hi ** 2 - side_lo ** 2) / (2.0 * math.log(side_hi / side_lo))
+    mean_work = mean_cells * 0.5 * (st_lo + st_hi)
+    unit_b = lr.Batch.unit_bytes(lr.FP64, 2)
+    pool_gb = 24.0
+    units = int(pool_gb * 1e9 / unit_b)
+    srv = lr.Server(units, 128, precision=lr.FP64, nmat_max=2, max_member_cells=side_hi * side_hi,
+                    max_chunk_steps=32)
+
+    def make(seed):
+        rng = np.random.default_rng(seed)
+        side = int(round(math.exp(rng.uniform(math.log(side_lo), math.log(side_hi)))))
+        return P.air_water(seed, side=side, steps_range=(st_lo, st_hi), sub=2)
+
+    # capacity: a closed-loop burst of 24 requests
+    burst = [make(900000 + q) for q in range(24)]
+    t0 = srv.clock()
+    ids = [srv.submit(p, max_steps=p.steps) for p in burst]
+    srv.drain()
+    cap = sum(p.cells * p.steps for p in burst) / (srv.clock() - t0)
+    for r in ids:
+        srv.release(r)
+    lam = args.serve_load * cap / mean_work
+    rng = np.random.default_rng(13409)
+    arrivals = np.cumsum(rng.exponential(1.0 / lam, n_req))
+    q = queue.Queue(maxsize=8)
+
+    def producer():
+        for k in range(n_req):
+            q.put(make(13409 + k))
+
+    th = threading.Thread(target=producer, daemon=True)
+    th.start()
+    base = srv.clock() + 0.5
+    ids, probs = [], []
+    for k in range(n_req):
+        p = q.get()
+        wait = base + arrivals[k] - srv.clock()
+        if wait > 0:
+            time.sleep(wait)
+        ids.append(srv.submit(p, max_steps=p.steps))
+        probs.append((p.cells, p.steps))
+        del p
+    srv.drain()
+    info = [srv.info(r) for r in ids]
+    st = srv.stats()
+    lat = np.array([i["done"] - i["submit"] for i in info])
+    qw = np.array([i["admit"] - i["submit"] for i in info])
+    work = sum(c * s for c, s in probs)
+    span = max(i["done"] for i in info) - min(i["submit"] for i in info)
+    for r in ids:
+        srv.release(r)
+    srv.close()
+    return {"workload": f"serving_air_water_{n_req}req_sides{side_lo}-{side_hi}_steps{st_lo}-{st_hi}_fp64",
+            "requests": n_req, "offered_load": args.serve_load, "arrival_rate_per_s": lam,
+            "capacity_cell_updates_per_s": cap, "pool_gb": pool_gb,
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean()), "max_s": float(lat.max()),
+            "queue_wait_p50_s": float(np.percentile(qw, 50)), "queue_wait_p99_s": float(np.percentile(qw, 99)),
+            "value": work / span, "unit": UNIT, "completed": st["completed"], "failed": st["failed"],
+            "busy_s": st["busy_s"], "span_s": span}
 
 
 def sod_accuracy():

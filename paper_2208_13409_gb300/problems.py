@@ -248,13 +248,13 @@ def ensemble(n: int = 512, seed: int = 2208) -> List[Problem]:
     return [random_box(seed + i) for i in range(n)]
 
 
-def air_water(seed: int, side: int = None, steps_range=(200, 2000)) -> Problem:
+def air_water(seed: int, side: int = None, steps_range=(200, 2000), sub: int = 8) -> Problem:
     """One serving request on [0,1]^2 m: air (gamma 1.4, rho 1.2, p 1e5) and
     stiffened-gas water (gamma 4.4, p_inf 6e8 Pa so pi = gamma p_inf,
     rho 1000, p 1e5) as a water column (x in [0.4,0.6]) or a droplet, hit by
     an air shock from the left (pressure ratio log-uniform in [10,100]) at
-    x = 0.1.  The requested step count is stored in `t_end`-free form as
-    attribute `steps`."""
+    x = 0.1.  The requested step count is stored as attribute `steps`; `sub`
+    is the droplet's sampling per cell side for the volume fractions."""
     rng = np.random.default_rng(seed)
     if side is None:
         side = int(round(math.exp(rng.uniform(math.log(128), math.log(2048)))))
@@ -264,7 +264,7 @@ def air_water(seed: int, side: int = None, steps_range=(200, 2000)) -> Problem:
     if rng.random() < 0.5:
         kw = ((xc > 0.4) & (xc < 0.6)).astype(np.float64)
     else:
-        kw = disc_fraction(nx, ny, x0, x1, y0, y1, 0.5, 0.5, rng.uniform(0.05, 0.2))
+        kw = disc_fraction(nx, ny, x0, x1, y0, y1, 0.5, 0.5, rng.uniform(0.05, 0.2), sub=sub)
     ka = 1.0 - kw
     ratio = math.exp(rng.uniform(math.log(10.0), math.log(100.0)))
     g = 1.4
