@@ -48,6 +48,8 @@ def parse():
                     help="advance the workload to this time before warm-up and timing (run ends at t=5)")
     ap.add_argument("--kernels-only", action="store_true",
                     help="init + warm-up + K steps of the workload and exit (for ncu captures)")
+    ap.add_argument("--kernels-only-ensemble", action="store_true",
+                    help="the batched ensemble: admission + warm-up + K steps and exit (for ncu captures)")
     ap.add_argument("--extras", type=int, default=1,
                     help="also measure the batched ensemble and the serving stream (rank 0, one GPU)")
     ap.add_argument("--ensemble-steps", type=int, default=20)
@@ -151,18 +153,20 @@ def units_per_launch(kernel, nx, ny):
     return (nx + 1) * (ny + 1)
 
 
-def kernel_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
-    None when the kernel source has changed since the counters were taken."""
+def kernel_counters(kernel):
+    """DRAM bytes per launch and FP64-pipe activity of `kernel` from the
+    committed ncu summary, or (None, None) when the kernel source has changed
+    since the counters were taken."""
     import hashlib
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
         src = open(os.path.join(ROOT, "paper_2208_13409_gb300", "csrc", "lr_kernels.cu"), "rb").read()
         if hashlib.sha256(src).hexdigest()[:16] != rec["kernel_source_sha256_prefix"]:
-            return None
-        return rec["dram_bytes_per_launch"].get(kernel.split("<")[0])
+            return None, None
+        k = kernel.split("<")[0]
+        return rec["dram_bytes_per_launch"].get(k), rec.get("fp64_pipe_active_pct", {}).get(k)
     except Exception:
-        return None
+        return None, None
 
 
 def fp64_peak_flops(sm_mhz=None):
@@ -310,16 +314,26 @@ def run_lr(args, world, rank, local):
     value = world * cells * K / (ms_max * 1e-3)
     step_ms = ms_max / K
 
-    # ---- per-kernel durations (separate pass, events on the library stream)
-    kms = kernel_profile(sim, K, flush, torch)
+    # ---- per-kernel durations: a second simulation replays the same steps
+    # (same start state, deterministic) with events around every launch
+    sim_p = lr.Sim(pr, precision=MODES[args.precision])
+    if args.t_start > 0:
+        sim_p.run(1 << 30, args.t_start)
+    for _ in range(args.warmup):
+        sim_p.step(sync=False)
+    kms = kernel_profile(sim_p, K, flush, torch)
+    sim_p.close()
     dom = max(kms, key=lambda k: kms[k])
     dom_ms = kms[dom]
     flops = FLOPS_PER_UNIT.get(dom, 0.0) * units_per_launch(dom, pr.nx, pr.ny)
     achieved = flops / (dom_ms * 1e-3) / 1e12
     peak = fp64_peak_flops() / 1e12
+    traffic, pipe = kernel_counters(dom) if args.precision == "fp64" else (None, None)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": kernel_traffic(dom), "kernel": dom,
-                "kernel_ms": dom_ms, "peak_source": "FP64: 152 SMs x 4 flop/clk x 2.07 GHz (unit counts)"}
+                "frac": achieved / peak, "traffic": traffic, "kernel": dom,
+                "kernel_ms": dom_ms, "fp64_pipe_active_pct_ncu": pipe,
+                "peak_source": "FP64: 152 SMs x 2 DFMA lanes/clk x 2 flop x 2.07 GHz (unit counts)",
+                "flops_per_unit": FLOPS_PER_UNIT.get(dom), "units_per_launch": units_per_launch(dom, pr.nx, pr.ny)}
     peaks = load_peaks()
     hbm = peaks.get("hbm_gbs", 6800.0)
     alg_bytes = 16 * (3 * pr.nmat + 2)  # read + write the FP64 state once per cell-step
@@ -564,9 +578,34 @@ def run_kernels_only(args):
     sim = lr.Sim(P.triple_point(), precision=MODES[args.precision])
     if args.t_start > 0:
         sim.run(1 << 30, args.t_start)
-    for _ in range(args.warmup + args.steps):
+    for _ in range(args.warmup):
         sim.step(sync=False)
     sim.sync()
+    # the steps a profiler should look at, inside one NVTX range ("timed")
+    torch.cuda.nvtx.range_push("timed")
+    for _ in range(args.steps):
+        sim.step(sync=False)
+    sim.sync()
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+
+
+def run_kernels_only_ensemble(args):
+    """The batched ensemble's steps and nothing else, for profiler captures."""
+    import torch
+    from paper_2208_13409_gb300 import lr, problems as P
+
+    probs = P.ensemble(512)
+    bt = lr.Batch(sum(lr.batch_units(p) for p in probs), len(probs), precision=MODES[args.precision],
+                  max_member_cells=512 * 512)
+    for p in probs:
+        bt.add(p, t_end=1e300, max_steps=500)
+    bt.step(args.warmup)
+    bt.sync()
+    torch.cuda.nvtx.range_push("timed")
+    bt.step(args.steps)
+    bt.sync()
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
 
 
@@ -575,6 +614,9 @@ def main():
     world, rank, local = dist_setup()
     if args.kernels_only:
         run_kernels_only(args)
+        return
+    if args.kernels_only_ensemble:
+        run_kernels_only_ensemble(args)
         return
     if args.impl == "reference":
         run_reference(args, world, rank)
