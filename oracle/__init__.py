@@ -35,6 +35,7 @@ class Config(ctypes.Structure):
         ("bc", ctypes.c_int * 4),
         ("face_order", ctypes.c_int), ("corner_recon", ctypes.c_int),
         ("dt_fixed", ctypes.c_double),
+        ("remap", ctypes.c_int),
     ]
 
 
@@ -111,6 +112,7 @@ class Oracle:
         c.face_order = problem.face_order
         c.corner_recon = problem.corner_recon
         c.dt_fixed = problem.dt_fixed
+        c.remap = getattr(problem, "remap", 0)
         g = _c64(problem.gamma)
         pi = _c64(problem.pinf)
         self._h = L.orc_create(ctypes.byref(c), _dp(g), _dp(pi))

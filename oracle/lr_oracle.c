@@ -3,6 +3,8 @@
  * Lagrange-Remap scheme of Chaudet (arXiv 2208.13409): SGPC Lagrange phase
  * (section 1.2 eqs. "prediction"/"correction", multi-material form of
  * section 4.1), one-step remap with face and corner fluxes (section 2.3),
+ * the comparators of section 2 (one-step face-only "Direct" remap and the
+ * alternate-directions "AD" remap, multi-material forms of section 4.3),
  * corner reconstructions (section 3.3), VOF/PLIC material fluxes on the
  * rectangular Lagrangian cell (section 4.4), dual-mesh momentum remap
  * (sections 2.1.1 and 2.3) and the CFL time step (annex CFL definition).
@@ -63,6 +65,9 @@ struct orc {
   int *ncut;
   int *cutmat;                  /* [cell][MAXM]: present materials in order */
   double *cn[MAXM - 1][3];      /* per cut: normal x, normal y, constant d */
+  double *cnY[MAXM - 1][3];     /* Direct remap: the cuts used for Y faces */
+  double *fdx, *fdy;            /* AD remap: full displacement dt u^{n+1/2} */
+  long nsteps;                  /* steps taken (AD sweep order) */
   double *outv[MAXM], *sclip[MAXM];
   int *dom;
   /* node intermediates */
@@ -290,6 +295,7 @@ orc* orc_create(const orc_config* cfg, const double* gamma, const double* pinf) 
   if (!cfg || cfg->nx < 2 || cfg->ny < 2 || cfg->nmat < 1 || cfg->nmat > MAXM) return NULL;
   if (cfg->bc[0] != cfg->bc[1] || cfg->bc[2] != cfg->bc[3]) return NULL;
   if (!(cfg->x1 > cfg->x0) || !(cfg->y1 > cfg->y0)) return NULL;
+  if (cfg->remap < ORC_REMAP_DIRECTCF || cfg->remap > ORC_REMAP_AD) return NULL;
   orc* s = (orc*)calloc(1, sizeof(orc));
   s->c = *cfg;
   s->nx = cfg->nx; s->ny = cfg->ny; s->M = cfg->nmat;
@@ -314,7 +320,8 @@ orc* orc_create(const orc_config* cfg, const double* gamma, const double* pinf) 
     s->yA[a] = dalloc(nfy); s->yMm[a] = dalloc(nfy); s->yE[a] = dalloc(nfy);
   }
   for (int q = 0; q < MAXM - 1; ++q)
-    for (int z = 0; z < 3; ++z) s->cn[q][z] = dalloc(nc);
+    for (int z = 0; z < 3; ++z) { s->cn[q][z] = dalloc(nc); s->cnY[q][z] = dalloc(nc); }
+  s->fdx = dalloc(nn); s->fdy = dalloc(nn);
   s->ncut = (int*)calloc((size_t)nc, sizeof(int));
   s->dom = (int*)calloc((size_t)nc, sizeof(int));
   s->cutmat = (int*)calloc((size_t)nc * MAXM, sizeof(int));
@@ -341,7 +348,8 @@ void orc_destroy(orc* s) {
     free(s->yA[a]); free(s->yMm[a]); free(s->yE[a]);
   }
   for (int q = 0; q < MAXM - 1; ++q)
-    for (int z = 0; z < 3; ++z) free(s->cn[q][z]);
+    for (int z = 0; z < 3; ++z) { free(s->cn[q][z]); free(s->cnY[q][z]); }
+  free(s->fdx); free(s->fdy);
   free(s->ncut); free(s->dom); free(s->cutmat);
   free(s->ux); free(s->uy); free(s->pux); free(s->puy);
   free(s->mc); free(s->cc); free(s->Q); free(s->Pi); free(s->volh); free(s->vollag); free(s->vcf);
@@ -635,6 +643,37 @@ static int face_fluxes(orc* s) {
   return 0;
 }
 
+/* Face volume fluxes of the Direct and AD remaps (sections 2.1 and 2.2):
+ * the face moves with the mean of its two nodes' velocities, so an X face
+ * sweeps the rectangle dVol = u_f.e_x dt dy = 1/2 (dx_{p-} + dx_{p+}) dy,
+ * region [0, xbar] x [0, dy] in the face frame (> 0 towards +x); Y faces
+ * likewise.  dirs: 1 = X faces, 2 = Y faces, 3 = both; the faces of a
+ * direction not in dirs carry no flux.  There are no corner fluxes. */
+static void face_fluxes_rect(orc* s, int dirs) {
+  int nx = s->nx, ny = s->ny;
+  double dx = s->dx, dy = s->dy;
+  int nxu = s->perx ? nx : nx + 1, nyu = s->pery ? ny : ny + 1;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nxu; ++i) {
+      int f = XI(s, i, j);
+      double xb = (dirs & 1) ? 0.5 * (s->ddx[NI(s, i, j)] + s->ddx[NI(s, i, j + 1)]) : 0.0;
+      s->fx[f] = xb * dy;
+      s->fxb[f] = xb; s->fxlo[f] = 0.0; s->fxhi[f] = dy;
+    }
+  for (int j = 0; j < nyu; ++j)
+    for (int i = 0; i < nx; ++i) {
+      int f = YI(s, i, j);
+      double yb = (dirs & 2) ? 0.5 * (s->ddy[NI(s, i, j)] + s->ddy[NI(s, i + 1, j)]) : 0.0;
+      s->fy[f] = yb * dx;
+      s->fyb[f] = yb; s->fylo[f] = 0.0; s->fyhi[f] = dx;
+    }
+  for (int j = 0; j < nyu; ++j)
+    for (int i = 0; i < nxu; ++i) s->fc[NI(s, i, j)] = 0.0;
+  fill_xface(s, s->fx);
+  fill_yface(s, s->fy);
+  fill_node_scalar(s, s->fc);
+}
+
 /* Corner donor table of section 3.3 (upwind corner value).  For node (i,j)
  * with displacement (dx,dy): dx>0,dy>0 -> donor (i-1,j-1), receiver (i,j);
  * dx<0,dy<0 -> donor (i,j), receiver (i-1,j-1); dx>0,dy<0 -> donor (i-1,j),
@@ -706,7 +745,21 @@ static int lagcf_volume(orc* s) {
  * k_a^n.  Three materials (reading; the paper treats two): nested
  * dissection in material index order, each present material except the last
  * cut from what the previous cuts left, the last one taking the remainder. */
+static void interfaces_in(orc* s, int rect, double* (*cn)[3]);
 static void interfaces(orc* s) {
+  if (s->c.remap == ORC_REMAP_DIRECT) {
+    /* Direct remap (section 4.3): the interface i^n displaced along X with
+     * its normal kept, placed so that k_a^n holds in the X-Lagrangian cell
+     * [xl, xr] x [0, dy], cuts the X-face fluxes; i^n displaced along Y
+     * (the Y-Lagrangian cell [0, dx] x [yb, yt]) cuts the Y-face fluxes. */
+    interfaces_in(s, 1, s->cn);
+    interfaces_in(s, 2, s->cnY);
+  } else {
+    interfaces_in(s, 0, s->cn);
+  }
+}
+/* rect: 0 the Lagrangian rectangle, 1 its X extent by dy, 2 dx by its Y extent. */
+static void interfaces_in(orc* s, int rect, double* (*cn)[3]) {
   int nx = s->nx, ny = s->ny, M = s->M;
   double dx = s->dx, dy = s->dy;
   for (int j = 0; j < ny; ++j)
@@ -725,7 +778,9 @@ static void interfaces(orc* s) {
       double xr = xl + s->wx[c];
       double yb = 0.5 * dy - 0.5 * s->wy[c] + s->oy[c];
       double yt = yb + s->wy[c];
-      double area = s->wx[c] * s->wy[c];
+      if (rect == 1) { yb = 0.0; yt = dy; }
+      if (rect == 2) { xl = 0.0; xr = dx; }
+      double area = (xr - xl) * (yt - yb);
       double poly[2 * MAXV];
       rect_poly(xl, xr, yb, yt, poly);
       int nv = 4;
@@ -743,7 +798,7 @@ static void interfaces(orc* s) {
         double rem = poly_area(poly, nv);
         if (target > rem) target = rem;
         double d = plic_solve(poly, nv, nxv, nyv, target);
-        s->cn[q][0][c] = nxv; s->cn[q][1][c] = nyv; s->cn[q][2][c] = d;
+        cn[q][0][c] = nxv; cn[q][1][c] = nyv; cn[q][2][c] = d;
         double tmp[2 * MAXV];
         int m = clip_poly(poly, nv, nxv, nyv, d, -1, tmp);
         memcpy(poly, tmp, sizeof(double) * 2 * m);
@@ -757,7 +812,8 @@ static void interfaces(orc* s) {
 /* Material split of one flux region (a rectangle in the donor's frame) by the
  * donor's interface lines: each cut material takes its part of what the
  * previous cuts left; the last present material takes the rest. */
-static void split_region(orc* s, int c, double x0, double x1, double y0, double y1, double vol, double* A) {
+static void split_region(orc* s, double* (*cn)[3], int c, double x0, double x1, double y0, double y1, double vol,
+                         double* A) {
   for (int a = 0; a < MAXM; ++a) A[a] = 0.0;
   int nc = s->ncut[c];
   if (nc == 0) {
@@ -770,7 +826,7 @@ static void split_region(orc* s, int c, double x0, double x1, double y0, double 
   double used = 0.0;
   for (int q = 0; q < nc; ++q) {
     int a = s->cutmat[(long)c * MAXM + q];
-    double nxv = s->cn[q][0][c], nyv = s->cn[q][1][c], d = s->cn[q][2][c];
+    double nxv = cn[q][0][c], nyv = cn[q][1][c], d = cn[q][2][c];
     double part = nv >= 3 ? halfplane_area(poly, nv, nxv, nyv, d) : 0.0;
     A[a] = part;
     used += part;
@@ -912,7 +968,7 @@ static void material_fluxes(orc* s) {
       int left = v > 0.0;
       int di = wrapx(s, left ? i - 1 : i), dj = j;
       xface_region(s, f, left, r);
-      split_region(s, CI(s, di, dj), r[0], r[1], r[2], r[3], fabs(v), A);
+      split_region(s, s->cn, CI(s, di, dj), r[0], r[1], r[2], r[3], fabs(v), A);
       for (int a = 0; a < M; ++a) { rawx[a][f] = A[a]; s->outv[a][CI(s, di, dj)] += A[a]; }
     }
   for (int j = 0; j < nyu; ++j)
@@ -923,7 +979,8 @@ static void material_fluxes(orc* s) {
       int below = v > 0.0;
       int di = i, dj = wrapy(s, below ? j - 1 : j);
       yface_region(s, f, below, r);
-      split_region(s, CI(s, di, dj), r[0], r[1], r[2], r[3], fabs(v), A);
+      split_region(s, s->c.remap == ORC_REMAP_DIRECT ? s->cnY : s->cn, CI(s, di, dj), r[0], r[1], r[2], r[3],
+                   fabs(v), A);
       for (int a = 0; a < M; ++a) { rawy[a][f] = A[a]; s->outv[a][CI(s, di, dj)] += A[a]; }
     }
   for (int j = 0; j < nyu; ++j)
@@ -933,7 +990,7 @@ static void material_fluxes(orc* s) {
       if (s->fc[n] == 0.0 || !corner_cells(s->ddx[n], s->ddy[n], i, j, &di, &dj, &ri, &rj)) continue;
       di = wrapx(s, di); dj = wrapy(s, dj);
       corner_region(s, s->ddx[n], s->ddy[n], r);
-      split_region(s, CI(s, di, dj), r[0], r[1], r[2], r[3], s->fc[n], A);
+      split_region(s, s->cn, CI(s, di, dj), r[0], r[1], r[2], r[3], s->fc[n], A);
       for (int a = 0; a < M; ++a) { rawc[a][n] = A[a]; s->outv[a][CI(s, di, dj)] += A[a]; }
     }
   /* clipping factors */
@@ -1189,6 +1246,73 @@ static void dual_remap(orc* s, double* nux, double* nuy) {
   apply_walls(s, nux, nuy);
 }
 
+/* One remap of the state held in s (k, r, elag, ulx/uly, mc) with the
+ * displacement in ddx/ddy: fluxes (kind 0 DirectCF faces and corners, 1
+ * rectangle X and Y faces, 2 rectangle X faces only, 3 rectangle Y faces
+ * only), Lagrangian volume and rectangles, interfaces, material fluxes,
+ * cell remap into nk/nr/ne and dual remap into nux/nuy. */
+static int remap_once(orc* s, int kind, double** nk, double** nr, double** ne, double* nux, double* nuy) {
+  int rc = 0;
+  if (kind == 0) rc = face_fluxes(s);
+  else face_fluxes_rect(s, kind == 1 ? 3 : kind == 2 ? 1 : 2);
+  if (rc) return rc;
+  rc = lagcf_volume(s);
+  if (rc) return rc;
+  interfaces(s);
+  material_fluxes(s);
+  rc = cell_update(s, nk, nr, ne);
+  if (!rc) dual_remap(s, nux, nuy);
+  long nn = (long)s->nw * s->nh;
+  if (!rc)
+    for (long v = 0; v < nn; ++v) if (!(nux[v] == nux[v]) || !(nuy[v] == nuy[v])) rc = -3;
+  return rc;
+}
+
+/* AD remap (section 2.1, multi-material section 4.3): an X remap with the
+ * displacement along X only (the X-Lagrangian cell is the rectangle
+ * [xl, xr] x [0, dy]; X-face fluxes u_f.e_x dt dy), whose result
+ * (k, rho, e, u and the cell masses; e^{lagy} = e^{projx}, interfaces and
+ * normals re-placed from k^{projx}) feeds a Y remap with the displacement
+ * along Y only; X-Y on the steps numbered 0, 2, 4, ..., Y-X on the others
+ * (section 2.1, remark 3). */
+static int remap_ad(orc* s, double** nk, double** nr, double** ne, double* nux, double* nuy) {
+  long nn = (long)s->nw * s->nh, nc = (long)s->cw * s->ch;
+  memcpy(s->fdx, s->ddx, sizeof(double) * nn);
+  memcpy(s->fdy, s->ddy, sizeof(double) * nn);
+  int first_x = (s->nsteps % 2) == 0;
+  for (int sweep = 0; sweep < 2; ++sweep) {
+    int alongx = (sweep == 0) == first_x;
+    for (long v = 0; v < nn; ++v) {
+      s->ddx[v] = alongx ? s->fdx[v] : 0.0;
+      s->ddy[v] = alongx ? 0.0 : s->fdy[v];
+    }
+    int rc = remap_once(s, alongx ? 2 : 3, nk, nr, ne, nux, nuy);
+    if (rc) return rc;
+    if (sweep == 1) break;
+    /* the X (or Y) remap's result is the next sweep's Lagrangian state */
+    for (int a = 0; a < s->M; ++a) {
+      memcpy(s->k[a], nk[a], sizeof(double) * nc);
+      memcpy(s->r[a], nr[a], sizeof(double) * nc);
+      memcpy(s->elag[a], ne[a], sizeof(double) * nc);
+      fill_cell(s, s->k[a]); fill_cell(s, s->r[a]); fill_cell(s, s->elag[a]);
+    }
+    for (int j = -G; j < s->ny + G; ++j)
+      for (int i = -G; i < s->nx + G; ++i) {
+        int c = CI(s, i, j);
+        double m = 0.0;
+        for (int a = 0; a < s->M; ++a) if (s->k[a][c] > 0.0) m += s->r[a][c] * s->k[a][c] * s->V;
+        s->mc[c] = m;
+      }
+    memcpy(s->ulx, nux, sizeof(double) * nn);
+    memcpy(s->uly, nuy, sizeof(double) * nn);
+    apply_walls(s, s->ulx, s->uly);
+    fill_node_vec(s, s->ulx, s->uly);
+  }
+  memcpy(s->ddx, s->fdx, sizeof(double) * nn);
+  memcpy(s->ddy, s->fdy, sizeof(double) * nn);
+  return 0;
+}
+
 int orc_step(orc* s, double t_end, double* dt_out) {
   if (!s->inited) return -5;
   int rc = state_derived(s);
@@ -1200,20 +1324,25 @@ int orc_step(orc* s, double t_end, double* dt_out) {
   s->lastdt = dt;
   rc = lagrange(s, dt);
   if (rc) return rc;
-  rc = face_fluxes(s);
-  if (rc) return rc;
-  rc = lagcf_volume(s);
-  if (rc) return rc;
-  interfaces(s);
-  material_fluxes(s);
   long nc = (long)s->cw * s->ch, nn = (long)s->nw * s->nh;
   double *nk[MAXM], *nr[MAXM], *ne[MAXM];
   for (int a = 0; a < MAXM; ++a) { nk[a] = dalloc(nc); nr[a] = dalloc(nc); ne[a] = dalloc(nc); }
   double *nux = dalloc(nn), *nuy = dalloc(nn);
-  rc = cell_update(s, nk, nr, ne);
-  if (!rc) dual_remap(s, nux, nuy);
-  if (!rc)
-    for (int v = 0; v < nn; ++v) if (!(nux[v] == nux[v]) || !(nuy[v] == nuy[v])) rc = -3;
+  /* the AD sweeps overwrite k, r with the intermediate state: keep t^n's */
+  double *k0[MAXM], *r0[MAXM];
+  int ad = s->c.remap == ORC_REMAP_AD;
+  for (int a = 0; a < MAXM; ++a) { k0[a] = NULL; r0[a] = NULL; }
+  if (ad)
+    for (int a = 0; a < s->M; ++a) {
+      k0[a] = dalloc(nc); r0[a] = dalloc(nc);
+      memcpy(k0[a], s->k[a], sizeof(double) * nc); memcpy(r0[a], s->r[a], sizeof(double) * nc);
+    }
+  if (ad) rc = remap_ad(s, nk, nr, ne, nux, nuy);
+  else rc = remap_once(s, s->c.remap == ORC_REMAP_DIRECT ? 1 : 0, nk, nr, ne, nux, nuy);
+  if (rc && ad)
+    for (int a = 0; a < s->M; ++a) {
+      memcpy(s->k[a], k0[a], sizeof(double) * nc); memcpy(s->r[a], r0[a], sizeof(double) * nc);
+    }
   if (!rc) {
     for (int a = 0; a < s->M; ++a) {
       double* t;
@@ -1225,8 +1354,9 @@ int orc_step(orc* s, double t_end, double* dt_out) {
     t = s->ux; s->ux = nux; nux = t;
     t = s->uy; s->uy = nuy; nuy = t;
     s->t += dt;
+    s->nsteps += 1;
   }
-  for (int a = 0; a < MAXM; ++a) { free(nk[a]); free(nr[a]); free(ne[a]); }
+  for (int a = 0; a < MAXM; ++a) { free(nk[a]); free(nr[a]); free(ne[a]); free(k0[a]); free(r0[a]); }
   free(nux); free(nuy);
   return rc;
 }

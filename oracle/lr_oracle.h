@@ -21,6 +21,11 @@ extern "C" {
 
 enum { ORC_BC_REFLECT = 0, ORC_BC_PERIODIC = 1 };
 enum { ORC_CORNER_UPWIND = 0, ORC_CORNER_DIAG = 1 };
+/* Remap of the step: one-step with corner fluxes (section 2.3), one-step
+ * with face fluxes only ("Direct", section 2.2), or alternate directions
+ * ("AD", section 2.1: an X remap then a Y remap, the order swapped every
+ * other step). */
+enum { ORC_REMAP_DIRECTCF = 0, ORC_REMAP_DIRECT = 1, ORC_REMAP_AD = 2 };
 
 typedef struct {
   int nx, ny;
@@ -31,6 +36,7 @@ typedef struct {
   int face_order;        /* 1 (upwind) or 2 (Van Leer limited linear) */
   int corner_recon;      /* ORC_CORNER_UPWIND or ORC_CORNER_DIAG */
   double dt_fixed;       /* >0: use this dt instead of the CFL rule */
+  int remap;             /* ORC_REMAP_* */
 } orc_config;
 
 typedef struct orc orc;

@@ -24,6 +24,7 @@ import numpy as np
 
 BC_REFLECT, BC_PERIODIC = 0, 1
 CORNER_UPWIND, CORNER_DIAG = 0, 1
+REMAP_DIRECTCF, REMAP_DIRECT, REMAP_AD = 0, 1, 2
 
 
 @dataclasses.dataclass
@@ -50,6 +51,7 @@ class Problem:
     corner_recon: int = CORNER_DIAG
     dt_fixed: float = 0.0
     t_end: float = 1e300
+    remap: int = 0                 # REMAP_DIRECTCF, REMAP_DIRECT or REMAP_AD
 
     @property
     def nmat(self) -> int:

@@ -466,3 +466,134 @@ def test_cells_and_edge_sizes():
     # t_end reached: no step taken
     o = oracle.Oracle(P.sod(nx=16))
     assert o.step(0.0) == 0.0
+
+
+# ------------------------------------------ comparator remaps (section 2)
+def _one_node_remap(eps, remap, centre_rho):
+    """Mono-material one-node displacement (section 3.2) with upwind values
+    (the order-1 remap is linear in rho, so the centre's excess density can
+    be isolated by subtracting the uniform run)."""
+    n = 5
+    pr = _periodic_box(n)
+    pr.rho[0, n // 2, n // 2] = centre_rho
+    pr.face_order, pr.corner_recon, pr.remap = 1, P.CORNER_UPWIND, remap
+    dx = 1.0 / n
+    dt = 1e-3
+    pr.dt_fixed = dt
+    vx = np.zeros((n + 1, n + 1)); vy = np.zeros((n + 1, n + 1))
+    c = n // 2
+    vx[c + 1, c + 1] = eps * dx / dt
+    vy[c + 1, c + 1] = eps * dx / dt
+    o = oracle.Oracle(pr)
+    o.set_prescribed(vx, vy)
+    o.step()
+    return o.get(oracle.F_RHO_MAT)[0], c
+
+
+@pytest.mark.parametrize("eps", [0.2, 0.1, 0.05, 0.01])
+def test_one_node_lagrangian_volume_ad_and_direct(eps):
+    """Section 3.2: the centre's effective Lagrangian volume m^n / m^{proj} is
+    (1 + eps/2)^2 = 1 + eps + eps^2/4 for AD (two sweeps, each adding half
+    of the displaced node's area) and exactly 1 + eps for Direct."""
+    for remap, ref in ((P.REMAP_AD, (1 + eps / 2) ** 2), (P.REMAP_DIRECT, 1 + eps)):
+        r2, c = _one_node_remap(eps, remap, 3.0)
+        r1, _ = _one_node_remap(eps, remap, 1.0)
+        kept = (r2[c, c] - r1[c, c]) / 2.0        # excess mass left in the centre / excess mass
+        assert 1.0 / kept == pytest.approx(ref, rel=1e-13), remap
+
+
+@pytest.mark.parametrize("eps", [0.1, 0.05, 0.02, 0.01])
+def test_one_node_corner_mass_ad_and_direct(eps):
+    """Section 3.2: mass reaching the diagonal cell through the top-right
+    corner, per unit of the centre's mass.  Direct: 0.  AD (X then Y,
+    eps' = 0): (eps^2/4)/(1+eps/2)^2, whose expansion is the paper's
+    eps^2/4 - eps^3/4."""
+    r2, c = _one_node_remap(eps, P.REMAP_DIRECT, 3.0)
+    r1, _ = _one_node_remap(eps, P.REMAP_DIRECT, 1.0)
+    assert abs(r2[c + 1, c + 1] - r1[c + 1, c + 1]) <= 1e-14
+    r2, c = _one_node_remap(eps, P.REMAP_AD, 3.0)
+    r1, _ = _one_node_remap(eps, P.REMAP_AD, 1.0)
+    dm = (r2[c + 1, c + 1] - r1[c + 1, c + 1]) / 2.0
+    assert dm == pytest.approx((eps ** 2 / 4) / (1 + eps / 2) ** 2, rel=1e-12)
+    assert abs(dm - (eps ** 2 / 4 - eps ** 3 / 4)) <= eps ** 4
+
+
+@pytest.mark.parametrize("remap", [1, 2])
+@pytest.mark.parametrize("sx,sy", [(1, 1), (-1, 1), (1, -1), (-1, -1)])
+def test_linear_advection_order1_ad_and_direct(remap, sx, sy):
+    """Section 3.1: uniform translation at order 1.  AD reproduces the
+    boxed nine-point formula (the same as DirectCF); Direct is the
+    five-point a (1 - ex - ey) + a_{i-1,j} ex + a_{i,j-1} ey."""
+    n = 8
+    rng = np.random.default_rng(6)
+    pr = _periodic_box(n)
+    rho0 = rng.uniform(0.5, 2.0, (n, n))
+    pr.rho[0] = rho0
+    pr.face_order, pr.corner_recon, pr.remap = 1, P.CORNER_UPWIND, remap
+    dx = 1.0 / n
+    ex, ey = 0.3, 0.2
+    dt = 1e-2
+    pr.dt_fixed = dt
+    pr.ux[:] = sx * ex * dx / dt
+    pr.uy[:] = sy * ey * dx / dt
+    o = oracle.Oracle(pr)
+    o.step()
+    a = rho0
+    sh = lambda di, dj: np.roll(np.roll(a, sy * dj, axis=0), sx * di, axis=1)
+    if remap == P.REMAP_AD:
+        ref = a * (1 - ex) * (1 - ey) + sh(1, 0) * ex * (1 - ey) + sh(0, 1) * ey * (1 - ex) + sh(1, 1) * ex * ey
+    else:
+        ref = a * (1 - ex - ey) + sh(1, 0) * ex + sh(0, 1) * ey
+    np.testing.assert_allclose(o.get(oracle.F_RHO_MAT)[0], ref, rtol=1e-13)
+    np.testing.assert_allclose(o.get(oracle.F_UX), sx * ex * dx / dt, rtol=1e-13)
+    if remap == P.REMAP_AD:  # the second step sweeps Y first: same result for uniform flow
+        o.step()
+        a = ref
+        ref2 = a * (1 - ex) * (1 - ey) + sh(1, 0) * ex * (1 - ey) + sh(0, 1) * ey * (1 - ex) + sh(1, 1) * ex * ey
+        np.testing.assert_allclose(o.get(oracle.F_RHO_MAT)[0], ref2, rtol=1e-13)
+
+
+@pytest.mark.parametrize("remap", [1, 2])
+def test_comparator_remaps_preserve_uniform_state_and_conserve(remap):
+    pr = P.uniform(16, 12, rho=1.3, p=0.7, u=(0.3, -0.2), periodic=True).copy(remap=remap)
+    o = oracle.Oracle(pr)
+    for _ in range(12):
+        o.step()
+    np.testing.assert_allclose(o.get(oracle.F_RHO), 1.3, rtol=1e-13)
+    np.testing.assert_allclose(o.get(oracle.F_P), 0.7, rtol=1e-12)
+    np.testing.assert_allclose(o.get(oracle.F_UX), 0.3, rtol=1e-13)
+    pr = P.random_box(7, nx=32, ny=28, nmat=3, velocity=0.3).copy(remap=remap, bc=(P.BC_PERIODIC,) * 4)
+    o = oracle.Oracle(pr)
+    c0 = o.get(oracle.F_CONS)
+    for _ in range(20):
+        o.step()
+        k = o.get(oracle.F_K)
+        assert k.min() >= 0.0 and np.abs(k.sum(axis=0) - 1.0).max() <= 1e-14
+    c1 = o.get(oracle.F_CONS)
+    for a in range(4):
+        assert c1[a] == pytest.approx(c0[a], rel=1e-12)
+    scale = c0[3] * 0.3
+    assert abs(c1[4] - c0[4]) <= 1e-12 * scale and abs(c1[5] - c0[5]) <= 1e-12 * scale
+
+
+def test_ad_translates_axis_aligned_interface_exactly():
+    """AD multi-material (section 4.3): a vertical interface moving along x
+    is remapped exactly by the X sweep; the Y sweep has nothing to do."""
+    n = 16
+    pr = P.uniform(n, n, rho=1.0, p=1.0, u=(0.0, 0.0), periodic=True, nmat=2).copy(remap=P.REMAP_AD)
+    x = (np.arange(n) + 0.5) / n
+    ka = np.where(x < 0.5, 1.0, 0.0)[None, :].repeat(n, axis=0)
+    pr.k = np.stack([ka, 1.0 - ka])
+    pr.rho = np.stack([np.where(ka > 0, 1.0, 0.0), np.where(ka < 1, 1.0, 0.0)])
+    pr.p = np.stack([np.where(ka > 0, 1.0, 0.0), np.where(ka < 1, 1.0, 0.0)])
+    eps, dt = 0.25, 1e-2
+    pr.dt_fixed = dt
+    pr.ux[:] = eps / n / dt
+    o = oracle.Oracle(pr)
+    o.step()
+    k = o.get(oracle.F_K)[0]
+    col = np.zeros(n)
+    col[:8] = 1.0
+    col[8] = eps
+    col[0] = 1.0 - eps   # the periodic image of the interface at x = 0
+    np.testing.assert_allclose(k, col[None, :].repeat(n, axis=0), atol=1e-14)
