@@ -53,6 +53,18 @@ typedef enum {
 enum { LR_BC_REFLECT = 0, LR_BC_PERIODIC = 1 };
 enum { LR_EOS_IDEAL = 0, LR_EOS_STIFFENED = 1 };
 enum { LR_CORNER_UPWIND = 0, LR_CORNER_DIAG = 1 };
+/* Remap of the step (lr_config.remap):
+ *   LR_REMAP_DIRECTCF  one step with face and corner fluxes (section 2.3; default);
+ *   LR_REMAP_DIRECT    one step with face fluxes only, the faces moving with
+ *                      their mean node velocity (section 2.2; multi-material:
+ *                      one interface displaced along X for the X faces, one
+ *                      along Y for the Y faces, section 4.3);
+ *   LR_REMAP_AD        alternate directions (section 2.1): an X remap then a
+ *                      Y remap, Y then X on every other step; multi-material
+ *                      interfaces re-placed before each sweep (section 4.3).
+ * The comparator remaps exist to compare against; they are not available in
+ * a batch (include/lr_batch.h). */
+enum { LR_REMAP_DIRECTCF = 0, LR_REMAP_DIRECT = 1, LR_REMAP_AD = 2 };
 /* Arithmetic of the step (lr_config.precision):
  *   LR_FP64  native IEEE double (GB300 runs FP64 at 1/64 of its FP32 rate);
  *   LR_DF64  double-float: each value is an unevaluated sum of two floats
@@ -87,6 +99,7 @@ typedef struct {
   double dt_fixed;        /* > 0: use this dt instead of the CFL rule */
   int mixed_lanes;        /* threads per mixed cell in the interface kernel:
                              1, 2, 4 or 8; 0 (default) picks per precision */
+  int remap;              /* LR_REMAP_DIRECTCF (default), LR_REMAP_DIRECT or LR_REMAP_AD */
   void* cuda_stream;      /* cudaStream_t to run on; NULL = library-owned stream */
 } lr_config;
 

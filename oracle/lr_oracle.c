@@ -778,9 +778,9 @@ static void interfaces_in(orc* s, int rect, double* (*cn)[3]) {
       double xr = xl + s->wx[c];
       double yb = 0.5 * dy - 0.5 * s->wy[c] + s->oy[c];
       double yt = yb + s->wy[c];
-      if (rect == 1) { yb = 0.0; yt = dy; }
-      if (rect == 2) { xl = 0.0; xr = dx; }
-      double area = (xr - xl) * (yt - yb);
+      double area = s->wx[c] * s->wy[c];
+      if (rect == 1) { yb = 0.0; yt = dy; area = s->wx[c] * dy; }
+      if (rect == 2) { xl = 0.0; xr = dx; area = dx * s->wy[c]; }
       double poly[2 * MAXV];
       rect_poly(xl, xr, yb, yt, poly);
       int nv = 4;

@@ -56,6 +56,10 @@ bool lr_config_ok(const lr_config* c, char* why, size_t nwhy) {
     return false;
   }
   if (c->dt_fixed < 0.0) { snprintf(why, nwhy, "dt_fixed < 0"); return false; }
+  if (c->remap != LR_REMAP_DIRECTCF && c->remap != LR_REMAP_DIRECT && c->remap != LR_REMAP_AD) {
+    snprintf(why, nwhy, "remap must be LR_REMAP_DIRECTCF, LR_REMAP_DIRECT or LR_REMAP_AD");
+    return false;
+  }
   if (c->mixed_lanes != 0 && c->mixed_lanes != 1 && c->mixed_lanes != 2 && c->mixed_lanes != 4 &&
       c->mixed_lanes != 8) {
     snprintf(why, nwhy, "mixed_lanes must be 0, 1, 2, 4 or 8");
@@ -87,6 +91,11 @@ void lr_fill_grid(const lr_config& f, LrGrid& g) {
   g.corner_o2 = f.corner_recon == LR_CORNER_DIAG;
   g.mode = f.precision == LR_DF64 ? LR_MODE_DF64 : f.precision == LR_FP32 ? LR_MODE_FP32 : LR_MODE_FP64;
   g.mixed_lanes = f.mixed_lanes ? f.mixed_lanes : lr_default_mixed_lanes(g.mode);
+  g.remap = f.remap;
+  g.sweep = 0;
+  g.corners = f.remap == LR_REMAP_DIRECTCF;
+  g.lagrange = 1;
+  g.finalize = 1;
 }
 
 // Field `field` of one simulation as doubles in dst (device); s is its
@@ -292,27 +301,52 @@ lr_status check_sticky(lr_ctx* ctx) {
   return LR_OK;
 }
 
+cudaError_t launch_one(lr_ctx* ctx, int k, const LrGrid& g, const LrState& cur, const LrState& nxt) {
+  if (!ctx->prof || k >= LRK_COUNT) return lr_launch(k, g, cur, nxt, ctx->w, ctx->stream);
+  lr_ctx::Pend p;
+  p.kid = k;
+  cudaEventCreate(&p.a);
+  cudaEventCreate(&p.b);
+  cudaEventRecord(p.a, ctx->stream);
+  cudaError_t e = lr_launch(k, g, cur, nxt, ctx->w, ctx->stream);
+  cudaEventRecord(p.b, ctx->stream);
+  ctx->pend.push_back(p);
+  return e;
+}
+
+// One step from buffer `from`.  One-step remaps: the nine kernels, result in
+// the other buffer.  Alternate directions: the Lagrange phase and the first
+// sweep into the other buffer, then the sweep preparation and the second
+// sweep back into `from` (the kernels read the sweep order from the step
+// count on the device).
 cudaError_t enqueue_step(lr_ctx* ctx, int from) {
   const LrState& cur = ctx->st[from];
   const LrState& nxt = ctx->st[1 - from];
-  for (int k = 0; k < LRK_COUNT; ++k) {
-    if (ctx->prof) {
-      lr_ctx::Pend p;
-      p.kid = k;
-      cudaEventCreate(&p.a);
-      cudaEventCreate(&p.b);
-      cudaEventRecord(p.a, ctx->stream);
-      cudaError_t e = lr_launch(k, ctx->g, cur, nxt, ctx->w, ctx->stream);
-      cudaEventRecord(p.b, ctx->stream);
-      ctx->pend.push_back(p);
-      if (e != cudaSuccess) return e;
-    } else {
-      cudaError_t e = lr_launch(k, ctx->g, cur, nxt, ctx->w, ctx->stream);
+  if (ctx->g.remap != LR_REMAP_AD) {
+    for (int k = 0; k < LRK_COUNT; ++k) {
+      cudaError_t e = launch_one(ctx, k, ctx->g, cur, nxt);
       if (e != cudaSuccess) return e;
     }
+    return cudaSuccess;
+  }
+  LrGrid g1 = ctx->g, g2 = ctx->g;
+  g1.sweep = 1; g1.finalize = 0;
+  g2.sweep = 2; g2.lagrange = 0;
+  for (int k = 0; k < LRK_COUNT; ++k) {
+    cudaError_t e = launch_one(ctx, k, g1, cur, nxt);
+    if (e != cudaSuccess) return e;
+  }
+  const int second[] = {LRK_SWEEP_PREP, LRK_CELL_LAG, LRK_CELL_CF, LRK_MIXED, LRK_MAT_FLUX,
+                        LRK_CELL_UPDATE, LRK_DUAL_FLUX, LRK_NODE_UPDATE};
+  for (int k : second) {
+    cudaError_t e = launch_one(ctx, k, g2, nxt, cur);
+    if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
+
+// Buffer holding the state after a step from `from`.
+int after_step(const lr_ctx* ctx, int from) { return ctx->g.remap == LR_REMAP_AD ? from : 1 - from; }
 
 lr_status ensure_graph(lr_ctx* ctx, int from) {
   if (ctx->gvalid[from]) return LR_OK;
@@ -480,7 +514,7 @@ lr_status lr_step(lr_ctx* ctx, double t_end, double* dt_taken) {
   if (ctx->sticky != LR_OK) return (lr_status)ctx->sticky;
   CK(lr_launch_set_tend(ctx->g, ctx->w, t_end, ctx->stream), "set t_end");
   CK(enqueue_step(ctx, ctx->cur), "step launch");
-  ctx->cur = 1 - ctx->cur;
+  ctx->cur = after_step(ctx, ctx->cur);
   if (dt_taken) {
     lr_status s = check_sticky(ctx);
     if (s != LR_OK) return s;
@@ -517,7 +551,7 @@ lr_status lr_run(lr_ctx* ctx, double t_end, long max_steps, long* steps_done, do
         if (s != LR_OK) return s;
         CK(cudaGraphLaunch(ctx->gexec[ctx->cur], ctx->stream), "graph launch");
       }
-      ctx->cur = 1 - ctx->cur;
+      ctx->cur = after_step(ctx, ctx->cur);
     }
     done += n;
     double sc[5];
@@ -573,8 +607,11 @@ lr_status lr_time(lr_ctx* ctx, double* t, double* dt_next) {
 }
 
 int lr_launches_per_step(const lr_ctx* ctx) {
-  // the t_end/dt kernel, then the step's kernels (no interface kernel with one material)
-  return ctx ? 1 + (int)LRK_COUNT - (ctx->g.M == 1 ? 1 : 0) : 0;
+  // the t_end/dt kernel, then the step's kernels (no interface kernel with one
+  // material); alternate directions: a second sweep of eight kernels
+  if (!ctx) return 0;
+  int one = (int)LRK_COUNT - (ctx->g.M == 1 ? 1 : 0);
+  return 1 + one + (ctx->g.remap == LR_REMAP_AD ? one - 1 : 0);
 }
 
 lr_status lr_set_profiling(lr_ctx* ctx, int on) {

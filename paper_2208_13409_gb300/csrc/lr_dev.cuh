@@ -31,6 +31,13 @@ struct LrGrid {
   double gam[LR_MAXM], pin[LR_MAXM];
   int face_o2, corner_o2, presc;
   int mixed_lanes;         // lanes per mixed cell in lr_mixed: 1, 2, 4 or 8
+  // Remap of the step (LR_REMAP_*) and, for the alternate-directions remap,
+  // the sweep a launch belongs to: sweep 0 remaps with the full displacement,
+  // 1 with its x part only (X faces), 2 with its y part only.  corners: the
+  // remap has corner fluxes; lagrange: lr_cell_lag also computes Vol^{lag}
+  // and e^{lag} (not in a second sweep); finalize: lr_node_update ends the
+  // step (CFL rule, time advance).
+  int remap, sweep, corners, lagrange, finalize;
   // Place of this simulation in arrays shared by a batch (all 0 for a lone
   // simulation): first cell, node and dual-cell index (face arrays use the
   // node offset, their per-instance slots being node-sized), its scalar
@@ -140,7 +147,8 @@ enum LrKernelId {
   LRK_CELL_PRE = 0, LRK_NODE_HALF, LRK_CELL_LAG, LRK_CELL_CF, LRK_MIXED, LRK_MAT_FLUX,
   LRK_CELL_UPDATE, LRK_DUAL_FLUX, LRK_NODE_UPDATE, LRK_COUNT,
   LRK_PREPARE = 100,   // initial state from the staging area
-  LRK_CFL_ONLY = 101   // CFL rule from the current state
+  LRK_CFL_ONLY = 101,  // CFL rule from the current state
+  LRK_SWEEP_PREP = 102 // alternate directions: the first sweep's result as the second's input
 };
 // Iteration domains of the kernels (tile tables of a batch are per domain).
 enum { LR_DOM_CELLS = 0, LR_DOM_NODES, LR_DOM_DUAL, LR_DOM_NODES_ALL, LR_NDOM };

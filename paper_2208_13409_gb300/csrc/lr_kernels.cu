@@ -15,6 +15,7 @@
 // double.  Boundary conditions are applied on read: an index outside the
 // domain maps to its mirror image (reflective wall, with the sign of the
 // mirrored vector component or flux flipped) or wraps (periodic).
+#include "../../include/lr.h"
 #include "lr_dev.cuh"
 #include "lr_real.cuh"
 #include <math.h>
@@ -129,6 +130,17 @@ template <class R> __device__ __forceinline__ R cellOY(const LrGrid& g, const R*
 __device__ __forceinline__ void set_err(int* err, int bit, int idx) {
   atomicOr(&err[0], bit);
   atomicCAS(&err[1], -1, idx);
+}
+
+// Displacement component an alternate-directions sweep remaps with: 0 both
+// (one-step remaps), 1 x only, 2 y only.  The first sweep of a step goes
+// along x when the number of steps taken so far is even, along y otherwise
+// (section 2.1, remark 3); the count is read on the device, so the order
+// follows the steps actually taken.
+__device__ __forceinline__ int sweep_axis(const LrGrid& g, const double* scal) {
+  if (g.sweep == 0) return 0;
+  bool even = (((long long)scal[LR_NSCAL * g.inst + 4]) & 1ll) == 0;
+  return ((g.sweep == 1) == even) ? 1 : 2;
 }
 
 // Per-simulation scalars and error word (slot g.inst).
@@ -306,6 +318,13 @@ __device__ __forceinline__ int corner_cells(R ddx, R ddy, int i, int j, int& di,
   return 0;
 }
 
+// Corner donor of a node in a remap with corner fluxes; none otherwise.
+template <class R>
+__device__ __forceinline__ int corner_of(const LrGrid& g, R ddx, R ddy, int i, int j, int& di, int& dj, int& ri,
+                                         int& rj) {
+  return g.corners ? corner_cells(ddx, ddy, i, j, di, dj, ri, rj) : 0;
+}
+
 // ============================================================== kernels
 // K1: pseudo-viscosity Q^n and the predictor thermodynamics (section 1.2,
 // section 4.1): Vol^{n+1/2} = F(x^n + dt/2 u^n); rho_a^{n+1/2} =
@@ -424,7 +443,10 @@ __device__ __forceinline__ void node_half_at(const LrGrid& g, const KC<R>& kc, c
   if (!g.pery && (j == 0 || j == g.ny)) { hy = Z; ly = Z; }
   w.uhx[n] = hx; w.uhy[n] = hy;
   w.ulx[n] = lx; w.uly[n] = ly;
-  w.ddx[n] = dt * hx; w.ddy[n] = dt * hy;
+  // displacement of the remap: the x or y part only in an alternate-directions sweep
+  int ax = sweep_axis(g, w.scal);
+  w.ddx[n] = ax == 2 ? Z : dt * hx;
+  w.ddy[n] = ax == 1 ? Z : dt * hy;
 }
 
 // K3: corrector (section 1.2): Vol^{lag} = F(x^n + dt u^{n+1/2}),
@@ -452,15 +474,26 @@ __device__ __forceinline__ void cell_lag_at(const LrGrid& g, const KC<R>& kc, co
     int ll = nb + j * nn + i, lr = nb + j * nn + i1, ul = nb + j1 * nn + i, ur = nb + j1 * nn + i1;
     R dxll = w.ddx[ll], dxlr = w.ddx[lr], dxul = w.ddx[ul], dxur = w.ddx[ur];
     R dyll = w.ddy[ll], dylr = w.ddy[lr], dyul = w.ddy[ul], dyur = w.ddy[ur];
-    R vol = cell_F(dxll, dyll, kc.dx + dxlr, dylr, dxul, kc.dy + dyul, kc.dx + dxur, kc.dy + dyur);
-    if (!O::pos(vol)) set_err(err_of(g, w.err), LR_DERR_VOLUME, c);
-    R dv = vol - kc.V;
-    unsigned msk = w.mask[c];
+    if (g.lagrange) {
+      // Lagrange phase: the full displacement dt u^{n+1/2} (the remap's is
+      // one component of it in an alternate-directions sweep)
+      R fxll = dxll, fxlr = dxlr, fxul = dxul, fxur = dxur;
+      R fyll = dyll, fylr = dylr, fyul = dyul, fyur = dyur;
+      if (g.sweep != 0) {
+        R dt = w.dtR[g.inst];
+        fxll = dt * w.uhx[ll]; fxlr = dt * w.uhx[lr]; fxul = dt * w.uhx[ul]; fxur = dt * w.uhx[ur];
+        fyll = dt * w.uhy[ll]; fylr = dt * w.uhy[lr]; fyul = dt * w.uhy[ul]; fyur = dt * w.uhy[ur];
+      }
+      R vol = cell_F(fxll, fyll, kc.dx + fxlr, fylr, fxul, kc.dy + fyul, kc.dx + fxur, kc.dy + fyur);
+      if (!O::pos(vol)) set_err(err_of(g, w.err), LR_DERR_VOLUME, c);
+      R dv = vol - kc.V;
+      unsigned msk = w.mask[c];
 #pragma unroll
-    for (int a = 0; a < M; ++a) {
-      R el = Z;
-      if (msk & (1u << a)) el = cur.e[a][c] - w.elc[a][c] * dv;
-      w.elag[a][c] = el;
+      for (int a = 0; a < M; ++a) {
+        R el = Z;
+        if (msk & (1u << a)) el = cur.e[a][c] - w.elc[a][c] * dv;
+        w.elag[a][c] = el;
+      }
     }
     R xl = H * (dxll + dxul), xr = kc.dx + H * (dxlr + dxur);
     R yb = H * (dyll + dylr), yt = kc.dy + H * (dyul + dyur);
@@ -468,6 +501,24 @@ __device__ __forceinline__ void cell_lag_at(const LrGrid& g, const KC<R>& kc, co
     w.oy[c] = H * (yb + yt) - H * kc.dy;
     w.wx[c] = xr - xl;
     w.wy[c] = yt - yb;
+  }
+  if (!g.corners) {
+    // Direct and alternate-directions remaps (sections 2.1, 2.2): a face
+    // moves with the mean of its nodes, sweeping the rectangle
+    // [0, xbar] x [0, dy] (X face) or [0, dx] x [0, ybar] (Y face)
+    if (j < g.ny) {
+      int pm = nb + j * nn + i, pp = nb + j1 * nn + i, f = nb + j * nn + i;
+      R xb = H * (w.ddx[pm] + w.ddx[pp]);
+      w.fx[f] = xb * kc.dy;
+      w.fxb[f] = xb; w.fxlo[f] = Z; w.fxhi[f] = kc.dy;
+    }
+    if (i < g.nx) {
+      int pm = nb + j * nn + i, pp = nb + j * nn + i1, f = nb + j * g.nx + i;
+      R yb = H * (w.ddy[pm] + w.ddy[pp]);
+      w.fy[f] = yb * kc.dx;
+      w.fyb[f] = yb; w.fylo[f] = Z; w.fyhi[f] = kc.dx;
+    }
+    return;
   }
   if (j < g.ny) {  // X face (i, j), canonical i
     int pm = nb + j * nn + i, pp = nb + j1 * nn + i;
@@ -516,7 +567,7 @@ __device__ __forceinline__ void cell_cf_at(const LrGrid& g, const KC<R>& kc, con
     int n = nix(g, i + a, j + b).idx;
     R cx = w.ddx[n], cy = w.ddy[n];
     int di, dj, ri, rj;
-    if (!corner_cells(cx, cy, i + a, j + b, di, dj, ri, rj)) continue;
+    if (!corner_of(g, cx, cy, i + a, j + b, di, dj, ri, rj)) continue;
     R f = O::abs(cx * cy);
     if (di == i && dj == j) v += f;
     if (ri == i && rj == j) v -= f;
@@ -592,10 +643,30 @@ __device__ __forceinline__ int donated_flux(const LrGrid& g, const LrWorkT<R>& w
   int n = nix(g, i + qa, j + qb).idx;
   double cx = O::todouble(w.ddx[n]), cy = O::todouble(w.ddy[n]);
   int di, dj, ri, rj;
-  if (!corner_cells(cx, cy, i + qa, j + qb, di, dj, ri, rj) || di != i || dj != j) return -1;
+  if (!corner_of(g, cx, cy, i + qa, j + qb, di, dj, ri, rj) || di != i || dj != j) return -1;
   corner_region(g, cx, cy, r);
   vol = fabs(cx * cy); fidx = n;
   return 2;
+}
+
+// Interface lines of a mixed cell in the rectangle [xl,xr] x [yb,yt] of
+// area `area`: the first present material's line by the closed-form PLIC,
+// a second one (three materials) cut from what the first left.  nrm: the
+// Youngs normals of the first two present materials; k0, k1 their fractions.
+__device__ __forceinline__ void place_cuts(int ncut, double k0, double k1, const double (*nrm)[2], double xl,
+                                           double xr, double yb, double yt, double area, double (*cut)[3]) {
+  cut[0][0] = nrm[0][0]; cut[0][1] = nrm[0][1];
+  cut[0][2] = rect_plic(xl, xr, yb, yt, nrm[0][0], nrm[0][1], k0);
+  if (ncut == 2) {
+    Poly rect, rest;
+    poly_rect(rect, xl, xr, yb, yt);
+    poly_clip(rect, cut[0][0], cut[0][1], cut[0][2], -1.0, rest);
+    double target = k1 * area;
+    double ra = poly_area(rest);
+    if (target > ra) target = ra;
+    cut[1][0] = nrm[1][0]; cut[1][1] = nrm[1][1];
+    cut[1][2] = poly_plic(rest, nrm[1][0], nrm[1][1], target);
+  }
 }
 
 // K4b: the interface work of mixed cells only (the list built by lr_cell_pre),
@@ -626,29 +697,23 @@ __device__ __forceinline__ void mixed_at(const LrGrid& g, const LrStateT<R>& cur
       if (msk & (1u << a)) order[np++] = a;
       if (kk[a] > kk[dom]) dom = a;
     }
-    // ---- interface lines in the rectangular Lagrangian cell
+    // ---- interface lines in the rectangular Lagrangian cell (Direct remap:
+    // one set in the X-Lagrangian cell [xl, xr] x [0, dy] for the X faces,
+    // one in the Y-Lagrangian cell [0, dx] x [yb, yt] for the Y faces)
     double wxc = O::todouble(w.wx[c]), wyc = O::todouble(w.wy[c]);
     double xl = 0.5 * g.dx - 0.5 * wxc + O::todouble(w.ox[c]), xr = xl + wxc;
     double yb = 0.5 * g.dy - 0.5 * wyc + O::todouble(w.oy[c]), yt = yb + wyc;
     int ncut = np - 1;
-    double cut[2][3];
-    {
-      double nxv, nyv;
-      youngs(g, cur.k[order[0]], i, j, nxv, nyv);
-      cut[0][0] = nxv; cut[0][1] = nyv;
-      cut[0][2] = rect_plic(xl, xr, yb, yt, nxv, nyv, kk[order[0]]);
-    }
-    if (ncut == 2) {
-      double nxv, nyv;
-      youngs(g, cur.k[order[1]], i, j, nxv, nyv);
-      Poly rect, rest;
-      poly_rect(rect, xl, xr, yb, yt);
-      poly_clip(rect, cut[0][0], cut[0][1], cut[0][2], -1.0, rest);
-      double target = kk[order[1]] * (wxc * wyc);
-      double ra = poly_area(rest);
-      if (target > ra) target = ra;
-      cut[1][0] = nxv; cut[1][1] = nyv;
-      cut[1][2] = poly_plic(rest, nxv, nyv, target);
+    const bool direct = g.remap == LR_REMAP_DIRECT;
+    double cut[2][3], cutY[2][3];
+    double nrm[2][2];
+    youngs(g, cur.k[order[0]], i, j, nrm[0][0], nrm[0][1]);
+    if (ncut == 2) youngs(g, cur.k[order[1]], i, j, nrm[1][0], nrm[1][1]);
+    if (direct) {
+      place_cuts(ncut, kk[order[0]], ncut == 2 ? kk[order[1]] : 0.0, nrm, xl, xr, 0.0, g.dy, wxc * g.dy, cut);
+      place_cuts(ncut, kk[order[0]], ncut == 2 ? kk[order[1]] : 0.0, nrm, 0.0, g.dx, yb, yt, g.dx * wyc, cutY);
+    } else {
+      place_cuts(ncut, kk[order[0]], ncut == 2 ? kk[order[1]] : 0.0, nrm, xl, xr, yb, yt, wxc * wyc, cut);
     }
     if (valid && lane == 0) {
       w.cut[0][c] = cut[0][0]; w.cut[1][c] = cut[0][1]; w.cut[2][c] = cut[0][2];
@@ -668,7 +733,7 @@ __device__ __forceinline__ void mixed_at(const LrGrid& g, const LrStateT<R>& cur
       int fidx = 0;
       int kind = valid ? donated_flux(g, w, i, j, lane * K + q, r, vol, fidx) : -1;
       if (kind >= 0) {
-        split_region<M>(ncut, order, cut, r, vol, A);
+        split_region<M>(ncut, order, (direct && kind == 1) ? cutY : cut, r, vol, A);
 #pragma unroll
         for (int a = 0; a < M; ++a) {
           R* dst = kind == 0 ? w.xAm[a] : kind == 1 ? w.yAm[a] : w.cAm[a];
@@ -921,7 +986,7 @@ __device__ __forceinline__ void mat_flux_at(const LrGrid& g, const KC<R>& kc, co
     unsigned dm = 0u;
     R fv = Z;
     bool pp = false;
-    if (corner_cells(ddx, ddy, i, j, di, dj, ri, rj)) {
+    if (corner_of(g, ddx, ddy, i, j, di, dj, ri, rj)) {
       fv = O::abs(ddx * ddy);
       dc = cix(g, di, dj).idx;
       dm = w.mask[dc];
@@ -990,7 +1055,7 @@ __device__ __forceinline__ void cell_update_at(const LrGrid& g, const KC<R>& kc,
     cn[q] = n;
     int di, dj, ri, rj;
     cs[q] = 0;
-    if (corner_cells(w.ddx[n], w.ddy[n], i + a, j + b, di, dj, ri, rj)) {
+    if (corner_of(g, w.ddx[n], w.ddy[n], i + a, j + b, di, dj, ri, rj)) {
       if (ri == i && rj == j) cs[q] = 1;
       if (di == i && dj == j) cs[q] = -1;
     }
@@ -1321,9 +1386,17 @@ __device__ __forceinline__ void node_update_at(const LrGrid& g, const KC<R>& kc,
     if (!g.pery && (j == 0 || j == g.ny)) uy1 = Z;
     nxt.ux[n] = ux1;
     nxt.uy[n] = uy1;
-    R cm = rmax(rmax(w.cc[cix(g, i - 1, j - 1).idx], w.cc[cix(g, i, j - 1).idx]),
-                rmax(w.cc[cix(g, i - 1, j).idx], w.cc[cix(g, i, j).idx]));
-    val = cm + O::sqrt(ux1 * ux1 + uy1 * uy1);
+    if (g.finalize) {
+      R cm = rmax(rmax(w.cc[cix(g, i - 1, j - 1).idx], w.cc[cix(g, i, j - 1).idx]),
+                  rmax(w.cc[cix(g, i - 1, j).idx], w.cc[cix(g, i, j).idx]));
+      val = cm + O::sqrt(ux1 * ux1 + uy1 * uy1);
+    }
+  }
+  if (!g.finalize) {
+    // first sweep of an alternate-directions step: its mixed-cell list has
+    // been consumed; the second sweep's preparation refills it
+    if (i == 0 && j == 0) w.red[g.mslot] = 0ull;
+    return;
   }
   cfl_finalize(g, kc, w, val, true, ntiles);
 }
@@ -1342,6 +1415,50 @@ __device__ __forceinline__ void cfl_only_at(const LrGrid& g, const KC<R>& kc, co
     val = cm + O::sqrt(ux1 * ux1 + uy1 * uy1);
   }
   cfl_finalize(g, kc, w, val, false, ntiles);
+}
+
+// Between the two sweeps of an alternate-directions step (sections 2.1 and
+// 4.3): the first sweep's result (state `cur`) becomes the second sweep's
+// Lagrangian state -- e^{lag} := e^{proj}, u^{lag} := u^{proj}, the cell
+// masses, the material masks and the mixed-cell list from k^{proj} -- and
+// the remap displacement becomes the other component of dt u^{n+1/2}.
+template <class R, int M>
+__device__ __forceinline__ void sweep_prep_at(const LrGrid& g, const KC<R>& kc, const LrStateT<R>& cur,
+                                              const LrWorkT<R>& w, int i, int j) {
+  using O = RealOps<R>;
+  if (i >= g.nxu || j >= g.nyu) return;
+  if (!step_live(g, w.scal)) return;
+  const R Z = O::c(0.0f);
+  R dt = w.dtR[g.inst];
+  int n = g.noff + j * (g.nx + 1) + i;
+  w.ulx[n] = cur.ux[n];
+  w.uly[n] = cur.uy[n];
+  int ax = sweep_axis(g, w.scal);
+  w.ddx[n] = ax == 2 ? Z : dt * w.uhx[n];
+  w.ddy[n] = ax == 1 ? Z : dt * w.uhy[n];
+  if (i >= g.nx || j >= g.ny) return;
+  int c = g.coff + j * g.nx + i;
+  R m = Z;
+  unsigned msk = 0u;
+#pragma unroll
+  for (int a = 0; a < M; ++a) {
+    R ka = cur.k[a][c];
+    R el = Z;
+    if (O::pos(ka)) {
+      msk |= 1u << a;
+      R ra = cur.r[a][c];
+      m += ra * ka * kc.V;
+      el = cur.e[a][c];
+    }
+    w.elag[a][c] = el;
+  }
+  w.mc[c] = m;
+  w.mask[c] = (unsigned char)msk;
+  if (msk & (msk - 1u)) {
+    int slot = g.moff + (int)atomicAdd(&w.red[g.mslot], 1ull);
+    w.mixed[slot] = c;
+    if (w.minst) w.minst[slot] = g.inst;
+  }
 }
 
 // Initial state from the staging area (doubles k, rho, p, ux, uy): drop
@@ -1632,6 +1749,12 @@ LR_KERNEL_PAIR(prepare, OpPrepare)
 #undef LR_KERNEL_PAIR
 
 template <class R, int M>
+__global__ void __launch_bounds__(256) lr_sweep_prep(LrGrid g, KC<R> kc, LrStateT<R> cur, LrStateT<R> nxt,
+                                                     LrWorkT<R> w) {
+  sweep_prep_at<R, M>(g, kc, cur, w, blockIdx.x * BX + threadIdx.x, blockIdx.y * BY + threadIdx.y);
+}
+
+template <class R, int M>
 __global__ void __launch_bounds__(128) lr_mixed(LrGrid g, LrStateT<R> cur, LrWorkT<R> w) {
   if (!step_live(g, w.scal)) return;
   mixed_loop<R, M>([&](int) -> const LrGrid& { return g; }, cur, w, g.mixed_lanes, g.mslot, g.moff);
@@ -1678,6 +1801,7 @@ cudaError_t launch_t(int kid, const LrGrid& g, const LrState& cur0, const LrStat
     case LRK_NODE_UPDATE: LR_1(lr_node_update, grid_for(g.nxu, g.nyu)); break;
     case LRK_PREPARE: LR_M(lr_prepare, grid_for(g.nx + 1, g.ny + 1)); break;
     case LRK_CFL_ONLY: LR_1(lr_cfl_only, grid_for(g.nxu, g.nyu)); break;
+    case LRK_SWEEP_PREP: LR_M(lr_sweep_prep, grid_for(g.nxu, g.nyu)); break;
     default: return cudaErrorInvalidValue;
   }
 #undef LR_M

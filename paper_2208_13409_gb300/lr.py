@@ -24,6 +24,7 @@ SERVE_HEADER = os.path.join(os.path.dirname(HEADER), "lr_serve.h")
 OK, ERR_ARG, ERR_OOM, ERR_NUMERIC, ERR_TIMEOUT, ERR_STATE, ERR_CUDA = 0, -1, -2, -3, -4, -5, -6
 BC_REFLECT, BC_PERIODIC = 0, 1
 CORNER_UPWIND, CORNER_DIAG = 0, 1
+REMAP_DIRECTCF, REMAP_DIRECT, REMAP_AD = 0, 1, 2
 FP64, DF64, FP32 = 0, 1, 2
 F_K, F_RHO_MAT, F_E_MAT, F_P, F_RHO, F_E, F_UX, F_UY, F_CONS, F_C = range(10)
 F_UHX, F_UHY, F_VOL_LAGCF, F_E_LAG, F_FX, F_FY, F_FC, F_MX, F_MY, F_MC, F_Q, F_DT = range(20, 32)
@@ -47,6 +48,7 @@ class Config(ctypes.Structure):
         ("precision", ctypes.c_int), ("face_order", ctypes.c_int), ("corner_recon", ctypes.c_int),
         ("dt_fixed", ctypes.c_double),
         ("mixed_lanes", ctypes.c_int),
+        ("remap", ctypes.c_int),
         ("cuda_stream", ctypes.c_void_p),
     ]
 
@@ -214,6 +216,7 @@ def make_config(problem, stream: Optional[int] = None, precision: int = FP64, mi
     c.corner_recon = problem.corner_recon
     c.dt_fixed = problem.dt_fixed
     c.mixed_lanes = mixed_lanes
+    c.remap = getattr(problem, "remap", 0)
     c.cuda_stream = stream
     return c
 

@@ -210,3 +210,46 @@ def test_conservation_on_gpu():
     orc = oracle.Oracle(pr)
     orc.run(25)
     np.testing.assert_allclose(c1, orc.get(oracle.F_CONS), rtol=1e-11, atol=1e-14)
+
+
+REMAPS = {"direct": P.REMAP_DIRECT, "ad": P.REMAP_AD}
+REMAP_CASES = {
+    "sod_256x4": lambda: P.sod(),
+    "triple_point_140x60": lambda: P.triple_point(140, 60),
+    "random2_walls_velocity": lambda: P.random_box(21, nx=77, ny=45, nmat=2, velocity=0.3),
+    "random3_walls_velocity": lambda: P.random_box(22, nx=53, ny=70, nmat=3, velocity=0.3),
+    "random3_periodic": lambda: P.random_box(23, nx=66, ny=39, nmat=3, velocity=0.4).copy(bc=(P.BC_PERIODIC,) * 4),
+    "mixed_bc_xper": lambda: P.random_box(24, nx=40, ny=33, nmat=2, velocity=0.2).copy(
+        bc=(P.BC_PERIODIC, P.BC_PERIODIC, P.BC_REFLECT, P.BC_REFLECT)),
+    "upwind_o1": lambda: P.random_box(25, nx=48, ny=48, nmat=2, velocity=0.3).copy(
+        face_order=1, corner_recon=P.CORNER_UPWIND),
+    "air_water_128": lambda: P.air_water(5, side=128),
+}
+
+
+@pytest.mark.parametrize("prec", sorted(PRECISIONS))
+@pytest.mark.parametrize("remap", sorted(REMAPS))
+@pytest.mark.parametrize("name", sorted(REMAP_CASES))
+def test_comparator_remaps_one_and_six_steps(name, remap, prec):
+    """Direct and alternate-directions remaps (section 2) against the
+    oracle; six steps cover both sweep orders of the AD remap."""
+    pr = REMAP_CASES[name]().copy(remap=REMAPS[remap])
+    sim, orc = _pair(pr, PRECISIONS[prec])
+    _steps(sim, orc, 1)
+    _assert_close(compare(sim, orc), TOL_1, f"{name} {remap} 1 step")
+    _steps(sim, orc, 5)
+    _assert_close(compare(sim, orc), 1e-10, f"{name} {remap} 6 steps")
+
+
+@pytest.mark.parametrize("remap", sorted(REMAPS))
+def test_comparator_remaps_100_steps_and_graphs(remap):
+    """100 steps through lr_run (CUDA graphs; the AD sweep order read from
+    the device step count) against the oracle, L1."""
+    pr = P.triple_point(140, 60).copy(remap=REMAPS[remap])
+    sim, orc = _pair(pr)
+    n, t = sim.run(100)
+    assert n == 100
+    for _ in range(100):
+        orc.step()
+    assert t == pytest.approx(orc.t, rel=1e-12)
+    _assert_close(compare(sim, orc, l1_rel), TOL_100, f"{remap} 100 steps")
