@@ -899,13 +899,92 @@ static double recon_corner(orc* s, const double* q, int ci, int cj, double ddx, 
 }
 static int pure_in(orc* s, int a, int ci, int cj) { return s->k[a][CI(s, ci, cj)] == 1.0; }
 
+/* Van Leer limited slopes of q in cell (ci,cj) (section 2.1.1 and the
+ * diagonal form of section 3.3): along x and y over the Lagrangian centres
+ * of the two neighbours, along v = (dx,dy)/|.| and v_perp = (dx,-dy)/|.|
+ * over the diagonal neighbours' Lagrangian centres projected on v, v_perp. */
+static double slope_axis(orc* s, const double* q, int ci, int cj, int dirx) {
+  int c = CI(s, ci, cj);
+  int cm = dirx ? CI(s, ci - 1, cj) : CI(s, ci, cj - 1);
+  int cp = dirx ? CI(s, ci + 1, cj) : CI(s, ci, cj + 1);
+  double h = dirx ? s->dx : s->dy;
+  const double* o = dirx ? s->ox : s->oy;
+  return vanleer((q[c] - q[cm]) / (h + o[c] - o[cm]), (q[cp] - q[c]) / (h + o[cp] - o[c]));
+}
+static double slope_diag(orc* s, const double* q, int ci, int cj, int pp) {
+  double dx = s->dx, dy = s->dy, D = sqrt(dx * dx + dy * dy);
+  int c = CI(s, ci, cj);
+  double sy = pp ? 1.0 : -1.0;
+  int sj = pp ? 1 : -1;
+  int cp = CI(s, ci + 1, cj + sj), cm = CI(s, ci - 1, cj - sj);
+  double sp = ((dx + s->ox[cp] - s->ox[c]) * dx + (sy * dy + s->oy[cp] - s->oy[c]) * sy * dy) / D;
+  double sm = ((dx + s->ox[c] - s->ox[cm]) * dx + (sy * dy + s->oy[c] - s->oy[cm]) * sy * dy) / D;
+  return vanleer((q[c] - q[cm]) / sm, (q[cp] - q[c]) / sp);
+}
+
+/* x-y corner value (section 3.3): a_c + delta_x/2 (sgn(dVol_fx) dx_c^{lag}
+ * - dt u_fx) + delta_y/2 (sgn(dVol_fy) dy_c^{lag} - dt u_fy), with f_x the
+ * donor's X face on the side of the corner (in the donor's row), f_y its Y
+ * face on that side (in its column); sgn(0) = 0. */
+static double recon_corner_xy(orc* s, const double* q, int di, int dj, double ddx, double ddy) {
+  int c = CI(s, di, dj);
+  int fxi = di + (ddx > 0.0 ? 1 : 0), fyj = dj + (ddy > 0.0 ? 1 : 0);
+  double vx = s->fx[XI(s, fxi, dj)], vy = s->fy[YI(s, di, fyj)];
+  double sgx = vx > 0.0 ? 1.0 : vx < 0.0 ? -1.0 : 0.0;
+  double sgy = vy > 0.0 ? 1.0 : vy < 0.0 ? -1.0 : 0.0;
+  double fdx = 0.5 * (s->ddx[NI(s, fxi, dj)] + s->ddx[NI(s, fxi, dj + 1)]);
+  double fdy = 0.5 * (s->ddy[NI(s, di, fyj)] + s->ddy[NI(s, di + 1, fyj)]);
+  return q[c] + 0.5 * slope_axis(s, q, di, dj, 1) * (sgx * s->wx[c] - fdx)
+              + 0.5 * slope_axis(s, q, di, dj, 0) * (sgy * s->wy[c] - fdy);
+}
+
+/* Multidimensional value (section 3.3): the plane a_c + G.(x - x_c) whose
+ * cell means best fit the 9-point stencil in least squares, G solving the
+ * normal equations (X^T X) G = X^T A with rows X = x_kl^{lag} - x_c^{lag}
+ * (the Lagrangian rectangles' centres; a rectangle's mean of x - x_c is its
+ * centre's offset) and A = a_kl - a_c; the gradient is scaled to the norm
+ * min(|delta_x|, |delta_y|, |delta_v|, |delta_vperp|) of the limited 1D
+ * slopes (direction kept) and evaluated at (px, py) in the donor's frame
+ * (origin at its Eulerian lower-left node). */
+static double recon_lsq(orc* s, const double* q, int di, int dj, double px, double py) {
+  int c = CI(s, di, dj);
+  double sxx = 0.0, sxy = 0.0, syy = 0.0, sxa = 0.0, sya = 0.0;
+  for (int l = -1; l <= 1; ++l)
+    for (int k = -1; k <= 1; ++k) {
+      if (k == 0 && l == 0) continue;
+      int n = CI(s, di + k, dj + l);
+      double X1 = k * s->dx + s->ox[n] - s->ox[c];
+      double X2 = l * s->dy + s->oy[n] - s->oy[c];
+      double A = q[n] - q[c];
+      sxx += X1 * X1; sxy += X1 * X2; syy += X2 * X2; sxa += X1 * A; sya += X2 * A;
+    }
+  double det = sxx * syy - sxy * sxy;
+  double g1 = (syy * sxa - sxy * sya) / det;
+  double g2 = (sxx * sya - sxy * sxa) / det;
+  double gn = sqrt(g1 * g1 + g2 * g2);
+  if (!(gn > 0.0)) return q[c];
+  double m = fabs(slope_axis(s, q, di, dj, 1));
+  double t = fabs(slope_axis(s, q, di, dj, 0)); if (t < m) m = t;
+  t = fabs(slope_diag(s, q, di, dj, 1)); if (t < m) m = t;
+  t = fabs(slope_diag(s, q, di, dj, 0)); if (t < m) m = t;
+  double phi = m / gn;
+  double cx = 0.5 * s->dx + s->ox[c], cy = 0.5 * s->dy + s->oy[c];
+  return q[c] + phi * (g1 * (px - cx) + g2 * (py - cy));
+}
+static int pure_stencil(orc* s, int a, int di, int dj) {
+  for (int l = -1; l <= 1; ++l)
+    for (int k = -1; k <= 1; ++k)
+      if (!pure_in(s, a, di + k, dj + l)) return 0;
+  return 1;
+}
+
 /* For one flux: final material volumes after clipping, then mass and energy
  * fluxes from the reconstructed rho_a^{lagCF} and e_a^{lag}.
  * kind: 0 X-face, 1 Y-face, 2 corner.  Order 2 is used for material a only
  * when the donor and its two neighbours along the reconstruction direction
  * are pure in a (section 4.2 remark: order 1 next to interfaces). */
 static void finish_flux(orc* s, int kind, int di, int dj, double sg, double fdisp,
-                        double ddx, double ddy, const double* Araw,
+                        double ddx, double ddy, const double* reg, const double* Araw,
                         double* Aout, double* Mout, double* Eout) {
   int c = CI(s, di, dj), M = s->M;
   double A[MAXM];
@@ -922,17 +1001,41 @@ static void finish_flux(orc* s, int kind, int di, int dj, double sg, double fdis
     Aout[a] = A[a]; Mout[a] = 0.0; Eout[a] = 0.0;
     if (!(A[a] > 0.0)) { Aout[a] = 0.0; continue; }
     double rf = s->rcf[a][c], ef = s->elag[a][c];
+    int cr = s->c.corner_recon;
+    int lsq = cr == ORC_CORNER_LSQ && (kind == 2 || s->c.face_order == 2);
     int o2 = 0;
-    if (kind == 0 && s->c.face_order == 2)
+    if (lsq)
+      o2 = pure_stencil(s, a, di, dj);
+    else if (kind == 0 && s->c.face_order == 2)
       o2 = pure_in(s, a, di - 1, dj) && pure_in(s, a, di, dj) && pure_in(s, a, di + 1, dj);
     else if (kind == 1 && s->c.face_order == 2)
       o2 = pure_in(s, a, di, dj - 1) && pure_in(s, a, di, dj) && pure_in(s, a, di, dj + 1);
-    else if (kind == 2 && s->c.corner_recon == ORC_CORNER_DIAG) {
+    else if (kind == 2 && cr == ORC_CORNER_DIAG) {
       int sj = ddx * ddy > 0.0 ? 1 : -1;
       o2 = pure_in(s, a, di - 1, dj - sj) && pure_in(s, a, di, dj) && pure_in(s, a, di + 1, dj + sj);
+    } else if (kind == 2 && cr == ORC_CORNER_AVG) {
+      /* the donor and the receiver (the cell diagonally across the node) */
+      o2 = pure_in(s, a, di, dj) && pure_in(s, a, di + (ddx > 0.0 ? 1 : -1), dj + (ddy > 0.0 ? 1 : -1));
+    } else if (kind == 2 && cr == ORC_CORNER_XY) {
+      o2 = pure_in(s, a, di - 1, dj) && pure_in(s, a, di, dj) && pure_in(s, a, di + 1, dj)
+        && pure_in(s, a, di, dj - 1) && pure_in(s, a, di, dj + 1);
     }
     if (o2) {
-      if (kind == 2) {
+      if (lsq) {
+        double px = 0.5 * (reg[0] + reg[1]), py = 0.5 * (reg[2] + reg[3]);
+        rf = recon_lsq(s, s->rcf[a], di, dj, px, py);
+        ef = recon_lsq(s, s->elag[a], di, dj, px, py);
+      } else if (kind == 2 && cr == ORC_CORNER_AVG) {
+        /* 1/2 (a_donor + a_receiver), clamped to the donor value (section
+         * 3.3: no negative donor mass) */
+        int rc = CI(s, di + (ddx > 0.0 ? 1 : -1), dj + (ddy > 0.0 ? 1 : -1));
+        double ra = 0.5 * (s->rcf[a][c] + s->rcf[a][rc]), ea = 0.5 * (s->elag[a][c] + s->elag[a][rc]);
+        rf = ra < rf ? ra : rf;
+        ef = ea < ef ? ea : ef;
+      } else if (kind == 2 && cr == ORC_CORNER_XY) {
+        rf = recon_corner_xy(s, s->rcf[a], di, dj, ddx, ddy);
+        ef = recon_corner_xy(s, s->elag[a], di, dj, ddx, ddy);
+      } else if (kind == 2) {
         rf = recon_corner(s, s->rcf[a], di, dj, ddx, ddy);
         ef = recon_corner(s, s->elag[a], di, dj, ddx, ddy);
       } else {
@@ -1017,7 +1120,8 @@ static void material_fluxes(orc* s) {
       int di = wrapx(s, left ? i - 1 : i);
       for (int a = 0; a < M; ++a) A[a] = rawx[a][f];
       double fd = 0.5 * (s->ddx[NI(s, i, j)] + s->ddx[NI(s, i, j + 1)]);
-      finish_flux(s, 0, di, j, left ? 1.0 : -1.0, fd, 0.0, 0.0, A, Ao, Mo, Eo);
+      xface_region(s, f, left, r);
+      finish_flux(s, 0, di, j, left ? 1.0 : -1.0, fd, 0.0, 0.0, r, A, Ao, Mo, Eo);
       double sg = left ? 1.0 : -1.0;
       for (int a = 0; a < M; ++a) { s->xA[a][f] = sg * Ao[a]; s->xMm[a][f] = sg * Mo[a]; s->xE[a][f] = sg * Eo[a]; }
     }
@@ -1031,7 +1135,8 @@ static void material_fluxes(orc* s) {
       int dj = wrapy(s, below ? j - 1 : j);
       for (int a = 0; a < M; ++a) A[a] = rawy[a][f];
       double fd = 0.5 * (s->ddy[NI(s, i, j)] + s->ddy[NI(s, i + 1, j)]);
-      finish_flux(s, 1, i, dj, below ? 1.0 : -1.0, fd, 0.0, 0.0, A, Ao, Mo, Eo);
+      yface_region(s, f, below, r);
+      finish_flux(s, 1, i, dj, below ? 1.0 : -1.0, fd, 0.0, 0.0, r, A, Ao, Mo, Eo);
       double sg = below ? 1.0 : -1.0;
       for (int a = 0; a < M; ++a) { s->yA[a][f] = sg * Ao[a]; s->yMm[a][f] = sg * Mo[a]; s->yE[a][f] = sg * Eo[a]; }
     }
@@ -1043,7 +1148,8 @@ static void material_fluxes(orc* s) {
       if (s->fc[n] == 0.0 || !corner_cells(s->ddx[n], s->ddy[n], i, j, &di, &dj, &ri, &rj)) continue;
       di = wrapx(s, di); dj = wrapy(s, dj);
       for (int a = 0; a < M; ++a) A[a] = rawc[a][n];
-      finish_flux(s, 2, di, dj, 0.0, 0.0, s->ddx[n], s->ddy[n], A, Ao, Mo, Eo);
+      corner_region(s, s->ddx[n], s->ddy[n], r);
+      finish_flux(s, 2, di, dj, 0.0, 0.0, s->ddx[n], s->ddy[n], r, A, Ao, Mo, Eo);
       for (int a = 0; a < M; ++a) { s->cA[a][n] = Ao[a]; s->cMm[a][n] = Mo[a]; s->cE[a][n] = Eo[a]; }
     }
   for (int a = 0; a < M; ++a) {
@@ -1177,7 +1283,10 @@ static void dual_remap(orc* s, double* nux, double* nuy) {
   fill_xface(s, s->MX);
   fill_yface(s, s->MY);
   fill_corner(s, s->Mpp, s->Mpm);
-  int fo2 = s->c.face_order == 2, co2 = s->c.corner_recon == ORC_CORNER_DIAG;
+  /* the dual mesh reconstructs corners along the diagonal for every
+   * second-order corner choice (reading: section 3.3 defines the variants
+   * for the cell-centred variables only) */
+  int fo2 = s->c.face_order == 2, co2 = s->c.corner_recon != ORC_CORNER_UPWIND;
   for (int j = 0; j <= ny; ++j)
     for (int i = 0; i <= nx; ++i) {
       if (!node_interior(i, nx, s->perx) || !node_interior(j, ny, s->pery)) continue;

@@ -20,7 +20,10 @@ extern "C" {
 #endif
 
 enum { ORC_BC_REFLECT = 0, ORC_BC_PERIODIC = 1 };
-enum { ORC_CORNER_UPWIND = 0, ORC_CORNER_DIAG = 1 };
+/* Corner reconstruction (section 3.3): upwind, diagonal limited linear,
+ * diagonal average (clamped to the donor value), x-y limited linear, and
+ * multidimensional least-squares plane (which also gives the face values). */
+enum { ORC_CORNER_UPWIND = 0, ORC_CORNER_DIAG = 1, ORC_CORNER_AVG = 2, ORC_CORNER_XY = 3, ORC_CORNER_LSQ = 4 };
 /* Remap of the step: one-step with corner fluxes (section 2.3), one-step
  * with face fluxes only ("Direct", section 2.2), or alternate directions
  * ("AD", section 2.1: an X remap then a Y remap, the order swapped every
@@ -34,7 +37,7 @@ typedef struct {
   double cfl, a1, a2;    /* CFL number, linear / quadratic pseudo-viscosity */
   int bc[4];             /* xlo, xhi, ylo, yhi; xlo==xhi and ylo==yhi required */
   int face_order;        /* 1 (upwind) or 2 (Van Leer limited linear) */
-  int corner_recon;      /* ORC_CORNER_UPWIND or ORC_CORNER_DIAG */
+  int corner_recon;      /* ORC_CORNER_* */
   double dt_fixed;       /* >0: use this dt instead of the CFL rule */
   int remap;             /* ORC_REMAP_* */
 } orc_config;

@@ -23,7 +23,7 @@ from typing import List, Sequence
 import numpy as np
 
 BC_REFLECT, BC_PERIODIC = 0, 1
-CORNER_UPWIND, CORNER_DIAG = 0, 1
+CORNER_UPWIND, CORNER_DIAG, CORNER_AVG, CORNER_XY, CORNER_LSQ = 0, 1, 2, 3, 4
 REMAP_DIRECTCF, REMAP_DIRECT, REMAP_AD = 0, 1, 2
 
 
