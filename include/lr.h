@@ -52,7 +52,13 @@ typedef enum {
 
 enum { LR_BC_REFLECT = 0, LR_BC_PERIODIC = 1 };
 enum { LR_EOS_IDEAL = 0, LR_EOS_STIFFENED = 1 };
-enum { LR_CORNER_UPWIND = 0, LR_CORNER_DIAG = 1 };
+/* Corner values of the remap (lr_config.corner_recon, section 3.3): upwind;
+ * diagonal limited linear (default); diagonal average of donor and
+ * receiver, clamped to the donor value; x-y limited linear; multidimensional
+ * least-squares plane with a scalar limiter (also used for the face values
+ * when face_order is 2).  The dual mesh uses the diagonal reconstruction for
+ * every second-order choice. */
+enum { LR_CORNER_UPWIND = 0, LR_CORNER_DIAG = 1, LR_CORNER_AVG = 2, LR_CORNER_XY = 3, LR_CORNER_LSQ = 4 };
 /* Remap of the step (lr_config.remap):
  *   LR_REMAP_DIRECTCF  one step with face and corner fluxes (section 2.3; default);
  *   LR_REMAP_DIRECT    one step with face fluxes only, the faces moving with
@@ -95,7 +101,7 @@ typedef struct {
                              xlo == xhi and ylo == yhi */
   int precision;          /* LR_FP64 (default), LR_DF64 or LR_FP32 */
   int face_order;         /* 1 upwind or 2 Van Leer limited linear (default 2) */
-  int corner_recon;       /* LR_CORNER_UPWIND or LR_CORNER_DIAG (default) */
+  int corner_recon;       /* LR_CORNER_* (default LR_CORNER_DIAG) */
   double dt_fixed;        /* > 0: use this dt instead of the CFL rule */
   int mixed_lanes;        /* threads per mixed cell in the interface kernel:
                              1, 2, 4 or 8; 0 (default) picks per precision */

@@ -50,7 +50,7 @@ bool lr_config_ok(const lr_config* c, char* why, size_t nwhy) {
   if (!(c->cfl > 0.0) || c->cfl > 1.0) { snprintf(why, nwhy, "cfl must be in (0,1]"); return false; }
   if (c->a1 < 0.0 || c->a2 < 0.0) { snprintf(why, nwhy, "negative viscosity coefficient"); return false; }
   if (c->face_order != 1 && c->face_order != 2) { snprintf(why, nwhy, "face_order must be 1 or 2"); return false; }
-  if (c->corner_recon != LR_CORNER_UPWIND && c->corner_recon != LR_CORNER_DIAG) { snprintf(why, nwhy, "bad corner_recon"); return false; }
+  if (c->corner_recon < LR_CORNER_UPWIND || c->corner_recon > LR_CORNER_LSQ) { snprintf(why, nwhy, "bad corner_recon"); return false; }
   if (c->precision != LR_FP64 && c->precision != LR_DF64 && c->precision != LR_FP32) {
     snprintf(why, nwhy, "precision must be LR_FP64, LR_DF64 or LR_FP32");
     return false;
@@ -88,7 +88,10 @@ void lr_fill_grid(const lr_config& f, LrGrid& g) {
   g.invD = 1.0 / g.D;
   g.cfl = f.cfl; g.a1 = f.a1; g.a2 = f.a2; g.dt_fixed = f.dt_fixed;
   g.face_o2 = f.face_order == 2;
-  g.corner_o2 = f.corner_recon == LR_CORNER_DIAG;
+  // the dual mesh reconstructs corners along the diagonal for every
+  // second-order corner choice
+  g.corner_o2 = f.corner_recon != LR_CORNER_UPWIND;
+  g.corner_kind = f.corner_recon;
   g.mode = f.precision == LR_DF64 ? LR_MODE_DF64 : f.precision == LR_FP32 ? LR_MODE_FP32 : LR_MODE_FP64;
   g.mixed_lanes = f.mixed_lanes ? f.mixed_lanes : lr_default_mixed_lanes(g.mode);
   g.remap = f.remap;

@@ -530,7 +530,10 @@ lr_status lr_batch_add(lr_batch* b, const lr_config* cfg, const lr_material* mat
   if (!cfg || !mats || !k || !rho || !p || !ux || !uy || !member) { setmsg(b, "lr_batch_add: null argument"); return LR_ERR_ARG; }
   if (!lr_config_ok(cfg, why, sizeof(why))) { setmsg(b, "lr_batch_add: %s", why); return LR_ERR_ARG; }
   if (cfg->precision != b->cfg.precision) { setmsg(b, "lr_batch_add: precision differs from the batch's"); return LR_ERR_ARG; }
-  if (cfg->remap != LR_REMAP_DIRECTCF) { setmsg(b, "lr_batch_add: batches run the DirectCF remap only"); return LR_ERR_ARG; }
+  if (cfg->remap != LR_REMAP_DIRECTCF || cfg->corner_recon > LR_CORNER_DIAG) {
+    setmsg(b, "lr_batch_add: batches run the DirectCF remap with upwind or diagonal corners only");
+    return LR_ERR_ARG;
+  }
   if (cfg->nmat > b->cfg.nmat_max) { setmsg(b, "lr_batch_add: nmat above nmat_max"); return LR_ERR_ARG; }
   if ((long)cfg->nx * cfg->ny > b->cfg.max_member_cells) { setmsg(b, "lr_batch_add: grid above max_member_cells"); return LR_ERR_ARG; }
   if (!(t_end >= 0.0)) { setmsg(b, "lr_batch_add: t_end must be >= 0"); return LR_ERR_ARG; }

@@ -29,7 +29,8 @@ struct LrGrid {
   double inv2dx, inv2dy, inv8dx, inv8dy, invV, invD;  // reciprocals of the constant divisors
   double cfl, a1, a2, dt_fixed;
   double gam[LR_MAXM], pin[LR_MAXM];
-  int face_o2, corner_o2, presc;
+  int face_o2, corner_o2, presc;  // corner_o2: second-order dual corners
+  int corner_kind;         // LR_CORNER_* of the primary mesh's corner values
   int mixed_lanes;         // lanes per mixed cell in lr_mixed: 1, 2, 4 or 8
   // Remap of the step (LR_REMAP_*) and, for the alternate-directions remap,
   // the sweep a launch belongs to: sweep 0 remaps with the full displacement,

@@ -882,6 +882,100 @@ __device__ __forceinline__ R recon_corner(const LrGrid& g, const KC<R>& kc, cons
   return a0 + sl * off;
 }
 
+// Van Leer limited slopes of q in cell (di,dj): along x or y over the
+// Lagrangian centres of the two neighbours, and along v (pp) or v_perp over
+// the diagonal neighbours' centres projected on v (as recon_face and
+// recon_corner compute them).
+template <class R>
+__device__ __forceinline__ R slope_axis(const LrGrid& g, const KC<R>& kc, const R* q, const LrWorkT<R>& w, int di,
+                                        int dj, bool xdir) {
+  int c = cix(g, di, dj).idx;
+  R a0 = q[c], am, ap, om, op, o0;
+  if (xdir) {
+    am = cellS(g, q, di - 1, dj); ap = cellS(g, q, di + 1, dj);
+    om = cellOX(g, w.ox, di - 1, dj); op = cellOX(g, w.ox, di + 1, dj); o0 = w.ox[c];
+  } else {
+    am = cellS(g, q, di, dj - 1); ap = cellS(g, q, di, dj + 1);
+    om = cellOY(g, w.oy, di, dj - 1); op = cellOY(g, w.oy, di, dj + 1); o0 = w.oy[c];
+  }
+  R h = xdir ? kc.dx : kc.dy;
+  return vl_slope(a0 - am, ap - a0, h + o0 - om, h + op - o0);
+}
+template <class R>
+__device__ __forceinline__ R slope_diag(const LrGrid& g, const KC<R>& kc, const R* q, const LrWorkT<R>& w, int di,
+                                        int dj, int sj) {
+  int c = cix(g, di, dj).idx;
+  R a0 = q[c], ox0 = w.ox[c], oy0 = w.oy[c];
+  R ap = cellS(g, q, di + 1, dj + sj), am = cellS(g, q, di - 1, dj - sj);
+  R oxp = cellOX(g, w.ox, di + 1, dj + sj), oyp = cellOY(g, w.oy, di + 1, dj + sj);
+  R oxm = cellOX(g, w.ox, di - 1, dj - sj), oym = cellOY(g, w.oy, di - 1, dj - sj);
+  R sdy = sj > 0 ? kc.dy : -kc.dy;
+  R hp = ((kc.dx + oxp - ox0) * kc.dx + (sdy + oyp - oy0) * sdy) * kc.invD;
+  R hm = ((kc.dx + ox0 - oxm) * kc.dx + (sdy + oy0 - oym) * sdy) * kc.invD;
+  return vl_slope(a0 - am, ap - a0, hm, hp);
+}
+// x-y corner value (section 3.3): a_c + delta_x/2 (sgn(dVol_fx) wx_c - dt u_fx)
+// + delta_y/2 (sgn(dVol_fy) wy_c - dt u_fy); f_x is the donor's X face on the
+// corner's side (donor row), f_y its Y face on that side; sgn(0) = 0.
+template <class R>
+__device__ __forceinline__ R recon_corner_xy(const LrGrid& g, const KC<R>& kc, const R* q, const LrWorkT<R>& w,
+                                            int di, int dj, R ddx, R ddy) {
+  using O = RealOps<R>;
+  const R Z = O::c(0.0f), ONE = O::c(1.0f), H = O::c(0.5f);
+  int c = cix(g, di, dj).idx;
+  int fxi = di + (O::pos(ddx) ? 1 : 0), fyj = dj + (O::pos(ddy) ? 1 : 0);
+  Ix qx = xix(g, fxi, dj), qy = yix(g, di, fyj);
+  R vx = w.fx[qx.idx], vy = w.fy[qy.idx];
+  if (qx.fx) vx = -vx;
+  if (qy.fy) vy = -vy;
+  R sgx = O::pos(vx) ? ONE : O::neg(vx) ? -ONE : Z;
+  R sgy = O::pos(vy) ? ONE : O::neg(vy) ? -ONE : Z;
+  R fdx = H * (nodeX(g, w.ddx, fxi, dj) + nodeX(g, w.ddx, fxi, dj + 1));
+  R fdy = H * (nodeY(g, w.ddy, di, fyj) + nodeY(g, w.ddy, di + 1, fyj));
+  return q[c] + H * slope_axis(g, kc, q, w, di, dj, true) * (sgx * w.wx[c] - fdx)
+              + H * slope_axis(g, kc, q, w, di, dj, false) * (sgy * w.wy[c] - fdy);
+}
+// Multidimensional value (section 3.3): the least-squares plane over the
+// 9-point stencil (normal equations of the cell-mean fit, rows the
+// Lagrangian centres' offsets), its gradient scaled to the smallest of the
+// four limited 1D slopes' magnitudes, evaluated at (px, py) in the donor's
+// frame.
+template <class R>
+__device__ __noinline__ R recon_lsq(const LrGrid& g, const KC<R>& kc, const R* q, const LrWorkT<R>& w, int di,
+                                    int dj, R px, R py) {
+  using O = RealOps<R>;
+  const R Z = O::c(0.0f), H = O::c(0.5f);
+  int c = cix(g, di, dj).idx;
+  R qc = q[c], oxc = w.ox[c], oyc = w.oy[c];
+  R sxx = Z, sxy = Z, syy = Z, sxa = Z, sya = Z;
+  for (int l = -1; l <= 1; ++l)
+    for (int k = -1; k <= 1; ++k) {
+      if (k == 0 && l == 0) continue;
+      R X1 = O::c((float)k) * kc.dx + cellOX(g, w.ox, di + k, dj + l) - oxc;
+      R X2 = O::c((float)l) * kc.dy + cellOY(g, w.oy, di + k, dj + l) - oyc;
+      R A = cellS(g, q, di + k, dj + l) - qc;
+      sxx += X1 * X1; sxy += X1 * X2; syy += X2 * X2; sxa += X1 * A; sya += X2 * A;
+    }
+  R det = sxx * syy - sxy * sxy;
+  R g1 = (syy * sxa - sxy * sya) / det;
+  R g2 = (sxx * sya - sxy * sxa) / det;
+  R gn = O::sqrt(g1 * g1 + g2 * g2);
+  if (!O::pos(gn)) return qc;
+  R m = O::abs(slope_axis(g, kc, q, w, di, dj, true));
+  m = rmin(m, O::abs(slope_axis(g, kc, q, w, di, dj, false)));
+  m = rmin(m, O::abs(slope_diag(g, kc, q, w, di, dj, 1)));
+  m = rmin(m, O::abs(slope_diag(g, kc, q, w, di, dj, -1)));
+  R phi = m / gn;
+  R cx = H * kc.dx + oxc, cy = H * kc.dy + oyc;
+  return qc + phi * (g1 * (px - cx) + g2 * (py - cy));
+}
+__device__ __forceinline__ bool pure_stencil(const LrGrid& g, const unsigned char* mask, int di, int dj, unsigned bit) {
+  bool ok = true;
+  for (int l = -1; l <= 1; ++l)
+    for (int k = -1; k <= 1; ++k) ok = ok && pure_in(g, mask, di + k, dj + l, bit);
+  return ok;
+}
+
 // K5: per flux object (X face, Y face, corner): final material volumes (a
 // pure donor gives its material the whole flux; mixed donors' splits come
 // from lr_mixed), reconstructed rho_a^{lagCF} and e_a^{lag} (order 2 only
@@ -889,7 +983,10 @@ __device__ __forceinline__ R recon_corner(const LrGrid& g, const KC<R>& kc, cons
 // material alone -- section 4.2 remark), mass and energy fluxes, and the
 // total mass fluxes the dual remap needs.  Materials absent from the donor
 // get stored zeros, no arithmetic.
-template <class R, int M>
+// VAR: compiled with the average, x-y and least-squares reconstructions
+// (kept out of the default instantiation, whose register budget they would
+// double).
+template <class R, int M, bool VAR>
 __device__ __forceinline__ void mat_flux_at(const LrGrid& g, const KC<R>& kc, const LrStateT<R>& cur,
                                             const LrWorkT<R>& w, int i, int j) {
   using O = RealOps<R>;
@@ -923,7 +1020,15 @@ __device__ __forceinline__ void mat_flux_at(const LrGrid& g, const KC<R>& kc, co
       R Ma = Z, Ea = Z;
       if (!mixed || O::pos(Aa)) {
         R rf = w.rcf[a][dc], ef = w.elag[a][dc];
-        if (!mixed && g.face_o2 && pure_in(g, w.mask, di - 1, j, bit) && pure_in(g, w.mask, di + 1, j, bit)) {
+        if (VAR && !mixed && g.face_o2 && g.corner_kind == LR_CORNER_LSQ) {
+          if (pure_stencil(g, w.mask, di, j, bit)) {
+            R xb = w.fxb[f];
+            R r0 = left ? kc.dx : xb, r1 = left ? kc.dx + xb : Z;
+            R px = H * (r0 + r1), py = H * (w.fxlo[f] + w.fxhi[f]);
+            rf = recon_lsq(g, kc, w.rcf[a], w, di, j, px, py);
+            ef = recon_lsq(g, kc, w.elag[a], w, di, j, px, py);
+          }
+        } else if (!mixed && g.face_o2 && pure_in(g, w.mask, di - 1, j, bit) && pure_in(g, w.mask, di + 1, j, bit)) {
           rf = recon_face(g, kc, w.rcf[a], w.ox, w.wx, di, j, sg, fd, true);
           ef = recon_face(g, kc, w.elag[a], w.ox, w.wx, di, j, sg, fd, true);
         }
@@ -962,7 +1067,15 @@ __device__ __forceinline__ void mat_flux_at(const LrGrid& g, const KC<R>& kc, co
       R Ma = Z, Ea = Z;
       if (!mixed || O::pos(Aa)) {
         R rf = w.rcf[a][dc], ef = w.elag[a][dc];
-        if (!mixed && g.face_o2 && pure_in(g, w.mask, i, dj - 1, bit) && pure_in(g, w.mask, i, dj + 1, bit)) {
+        if (VAR && !mixed && g.face_o2 && g.corner_kind == LR_CORNER_LSQ) {
+          if (pure_stencil(g, w.mask, i, dj, bit)) {
+            R yb = w.fyb[f];
+            R r2 = below ? kc.dy : yb, r3 = below ? kc.dy + yb : Z;
+            R px = H * (w.fylo[f] + w.fyhi[f]), py = H * (r2 + r3);
+            rf = recon_lsq(g, kc, w.rcf[a], w, i, dj, px, py);
+            ef = recon_lsq(g, kc, w.elag[a], w, i, dj, px, py);
+          }
+        } else if (!mixed && g.face_o2 && pure_in(g, w.mask, i, dj - 1, bit) && pure_in(g, w.mask, i, dj + 1, bit)) {
           rf = recon_face(g, kc, w.rcf[a], w.oy, w.wy, i, dj, sg, fd, false);
           ef = recon_face(g, kc, w.elag[a], w.oy, w.wy, i, dj, sg, fd, false);
         }
@@ -1002,10 +1115,28 @@ __device__ __forceinline__ void mat_flux_at(const LrGrid& g, const KC<R>& kc, co
       R Ma = Z, Ea = Z;
       if (!mixed || O::pos(Aa)) {
         R rf = w.rcf[a][dc], ef = w.elag[a][dc];
-        if (!mixed && g.corner_o2 && pure_in(g, w.mask, di - 1, dj - sj, bit) &&
+        int ck = mixed ? LR_CORNER_UPWIND : g.corner_kind;
+        if (ck == LR_CORNER_DIAG && pure_in(g, w.mask, di - 1, dj - sj, bit) &&
             pure_in(g, w.mask, di + 1, dj + sj, bit)) {
           rf = recon_corner(g, kc, w.rcf[a], w, di, dj, ddx, ddy, sj);
           ef = recon_corner(g, kc, w.elag[a], w, di, dj, ddx, ddy, sj);
+        } else if (VAR && ck == LR_CORNER_AVG && pure_in(g, w.mask, ri, rj, bit)) {
+          // 1/2 (donor + receiver), clamped to the donor value (section 3.3)
+          int rc = cix(g, ri, rj).idx;
+          R ra = H * (w.rcf[a][dc] + w.rcf[a][rc]), ea = H * (w.elag[a][dc] + w.elag[a][rc]);
+          rf = rmin(ra, rf);
+          ef = rmin(ea, ef);
+        } else if (VAR && ck == LR_CORNER_XY && pure_in(g, w.mask, di - 1, dj, bit) && pure_in(g, w.mask, di + 1, dj, bit) &&
+                   pure_in(g, w.mask, di, dj - 1, bit) && pure_in(g, w.mask, di, dj + 1, bit)) {
+          rf = recon_corner_xy(g, kc, w.rcf[a], w, di, dj, ddx, ddy);
+          ef = recon_corner_xy(g, kc, w.elag[a], w, di, dj, ddx, ddy);
+        } else if (VAR && ck == LR_CORNER_LSQ && pure_stencil(g, w.mask, di, dj, bit)) {
+          R nxp = O::pos(ddx) ? kc.dx : Z, nyp = O::pos(ddy) ? kc.dy : Z;
+          R r0 = O::pos(ddx) ? nxp : nxp + ddx, r1 = O::pos(ddx) ? nxp + ddx : nxp;
+          R r2 = O::pos(ddy) ? nyp : nyp + ddy, r3 = O::pos(ddy) ? nyp + ddy : nyp;
+          R px = H * (r0 + r1), py = H * (r2 + r3);
+          rf = recon_lsq(g, kc, w.rcf[a], w, di, dj, px, py);
+          ef = recon_lsq(g, kc, w.elag[a], w, di, dj, px, py);
         }
         Ma = rf * Aa;
         Ea = Ma * ef;
@@ -1676,7 +1807,7 @@ LR_OP(OpCellPre, (cell_pre_at<R, M>(g, kc, cur, w, i, j)))
 LR_OP(OpNodeHalf, (node_half_at<R>(g, kc, cur, w, i, j)))
 LR_OP(OpCellLag, (cell_lag_at<R, M>(g, kc, cur, w, i, j)))
 LR_OP(OpCellCf, (cell_cf_at<R, M>(g, kc, cur, w, i, j)))
-LR_OP(OpMatFlux, (mat_flux_at<R, M>(g, kc, cur, w, i, j)))
+LR_OP(OpMatFlux, (mat_flux_at<R, M, false>(g, kc, cur, w, i, j)))
 LR_OP(OpCellUpdate, (cell_update_at<R, M>(g, kc, cur, nxt, w, i, j)))
 LR_OP(OpDualFlux, (dual_flux_at<R>(g, kc, w, i - 1, j - 1)))
 LR_OP(OpNodeUpdate, (node_update_at<R>(g, kc, cur, nxt, w, i, j, nt)))
@@ -1749,6 +1880,12 @@ LR_KERNEL_PAIR(prepare, OpPrepare)
 #undef LR_KERNEL_PAIR
 
 template <class R, int M>
+__global__ void __launch_bounds__(256) lr_mat_flux_var(LrGrid g, KC<R> kc, LrStateT<R> cur, LrStateT<R> nxt,
+                                                       LrWorkT<R> w) {
+  mat_flux_at<R, M, true>(g, kc, cur, w, blockIdx.x * BX + threadIdx.x, blockIdx.y * BY + threadIdx.y);
+}
+
+template <class R, int M>
 __global__ void __launch_bounds__(256) lr_sweep_prep(LrGrid g, KC<R> kc, LrStateT<R> cur, LrStateT<R> nxt,
                                                      LrWorkT<R> w) {
   sweep_prep_at<R, M>(g, kc, cur, w, blockIdx.x * BX + threadIdx.x, blockIdx.y * BY + threadIdx.y);
@@ -1795,7 +1932,10 @@ cudaError_t launch_t(int kid, const LrGrid& g, const LrState& cur0, const LrStat
       else lr_mixed<R, 3><<<nb, 128, 0, s>>>(g, cur, w);
       break;
     }
-    case LRK_MAT_FLUX: LR_M(lr_mat_flux, grid_for(g.nxu, g.nyu)); break;
+    case LRK_MAT_FLUX:
+      if (g.corner_kind > LR_CORNER_DIAG) LR_M(lr_mat_flux_var, grid_for(g.nxu, g.nyu));
+      else LR_M(lr_mat_flux, grid_for(g.nxu, g.nyu));
+      break;
     case LRK_CELL_UPDATE: LR_M(lr_cell_update, grid_for(g.nx, g.ny)); break;
     case LRK_DUAL_FLUX: LR_1(lr_dual_flux, grid_for(g.nx + 2, g.ny + 2)); break;
     case LRK_NODE_UPDATE: LR_1(lr_node_update, grid_for(g.nxu, g.nyu)); break;

@@ -253,3 +253,35 @@ def test_comparator_remaps_100_steps_and_graphs(remap):
         orc.step()
     assert t == pytest.approx(orc.t, rel=1e-12)
     _assert_close(compare(sim, orc, l1_rel), TOL_100, f"{remap} 100 steps")
+
+
+CORNERS = {"avg": P.CORNER_AVG, "xy": P.CORNER_XY, "lsq": P.CORNER_LSQ}
+CORNER_CASES = {
+    "triple_point_140x60": lambda: P.triple_point(140, 60),
+    "random3_walls_velocity": lambda: P.random_box(22, nx=53, ny=70, nmat=3, velocity=0.3),
+    "random2_periodic": lambda: P.random_box(23, nx=66, ny=39, nmat=2, velocity=0.4).copy(bc=(P.BC_PERIODIC,) * 4),
+    "mono_smooth_periodic": lambda: P.uniform(40, 36, rho=1.0, p=1.0, u=(0.3, -0.2)).copy(
+        rho=np.array([1.0 + 0.3 * np.sin(np.linspace(0, 6.28, 40))[None, :] * np.cos(np.linspace(0, 6.28, 36))[:, None]])),
+}
+
+
+@pytest.mark.parametrize("prec", sorted(PRECISIONS))
+@pytest.mark.parametrize("corner", sorted(CORNERS))
+@pytest.mark.parametrize("name", sorted(CORNER_CASES))
+def test_corner_variants_one_and_six_steps(name, corner, prec):
+    """Average, x-y and least-squares corner values (section 3.3) against
+    the oracle."""
+    pr = CORNER_CASES[name]().copy(corner_recon=CORNERS[corner])
+    sim, orc = _pair(pr, PRECISIONS[prec])
+    _steps(sim, orc, 1)
+    _assert_close(compare(sim, orc), TOL_1, f"{name} {corner} 1 step")
+    _steps(sim, orc, 5)
+    _assert_close(compare(sim, orc), 1e-10, f"{name} {corner} 6 steps")
+
+
+@pytest.mark.parametrize("remap", sorted(REMAPS))
+def test_least_squares_faces_with_comparator_remaps(remap):
+    pr = P.random_box(22, nx=53, ny=70, nmat=3, velocity=0.3).copy(corner_recon=P.CORNER_LSQ, remap=REMAPS[remap])
+    sim, orc = _pair(pr)
+    _steps(sim, orc, 6)
+    _assert_close(compare(sim, orc), 1e-10, f"lsq {remap} 6 steps")
