@@ -391,6 +391,7 @@ def run_lr(args, world, rank, local):
         torch.cuda.empty_cache()
         extras["ensemble"] = ensemble_bench(args)
         extras["serving"] = serving_bench(args)
+        extras["variants"] = variants_bench(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_baseline_steps)
         accuracy = sod_accuracy()
@@ -460,6 +461,35 @@ def ensemble_bench(args):
                      "schedule": {"tile": [f"{a}x{b}" for a, b in shapes], "blocks_per_sm": bps, "lanes": lanes}}
         bt.close()
         torch.cuda.empty_cache()
+    return out
+
+
+def variants_bench(args, t_start=1.0, steps=200):
+    """The paper's comparators and variants on the same workload (FP64):
+    the Direct and alternate-directions remaps, and the average, x-y and
+    least-squares corner reconstructions of DirectCF; each advanced to
+    t = 1 and timed over 200 steps with CUDA events (L2 flushed between
+    steps)."""
+    import torch
+    from paper_2208_13409_gb300 import lr, problems as P
+
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    out = {"workload": WORKLOAD, "t_start": t_start, "steps_timed": steps}
+    cases = {"remap_direct": dict(remap=P.REMAP_DIRECT), "remap_ad": dict(remap=P.REMAP_AD),
+             "corner_avg": dict(corner_recon=P.CORNER_AVG), "corner_xy": dict(corner_recon=P.CORNER_XY),
+             "corner_lsq": dict(corner_recon=P.CORNER_LSQ)}
+    for name, kw in cases.items():
+        pr = P.triple_point().copy(**kw)
+        sim = lr.Sim(pr)
+        sim.run(1 << 30, t_start)
+        for _ in range(3):
+            sim.step(sync=False)
+        ms = timed_steps(sim, steps, flush, torch)
+        out[name] = {"value": pr.cells * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+                     "launches_per_step": sim.launches_per_step()}
+        sim.close()
+    del flush
+    torch.cuda.empty_cache()
     return out
 
 

@@ -22,6 +22,8 @@ struct lr_ctx {
   bool own_arena;
   cudaStream_t stream;
   bool own_stream;
+  cudaStream_t aux;            // the interface kernel runs here, beside lr_mat_flux
+  cudaEvent_t ev_fork, ev_join;
   bool have_mats, inited;
   int sticky;
   char msg[512];
@@ -247,6 +249,8 @@ size_t layout(const lr_config* cfg, char* base, LrState* st, LrWork* w, double**
   W.red = b.take<unsigned long long>(LR_RED_INST + 2);
   W.err = b.take<int>(2);
   W.mixed = b.take<int>(nc);
+  W.minst = b.take<int>(nc);
+  W.gdev = b.take<LrGrid>(1);
   W.mask = b.take<unsigned char>(nc);
   for (int q = 0; q < 6; ++q) W.cut[q] = b.take<double>(nc);
   W.stage = b.take<double>(3 * M * nc + 2 * nn);
@@ -283,9 +287,15 @@ size_t layout(const lr_config* cfg, char* base, LrState* st, LrWork* w, double**
 
 void fill_grid(lr_ctx* c) { lr_fill_grid(c->cfg, c->g); }
 
+// Captured graphs hold the grid by value: drop them when it changes, and
+// refresh the device copy the interface kernel reads.
 void drop_graphs(lr_ctx* c) {
   for (int q = 0; q < 2; ++q)
     if (c->gvalid[q]) { cudaGraphExecDestroy(c->gexec[q]); c->gvalid[q] = false; }
+  if (c->w.gdev) {
+    cudaMemcpyAsync(const_cast<LrGrid*>(c->w.gdev), &c->g, sizeof(LrGrid), cudaMemcpyHostToDevice, c->stream);
+    cudaStreamSynchronize(c->stream);
+  }
 }
 
 lr_status check_sticky(lr_ctx* ctx) {
@@ -304,17 +314,34 @@ lr_status check_sticky(lr_ctx* ctx) {
   return LR_OK;
 }
 
-cudaError_t launch_one(lr_ctx* ctx, int k, const LrGrid& g, const LrState& cur, const LrState& nxt) {
-  if (!ctx->prof || k >= LRK_COUNT) return lr_launch(k, g, cur, nxt, ctx->w, ctx->stream);
+cudaError_t launch_on(lr_ctx* ctx, int k, const LrGrid& g, const LrState& cur, const LrState& nxt, cudaStream_t st) {
+  if (!ctx->prof || k >= LRK_COUNT) return lr_launch(k, g, cur, nxt, ctx->w, st);
   lr_ctx::Pend p;
   p.kid = k;
   cudaEventCreate(&p.a);
   cudaEventCreate(&p.b);
-  cudaEventRecord(p.a, ctx->stream);
-  cudaError_t e = lr_launch(k, g, cur, nxt, ctx->w, ctx->stream);
-  cudaEventRecord(p.b, ctx->stream);
+  cudaEventRecord(p.a, st);
+  cudaError_t e = lr_launch(k, g, cur, nxt, ctx->w, st);
+  cudaEventRecord(p.b, st);
   ctx->pend.push_back(p);
   return e;
+}
+
+// One kernel of the step.  The interface kernel runs on the auxiliary
+// stream, forked after lr_cell_cf and joined before lr_cell_update, so it
+// overlaps lr_mat_flux (each finishes a disjoint set of flux objects).
+cudaError_t launch_one(lr_ctx* ctx, int k, const LrGrid& g, const LrState& cur, const LrState& nxt) {
+  cudaError_t e;
+  if (k == LRK_MIXED) {
+    if (g.M == 1) return cudaSuccess;
+    if ((e = cudaEventRecord(ctx->ev_fork, ctx->stream)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0)) != cudaSuccess) return e;
+    if ((e = launch_on(ctx, k, g, cur, nxt, ctx->aux)) != cudaSuccess) return e;
+    return cudaEventRecord(ctx->ev_join, ctx->aux);
+  }
+  if (k == LRK_CELL_UPDATE && g.M > 1 && (e = cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0)) != cudaSuccess)
+    return e;
+  return launch_on(ctx, k, g, cur, nxt, ctx->stream);
 }
 
 // One step from buffer `from`.  One-step remaps: the nine kernels, result in
@@ -397,8 +424,18 @@ lr_status create_common(const lr_config* cfg, void* mem, size_t bytes, bool own,
     }
     ctx->own_stream = true;
   }
+  if (cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    if (own) cudaFree(mem);
+    delete ctx;
+    return LR_ERR_CUDA;
+  }
   ctx->sticky = LR_OK;
-  if (lr_launch_reset(ctx->g.mode, ctx->w, 1, ctx->stream) != cudaSuccess ||
+  if (cudaMemcpyAsync(const_cast<LrGrid*>(ctx->w.gdev), &ctx->g, sizeof(LrGrid), cudaMemcpyHostToDevice,
+                      ctx->stream) != cudaSuccess ||
+      lr_launch_reset(ctx->g.mode, ctx->w, 1, ctx->stream) != cudaSuccess ||
       cudaMemsetAsync(ctx->w.pux, 0, lr_real_size(ctx->g.mode) * (cfg->nx + 1) * (cfg->ny + 1), ctx->stream) != cudaSuccess ||
       cudaMemsetAsync(ctx->w.puy, 0, lr_real_size(ctx->g.mode) * (cfg->nx + 1) * (cfg->ny + 1), ctx->stream) != cudaSuccess ||
       cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
@@ -651,6 +688,10 @@ void lr_destroy(lr_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   drop_graphs(ctx);
   for (auto& p : ctx->pend) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+  cudaStreamSynchronize(ctx->aux);
+  cudaStreamDestroy(ctx->aux);
+  cudaEventDestroy(ctx->ev_fork);
+  cudaEventDestroy(ctx->ev_join);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   if (ctx->own_arena) cudaFree(ctx->arena);
   delete ctx;

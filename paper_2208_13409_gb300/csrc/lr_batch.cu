@@ -75,6 +75,8 @@ struct lr_batch {
   Schedule sch;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  cudaStream_t aux = nullptr;   // interface kernels, beside lb_mat_flux
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t gexec[2];
   bool gvalid[2] = {false, false};
   int launches = 0;
@@ -299,16 +301,17 @@ int grid_for_tiles(lr_batch* b, int bps, int ntiles) {
   return g < ntiles ? g : ntiles;
 }
 
-cudaError_t launch_timed(lr_batch* b, int kid, const LrBatchArgs& a, const LrState& cur, const LrState& nxt) {
+cudaError_t launch_timed(lr_batch* b, int kid, const LrBatchArgs& a, const LrState& cur, const LrState& nxt,
+                         cudaStream_t st) {
   b->launches += 1;
-  if (!b->prof) return lr_launch_batch(kid, a, cur, nxt, b->w, b->stream);
+  if (!b->prof) return lr_launch_batch(kid, a, cur, nxt, b->w, st);
   lr_batch::Pend p;
   p.kid = kid;
   cudaEventCreate(&p.a);
   cudaEventCreate(&p.b);
-  cudaEventRecord(p.a, b->stream);
-  cudaError_t e = lr_launch_batch(kid, a, cur, nxt, b->w, b->stream);
-  cudaEventRecord(p.b, b->stream);
+  cudaEventRecord(p.a, st);
+  cudaError_t e = lr_launch_batch(kid, a, cur, nxt, b->w, st);
+  cudaEventRecord(p.b, st);
   b->pend.push_back(p);
   return e;
 }
@@ -321,7 +324,18 @@ cudaError_t enqueue_step(lr_batch* b, int from) {
   b->launches = 0;
   for (int k = 0; k < LRK_COUNT; ++k) {
     LrBatchArgs a = base_args(b);
+    bool any_mixed = b->group_members[2] + b->group_members[3] > 0;
+    if (k == LRK_CELL_UPDATE && any_mixed) {
+      cudaError_t e = cudaStreamWaitEvent(b->stream, b->ev_join, 0);
+      if (e != cudaSuccess) return e;
+    }
     if (k == LRK_MIXED) {
+      // the interface kernels run on the auxiliary stream beside lb_mat_flux
+      // (disjoint flux objects), joined before lb_cell_update
+      if (!any_mixed) continue;
+      cudaError_t e = cudaEventRecord(b->ev_fork, b->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->aux, b->ev_fork, 0);
+      if (e != cudaSuccess) return e;
       for (int M = 2; M <= LR_MAXM; ++M) {
         if (b->group_members[M] == 0) continue;
         a.M = M;
@@ -331,9 +345,11 @@ cudaError_t enqueue_step(lr_batch* b, int from) {
         long lanes = (long)b->sch.lanes * b->group_units[M];
         long nb = (lanes + 127) / 128;
         a.grid = (int)(nb < (long)b->nsm * 16 ? nb : (long)b->nsm * 16);
-        cudaError_t e = launch_timed(b, k, a, cur, nxt);
+        e = launch_timed(b, k, a, cur, nxt, b->aux);
         if (e != cudaSuccess) return e;
       }
+      e = cudaEventRecord(b->ev_join, b->aux);
+      if (e != cudaSuccess) return e;
       continue;
     }
     int s = b->sch.shape[k], d = lr_kernel_domain(k);
@@ -348,7 +364,7 @@ cudaError_t enqueue_step(lr_batch* b, int from) {
       a.tiles = b->d_tiles + r.start;
       a.ntiles = r.count;
       a.grid = grid_for_tiles(b, b->sch.bps[k], r.count);
-      cudaError_t e = launch_timed(b, k, a, cur, nxt);
+      cudaError_t e = launch_timed(b, k, a, cur, nxt, b->stream);
       if (e != cudaSuccess) return e;
     }
   }
@@ -490,6 +506,14 @@ lr_status lr_batch_create(const lr_batch_config* cfg, lr_batch** out) {
     delete b;
     return LR_ERR_CUDA;
   }
+  if (cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    cudaFree(b->arena);
+    delete b;
+    return LR_ERR_CUDA;
+  }
   b->mem.resize(b->S);
   b->freel.push_back(std::make_pair(0L, b->P));
   default_schedule(b);
@@ -514,6 +538,10 @@ void lr_batch_destroy(lr_batch* b) {
   for (auto& p : b->pend) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
   if (b->d_tiles) cudaFree(b->d_tiles);
   if (b->d_adm) cudaFree(b->d_adm);
+  cudaStreamSynchronize(b->aux);
+  cudaStreamDestroy(b->aux);
+  cudaEventDestroy(b->ev_fork);
+  cudaEventDestroy(b->ev_join);
   if (b->own_stream) cudaStreamDestroy(b->stream);
   cudaFree(b->arena);
   delete b;

@@ -97,7 +97,8 @@ struct LrWorkT {
   unsigned long long* red; // mixed-cell counters, then CFL key and tile counter per simulation
   int* err;                // per simulation: [0] error bits, [1] first failing index
   int* mixed;              // work list of mixed cells (cell indices), red[mslot] entries
-  int* minst;              // batch only: simulation slot of each list entry (else null)
+  int* minst;              // simulation slot of each list entry
+  const LrGrid* gdev;      // lone simulation: its grid in device memory (the interface kernel reads it)
   unsigned char* mask;     // bit a set when material a is present in the cell at t^n
   double* cut[6];          // interface lines of mixed cells (n0x, n0y, d0, n1x, n1y, d1)
   double* stage;           // init staging: k, rho, p [3][nmat][nc] then ux, uy [2][nn]
@@ -126,7 +127,8 @@ inline LrStateT<R> typed(const LrState& s) {
 template <class R>
 inline LrWorkT<R> typed(const LrWork& w) {
   LrWorkT<R> t;
-  t.scal = w.scal; t.red = w.red; t.err = w.err; t.mixed = w.mixed; t.minst = w.minst; t.mask = w.mask;
+  t.scal = w.scal; t.red = w.red; t.err = w.err; t.mixed = w.mixed; t.minst = w.minst; t.gdev = w.gdev;
+  t.mask = w.mask;
   t.stage = w.stage;
   for (int q = 0; q < 6; ++q) t.cut[q] = w.cut[q];
 #define LR_F1(n) t.n = static_cast<R*>(w.n);

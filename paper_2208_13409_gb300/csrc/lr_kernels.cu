@@ -768,24 +768,71 @@ __device__ __forceinline__ void mixed_at(const LrGrid& g, const LrStateT<R>& cur
       double avail = kk[a] * v;
       if (o[a] > avail) { sc[a] = avail / o[a]; clip = true; }
     }
-    if (!(valid && clip)) return;
+    if (!valid) return;
+    // ---- final fluxes of this donor's objects (lr_mat_flux leaves objects
+    // with a mixed donor to this kernel): the clipped material volumes and,
+    // at order 1 next to the interface (section 4.2 remark), the donor's
+    // rho_a^{lagCF} and e_a^{lag}; signed like lr_mat_flux's
+    const R Z = O::c(0.0f);
     for (int q = 0; q < K; ++q) {
       double r[4], vol;
-      int fidx = 0;
-      int kind = donated_flux(g, w, i, j, lane * K + q, r, vol, fidx);
+      int fidx = 0, fl = lane * K + q;
+      int kind = donated_flux(g, w, i, j, fl, r, vol, fidx);
       if (kind < 0) continue;
-      double A[M], moved = 0.0;
+      R AR[M];
+      if (clip) {
+        double A[M], moved = 0.0;
 #pragma unroll
-      for (int a = 0; a < M; ++a) {
-        const R* src = kind == 0 ? w.xAm[a] : kind == 1 ? w.yAm[a] : w.cAm[a];
-        A[a] = O::todouble(src[fidx]);
-        if (sc[a] < 1.0) { moved += (1.0 - sc[a]) * A[a]; A[a] *= sc[a]; }
+        for (int a = 0; a < M; ++a) {
+          const R* src = kind == 0 ? w.xAm[a] : kind == 1 ? w.yAm[a] : w.cAm[a];
+          A[a] = O::todouble(src[fidx]);
+          if (sc[a] < 1.0) { moved += (1.0 - sc[a]) * A[a]; A[a] *= sc[a]; }
+        }
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+          if (a == dom) A[a] += moved;
+          AR[a] = from_double<R>(A[a]);
+        }
+      } else {
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+          const R* src = kind == 0 ? w.xAm[a] : kind == 1 ? w.yAm[a] : w.cAm[a];
+          AR[a] = src[fidx];
+        }
       }
+      // positive sense: towards +x / +y for faces (lane 1 and 3 donate
+      // forwards, 0 and 2 backwards); corners store magnitudes
+      bool fwd = kind == 2 || (fl & 1);
+      R mt = Z;
 #pragma unroll
       for (int a = 0; a < M; ++a) {
-        if (a == dom) A[a] += moved;
-        R* dst = kind == 0 ? w.xAm[a] : kind == 1 ? w.yAm[a] : w.cAm[a];
-        dst[fidx] = from_double<R>(A[a]);
+        if (!(msk & (1u << a))) {  // absent from the donor: stored zeros
+          if (kind == 0) { w.xA[a][fidx] = Z; w.xMm[a][fidx] = Z; w.xE[a][fidx] = Z; }
+          else if (kind == 1) { w.yA[a][fidx] = Z; w.yMm[a][fidx] = Z; w.yE[a][fidx] = Z; }
+          else { w.cA[a][fidx] = Z; w.cMm[a][fidx] = Z; w.cE[a][fidx] = Z; }
+          continue;
+        }
+        R Aa = AR[a], Ma = Z, Ea = Z;
+        if (O::pos(Aa)) {
+          Ma = O::mul(w.rcf[a][c], Aa);
+          Ea = O::mul(Ma, w.elag[a][c]);
+        } else {
+          Aa = Z;
+        }
+        R sM = fwd ? Ma : -Ma;
+        if (kind == 0) { w.xA[a][fidx] = fwd ? Aa : -Aa; w.xMm[a][fidx] = sM; w.xE[a][fidx] = fwd ? Ea : -Ea; }
+        else if (kind == 1) { w.yA[a][fidx] = fwd ? Aa : -Aa; w.yMm[a][fidx] = sM; w.yE[a][fidx] = fwd ? Ea : -Ea; }
+        else { w.cA[a][fidx] = Aa; w.cMm[a][fidx] = Ma; w.cE[a][fidx] = Ea; }
+        mt = O::add(mt, sM);
+      }
+      if (kind == 0) w.MX[fidx] = mt;
+      else if (kind == 1) w.MY[fidx] = mt;
+      else {
+        R cx = w.ddx[fidx], cy = w.ddy[fidx];
+        bool pp = O::pos(cx) == O::pos(cy);
+        R sgm = O::pos(cx) ? mt : -mt;  // signed along +x
+        w.Mpp[fidx] = pp ? sgm : Z;
+        w.Mpm[fidx] = pp ? Z : sgm;
       }
     }
   }
@@ -976,9 +1023,10 @@ __device__ __forceinline__ bool pure_stencil(const LrGrid& g, const unsigned cha
   return ok;
 }
 
-// K5: per flux object (X face, Y face, corner): final material volumes (a
-// pure donor gives its material the whole flux; mixed donors' splits come
-// from lr_mixed), reconstructed rho_a^{lagCF} and e_a^{lag} (order 2 only
+// K5: per flux object (X face, Y face, corner) with a pure donor (lr_mixed
+// finishes the objects of mixed donors, so the two kernels run side by
+// side): the donor's material takes the whole flux; reconstructed
+// rho_a^{lagCF} and e_a^{lag} (order 2 only
 // where the donor and its two neighbours along the direction hold that
 // material alone -- section 4.2 remark), mass and energy fluxes, and the
 // total mass fluxes the dual remap needs.  Materials absent from the donor
@@ -1012,6 +1060,7 @@ __device__ __forceinline__ void mat_flux_at(const LrGrid& g, const KC<R>& kc, co
       fd = H * (w.ddx[nb + j * nn + i] + w.ddx[nb + j1 * nn + i]);
     }
     bool mixed = (dm & (dm - 1u)) != 0u;
+    if (!mixed) {  // a mixed donor's objects are finished by lr_mixed
 #pragma unroll
     for (int a = 0; a < M; ++a) {
       unsigned bit = 1u << a;
@@ -1032,16 +1081,17 @@ __device__ __forceinline__ void mat_flux_at(const LrGrid& g, const KC<R>& kc, co
           rf = recon_face(g, kc, w.rcf[a], w.ox, w.wx, di, j, sg, fd, true);
           ef = recon_face(g, kc, w.elag[a], w.ox, w.wx, di, j, sg, fd, true);
         }
-        Ma = rf * Aa;
-        Ea = Ma * ef;
+        Ma = O::mul(rf, Aa);
+        Ea = O::mul(Ma, ef);
       } else {
         Aa = Z;
       }
       R sMa = left ? Ma : -Ma;
       w.xA[a][f] = left ? Aa : -Aa; w.xMm[a][f] = sMa; w.xE[a][f] = left ? Ea : -Ea;
-      mt += sMa;
+      mt = O::add(mt, sMa);
     }
     w.MX[f] = mt;
+    }
   }
   // ---- Y face (i, j)
   if (i < g.nx) {
@@ -1059,6 +1109,7 @@ __device__ __forceinline__ void mat_flux_at(const LrGrid& g, const KC<R>& kc, co
       fd = H * (w.ddy[nb + j * nn + i] + w.ddy[nb + j * nn + i1]);
     }
     bool mixed = (dm & (dm - 1u)) != 0u;
+    if (!mixed) {
 #pragma unroll
     for (int a = 0; a < M; ++a) {
       unsigned bit = 1u << a;
@@ -1079,16 +1130,17 @@ __device__ __forceinline__ void mat_flux_at(const LrGrid& g, const KC<R>& kc, co
           rf = recon_face(g, kc, w.rcf[a], w.oy, w.wy, i, dj, sg, fd, false);
           ef = recon_face(g, kc, w.elag[a], w.oy, w.wy, i, dj, sg, fd, false);
         }
-        Ma = rf * Aa;
-        Ea = Ma * ef;
+        Ma = O::mul(rf, Aa);
+        Ea = O::mul(Ma, ef);
       } else {
         Aa = Z;
       }
       R sMa = below ? Ma : -Ma;
       w.yA[a][f] = below ? Aa : -Aa; w.yMm[a][f] = sMa; w.yE[a][f] = below ? Ea : -Ea;
-      mt += sMa;
+      mt = O::add(mt, sMa);
     }
     w.MY[f] = mt;
+    }
   }
   // ---- corner at node (i, j)
   {
@@ -1107,6 +1159,7 @@ __device__ __forceinline__ void mat_flux_at(const LrGrid& g, const KC<R>& kc, co
       sj = pp ? 1 : -1;
     }
     bool mixed = (dm & (dm - 1u)) != 0u;
+    if (!mixed) {
 #pragma unroll
     for (int a = 0; a < M; ++a) {
       unsigned bit = 1u << a;
@@ -1138,17 +1191,18 @@ __device__ __forceinline__ void mat_flux_at(const LrGrid& g, const KC<R>& kc, co
           rf = recon_lsq(g, kc, w.rcf[a], w, di, dj, px, py);
           ef = recon_lsq(g, kc, w.elag[a], w, di, dj, px, py);
         }
-        Ma = rf * Aa;
-        Ea = Ma * ef;
+        Ma = O::mul(rf, Aa);
+        Ea = O::mul(Ma, ef);
       } else {
         Aa = Z;
       }
       w.cA[a][n] = Aa; w.cMm[a][n] = Ma; w.cE[a][n] = Ea;
-      mt += Ma;
+      mt = O::add(mt, Ma);
     }
     R sgm = O::pos(ddx) ? mt : -mt;  // signed along +x
     w.Mpp[n] = (dm && pp) ? sgm : Z;
     w.Mpm[n] = (dm && !pp) ? sgm : Z;
+    }
   }
 }
 
@@ -1891,11 +1945,10 @@ __global__ void __launch_bounds__(256) lr_sweep_prep(LrGrid g, KC<R> kc, LrState
   sweep_prep_at<R, M>(g, kc, cur, w, blockIdx.x * BX + threadIdx.x, blockIdx.y * BY + threadIdx.y);
 }
 
-template <class R, int M>
-__global__ void __launch_bounds__(128) lr_mixed(LrGrid g, LrStateT<R> cur, LrWorkT<R> w) {
-  if (!step_live(g, w.scal)) return;
-  mixed_loop<R, M>([&](int) -> const LrGrid& { return g; }, cur, w, g.mixed_lanes, g.mslot, g.moff);
-}
+// One interface kernel for lone simulations and batches (a lone simulation
+// passes a one-entry grid array), so both run the same compiled code and
+// give bit-identical results (separately inlined copies may fuse
+// multiply-adds differently).
 template <class R, int M>
 __global__ void __launch_bounds__(128) lb_mixed(const LrGrid* __restrict__ gs, LrStateT<R> cur, LrWorkT<R> w,
                                                 int lanes, int mslot, int moff) {
@@ -1925,11 +1978,12 @@ cudaError_t launch_t(int kid, const LrGrid& g, const LrState& cur0, const LrStat
     case LRK_CELL_CF: LR_M(lr_cell_cf, grid_for(g.nx, g.ny)); break;
     case LRK_MIXED: {
       if (g.M == 1) break;  // one material: no interfaces
+      if (!w.gdev) return cudaErrorInvalidValue;
       long long lanes = (long long)g.mixed_lanes * g.nx * g.ny;
       int nb = (int)((lanes + 127) / 128);
       if (nb > 152 * 16) nb = 152 * 16;
-      if (g.M == 2) lr_mixed<R, 2><<<nb, 128, 0, s>>>(g, cur, w);
-      else lr_mixed<R, 3><<<nb, 128, 0, s>>>(g, cur, w);
+      if (g.M == 2) lb_mixed<R, 2><<<nb, 128, 0, s>>>(w.gdev, cur, w, g.mixed_lanes, g.mslot, g.moff);
+      else lb_mixed<R, 3><<<nb, 128, 0, s>>>(w.gdev, cur, w, g.mixed_lanes, g.mslot, g.moff);
       break;
     }
     case LRK_MAT_FLUX:

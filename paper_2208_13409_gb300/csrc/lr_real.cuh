@@ -98,8 +98,12 @@ __device__ __forceinline__ bool operator!=(df64 a, df64 b) { return !(a == b); }
 
 // ---- uniform helpers over double, float and df64
 template <class R> struct RealOps;
+// mul/add: rounded operations the compiler may not fuse into a multiply-add
+// (used where two kernels must give bit-identical results).
 template <> struct RealOps<double> {
   __device__ static __forceinline__ double c(float v) { return (double)v; }
+  __device__ static __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  __device__ static __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
   __device__ static __forceinline__ double abs(double x) { return fabs(x); }
   __device__ static __forceinline__ double sqrt(double x) { return ::sqrt(x); }
   __device__ static __forceinline__ double rcp(double x) { return 1.0 / x; }
@@ -111,6 +115,8 @@ template <> struct RealOps<double> {
 };
 template <> struct RealOps<float> {
   __device__ static __forceinline__ float c(float v) { return v; }
+  __device__ static __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  __device__ static __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
   __device__ static __forceinline__ float abs(float x) { return fabsf(x); }
   __device__ static __forceinline__ float sqrt(float x) { return sqrtf(x); }
   __device__ static __forceinline__ float rcp(float x) { return 1.0f / x; }
@@ -122,6 +128,8 @@ template <> struct RealOps<float> {
 };
 template <> struct RealOps<df64> {
   __device__ static __forceinline__ df64 c(float v) { return df64(v, 0.0f); }
+  __device__ static __forceinline__ df64 mul(df64 a, df64 b) { return dfops::mul(a, b); }
+  __device__ static __forceinline__ df64 add(df64 a, df64 b) { return dfops::add(a, b); }
   __device__ static __forceinline__ df64 abs(df64 x) { return x.hi < 0.0f ? dfops::neg(x) : x; }
   __device__ static __forceinline__ df64 sqrt(df64 x) { return dfops::sqrt_(x); }
   __device__ static __forceinline__ df64 rcp(df64 x) { return dfops::div(df64(1.0f, 0.0f), x); }
