@@ -30,6 +30,17 @@ constexpr double EPS_K = 1e-12;  // material dropped when its volume <= EPS_K dx
 constexpr double EPS_K_FP32 = 1e-6;  // the same in the FP32 bulk mode (above float round-off)
 constexpr double EPS_C = 1e-3;   // sound-speed weight min(1, k / EPS_C)
 constexpr int BX = 32, BY = 8;
+// Register caps of the float and double-float kernels (MinBlocks below),
+// from a sweep on the 1400x600 triple point: 6 and 4 resident 256-thread
+// blocks per SM (42 and 64 registers) cut the FP32 step by 11 % and the
+// double-float step by 8 % against the compiler's choice, without spills in
+// the step kernels.
+#ifndef LR_MINB_F32
+#define LR_MINB_F32 6
+#endif
+#ifndef LR_MINB_DF64
+#define LR_MINB_DF64 4
+#endif
 
 // Constants of the scheme in the kernels' arithmetic type (converted on the
 // host, so no kernel converts from double).
@@ -1895,15 +1906,23 @@ static_assert(sizeof(LrGrid) % 8 == 0 && alignof(LrGrid) <= 16, "grid descriptor
 static_assert(sizeof(KC<float>) % 4 == 0 && sizeof(KC<double>) % 8 == 0 && sizeof(KC<df64>) % 8 == 0 &&
               alignof(KC<double>) <= 16 && alignof(KC<df64>) <= 16, "constants copied in words");
 
+// Minimum resident blocks per SM the compiler must allow (register cap):
+// the FP64 kernels are bound by the FP64 pipe and keep the compiler's
+// choice; the float and double-float ones are latency bound and gain from
+// more resident warps.
+template <class R> struct MinBlocks { static constexpr int value = 1; };
+template <> struct MinBlocks<float> { static constexpr int value = LR_MINB_F32; };
+template <> struct MinBlocks<df64> { static constexpr int value = LR_MINB_DF64; };
+
 #define LR_KERNEL_PAIR(NAME, OP)                                                                          \
   template <class R, int M>                                                                               \
-  __global__ void __launch_bounds__(256) lr_##NAME(LrGrid g, KC<R> kc, LrStateT<R> cur, LrStateT<R> nxt,  \
+  __global__ void __launch_bounds__(256, MinBlocks<R>::value) lr_##NAME(LrGrid g, KC<R> kc, LrStateT<R> cur, LrStateT<R> nxt,  \
                                                    LrWorkT<R> w) {                                        \
     OP::template at<R, M>(g, kc, cur, nxt, w, blockIdx.x * BX + threadIdx.x, blockIdx.y * BY + threadIdx.y, \
                           (unsigned long long)gridDim.x * gridDim.y);                                     \
   }                                                                                                       \
   template <class R, int M>                                                                               \
-  __global__ void __launch_bounds__(256) lb_##NAME(const LrGrid* __restrict__ gs, const KC<R>* __restrict__ kcs, \
+  __global__ void __launch_bounds__(256, MinBlocks<R>::value) lb_##NAME(const LrGrid* __restrict__ gs, const KC<R>* __restrict__ kcs, \
                                                    const LrTile* __restrict__ tl, int nt, LrStateT<R> cur,   \
                                                    LrStateT<R> nxt, LrWorkT<R> w) {                         \
     __shared__ Staged<R> sd;                                                                              \
