@@ -253,6 +253,8 @@ size_t layout(const lr_config* cfg, char* base, LrState* st, LrWork* w, double**
   W.gdev = b.take<LrGrid>(1);
   W.mask = b.take<unsigned char>(nc);
   for (int q = 0; q < 6; ++q) W.cut[q] = b.take<double>(nc);
+  if (cfg->remap == LR_REMAP_DIRECT)
+    for (int q = 0; q < 6; ++q) W.cutY[q] = b.take<double>(nc);
   W.stage = b.take<double>(3 * M * nc + 2 * nn);
   W.dtR = R(1);
   W.pux = R(nn); W.puy = R(nn);

@@ -101,6 +101,7 @@ struct LrWorkT {
   const LrGrid* gdev;      // lone simulation: its grid in device memory (the interface kernel reads it)
   unsigned char* mask;     // bit a set when material a is present in the cell at t^n
   double* cut[6];          // interface lines of mixed cells (n0x, n0y, d0, n1x, n1y, d1)
+  double* cutY[6];         // Direct remap: the lines that cut the Y faces (else null)
   double* stage;           // init staging: k, rho, p [3][nmat][nc] then ux, uy [2][nn]
 #define LR_F1(n) R* n;
   LR_WORK_REALS(LR_F1)
@@ -130,7 +131,7 @@ inline LrWorkT<R> typed(const LrWork& w) {
   t.scal = w.scal; t.red = w.red; t.err = w.err; t.mixed = w.mixed; t.minst = w.minst; t.gdev = w.gdev;
   t.mask = w.mask;
   t.stage = w.stage;
-  for (int q = 0; q < 6; ++q) t.cut[q] = w.cut[q];
+  for (int q = 0; q < 6; ++q) { t.cut[q] = w.cut[q]; t.cutY[q] = w.cutY[q]; }
 #define LR_F1(n) t.n = static_cast<R*>(w.n);
   LR_WORK_REALS(LR_F1)
 #undef LR_F1

@@ -38,6 +38,9 @@ constexpr int BX = 32, BY = 8;
 #ifndef LR_MINB_F32
 #define LR_MINB_F32 6
 #endif
+#ifndef LR_DEFAULT_LANES
+#define LR_DEFAULT_LANES 8
+#endif
 #ifndef LR_MINB_DF64
 #define LR_MINB_DF64 4
 #endif
@@ -264,9 +267,12 @@ __host__ __device__ double poly_half_area(const Poly& p, double nx, double ny, d
 // Line constant d with area(P & {x.n <= d}) = target, exactly: the area is
 // a quadratic in d between consecutive vertex levels, so bracket the target
 // by the vertex levels just below and just above it and solve the quadratic
-// through the area at the two ends and the middle of that bracket.  (No
-// local scratch array: every level is evaluated in place, n <= 8.)
-__host__ __device__ __noinline__ double poly_plic(const Poly& p, double nx, double ny, double target) {
+// through the area at the two ends and the middle of that bracket.  The
+// vertex levels are shared out over the eight lanes of an aligned lane group
+// (lane l evaluates vertex l; the bracket is reduced with shuffles among the
+// group), one area evaluation per lane; no local scratch array.
+__device__ __noinline__ double poly_plic8(const Poly& p, double nx, double ny, double target, int lane) {
+  const unsigned gm = 0xffu << (threadIdx.x & 24u);  // this lane's group of eight
   int n = p.n;
   double lo = 1e300, hi = -1e300;
   for (int a = 0; a < n; ++a) {
@@ -274,19 +280,24 @@ __host__ __device__ __noinline__ double poly_plic(const Poly& p, double nx, doub
     lo = fmin(lo, v);
     hi = fmax(hi, v);
   }
-  double alo = 0.0, ahi = poly_area(p);
-  double blo = lo, bhi = hi;
-  for (int a = 0; a < n; ++a) {
-    double v = p.x[a] * nx + p.y[a] * ny;
-    if (!(v > blo) || !(v < bhi)) continue;
-    double av = poly_half_area(p, nx, ny, v);
-    if (av < target) { blo = v; alo = av; }
-    else { bhi = v; ahi = av; }
+  double blo = lo, alo = 0.0, bhi = hi, ahi = poly_area(p);
+  if (lane < n) {
+    double v = p.x[lane] * nx + p.y[lane] * ny;
+    if (v > lo && v < hi) {
+      double av = poly_half_area(p, nx, ny, v);
+      if (av < target) { blo = v; alo = av; }
+      else { bhi = v; ahi = av; }
+    }
+  }
+  for (int off = 1; off < 8; off <<= 1) {
+    double ob = __shfl_xor_sync(gm, blo, off), oa = __shfl_xor_sync(gm, alo, off);
+    double oh = __shfl_xor_sync(gm, bhi, off), oah = __shfl_xor_sync(gm, ahi, off);
+    if (ob > blo) { blo = ob; alo = oa; }
+    if (oh < bhi) { bhi = oh; ahi = oah; }
   }
   double h = bhi - blo;
   if (!(h > 0.0)) return blo;
   double amid = poly_half_area(p, nx, ny, blo + 0.5 * h);
-  // A(blo + t h) = alo + c1 t + c2 t^2, t in [0,1]
   double c2 = 2.0 * (ahi + alo) - 4.0 * amid;
   double c1 = (ahi - alo) - c2;
   double T = target - alo;
@@ -665,7 +676,8 @@ __device__ __forceinline__ int donated_flux(const LrGrid& g, const LrWorkT<R>& w
 // a second one (three materials) cut from what the first left.  nrm: the
 // Youngs normals of the first two present materials; k0, k1 their fractions.
 __device__ __forceinline__ void place_cuts(int ncut, double k0, double k1, const double (*nrm)[2], double xl,
-                                           double xr, double yb, double yt, double area, double (*cut)[3]) {
+                                           double xr, double yb, double yt, double area, double (*cut)[3],
+                                           int lane) {
   cut[0][0] = nrm[0][0]; cut[0][1] = nrm[0][1];
   cut[0][2] = rect_plic(xl, xr, yb, yt, nrm[0][0], nrm[0][1], k0);
   if (ncut == 2) {
@@ -676,14 +688,13 @@ __device__ __forceinline__ void place_cuts(int ncut, double k0, double k1, const
     double ra = poly_area(rest);
     if (target > ra) target = ra;
     cut[1][0] = nrm[1][0]; cut[1][1] = nrm[1][1];
-    cut[1][2] = poly_plic(rest, nrm[1][0], nrm[1][1], target);
+    cut[1][2] = poly_plic8(rest, nrm[1][0], nrm[1][1], target, lane);
   }
 }
 
-// K4b: the interface work of mixed cells only (the list built by lr_cell_pre),
-// in double whatever the step's arithmetic: Youngs normals and PLIC lines in
-// the rectangular Lagrangian cell (sections 4.1 and 4.4; three materials by
-// nested cuts in material order), the split of every flux the cell donates,
+// K4b: the flux work of mixed cells only (the list built by lr_cell_pre), in
+// double whatever the step's arithmetic, after place_at has placed their
+// interface lines: the split of every flux the cell donates by those lines,
 // and the clipping of a material's outgoing volume to what it holds (excess
 // to the dominant material).  L lanes (1, 2, 4 or 8) work on one cell: all
 // place the interface, lane l splits fluxes 8l/L .. 8(l+1)/L - 1; the
@@ -692,6 +703,52 @@ __device__ __forceinline__ void place_cuts(int ncut, double k0, double k1, const
 // placement L times per warp instruction, so L is chosen per arithmetic.
 // Splits are stored unclipped; the rare cell whose material runs short
 // rescales its own stored splits in a second pass.
+// Interface lines of mixed cell c (sections 4.1 and 4.4), in double
+// whatever the step's arithmetic: Youngs normals and PLIC lines in the
+// rectangular Lagrangian cell (three materials by nested cuts in material
+// order); the Direct remap places one set in the X-Lagrangian cell
+// [xl, xr] x [0, dy] for the X faces and one in the Y-Lagrangian cell
+// [0, dx] x [yb, yt] for the Y faces.  Stored in w.cut (and w.cutY).  The
+// eight lanes of a group share the cell (the three-material solve spreads
+// its vertex levels over them); lane 0 stores.
+template <class R, int M>
+__device__ __forceinline__ void place_at(const LrGrid& g, const LrStateT<R>& cur, const LrWorkT<R>& w, int c,
+                                         bool valid, int lane) {
+  using O = RealOps<R>;
+  int i = (c - g.coff) % g.nx, j = (c - g.coff) / g.nx;
+  double kk[M];
+  int np = 0, order[LR_MAXM] = {0, 0, 0};
+  unsigned msk = w.mask[c];
+#pragma unroll
+  for (int a = 0; a < M; ++a) {
+    kk[a] = (msk & (1u << a)) ? O::todouble(cur.k[a][c]) : 0.0;
+    if (msk & (1u << a)) order[np++] = a;
+  }
+  double wxc = O::todouble(w.wx[c]), wyc = O::todouble(w.wy[c]);
+  double xl = 0.5 * g.dx - 0.5 * wxc + O::todouble(w.ox[c]), xr = xl + wxc;
+  double yb = 0.5 * g.dy - 0.5 * wyc + O::todouble(w.oy[c]), yt = yb + wyc;
+  int ncut = np - 1;
+  double cut[2][3], nrm[2][2];
+  youngs(g, cur.k[order[0]], i, j, nrm[0][0], nrm[0][1]);
+  if (ncut == 2) youngs(g, cur.k[order[1]], i, j, nrm[1][0], nrm[1][1]);
+  double k1 = ncut == 2 ? kk[order[1]] : 0.0;
+  if (g.remap == LR_REMAP_DIRECT) {
+    place_cuts(ncut, kk[order[0]], k1, nrm, xl, xr, 0.0, g.dy, wxc * g.dy, cut, lane);
+    if (valid && lane == 0)
+      for (int q = 0; q < ncut; ++q)
+        for (int z = 0; z < 3; ++z) w.cut[3 * q + z][c] = cut[q][z];
+    place_cuts(ncut, kk[order[0]], k1, nrm, 0.0, g.dx, yb, yt, g.dx * wyc, cut, lane);
+    if (valid && lane == 0)
+      for (int q = 0; q < ncut; ++q)
+        for (int z = 0; z < 3; ++z) w.cutY[3 * q + z][c] = cut[q][z];
+  } else {
+    place_cuts(ncut, kk[order[0]], k1, nrm, xl, xr, yb, yt, wxc * wyc, cut, lane);
+    if (valid && lane == 0)
+      for (int q = 0; q < ncut; ++q)
+        for (int z = 0; z < 3; ++z) w.cut[3 * q + z][c] = cut[q][z];
+  }
+}
+
 template <class R, int M>
 __device__ __forceinline__ void mixed_at(const LrGrid& g, const LrStateT<R>& cur, const LrWorkT<R>& w, int c,
                                          bool valid, int lane, int L) {
@@ -708,28 +765,17 @@ __device__ __forceinline__ void mixed_at(const LrGrid& g, const LrStateT<R>& cur
       if (msk & (1u << a)) order[np++] = a;
       if (kk[a] > kk[dom]) dom = a;
     }
-    // ---- interface lines in the rectangular Lagrangian cell (Direct remap:
-    // one set in the X-Lagrangian cell [xl, xr] x [0, dy] for the X faces,
-    // one in the Y-Lagrangian cell [0, dx] x [yb, yt] for the Y faces)
-    double wxc = O::todouble(w.wx[c]), wyc = O::todouble(w.wy[c]);
-    double xl = 0.5 * g.dx - 0.5 * wxc + O::todouble(w.ox[c]), xr = xl + wxc;
-    double yb = 0.5 * g.dy - 0.5 * wyc + O::todouble(w.oy[c]), yt = yb + wyc;
+    // ---- interface lines placed by lr_mixed_place (place_at)
     int ncut = np - 1;
     const bool direct = g.remap == LR_REMAP_DIRECT;
     double cut[2][3], cutY[2][3];
-    double nrm[2][2];
-    youngs(g, cur.k[order[0]], i, j, nrm[0][0], nrm[0][1]);
-    if (ncut == 2) youngs(g, cur.k[order[1]], i, j, nrm[1][0], nrm[1][1]);
-    if (direct) {
-      place_cuts(ncut, kk[order[0]], ncut == 2 ? kk[order[1]] : 0.0, nrm, xl, xr, 0.0, g.dy, wxc * g.dy, cut);
-      place_cuts(ncut, kk[order[0]], ncut == 2 ? kk[order[1]] : 0.0, nrm, 0.0, g.dx, yb, yt, g.dx * wyc, cutY);
-    } else {
-      place_cuts(ncut, kk[order[0]], ncut == 2 ? kk[order[1]] : 0.0, nrm, xl, xr, yb, yt, wxc * wyc, cut);
-    }
-    if (valid && lane == 0) {
-      w.cut[0][c] = cut[0][0]; w.cut[1][c] = cut[0][1]; w.cut[2][c] = cut[0][2];
-      if (ncut == 2) { w.cut[3][c] = cut[1][0]; w.cut[4][c] = cut[1][1]; w.cut[5][c] = cut[1][2]; }
-    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+      for (int z = 0; z < 3; ++z) {
+        cut[q][z] = q < ncut ? w.cut[3 * q + z][c] : 0.0;
+        cutY[q][z] = (direct && q < ncut) ? w.cutY[3 * q + z][c] : 0.0;
+      }
     // ---- this lane's fluxes K lane .. K lane + K - 1 (K = 8 / L): split and
     // store.  Their outgoing volumes are summed in the fixed pairwise order
     // ((0+1)+(2+3))+((4+5)+(6+7)) of the eight fluxes -- the lane's block
@@ -1968,6 +2014,22 @@ __global__ void __launch_bounds__(256) lr_sweep_prep(LrGrid g, KC<R> kc, LrState
 // passes a one-entry grid array), so both run the same compiled code and
 // give bit-identical results (separately inlined copies may fuse
 // multiply-adds differently).
+// Eight lanes per mixed cell; a warp's groups iterate together.
+template <class R, int M>
+__global__ void __launch_bounds__(128) lb_mixed_place(const LrGrid* __restrict__ gs, LrStateT<R> cur,
+                                                      LrWorkT<R> w, int mslot, int moff) {
+  int count = (int)w.red[mslot];
+  int lane = threadIdx.x & 7;
+  int group = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 3);
+  int ngroups = (int)((gridDim.x * blockDim.x) >> 3);
+  for (int k = 0;; ++k) {
+    if ((group & ~3) + k * ngroups >= count) break;
+    int t = group + k * ngroups;
+    bool valid = t < count;
+    int e = moff + (valid ? t : 0);
+    place_at<R, M>(gs[w.minst[e]], cur, w, w.mixed[e], valid, lane);
+  }
+}
 template <class R, int M>
 __global__ void __launch_bounds__(128) lb_mixed(const LrGrid* __restrict__ gs, LrStateT<R> cur, LrWorkT<R> w,
                                                 int lanes, int mslot, int moff) {
@@ -2001,8 +2063,16 @@ cudaError_t launch_t(int kid, const LrGrid& g, const LrState& cur0, const LrStat
       long long lanes = (long long)g.mixed_lanes * g.nx * g.ny;
       int nb = (int)((lanes + 127) / 128);
       if (nb > 152 * 16) nb = 152 * 16;
-      if (g.M == 2) lb_mixed<R, 2><<<nb, 128, 0, s>>>(w.gdev, cur, w, g.mixed_lanes, g.mslot, g.moff);
-      else lb_mixed<R, 3><<<nb, 128, 0, s>>>(w.gdev, cur, w, g.mixed_lanes, g.mslot, g.moff);
+      long long cells = 8ll * g.nx * g.ny;
+      int np = (int)((cells + 127) / 128);
+      if (np > 152 * 16) np = 152 * 16;
+      if (g.M == 2) {
+        lb_mixed_place<R, 2><<<np, 128, 0, s>>>(w.gdev, cur, w, g.mslot, g.moff);
+        lb_mixed<R, 2><<<nb, 128, 0, s>>>(w.gdev, cur, w, g.mixed_lanes, g.mslot, g.moff);
+      } else {
+        lb_mixed_place<R, 3><<<np, 128, 0, s>>>(w.gdev, cur, w, g.mslot, g.moff);
+        lb_mixed<R, 3><<<nb, 128, 0, s>>>(w.gdev, cur, w, g.mixed_lanes, g.mslot, g.moff);
+      }
       break;
     }
     case LRK_MAT_FLUX:
@@ -2030,8 +2100,15 @@ cudaError_t launch_batch_t(int kid, const LrBatchArgs& a, const LrState& cur0, c
   const KC<R>* kcs = static_cast<const KC<R>*>(a.kcs);
   if (kid == LRK_MIXED) {
     if (a.M == 1 || a.grid <= 0) return cudaSuccess;
-    if (a.M == 2) lb_mixed<R, 2><<<a.grid, 128, 0, s>>>(a.gs, cur, w, a.lanes, a.mslot, a.moff);
-    else lb_mixed<R, 3><<<a.grid, 128, 0, s>>>(a.gs, cur, w, a.lanes, a.mslot, a.moff);
+    int np = a.lanes == 8 ? a.grid : (int)(((long long)a.grid * 8 + a.lanes - 1) / a.lanes);  // 8 lanes per cell
+    if (np > 152 * 16) np = 152 * 16;
+    if (a.M == 2) {
+      lb_mixed_place<R, 2><<<np, 128, 0, s>>>(a.gs, cur, w, a.mslot, a.moff);
+      lb_mixed<R, 2><<<a.grid, 128, 0, s>>>(a.gs, cur, w, a.lanes, a.mslot, a.moff);
+    } else {
+      lb_mixed_place<R, 3><<<np, 128, 0, s>>>(a.gs, cur, w, a.mslot, a.moff);
+      lb_mixed<R, 3><<<a.grid, 128, 0, s>>>(a.gs, cur, w, a.lanes, a.mslot, a.moff);
+    }
     return cudaGetLastError();
   }
   if (a.ntiles <= 0) return cudaSuccess;
@@ -2073,7 +2150,7 @@ __global__ void lr_reset_k(LrWorkT<R> w, int nsim) {
 
 }  // namespace
 
-int lr_default_mixed_lanes(int mode) { return mode == LR_MODE_FP32 ? 8 : 4; }
+int lr_default_mixed_lanes(int mode) { return LR_DEFAULT_LANES; }
 
 size_t lr_real_size(int mode) { return mode == LR_MODE_FP32 ? sizeof(float) : mode == LR_MODE_DF64 ? sizeof(df64) : sizeof(double); }
 
