@@ -652,7 +652,8 @@ int lr_launches_per_step(const lr_ctx* ctx) {
   // the t_end/dt kernel, then the step's kernels (no interface kernel with one
   // material); alternate directions: a second sweep of eight kernels
   if (!ctx) return 0;
-  int one = (int)LRK_COUNT - (ctx->g.M == 1 ? 1 : 0);
+  // the interface work is two kernels (placement, then the flux split)
+  int one = (int)LRK_COUNT + (ctx->g.M == 1 ? -1 : 1);
   return 1 + one + (ctx->g.remap == LR_REMAP_AD ? one - 1 : 0);
 }
 

@@ -755,8 +755,8 @@ int lr_batch_launches_per_step(const lr_batch* b) {
   if (!b) return 0;
   int n = 0;
   for (int k = 0; k < LRK_COUNT; ++k) {
-    if (k == LRK_MIXED) {
-      for (int M = 2; M <= LR_MAXM; ++M) n += b->group_members[M] > 0;
+    if (k == LRK_MIXED) {  // placement and flux split: two kernels per group
+      for (int M = 2; M <= LR_MAXM; ++M) n += 2 * (b->group_members[M] > 0);
       continue;
     }
     bool per_m = !(k == LRK_NODE_HALF || k == LRK_DUAL_FLUX || k == LRK_NODE_UPDATE);
