@@ -164,7 +164,7 @@ __device__ __forceinline__ int* err_of(const LrGrid& g, int* err) { return err +
 // lr_set_tend at each call and by the previous step's finalize; 0 when the
 // simulation is idle (t_end or its step limit reached).
 __device__ __forceinline__ bool step_live(const LrGrid& g, const double* scal) {
-  return scal[LR_NSCAL * g.inst + 5] > 0.0;
+  return dbits::pos(scal[LR_NSCAL * g.inst + 5]);
 }
 
 // ---------------------------------------------------------------- EOS
@@ -384,11 +384,13 @@ __device__ __forceinline__ void cell_pre_at(const LrGrid& g, const KC<R>& kc, co
       pa[a] = eos_p(kc.gm1[a], kc.pin[a], rr[a], ee[a]);
       R c2 = (kc.gam[a] * pa[a] + kc.pin[a]) * ir[a];
       R wk = kk[a] * kc.invEpsC;
-      R wgt = wk < ONE ? wk : ONE;
-      if (!(wk < ONE) && !O::pos(c2)) set_err(err_of(g, w.err), LR_DERR_SOUND, c);
-      R ca = O::pos(c2) ? O::sqrt(c2) : Z;
+      bool thin = O::lt(wk, ONE);
+      R wgt = thin ? wk : ONE;
+      bool c2p = O::pos(c2);
+      if (!thin && !c2p) set_err(err_of(g, w.err), LR_DERR_SOUND, c);
+      R ca = c2p ? O::sqrt(c2) : Z;
       R wc = wgt * ca;
-      if (cmax < wc) cmax = wc;
+      if (O::lt(cmax, wc)) cmax = wc;
       m += rr[a] * kk[a] * kc.V;
     }
   }
@@ -547,7 +549,7 @@ __device__ __forceinline__ void cell_lag_at(const LrGrid& g, const KC<R>& kc, co
     R ax = w.ddx[pm], ay = w.ddy[pm], bx = w.ddx[pp], dyp = w.ddy[pp], by = kc.dy + dyp;
     R ylo = O::pos(ay) ? ay : Z;
     R yhi = kc.dy + (O::neg(dyp) ? dyp : Z);
-    if (!(ylo < yhi)) set_err(err_of(g, w.err), LR_DERR_GEOM, pm);
+    if (!O::lt(ylo, yhi)) set_err(err_of(g, w.err), LR_DERR_GEOM, pm);
     R sl = (bx - ax) / (by - ay);
     R xlo = ax + sl * (ylo - ay), xhi = ax + sl * (yhi - ay);
     R xb = H * (xlo + xhi);
@@ -560,7 +562,7 @@ __device__ __forceinline__ void cell_lag_at(const LrGrid& g, const KC<R>& kc, co
     R ax = w.ddx[pm], ay = w.ddy[pm], dxp = w.ddx[pp], bx = kc.dx + dxp, by = w.ddy[pp];
     R xlo = O::pos(ax) ? ax : Z;
     R xhi = kc.dx + (O::neg(dxp) ? dxp : Z);
-    if (!(xlo < xhi)) set_err(err_of(g, w.err), LR_DERR_GEOM, pm);
+    if (!O::lt(xlo, xhi)) set_err(err_of(g, w.err), LR_DERR_GEOM, pm);
     R sl = (by - ay) / (bx - ax);
     R ylo = ay + sl * (xlo - ax), yhi = ay + sl * (xhi - ax);
     R yb = H * (ylo + yhi);
@@ -1332,12 +1334,12 @@ __device__ __forceinline__ void cell_update_at(const LrGrid& g, const KC<R>& kc,
   R tot = Z, lm = Z, le = Z;
 #pragma unroll
   for (int a = 0; a < M; ++a) {
-    keep[a] = (nb & (1u << a)) && kc.epsKV < vol[a];
+    keep[a] = (nb & (1u << a)) && O::lt(kc.epsKV, vol[a]);
     if (keep[a]) {
       tot += vol[a];
       ++nkeep;
       if (big < 0) big = a;
-      else if (vol[big] < vol[a]) big = a;
+      else if (O::lt(vol[big], vol[a])) big = a;
     } else {
       lm += mas[a];
       le += ene[a];
@@ -1362,11 +1364,13 @@ __device__ __forceinline__ void cell_update_at(const LrGrid& g, const KC<R>& kc,
       R pa = eos_p(kc.gm1[a], kc.pin[a], ra, ea);
       R c2 = (kc.gam[a] * pa + kc.pin[a]) * (kV * im);
       R wk = ka * kc.invEpsC;
-      R wgt = wk < ONE ? wk : ONE;
-      if (!(wk < ONE) && !O::pos(c2)) set_err(err_of(g, w.err), LR_DERR_SOUND, c);
-      R ca = O::pos(c2) ? O::sqrt(c2) : Z;
+      bool thin = O::lt(wk, ONE);
+      R wgt = thin ? wk : ONE;
+      bool c2p = O::pos(c2);
+      if (!thin && !c2p) set_err(err_of(g, w.err), LR_DERR_SOUND, c);
+      R ca = c2p ? O::sqrt(c2) : Z;
       R wc = wgt * ca;
-      if (cmax < wc) cmax = wc;
+      if (O::lt(cmax, wc)) cmax = wc;
       if (!O::finite(ra) || !O::finite(ea)) set_err(err_of(g, w.err), LR_DERR_NAN, c);
     }
     nxt.k[a][c] = ka; nxt.r[a][c] = ra; nxt.e[a][c] = ea;
@@ -1521,7 +1525,7 @@ template <> struct Key<df64> {
   __device__ static df64 dec(unsigned long long k) { return df64(__uint_as_float((unsigned)(k >> 32)), unord((unsigned)k)); }
 };
 template <class R>
-__device__ __forceinline__ R key_max(R a, R b) { return a < b ? b : a; }
+__device__ __forceinline__ R key_max(R a, R b) { return RealOps<R>::lt(a, b) ? b : a; }
 
 // Block-wide max of v >= 0 folded into the simulation's CFL key; the last of
 // its `ntiles` blocks (tiles) turns it into the CFL time step (dt = cfl

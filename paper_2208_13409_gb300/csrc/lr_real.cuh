@@ -100,6 +100,38 @@ __device__ __forceinline__ bool operator!=(df64 a, df64 b) { return !(a == b); }
 template <class R> struct RealOps;
 // mul/add: rounded operations the compiler may not fuse into a multiply-add
 // (used where two kernels must give bit-identical results).
+// Predicates and ordering of doubles on the integer units.  A double
+// comparison issues on the FP64 pipe, the binding resource of the native
+// double kernels (one warp instruction holds it for 16 clocks), while these
+// take a few integer operations on the bit pattern.  They have IEEE 754
+// semantics exactly: false when an operand is NaN, -0 equal to +0.
+namespace dbits {
+__device__ __forceinline__ long long bits(double x) { return __double_as_longlong(x); }
+// +inf's pattern; a NaN's magnitude lies above it.
+constexpr unsigned long long kInf = 0x7ff0000000000000ULL;
+// x > 0: the patterns 1 .. kInf (smallest subnormal .. +inf) shifted down by one.
+__device__ __forceinline__ bool pos(double x) { return (unsigned long long)(bits(x) - 1) < kInf; }
+// x < 0: the patterns of -smallest subnormal .. -inf, sign bit set, likewise.
+__device__ __forceinline__ bool neg(double x) {
+  return (unsigned long long)bits(x) - 0x8000000000000001ULL < kInf;
+}
+__device__ __forceinline__ bool zero(double x) { return (bits(x) << 1) == 0; }
+__device__ __forceinline__ bool finite(double x) {
+  return ((unsigned)__double2hiint(x) & 0x7ff00000u) != 0x7ff00000u;
+}
+__device__ __forceinline__ bool nan_b(long long v) { return ((unsigned long long)v << 1) > (kInf << 1); }
+// Sign-magnitude to two's-complement order: negative patterns have their
+// magnitude bits flipped, so signed integer order is numeric order (with -0
+// just below +0, which lt treats as equal).
+__device__ __forceinline__ long long okey(long long v) { return v ^ ((v >> 63) & 0x7fffffffffffffffLL); }
+__device__ __forceinline__ bool lt(double a, double b) {
+  long long u = bits(a), v = bits(b);
+  bool ord = !(nan_b(u) | nan_b(v));
+  bool zz = ((u | v) << 1) == 0;
+  return ord & !zz & (okey(u) < okey(v));
+}
+}  // namespace dbits
+
 template <> struct RealOps<double> {
   __device__ static __forceinline__ double c(float v) { return (double)v; }
   __device__ static __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
@@ -107,10 +139,11 @@ template <> struct RealOps<double> {
   __device__ static __forceinline__ double abs(double x) { return fabs(x); }
   __device__ static __forceinline__ double sqrt(double x) { return ::sqrt(x); }
   __device__ static __forceinline__ double rcp(double x) { return 1.0 / x; }
-  __device__ static __forceinline__ bool finite(double x) { return isfinite(x); }
-  __device__ static __forceinline__ bool pos(double x) { return x > 0.0; }
-  __device__ static __forceinline__ bool neg(double x) { return x < 0.0; }
-  __device__ static __forceinline__ bool zero(double x) { return x == 0.0; }
+  __device__ static __forceinline__ bool finite(double x) { return dbits::finite(x); }
+  __device__ static __forceinline__ bool pos(double x) { return dbits::pos(x); }
+  __device__ static __forceinline__ bool neg(double x) { return dbits::neg(x); }
+  __device__ static __forceinline__ bool zero(double x) { return dbits::zero(x); }
+  __device__ static __forceinline__ bool lt(double a, double b) { return dbits::lt(a, b); }
   __host__ __device__ static __forceinline__ double todouble(double x) { return x; }
 };
 template <> struct RealOps<float> {
@@ -124,6 +157,7 @@ template <> struct RealOps<float> {
   __device__ static __forceinline__ bool pos(float x) { return x > 0.0f; }
   __device__ static __forceinline__ bool neg(float x) { return x < 0.0f; }
   __device__ static __forceinline__ bool zero(float x) { return x == 0.0f; }
+  __device__ static __forceinline__ bool lt(float a, float b) { return a < b; }
   __host__ __device__ static __forceinline__ double todouble(float x) { return (double)x; }
 };
 template <> struct RealOps<df64> {
@@ -137,6 +171,7 @@ template <> struct RealOps<df64> {
   __device__ static __forceinline__ bool pos(df64 x) { return x.hi > 0.0f; }
   __device__ static __forceinline__ bool neg(df64 x) { return x.hi < 0.0f; }
   __device__ static __forceinline__ bool zero(df64 x) { return x.hi == 0.0f; }
+  __device__ static __forceinline__ bool lt(df64 a, df64 b) { return a < b; }
   __host__ __device__ static __forceinline__ double todouble(df64 x) { return (double)x.hi + (double)x.lo; }
 };
 
@@ -151,5 +186,5 @@ template <> __host__ __device__ inline df64 from_double<df64>(double v) {
   return df64(h, l);
 }
 
-template <class R> __device__ __forceinline__ R rmin(R a, R b) { return b < a ? b : a; }
-template <class R> __device__ __forceinline__ R rmax(R a, R b) { return a < b ? b : a; }
+template <class R> __device__ __forceinline__ R rmin(R a, R b) { return RealOps<R>::lt(b, a) ? b : a; }
+template <class R> __device__ __forceinline__ R rmax(R a, R b) { return RealOps<R>::lt(a, b) ? b : a; }
