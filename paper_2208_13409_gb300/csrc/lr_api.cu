@@ -22,8 +22,8 @@ struct lr_ctx {
   bool own_arena;
   cudaStream_t stream;
   bool own_stream;
-  cudaStream_t aux;            // the interface kernel runs here, beside lr_mat_flux
-  cudaEvent_t ev_fork, ev_join;
+  cudaStream_t aux;            // the interface kernels run here, beside lr_cell_cf and lr_mat_flux
+  cudaEvent_t ev_fork, ev_cf, ev_join;
   bool have_mats, inited;
   int sticky;
   char msg[512];
@@ -172,6 +172,13 @@ cudaError_t lr_field_view(const LrGrid& g, const LrState& s, const LrState& prev
 }
 
 
+cudaError_t lr_create_aux_stream(cudaStream_t* s) {
+  int least = 0, greatest = 0;
+  cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+  if (e != cudaSuccess) return e;
+  return cudaStreamCreateWithPriority(s, cudaStreamNonBlocking, greatest);
+}
+
 size_t lr_field_count(const LrGrid& g, int field) {
   size_t nx = g.nx, ny = g.ny, M = g.M;
   switch (field) {
@@ -317,9 +324,10 @@ lr_status check_sticky(lr_ctx* ctx) {
 }
 
 cudaError_t launch_on(lr_ctx* ctx, int k, const LrGrid& g, const LrState& cur, const LrState& nxt, cudaStream_t st) {
-  if (!ctx->prof || k >= LRK_COUNT) return lr_launch(k, g, cur, nxt, ctx->w, st);
+  int slot = k == LRK_MIXED_PLACE ? (int)LRK_MIXED : k;  // both interface kernels time as lr_mixed
+  if (!ctx->prof || slot >= LRK_COUNT) return lr_launch(k, g, cur, nxt, ctx->w, st);
   lr_ctx::Pend p;
-  p.kid = k;
+  p.kid = slot;
   cudaEventCreate(&p.a);
   cudaEventCreate(&p.b);
   cudaEventRecord(p.a, st);
@@ -329,15 +337,24 @@ cudaError_t launch_on(lr_ctx* ctx, int k, const LrGrid& g, const LrState& cur, c
   return e;
 }
 
-// One kernel of the step.  The interface kernel runs on the auxiliary
-// stream, forked after lr_cell_cf and joined before lr_cell_update, so it
-// overlaps lr_mat_flux (each finishes a disjoint set of flux objects).
+// One kernel of the step.  The interface kernels run on the auxiliary
+// stream: the placement of the interface lines (it needs the mixed-cell list
+// and the Lagrangian rectangles) forked after lr_cell_lag, beside
+// lr_cell_cf; the flux split (it needs rho^{lagCF}) after lr_cell_cf, beside
+// lr_mat_flux (each finishes a disjoint set of flux objects); joined before
+// lr_cell_update.
 cudaError_t launch_one(lr_ctx* ctx, int k, const LrGrid& g, const LrState& cur, const LrState& nxt) {
   cudaError_t e;
-  if (k == LRK_MIXED) {
-    if (g.M == 1) return cudaSuccess;
+  if (k == LRK_CELL_LAG && g.M > 1) {
+    if ((e = launch_on(ctx, k, g, cur, nxt, ctx->stream)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(ctx->ev_fork, ctx->stream)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0)) != cudaSuccess) return e;
+    return launch_on(ctx, LRK_MIXED_PLACE, g, cur, nxt, ctx->aux);
+  }
+  if (k == LRK_MIXED) {
+    if (g.M == 1) return cudaSuccess;
+    if ((e = cudaEventRecord(ctx->ev_cf, ctx->stream)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(ctx->aux, ctx->ev_cf, 0)) != cudaSuccess) return e;
     if ((e = launch_on(ctx, k, g, cur, nxt, ctx->aux)) != cudaSuccess) return e;
     return cudaEventRecord(ctx->ev_join, ctx->aux);
   }
@@ -426,8 +443,9 @@ lr_status create_common(const lr_config* cfg, void* mem, size_t bytes, bool own,
     }
     ctx->own_stream = true;
   }
-  if (cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking) != cudaSuccess ||
+  if (lr_create_aux_stream(&ctx->aux) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_cf, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     if (own) cudaFree(mem);
@@ -694,6 +712,7 @@ void lr_destroy(lr_ctx* ctx) {
   cudaStreamSynchronize(ctx->aux);
   cudaStreamDestroy(ctx->aux);
   cudaEventDestroy(ctx->ev_fork);
+  cudaEventDestroy(ctx->ev_cf);
   cudaEventDestroy(ctx->ev_join);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   if (ctx->own_arena) cudaFree(ctx->arena);

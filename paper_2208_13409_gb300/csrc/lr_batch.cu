@@ -76,7 +76,7 @@ struct lr_batch {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   cudaStream_t aux = nullptr;   // interface kernels, beside lb_mat_flux
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_cf = nullptr, ev_join = nullptr;
   cudaGraphExec_t gexec[2];
   bool gvalid[2] = {false, false};
   int launches = 0;
@@ -306,7 +306,7 @@ cudaError_t launch_timed(lr_batch* b, int kid, const LrBatchArgs& a, const LrSta
   b->launches += 1;
   if (!b->prof) return lr_launch_batch(kid, a, cur, nxt, b->w, st);
   lr_batch::Pend p;
-  p.kid = kid;
+  p.kid = kid == LRK_MIXED_PLACE ? (int)LRK_MIXED : kid;  // both interface kernels time as lr_mixed
   cudaEventCreate(&p.a);
   cudaEventCreate(&p.b);
   cudaEventRecord(p.a, st);
@@ -314,6 +314,17 @@ cudaError_t launch_timed(lr_batch* b, int kid, const LrBatchArgs& a, const LrSta
   cudaEventRecord(p.b, st);
   b->pend.push_back(p);
   return e;
+}
+
+// Arguments of an interface kernel over material-count group M with `lanes`
+// threads per mixed cell (blocks of 128 threads, at most 16 per SM).
+void set_mixed_args(const lr_batch* b, int M, int lanes, LrBatchArgs& a) {
+  a.M = M;
+  a.lanes = lanes;
+  a.mslot = M - 1;
+  a.moff = (M - 2) * (int)b->P;
+  long nb = ((long)lanes * b->group_units[M] + 127) / 128;
+  a.grid = (int)(nb < (long)b->nsm * 16 ? nb : (long)b->nsm * 16);
 }
 
 // One step of every member: for each kernel, one launch per material-count
@@ -330,21 +341,16 @@ cudaError_t enqueue_step(lr_batch* b, int from) {
       if (e != cudaSuccess) return e;
     }
     if (k == LRK_MIXED) {
-      // the interface kernels run on the auxiliary stream beside lb_mat_flux
-      // (disjoint flux objects), joined before lb_cell_update
+      // the flux split of the mixed cells runs on the auxiliary stream after
+      // lb_cell_cf, beside lb_mat_flux (disjoint flux objects), joined
+      // before lb_cell_update
       if (!any_mixed) continue;
-      cudaError_t e = cudaEventRecord(b->ev_fork, b->stream);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->aux, b->ev_fork, 0);
+      cudaError_t e = cudaEventRecord(b->ev_cf, b->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->aux, b->ev_cf, 0);
       if (e != cudaSuccess) return e;
       for (int M = 2; M <= LR_MAXM; ++M) {
         if (b->group_members[M] == 0) continue;
-        a.M = M;
-        a.lanes = b->sch.lanes;
-        a.mslot = M - 1;
-        a.moff = (M - 2) * (int)b->P;
-        long lanes = (long)b->sch.lanes * b->group_units[M];
-        long nb = (lanes + 127) / 128;
-        a.grid = (int)(nb < (long)b->nsm * 16 ? nb : (long)b->nsm * 16);
+        set_mixed_args(b, M, b->sch.lanes, a);
         e = launch_timed(b, k, a, cur, nxt, b->aux);
         if (e != cudaSuccess) return e;
       }
@@ -366,6 +372,20 @@ cudaError_t enqueue_step(lr_batch* b, int from) {
       a.grid = grid_for_tiles(b, b->sch.bps[k], r.count);
       cudaError_t e = launch_timed(b, k, a, cur, nxt, b->stream);
       if (e != cudaSuccess) return e;
+    }
+    if (k == LRK_CELL_LAG && any_mixed) {
+      // the interface lines of the mixed cells need the Lagrangian
+      // rectangles: placed on the auxiliary stream beside lb_cell_cf
+      cudaError_t e = cudaEventRecord(b->ev_fork, b->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->aux, b->ev_fork, 0);
+      if (e != cudaSuccess) return e;
+      for (int M = 2; M <= LR_MAXM; ++M) {
+        if (b->group_members[M] == 0) continue;
+        LrBatchArgs pa = base_args(b);
+        set_mixed_args(b, M, 8, pa);
+        e = launch_timed(b, LRK_MIXED_PLACE, pa, cur, nxt, b->aux);
+        if (e != cudaSuccess) return e;
+      }
     }
   }
   return cudaSuccess;
@@ -506,8 +526,9 @@ lr_status lr_batch_create(const lr_batch_config* cfg, lr_batch** out) {
     delete b;
     return LR_ERR_CUDA;
   }
-  if (cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking) != cudaSuccess ||
+  if (lr_create_aux_stream(&b->aux) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_cf, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess) {
     if (b->own_stream) cudaStreamDestroy(b->stream);
     cudaFree(b->arena);
@@ -541,6 +562,7 @@ void lr_batch_destroy(lr_batch* b) {
   cudaStreamSynchronize(b->aux);
   cudaStreamDestroy(b->aux);
   cudaEventDestroy(b->ev_fork);
+  cudaEventDestroy(b->ev_cf);
   cudaEventDestroy(b->ev_join);
   if (b->own_stream) cudaStreamDestroy(b->stream);
   cudaFree(b->arena);

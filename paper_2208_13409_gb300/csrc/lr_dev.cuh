@@ -152,7 +152,8 @@ enum LrKernelId {
   LRK_CELL_UPDATE, LRK_DUAL_FLUX, LRK_NODE_UPDATE, LRK_COUNT,
   LRK_PREPARE = 100,   // initial state from the staging area
   LRK_CFL_ONLY = 101,  // CFL rule from the current state
-  LRK_SWEEP_PREP = 102 // alternate directions: the first sweep's result as the second's input
+  LRK_SWEEP_PREP = 102, // alternate directions: the first sweep's result as the second's input
+  LRK_MIXED_PLACE = 103 // interface lines of the mixed cells; LRK_MIXED then splits their fluxes
 };
 // Iteration domains of the kernels (tile tables of a batch are per domain).
 enum { LR_DOM_CELLS = 0, LR_DOM_NODES, LR_DOM_DUAL, LR_DOM_NODES_ALL, LR_NDOM };

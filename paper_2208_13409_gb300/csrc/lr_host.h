@@ -16,3 +16,8 @@ cudaError_t lr_field_view(const LrGrid& g, const LrState& s, const LrState& prev
                           int field, double* dst, cudaStream_t st, bool* unknown);
 // Number of doubles of a field, 0 if unknown.
 size_t lr_field_count(const LrGrid& g, int field);
+// The auxiliary stream of the interface kernels, at the device's highest
+// priority: its blocks are scheduled ahead of the step kernels they run
+// beside, so the short, latency-bound interface work is not left to the
+// tail of lr_mat_flux.
+cudaError_t lr_create_aux_stream(cudaStream_t* s);

@@ -119,26 +119,22 @@ __device__ __forceinline__ int dix(const LrGrid& g, int i, int j) {
 // mirrored reads: node vector components, cell scalars, centre offsets
 template <class R> __device__ __forceinline__ R nodeX(const LrGrid& g, const R* a, int i, int j) {
   Ix q = nix(g, i, j);
-  R v = a[q.idx];
-  return q.fx ? -v : v;
+  return RealOps<R>::flip(q.fx, a[q.idx]);
 }
 template <class R> __device__ __forceinline__ R nodeY(const LrGrid& g, const R* a, int i, int j) {
   Ix q = nix(g, i, j);
-  R v = a[q.idx];
-  return q.fy ? -v : v;
+  return RealOps<R>::flip(q.fy, a[q.idx]);
 }
 template <class R> __device__ __forceinline__ R cellS(const LrGrid& g, const R* a, int i, int j) {
   return a[cix(g, i, j).idx];
 }
 template <class R> __device__ __forceinline__ R cellOX(const LrGrid& g, const R* a, int i, int j) {
   Ix q = cix(g, i, j);
-  R v = a[q.idx];
-  return q.fx ? -v : v;
+  return RealOps<R>::flip(q.fx, a[q.idx]);
 }
 template <class R> __device__ __forceinline__ R cellOY(const LrGrid& g, const R* a, int i, int j) {
   Ix q = cix(g, i, j);
-  R v = a[q.idx];
-  return q.fy ? -v : v;
+  return RealOps<R>::flip(q.fy, a[q.idx]);
 }
 
 __device__ __forceinline__ void set_err(int* err, int bit, int idx) {
@@ -189,6 +185,15 @@ __device__ __forceinline__ R vl_slope(R dm, R dp, R hm, R hp) {
   using O = RealOps<R>;
   R pr = dm * dp;
   return O::pos(pr) ? O::c(2.0f) * pr / (dp * hm + dm * hp) : O::c(0.0f);
+}
+// The same slope times X/2, as dm dp X / (dp hm + dm hp): the form every
+// reconstruction a + slope (offset) takes with offset = X/2.  A factor common
+// to hm and hp carries over to X unchanged (it cancels).
+template <class R>
+__device__ __forceinline__ R vl_term(R dm, R dp, R hm, R hp, R X) {
+  using O = RealOps<R>;
+  R pr = dm * dp;
+  return O::pos(pr) ? pr * X / (dp * hm + dm * hp) : O::c(0.0f);
 }
 
 // --------------------------------------------------- half-plane geometry
@@ -878,9 +883,9 @@ __device__ __forceinline__ void mixed_at(const LrGrid& g, const LrStateT<R>& cur
         } else {
           Aa = Z;
         }
-        R sM = fwd ? Ma : -Ma;
-        if (kind == 0) { w.xA[a][fidx] = fwd ? Aa : -Aa; w.xMm[a][fidx] = sM; w.xE[a][fidx] = fwd ? Ea : -Ea; }
-        else if (kind == 1) { w.yA[a][fidx] = fwd ? Aa : -Aa; w.yMm[a][fidx] = sM; w.yE[a][fidx] = fwd ? Ea : -Ea; }
+        R sA = O::flip(!fwd, Aa), sM = O::flip(!fwd, Ma), sE = O::flip(!fwd, Ea);
+        if (kind == 0) { w.xA[a][fidx] = sA; w.xMm[a][fidx] = sM; w.xE[a][fidx] = sE; }
+        else if (kind == 1) { w.yA[a][fidx] = sA; w.yMm[a][fidx] = sM; w.yE[a][fidx] = sE; }
         else { w.cA[a][fidx] = Aa; w.cMm[a][fidx] = Ma; w.cE[a][fidx] = Ea; }
         mt = O::add(mt, sM);
       }
@@ -889,7 +894,7 @@ __device__ __forceinline__ void mixed_at(const LrGrid& g, const LrStateT<R>& cur
       else {
         R cx = w.ddx[fidx], cy = w.ddy[fidx];
         bool pp = O::pos(cx) == O::pos(cy);
-        R sgm = O::pos(cx) ? mt : -mt;  // signed along +x
+        R sgm = O::flip(!O::pos(cx), mt);  // signed along +x
         w.Mpp[fidx] = pp ? sgm : Z;
         w.Mpm[fidx] = pp ? Z : sgm;
       }
@@ -948,7 +953,7 @@ __device__ __forceinline__ bool pure_in(const LrGrid& g, const unsigned char* ma
 // Face value (section 2.1.1): a_d + slope/2 (sgn(dVol) wx_d - dt u_f).
 template <class R>
 __device__ __forceinline__ R recon_face(const LrGrid& g, const KC<R>& kc, const R* q, const R* ox, const R* wx,
-                                       int di, int dj, R sg, R fdisp, bool xdir) {
+                                       int di, int dj, bool fwd, R fdisp, bool xdir) {
   using O = RealOps<R>;
   int c = cix(g, di, dj).idx;
   R a0 = q[c];
@@ -962,8 +967,7 @@ __device__ __forceinline__ R recon_face(const LrGrid& g, const KC<R>& kc, const 
   }
   R o0 = ox[c];
   R h = xdir ? kc.dx : kc.dy;
-  R sl = vl_slope(a0 - am, ap - a0, h + o0 - om, h + op - o0);
-  return a0 + O::c(0.5f) * sl * (sg * wx[c] - fdisp);
+  return a0 + vl_term(a0 - am, ap - a0, h + o0 - om, h + op - o0, O::flip(!fwd, wx[c]) - fdisp);
 }
 // Corner value, diagonal limited reconstruction (section 3.3): along v (or
 // v_perp when dx dy < 0), slope over the diagonal neighbours' Lagrangian
@@ -978,14 +982,13 @@ __device__ __forceinline__ R recon_corner(const LrGrid& g, const KC<R>& kc, cons
   R ap = cellS(g, q, di + 1, dj + sj), am = cellS(g, q, di - 1, dj - sj);
   R oxp = cellOX(g, w.ox, di + 1, dj + sj), oyp = cellOY(g, w.oy, di + 1, dj + sj);
   R oxm = cellOX(g, w.ox, di - 1, dj - sj), oym = cellOY(g, w.oy, di - 1, dj - sj);
-  R sdy = sj > 0 ? kc.dy : -kc.dy;
-  R hp = ((kc.dx + oxp - ox0) * kc.dx + (sdy + oyp - oy0) * sdy) * kc.invD;
-  R hm = ((kc.dx + ox0 - oxm) * kc.dx + (sdy + oy0 - oym) * sdy) * kc.invD;
-  R sl = vl_slope(a0 - am, ap - a0, hm, hp);
+  R sdy = O::flip(sj < 0, kc.dy);
+  // spacings and offset along v, all scaled by |v|^2 = dx^2 + dy^2
+  R hp = (kc.dx + oxp - ox0) * kc.dx + (sdy + oyp - oy0) * sdy;
+  R hm = (kc.dx + ox0 - oxm) * kc.dx + (sdy + oy0 - oym) * sdy;
   R wsum = w.wx[c] * kc.dx + w.wy[c] * kc.dy;
   R dsum = ddx * kc.dx + ddy * sdy;
-  R off = O::c(0.5f) * ((O::pos(ddx) ? wsum : -wsum) - dsum) * kc.invD;
-  return a0 + sl * off;
+  return a0 + vl_term(a0 - am, ap - a0, hm, hp, O::flip(!O::pos(ddx), wsum) - dsum);
 }
 
 // Van Leer limited slopes of q in cell (di,dj): along x or y over the
@@ -1015,7 +1018,7 @@ __device__ __forceinline__ R slope_diag(const LrGrid& g, const KC<R>& kc, const 
   R ap = cellS(g, q, di + 1, dj + sj), am = cellS(g, q, di - 1, dj - sj);
   R oxp = cellOX(g, w.ox, di + 1, dj + sj), oyp = cellOY(g, w.oy, di + 1, dj + sj);
   R oxm = cellOX(g, w.ox, di - 1, dj - sj), oym = cellOY(g, w.oy, di - 1, dj - sj);
-  R sdy = sj > 0 ? kc.dy : -kc.dy;
+  R sdy = RealOps<R>::flip(sj < 0, kc.dy);
   R hp = ((kc.dx + oxp - ox0) * kc.dx + (sdy + oyp - oy0) * sdy) * kc.invD;
   R hm = ((kc.dx + ox0 - oxm) * kc.dx + (sdy + oy0 - oym) * sdy) * kc.invD;
   return vl_slope(a0 - am, ap - a0, hm, hp);
@@ -1111,7 +1114,7 @@ __device__ __forceinline__ void mat_flux_at(const LrGrid& g, const KC<R>& kc, co
     unsigned dm = 0u;
     int di = 0, dc = 0;
     bool left = O::pos(v);
-    R sg = left ? ONE : -ONE, fd = Z;
+    R fd = Z;
     if (!O::zero(v)) {
       di = left ? i - 1 : i;
       dc = cix(g, di, j).idx;
@@ -1137,16 +1140,16 @@ __device__ __forceinline__ void mat_flux_at(const LrGrid& g, const KC<R>& kc, co
             ef = recon_lsq(g, kc, w.elag[a], w, di, j, px, py);
           }
         } else if (!mixed && g.face_o2 && pure_in(g, w.mask, di - 1, j, bit) && pure_in(g, w.mask, di + 1, j, bit)) {
-          rf = recon_face(g, kc, w.rcf[a], w.ox, w.wx, di, j, sg, fd, true);
-          ef = recon_face(g, kc, w.elag[a], w.ox, w.wx, di, j, sg, fd, true);
+          rf = recon_face(g, kc, w.rcf[a], w.ox, w.wx, di, j, left, fd, true);
+          ef = recon_face(g, kc, w.elag[a], w.ox, w.wx, di, j, left, fd, true);
         }
         Ma = O::mul(rf, Aa);
         Ea = O::mul(Ma, ef);
       } else {
         Aa = Z;
       }
-      R sMa = left ? Ma : -Ma;
-      w.xA[a][f] = left ? Aa : -Aa; w.xMm[a][f] = sMa; w.xE[a][f] = left ? Ea : -Ea;
+      R sMa = O::flip(!left, Ma);
+      w.xA[a][f] = O::flip(!left, Aa); w.xMm[a][f] = sMa; w.xE[a][f] = O::flip(!left, Ea);
       mt = O::add(mt, sMa);
     }
     w.MX[f] = mt;
@@ -1160,7 +1163,7 @@ __device__ __forceinline__ void mat_flux_at(const LrGrid& g, const KC<R>& kc, co
     unsigned dm = 0u;
     int dj = 0, dc = 0;
     bool below = O::pos(v);
-    R sg = below ? ONE : -ONE, fd = Z;
+    R fd = Z;
     if (!O::zero(v)) {
       dj = below ? j - 1 : j;
       dc = cix(g, i, dj).idx;
@@ -1186,16 +1189,16 @@ __device__ __forceinline__ void mat_flux_at(const LrGrid& g, const KC<R>& kc, co
             ef = recon_lsq(g, kc, w.elag[a], w, i, dj, px, py);
           }
         } else if (!mixed && g.face_o2 && pure_in(g, w.mask, i, dj - 1, bit) && pure_in(g, w.mask, i, dj + 1, bit)) {
-          rf = recon_face(g, kc, w.rcf[a], w.oy, w.wy, i, dj, sg, fd, false);
-          ef = recon_face(g, kc, w.elag[a], w.oy, w.wy, i, dj, sg, fd, false);
+          rf = recon_face(g, kc, w.rcf[a], w.oy, w.wy, i, dj, below, fd, false);
+          ef = recon_face(g, kc, w.elag[a], w.oy, w.wy, i, dj, below, fd, false);
         }
         Ma = O::mul(rf, Aa);
         Ea = O::mul(Ma, ef);
       } else {
         Aa = Z;
       }
-      R sMa = below ? Ma : -Ma;
-      w.yA[a][f] = below ? Aa : -Aa; w.yMm[a][f] = sMa; w.yE[a][f] = below ? Ea : -Ea;
+      R sMa = O::flip(!below, Ma);
+      w.yA[a][f] = O::flip(!below, Aa); w.yMm[a][f] = sMa; w.yE[a][f] = O::flip(!below, Ea);
       mt = O::add(mt, sMa);
     }
     w.MY[f] = mt;
@@ -1258,7 +1261,7 @@ __device__ __forceinline__ void mat_flux_at(const LrGrid& g, const KC<R>& kc, co
       w.cA[a][n] = Aa; w.cMm[a][n] = Ma; w.cE[a][n] = Ea;
       mt = O::add(mt, Ma);
     }
-    R sgm = O::pos(ddx) ? mt : -mt;  // signed along +x
+    R sgm = O::flip(!O::pos(ddx), mt);  // signed along +x
     w.Mpp[n] = (dm && pp) ? sgm : Z;
     w.Mpm[n] = (dm && !pp) ? sgm : Z;
     }
@@ -1383,7 +1386,7 @@ __device__ __forceinline__ void cell_update_at(const LrGrid& g, const KC<R>& kc,
 // width dx + (d_{q+1} - d_{q-1})/2, face displacement fdisp).
 template <class R>
 __device__ __forceinline__ R recon_dual_face(const LrGrid& g, const KC<R>& kc, const R* u, bool ucomp_x,
-                                            const R* dd, int qi, int qj, bool xdir, R sg, R fdisp) {
+                                            const R* dd, int qi, int qj, bool xdir, bool fwd, R fdisp) {
   using O = RealOps<R>;
   auto U = [&](int a, int b) { return ucomp_x ? nodeX(g, u, a, b) : nodeY(g, u, a, b); };
   auto Dd = [&](int a, int b) { return xdir ? nodeX(g, dd, a, b) : nodeY(g, dd, a, b); };
@@ -1391,9 +1394,8 @@ __device__ __forceinline__ R recon_dual_face(const LrGrid& g, const KC<R>& kc, c
   R u0 = U(qi, qj), up = U(qi + mi, qj + mj), um = U(qi - mi, qj - mj);
   R d0 = Dd(qi, qj), dp = Dd(qi + mi, qj + mj), dm = Dd(qi - mi, qj - mj);
   R h = xdir ? kc.dx : kc.dy;
-  R sl = vl_slope(u0 - um, up - u0, h + d0 - dm, h + dp - d0);
   R wd = h + O::c(0.5f) * (dp - dm);
-  return u0 + O::c(0.5f) * sl * (sg * wd - fdisp);
+  return u0 + vl_term(u0 - um, up - u0, h + d0 - dm, h + dp - d0, O::flip(!fwd, wd) - fdisp);
 }
 
 // K7a: dual-mesh fluxes (sections 2.1.1 and 2.3).  Dual X face between nodes
@@ -1415,14 +1417,15 @@ __device__ __forceinline__ void dual_flux_at(const LrGrid& g, const KC<R>& kc, c
   bool xnode = i >= 0 && i < g.nxu;                     // canonical node in x
   bool ynode = j >= 0 && j < g.nyu;
   int o = g.doff + (j + 1) * (g.nx + 2) + (i + 1);
-  auto MXr = [&](int a, int b) { Ix q = xix(g, a, b); R v = w.MX[q.idx]; return q.fx ? -v : v; };
-  auto MYr = [&](int a, int b) { Ix q = yix(g, a, b); R v = w.MY[q.idx]; return q.fy ? -v : v; };
+  auto MXr = [&](int a, int b) { Ix q = xix(g, a, b); return O::flip(q.fx, w.MX[q.idx]); };
+  auto MYr = [&](int a, int b) { Ix q = yix(g, a, b); return O::flip(q.fy, w.MY[q.idx]); };
   auto CPr = [&](int a, int b, R& pp, R& pm) {
     Ix q = nix(g, a, b);
     R x = w.Mpp[q.idx], y = w.Mpm[q.idx];
-    if (q.fx) { R t = -y; y = -x; x = t; }
-    if (q.fy) { R t = y; y = x; x = t; }
-    pp = x; pm = y;
+    // a mirror in x maps (pp, pm) to (-pm, -pp), one in y to (pm, pp)
+    bool sw = q.fx != q.fy;
+    pp = O::flip(q.fx, sw ? y : x);
+    pm = O::flip(q.fx, sw ? x : y);
   };
   if (xdual && ynode) {  // dual X face between nodes (i,j), (i+1,j)
     R Dm = Q4 * (MXr(i, j - 1) + MXr(i + 1, j - 1) + MXr(i, j) + MXr(i + 1, j));
@@ -1430,12 +1433,11 @@ __device__ __forceinline__ void dual_flux_at(const LrGrid& g, const KC<R>& kc, c
     if (!O::zero(Dm)) {
       bool fwd = O::pos(Dm);
       int qi = fwd ? i : i + 1;
-      R sg = fwd ? ONE : -ONE;
       R fd = H * (nodeX(g, w.ddx, i, j) + nodeX(g, w.ddx, i + 1, j));
       R vx, vy;
       if (g.face_o2) {
-        vx = recon_dual_face(g, kc, w.ulx, true, w.ddx, qi, j, true, sg, fd);
-        vy = recon_dual_face(g, kc, w.uly, false, w.ddx, qi, j, true, sg, fd);
+        vx = recon_dual_face(g, kc, w.ulx, true, w.ddx, qi, j, true, fwd, fd);
+        vy = recon_dual_face(g, kc, w.uly, false, w.ddx, qi, j, true, fwd, fd);
       } else {
         vx = nodeX(g, w.ulx, qi, j); vy = nodeY(g, w.uly, qi, j);
       }
@@ -1449,12 +1451,11 @@ __device__ __forceinline__ void dual_flux_at(const LrGrid& g, const KC<R>& kc, c
     if (!O::zero(Dm)) {
       bool fwd = O::pos(Dm);
       int qj = fwd ? j : j + 1;
-      R sg = fwd ? ONE : -ONE;
       R fd = H * (nodeY(g, w.ddy, i, j) + nodeY(g, w.ddy, i, j + 1));
       R vx, vy;
       if (g.face_o2) {
-        vx = recon_dual_face(g, kc, w.ulx, true, w.ddy, i, qj, false, sg, fd);
-        vy = recon_dual_face(g, kc, w.uly, false, w.ddy, i, qj, false, sg, fd);
+        vx = recon_dual_face(g, kc, w.ulx, true, w.ddy, i, qj, false, fwd, fd);
+        vy = recon_dual_face(g, kc, w.uly, false, w.ddy, i, qj, false, fwd, fd);
       } else {
         vx = nodeX(g, w.ulx, i, qj); vy = nodeY(g, w.uly, i, qj);
       }
@@ -1480,20 +1481,21 @@ __device__ __forceinline__ void dual_flux_at(const LrGrid& g, const KC<R>& kc, c
         R vx = nodeX(g, w.ulx, qi, qj), vy = nodeY(g, w.uly, qi, qj);
         if (g.corner_o2) {
           int sj = pp ? 1 : -1;
-          R sdy = pp ? kc.dy : -kc.dy;
+          R sdy = O::flip(!pp, kc.dy);
           R dx0 = nodeX(g, w.ddx, qi, qj), dy0 = nodeY(g, w.ddy, qi, qj);
           R dxp = nodeX(g, w.ddx, qi + 1, qj + sj), dyp = nodeY(g, w.ddy, qi + 1, qj + sj);
           R dxm = nodeX(g, w.ddx, qi - 1, qj - sj), dym = nodeY(g, w.ddy, qi - 1, qj - sj);
-          R hp = ((kc.dx + dxp - dx0) * kc.dx + (sdy + dyp - dy0) * sdy) * kc.invD;
-          R hm = ((kc.dx + dx0 - dxm) * kc.dx + (sdy + dy0 - dym) * sdy) * kc.invD;
+          // spacings and offset along v, all scaled by |v|^2 = dx^2 + dy^2
+          R hp = (kc.dx + dxp - dx0) * kc.dx + (sdy + dyp - dy0) * sdy;
+          R hm = (kc.dx + dx0 - dxm) * kc.dx + (sdy + dy0 - dym) * sdy;
           R wxq = kc.dx + H * (nodeX(g, w.ddx, qi + 1, qj) - nodeX(g, w.ddx, qi - 1, qj));
           R wyq = kc.dy + H * (nodeY(g, w.ddy, qi, qj + 1) - nodeY(g, w.ddy, qi, qj - 1));
           R wsum = wxq * kc.dx + wyq * kc.dy;
-          R off = H * ((fwd ? wsum : -wsum) - (cdx * kc.dx + cdy * sdy)) * kc.invD;
+          R X = O::flip(!fwd, wsum) - (cdx * kc.dx + cdy * sdy);
           R uxp = nodeX(g, w.ulx, qi + 1, qj + sj), uxm = nodeX(g, w.ulx, qi - 1, qj - sj);
           R uyp = nodeY(g, w.uly, qi + 1, qj + sj), uym = nodeY(g, w.uly, qi - 1, qj - sj);
-          vx = vx + vl_slope(vx - uxm, uxp - vx, hm, hp) * off;
-          vy = vy + vl_slope(vy - uym, uyp - vy, hm, hp) * off;
+          vx = vx + vl_term(vx - uxm, uxp - vx, hm, hp, X);
+          vy = vy + vl_term(vy - uym, uyp - vy, hm, hp, X);
         }
         px = Dm * vx; py = Dm * vy;
       }
@@ -2061,22 +2063,23 @@ cudaError_t launch_t(int kid, const LrGrid& g, const LrState& cur0, const LrStat
     case LRK_NODE_HALF: LR_1(lr_node_half, grid_for(g.nxu, g.nyu)); break;
     case LRK_CELL_LAG: LR_M(lr_cell_lag, grid_for(g.nxu, g.nyu)); break;
     case LRK_CELL_CF: LR_M(lr_cell_cf, grid_for(g.nx, g.ny)); break;
+    case LRK_MIXED_PLACE:
     case LRK_MIXED: {
       if (g.M == 1) break;  // one material: no interfaces
       if (!w.gdev) return cudaErrorInvalidValue;
+      if (kid == LRK_MIXED_PLACE) {
+        long long cells = 8ll * g.nx * g.ny;  // a group of eight lanes per cell
+        int np = (int)((cells + 127) / 128);
+        if (np > 152 * 16) np = 152 * 16;
+        if (g.M == 2) lb_mixed_place<R, 2><<<np, 128, 0, s>>>(w.gdev, cur, w, g.mslot, g.moff);
+        else lb_mixed_place<R, 3><<<np, 128, 0, s>>>(w.gdev, cur, w, g.mslot, g.moff);
+        break;
+      }
       long long lanes = (long long)g.mixed_lanes * g.nx * g.ny;
       int nb = (int)((lanes + 127) / 128);
       if (nb > 152 * 16) nb = 152 * 16;
-      long long cells = 8ll * g.nx * g.ny;
-      int np = (int)((cells + 127) / 128);
-      if (np > 152 * 16) np = 152 * 16;
-      if (g.M == 2) {
-        lb_mixed_place<R, 2><<<np, 128, 0, s>>>(w.gdev, cur, w, g.mslot, g.moff);
-        lb_mixed<R, 2><<<nb, 128, 0, s>>>(w.gdev, cur, w, g.mixed_lanes, g.mslot, g.moff);
-      } else {
-        lb_mixed_place<R, 3><<<np, 128, 0, s>>>(w.gdev, cur, w, g.mslot, g.moff);
-        lb_mixed<R, 3><<<nb, 128, 0, s>>>(w.gdev, cur, w, g.mixed_lanes, g.mslot, g.moff);
-      }
+      if (g.M == 2) lb_mixed<R, 2><<<nb, 128, 0, s>>>(w.gdev, cur, w, g.mixed_lanes, g.mslot, g.moff);
+      else lb_mixed<R, 3><<<nb, 128, 0, s>>>(w.gdev, cur, w, g.mixed_lanes, g.mslot, g.moff);
       break;
     }
     case LRK_MAT_FLUX:
@@ -2102,16 +2105,14 @@ cudaError_t launch_batch_t(int kid, const LrBatchArgs& a, const LrState& cur0, c
   LrStateT<R> cur = typed<R>(cur0), nxt = typed<R>(nxt0);
   LrWorkT<R> w = typed<R>(w0);
   const KC<R>* kcs = static_cast<const KC<R>*>(a.kcs);
-  if (kid == LRK_MIXED) {
+  if (kid == LRK_MIXED_PLACE || kid == LRK_MIXED) {
     if (a.M == 1 || a.grid <= 0) return cudaSuccess;
-    int np = a.lanes == 8 ? a.grid : (int)(((long long)a.grid * 8 + a.lanes - 1) / a.lanes);  // 8 lanes per cell
-    if (np > 152 * 16) np = 152 * 16;
-    if (a.M == 2) {
-      lb_mixed_place<R, 2><<<np, 128, 0, s>>>(a.gs, cur, w, a.mslot, a.moff);
-      lb_mixed<R, 2><<<a.grid, 128, 0, s>>>(a.gs, cur, w, a.lanes, a.mslot, a.moff);
-    } else {
-      lb_mixed_place<R, 3><<<np, 128, 0, s>>>(a.gs, cur, w, a.mslot, a.moff);
-      lb_mixed<R, 3><<<a.grid, 128, 0, s>>>(a.gs, cur, w, a.lanes, a.mslot, a.moff);
+    if (kid == LRK_MIXED_PLACE) {  // a.grid: blocks of 128 threads, eight lanes per cell
+      if (a.M == 2) lb_mixed_place<R, 2><<<a.grid, 128, 0, s>>>(a.gs, cur, w, a.mslot, a.moff);
+      else lb_mixed_place<R, 3><<<a.grid, 128, 0, s>>>(a.gs, cur, w, a.mslot, a.moff);
+    } else {  // a.grid: blocks of 128 threads, a.lanes per cell
+      if (a.M == 2) lb_mixed<R, 2><<<a.grid, 128, 0, s>>>(a.gs, cur, w, a.lanes, a.mslot, a.moff);
+      else lb_mixed<R, 3><<<a.grid, 128, 0, s>>>(a.gs, cur, w, a.lanes, a.mslot, a.moff);
     }
     return cudaGetLastError();
   }

@@ -116,6 +116,12 @@ __device__ __forceinline__ bool neg(double x) {
   return (unsigned long long)bits(x) - 0x8000000000000001ULL < kInf;
 }
 __device__ __forceinline__ bool zero(double x) { return (bits(x) << 1) == 0; }
+// -x when f, x otherwise, and |x|: the sign bit alone (a negation written
+// as such costs an FP64 add).
+__device__ __forceinline__ double flip(bool f, double x) {
+  return __longlong_as_double(bits(x) ^ ((long long)f << 63));
+}
+__device__ __forceinline__ double absb(double x) { return __longlong_as_double(bits(x) & 0x7fffffffffffffffLL); }
 __device__ __forceinline__ bool finite(double x) {
   return ((unsigned)__double2hiint(x) & 0x7ff00000u) != 0x7ff00000u;
 }
@@ -136,7 +142,8 @@ template <> struct RealOps<double> {
   __device__ static __forceinline__ double c(float v) { return (double)v; }
   __device__ static __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
   __device__ static __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
-  __device__ static __forceinline__ double abs(double x) { return fabs(x); }
+  __device__ static __forceinline__ double abs(double x) { return dbits::absb(x); }
+  __device__ static __forceinline__ double flip(bool f, double x) { return dbits::flip(f, x); }
   __device__ static __forceinline__ double sqrt(double x) { return ::sqrt(x); }
   __device__ static __forceinline__ double rcp(double x) { return 1.0 / x; }
   __device__ static __forceinline__ bool finite(double x) { return dbits::finite(x); }
@@ -151,6 +158,7 @@ template <> struct RealOps<float> {
   __device__ static __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
   __device__ static __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
   __device__ static __forceinline__ float abs(float x) { return fabsf(x); }
+  __device__ static __forceinline__ float flip(bool f, float x) { return f ? -x : x; }
   __device__ static __forceinline__ float sqrt(float x) { return sqrtf(x); }
   __device__ static __forceinline__ float rcp(float x) { return 1.0f / x; }
   __device__ static __forceinline__ bool finite(float x) { return isfinite(x); }
@@ -165,6 +173,7 @@ template <> struct RealOps<df64> {
   __device__ static __forceinline__ df64 mul(df64 a, df64 b) { return dfops::mul(a, b); }
   __device__ static __forceinline__ df64 add(df64 a, df64 b) { return dfops::add(a, b); }
   __device__ static __forceinline__ df64 abs(df64 x) { return x.hi < 0.0f ? dfops::neg(x) : x; }
+  __device__ static __forceinline__ df64 flip(bool f, df64 x) { return f ? dfops::neg(x) : x; }
   __device__ static __forceinline__ df64 sqrt(df64 x) { return dfops::sqrt_(x); }
   __device__ static __forceinline__ df64 rcp(df64 x) { return dfops::div(df64(1.0f, 0.0f), x); }
   __device__ static __forceinline__ bool finite(df64 x) { return isfinite(x.hi) && isfinite(x.lo); }
