@@ -250,6 +250,23 @@ lr_status lr_cfl_dt_noalloc(const lr_config* cfg, const lr_material* mats, const
                             const double* rho, const double* e, const double* ux, const double* uy,
                             double* dt_out);
 
+/* Arithmetic check: out[i] = a[i] op b[i], i < n, computed on the device by
+ * the routine the FP64 step kernels use for that operation, so that a test
+ * can compare it with IEEE 754 arithmetic.
+ *   op LR_ARITH_DIV: the quotient a/b by Newton-Raphson refinement with
+ *      fused multiply-add residuals (P. W. Markstein, IBM J. Res. Dev. 34(1),
+ *      1990) from a float reciprocal seed; correctly rounded except within
+ *      about 2^-66 (relative) of a rounding midpoint, where it is one ulp
+ *      off; b zero, subnormal, infinite, NaN or |b| >= 2^1020 take IEEE
+ *      division.  The FP64 step uses it for every division except the
+ *      reciprocals 1/x, which stay IEEE.
+ * a, b, out: device pointers to n doubles (out may alias a or b).
+ * cuda_stream: cudaStream_t, NULL = the legacy default stream; the work is
+ * enqueued, nothing is synchronised.  LR_ERR_ARG: unknown op, or n > 0 with
+ * a NULL pointer; LR_ERR_CUDA: the launch failed. */
+enum { LR_ARITH_DIV = 0 };
+lr_status lr_arith_check(int op, const double* a, const double* b, double* out, size_t n, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -53,6 +53,7 @@ struct lr_batch {
   char* arena = nullptr;
   size_t state_bytes = 0;  // one state buffer (contiguous)
   size_t scal_bytes = 0;   // scal, red, err, dtR (contiguous)
+  size_t cc_bytes = 0;     // w.cc: the state's sound-speed term, read by the next lb_cell_pre
   LrState st[2];
   int cur = 0;
   LrWork w;
@@ -191,6 +192,7 @@ size_t layout(const lr_batch_config* c, char* base, lr_batch* b) {
     b->st[0] = s[0]; b->st[1] = s[1]; b->w = W;
     b->state_bytes = s0;
     b->scal_bytes = sc1 - sc0;
+    b->cc_bytes = P * es;
     b->d_gs = gs; b->d_kcs = kcs; b->kcb = kcb;
     b->tmp = tmp; b->rows = rows;
   }
@@ -839,9 +841,11 @@ lr_status lr_batch_autotune(lr_batch* b, int trial_steps) {
   for (auto& m : b->mem) any |= m.used;
   if (!any) { setmsg(b, "lr_batch_autotune: no members"); return LR_ERR_STATE; }
   CK(cudaStreamSynchronize(b->stream), "sync");
-  // snapshot of the current state buffer and the scalars
+  // snapshot of the current state buffer, the scalars and the sound-speed
+  // term the next step's lb_cell_pre reads
   char* snap = nullptr;
-  size_t nb = b->state_bytes + b->scal_bytes;
+  size_t nb = b->state_bytes + b->scal_bytes + b->cc_bytes;
+  char* cc0 = static_cast<char*>(b->w.cc);
   CK(cudaMalloc(&snap, nb), "autotune snapshot");
   const int cur0 = b->cur;
   char* st0 = static_cast<char*>(b->st[cur0].k[0]);
@@ -850,6 +854,8 @@ lr_status lr_batch_autotune(lr_batch* b, int trial_steps) {
   auto restore = [&]() -> lr_status {
     CK(cudaMemcpyAsync(static_cast<char*>(b->st[cur0].k[0]), snap, b->state_bytes, cudaMemcpyDeviceToDevice, b->stream), "restore");
     CK(cudaMemcpyAsync(sc0, snap + b->state_bytes, b->scal_bytes, cudaMemcpyDeviceToDevice, b->stream), "restore");
+    CK(cudaMemcpyAsync(cc0, snap + b->state_bytes + b->scal_bytes, b->cc_bytes, cudaMemcpyDeviceToDevice, b->stream),
+       "restore");
     b->cur = cur0;
     CK(cudaStreamSynchronize(b->stream), "sync");
     return LR_OK;
@@ -872,6 +878,8 @@ lr_status lr_batch_autotune(lr_batch* b, int trial_steps) {
   };
   CK(cudaMemcpyAsync(snap, st0, b->state_bytes, cudaMemcpyDeviceToDevice, b->stream), "snapshot");
   CK(cudaMemcpyAsync(snap + b->state_bytes, sc0, b->scal_bytes, cudaMemcpyDeviceToDevice, b->stream), "snapshot");
+  CK(cudaMemcpyAsync(snap + b->state_bytes + b->scal_bytes, cc0, b->cc_bytes, cudaMemcpyDeviceToDevice, b->stream),
+     "snapshot");
   Schedule best = b->sch;
   double bestt[LRK_COUNT];
   for (int k = 0; k < LRK_COUNT; ++k) bestt[k] = 1e300;

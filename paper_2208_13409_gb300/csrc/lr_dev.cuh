@@ -189,6 +189,7 @@ void lr_make_kc(const LrGrid& g, void* out);
 cudaError_t lr_launch_view(const LrGrid& g, const void* src, double* dst, size_t n, int kind, cudaStream_t s);
 cudaError_t lr_launch_mixture(const LrGrid& g, const LrState& st, double* dst, int which, cudaStream_t s);
 cudaError_t lr_launch_cons(const LrGrid& g, const LrState& st, double* rows, double* dst, cudaStream_t s);
+cudaError_t lr_launch_arith(int op, const double* a, const double* b, double* out, size_t n, cudaStream_t s);
 cudaError_t lr_launch_corner_debug(const LrGrid& g, const LrWork& w, double* fc_out, double* mc_out,
                                    cudaStream_t s);
 cudaError_t lr_launch_cuts(const LrGrid& g, const LrState& prev, const LrWork& w, double* dst, cudaStream_t s);

@@ -184,7 +184,7 @@ template <class R>
 __device__ __forceinline__ R vl_slope(R dm, R dp, R hm, R hp) {
   using O = RealOps<R>;
   R pr = dm * dp;
-  return O::pos(pr) ? O::c(2.0f) * pr / (dp * hm + dm * hp) : O::c(0.0f);
+  return O::pos(pr) ? O::div(O::c(2.0f) * pr, dp * hm + dm * hp) : O::c(0.0f);
 }
 // The same slope times X/2, as dm dp X / (dp hm + dm hp): the form every
 // reconstruction a + slope (offset) takes with offset = X/2.  A factor common
@@ -193,7 +193,7 @@ template <class R>
 __device__ __forceinline__ R vl_term(R dm, R dp, R hm, R hp, R X) {
   using O = RealOps<R>;
   R pr = dm * dp;
-  return O::pos(pr) ? pr * X / (dp * hm + dm * hp) : O::c(0.0f);
+  return O::pos(pr) ? O::div(pr * X, dp * hm + dm * hp) : O::c(0.0f);
 }
 
 // --------------------------------------------------- half-plane geometry
@@ -375,7 +375,11 @@ __device__ __forceinline__ void cell_pre_at(const LrGrid& g, const KC<R>& kc, co
   R uxll = cur.ux[ll], uxlr = cur.ux[lr], uxul = cur.ux[ul], uxur = cur.ux[ur];
   R uyll = cur.uy[ll], uylr = cur.uy[lr], uyul = cur.uy[ul], uyur = cur.uy[ur];
   R kk[M], rr[M], ee[M], pa[M], ir[M];
-  R m = Z, cmax = Z;
+  R m = Z;
+  // max over materials of the weighted sound speed of this state: computed
+  // (and checked) by lr_cell_update at the end of the previous step, or by
+  // the preparation of the initial state
+  R cmax = w.cc[c];
   unsigned msk = 0u;
 #pragma unroll
   for (int a = 0; a < M; ++a) {
@@ -387,15 +391,6 @@ __device__ __forceinline__ void cell_pre_at(const LrGrid& g, const KC<R>& kc, co
       ee[a] = cur.e[a][c];
       ir[a] = O::rcp(rr[a]);
       pa[a] = eos_p(kc.gm1[a], kc.pin[a], rr[a], ee[a]);
-      R c2 = (kc.gam[a] * pa[a] + kc.pin[a]) * ir[a];
-      R wk = kk[a] * kc.invEpsC;
-      bool thin = O::lt(wk, ONE);
-      R wgt = thin ? wk : ONE;
-      bool c2p = O::pos(c2);
-      if (!thin && !c2p) set_err(err_of(g, w.err), LR_DERR_SOUND, c);
-      R ca = c2p ? O::sqrt(c2) : Z;
-      R wc = wgt * ca;
-      if (O::lt(cmax, wc)) cmax = wc;
       m += rr[a] * kk[a] * kc.V;
     }
   }
@@ -411,7 +406,7 @@ __device__ __forceinline__ void cell_pre_at(const LrGrid& g, const KC<R>& kc, co
                  kc.dx + h * uxur, kc.dy + h * uyur);
   if (!O::pos(vol)) set_err(err_of(g, w.err), LR_DERR_VOLUME, c);
   R dv = vol - kc.V;
-  R vV = kc.V / vol;
+  R vV = O::div(kc.V, vol);
   R P = Z;
 #pragma unroll
   for (int a = 0; a < M; ++a) {
@@ -459,7 +454,7 @@ __device__ __forceinline__ void node_half_at(const LrGrid& g, const KC<R>& kc, c
     R gx = ((w.Pi[B] + w.Pi[D]) - (w.Pi[A] + w.Pi[C])) * kc.inv2dx;
     R gy = ((w.Pi[C] + w.Pi[D]) - (w.Pi[A] + w.Pi[B])) * kc.inv2dy;
     R mp = O::c(0.25f) * (w.mc[A] + w.mc[B] + w.mc[C] + w.mc[D]);
-    R f = O::c(0.5f) * dt * kc.V / mp;  // dt/2 / rho_p
+    R f = O::div(O::c(0.5f) * dt * kc.V, mp);  // dt/2 / rho_p
     R u0x = cur.ux[n], u0y = cur.uy[n];
     hx = u0x - f * gx;
     hy = u0y - f * gy;
@@ -555,7 +550,7 @@ __device__ __forceinline__ void cell_lag_at(const LrGrid& g, const KC<R>& kc, co
     R ylo = O::pos(ay) ? ay : Z;
     R yhi = kc.dy + (O::neg(dyp) ? dyp : Z);
     if (!O::lt(ylo, yhi)) set_err(err_of(g, w.err), LR_DERR_GEOM, pm);
-    R sl = (bx - ax) / (by - ay);
+    R sl = O::div(bx - ax, by - ay);
     R xlo = ax + sl * (ylo - ay), xhi = ax + sl * (yhi - ay);
     R xb = H * (xlo + xhi);
     int f = nb + j * nn + i;
@@ -568,7 +563,7 @@ __device__ __forceinline__ void cell_lag_at(const LrGrid& g, const KC<R>& kc, co
     R xlo = O::pos(ax) ? ax : Z;
     R xhi = kc.dx + (O::neg(dxp) ? dxp : Z);
     if (!O::lt(xlo, xhi)) set_err(err_of(g, w.err), LR_DERR_GEOM, pm);
-    R sl = (by - ay) / (bx - ax);
+    R sl = O::div(by - ay, bx - ax);
     R ylo = ay + sl * (xlo - ax), yhi = ay + sl * (xhi - ax);
     R yb = H * (ylo + yhi);
     int f = nb + j * g.nx + i;
@@ -604,7 +599,7 @@ __device__ __forceinline__ void cell_cf_at(const LrGrid& g, const KC<R>& kc, con
   if (!O::pos(v)) set_err(err_of(g, w.err), LR_DERR_VOLUME, c);
   w.vcf[c] = v;
   unsigned msk = w.mask[c];
-  R vV = kc.V / v;
+  R vV = O::div(kc.V, v);
 #pragma unroll
   for (int a = 0; a < M; ++a) w.rcf[a][c] = (msk & (1u << a)) ? cur.r[a][c] * vV : O::c(0.0f);
 }
@@ -1066,15 +1061,15 @@ __device__ __noinline__ R recon_lsq(const LrGrid& g, const KC<R>& kc, const R* q
       sxx += X1 * X1; sxy += X1 * X2; syy += X2 * X2; sxa += X1 * A; sya += X2 * A;
     }
   R det = sxx * syy - sxy * sxy;
-  R g1 = (syy * sxa - sxy * sya) / det;
-  R g2 = (sxx * sya - sxy * sxa) / det;
+  R g1 = O::div(syy * sxa - sxy * sya, det);
+  R g2 = O::div(sxx * sya - sxy * sxa, det);
   R gn = O::sqrt(g1 * g1 + g2 * g2);
   if (!O::pos(gn)) return qc;
   R m = O::abs(slope_axis(g, kc, q, w, di, dj, true));
   m = rmin(m, O::abs(slope_axis(g, kc, q, w, di, dj, false)));
   m = rmin(m, O::abs(slope_diag(g, kc, q, w, di, dj, 1)));
   m = rmin(m, O::abs(slope_diag(g, kc, q, w, di, dj, -1)));
-  R phi = m / gn;
+  R phi = O::div(m, gn);
   R cx = H * kc.dx + oxc, cy = H * kc.dy + oyc;
   return qc + phi * (g1 * (px - cx) + g2 * (py - cy));
 }
@@ -1358,11 +1353,11 @@ __device__ __forceinline__ void cell_update_at(const LrGrid& g, const KC<R>& kc,
   for (int a = 0; a < M; ++a) {
     R ka = Z, ra = Z, ea = Z;
     if (keep[a]) {
-      ka = nkeep == 1 ? ONE : vol[a] / tot;
+      ka = nkeep == 1 ? ONE : O::div(vol[a], tot);
       if (!O::pos(mas[a])) set_err(err_of(g, w.err), LR_DERR_MASS, c);
       R im = O::rcp(mas[a]);
       R kV = ka * kc.V;
-      ra = nkeep == 1 ? mas[a] * kc.invV : mas[a] / kV;
+      ra = nkeep == 1 ? mas[a] * kc.invV : O::div(mas[a], kV);
       ea = ene[a] * im;
       R pa = eos_p(kc.gm1[a], kc.pin[a], ra, ea);
       R c2 = (kc.gam[a] * pa + kc.pin[a]) * (kV * im);
@@ -2240,6 +2235,20 @@ cudaError_t lr_launch_cons(const LrGrid& g, const LrState& st, double* rows, dou
   else if (g.mode == LR_MODE_DF64) lr_cons_rows<df64><<<nb, 64, 0, s>>>(g, typed<df64>(st), rows);
   else lr_cons_rows<double><<<nb, 64, 0, s>>>(g, typed<double>(st), rows);
   lr_cons_sum<<<1, 1, 0, s>>>(rows, nrows, dst);
+  return cudaGetLastError();
+}
+
+// Elementwise check of the FP64 step's arithmetic routines (lr_arith_check).
+__global__ void lr_arith_k(int op, const double* a, const double* b, double* out, size_t n) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  if (op == LR_ARITH_DIV) out[t] = RealOps<double>::div(a[t], b[t]);
+}
+cudaError_t lr_launch_arith(int op, const double* a, const double* b, double* out, size_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  size_t nb = (n + 255) / 256;
+  if (nb > 0x7fffffffull) return cudaErrorInvalidValue;
+  lr_arith_k<<<(unsigned)nb, 256, 0, s>>>(op, a, b, out, n);
   return cudaGetLastError();
 }
 

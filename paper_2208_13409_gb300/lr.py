@@ -29,6 +29,7 @@ FP64, DF64, FP32 = 0, 1, 2
 F_K, F_RHO_MAT, F_E_MAT, F_P, F_RHO, F_E, F_UX, F_UY, F_CONS, F_C = range(10)
 F_UHX, F_UHY, F_VOL_LAGCF, F_E_LAG, F_FX, F_FY, F_FC, F_MX, F_MY, F_MC, F_Q, F_DT = range(20, 32)
 F_CUTS, F_XA, F_YA, F_CA, F_NMIXED = range(32, 37)
+ARITH_DIV = 0
 
 
 class LrError(RuntimeError):
@@ -129,6 +130,8 @@ def load(build_if_missing: bool = True):
     L.lr_last_error.restype = ctypes.c_char_p
     L.lr_cfl_dt_noalloc.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(Material), vp, vp, vp, vp, vp, vp]
     L.lr_cfl_dt_noalloc.restype = ctypes.c_int
+    L.lr_arith_check.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.c_size_t, vp]
+    L.lr_arith_check.restype = ctypes.c_int
     bp = ctypes.POINTER(BatchConfig)
     L.lr_batch_config_default.argtypes = [bp]
     L.lr_batch_config_default.restype = None
@@ -192,6 +195,19 @@ def load(build_if_missing: bool = True):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
+
+
+def arith_check(op: int, a, b, out, stream: int = 0) -> None:
+    """lr_arith_check on device buffers: a, b, out are contiguous float64
+    CUDA tensors of one size (out may be a or b); enqueued on ``stream``."""
+    L = load()
+    n = out.numel()
+    if a.numel() != n or b.numel() != n:
+        raise LrError("lr_arith_check: a, b and out differ in size")
+    rc = L.lr_arith_check(op, ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()),
+                          ctypes.c_void_p(out.data_ptr()), n, ctypes.c_void_p(stream))
+    if rc != OK:
+        raise LrError(f"lr_arith_check failed ({rc})")
 
 
 def _c64(a) -> np.ndarray:
