@@ -23,7 +23,7 @@ struct lr_ctx {
   cudaStream_t stream;
   bool own_stream;
   cudaStream_t aux;            // the interface kernels run here, beside lr_cell_cf and lr_mat_flux
-  cudaEvent_t ev_fork, ev_cf, ev_join;
+  cudaEvent_t ev_fork, ev_cf, ev_join, ev_mf, ev_dual;
   bool have_mats, inited;
   int sticky;
   char msg[512];
@@ -350,7 +350,9 @@ cudaError_t launch_on(lr_ctx* ctx, int k, const LrGrid& g, const LrState& cur, c
 // and the Lagrangian rectangles) forked after lr_cell_lag, beside
 // lr_cell_cf; the flux split (it needs rho^{lagCF}) after lr_cell_cf, beside
 // lr_mat_flux (each finishes a disjoint set of flux objects); joined before
-// lr_cell_update.
+// lr_cell_update.  lr_dual_flux needs only the mass fluxes (lr_mat_flux and
+// the flux split), not the cell update: it runs on the auxiliary stream
+// beside lr_cell_update, joined before lr_node_update.
 cudaError_t launch_one(lr_ctx* ctx, int k, const LrGrid& g, const LrState& cur, const LrState& nxt) {
   cudaError_t e;
   if (k == LRK_CELL_LAG && g.M > 1) {
@@ -366,8 +368,16 @@ cudaError_t launch_one(lr_ctx* ctx, int k, const LrGrid& g, const LrState& cur, 
     if ((e = launch_on(ctx, k, g, cur, nxt, ctx->aux)) != cudaSuccess) return e;
     return cudaEventRecord(ctx->ev_join, ctx->aux);
   }
-  if (k == LRK_CELL_UPDATE && g.M > 1 && (e = cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0)) != cudaSuccess)
-    return e;
+  if (k == LRK_CELL_UPDATE) {
+    if ((e = cudaEventRecord(ctx->ev_mf, ctx->stream)) != cudaSuccess) return e;  // lr_mat_flux done
+    if (g.M > 1 && (e = cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0)) != cudaSuccess) return e;
+  }
+  if (k == LRK_DUAL_FLUX) {
+    if ((e = cudaStreamWaitEvent(ctx->aux, ctx->ev_mf, 0)) != cudaSuccess) return e;
+    if ((e = launch_on(ctx, k, g, cur, nxt, ctx->aux)) != cudaSuccess) return e;
+    return cudaEventRecord(ctx->ev_dual, ctx->aux);
+  }
+  if (k == LRK_NODE_UPDATE && (e = cudaStreamWaitEvent(ctx->stream, ctx->ev_dual, 0)) != cudaSuccess) return e;
   return launch_on(ctx, k, g, cur, nxt, ctx->stream);
 }
 
@@ -454,7 +464,9 @@ lr_status create_common(const lr_config* cfg, void* mem, size_t bytes, bool own,
   if (lr_create_aux_stream(&ctx->aux) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->ev_cf, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_mf, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_dual, cudaEventDisableTiming) != cudaSuccess) {
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     if (own) cudaFree(mem);
     delete ctx;
@@ -722,6 +734,8 @@ void lr_destroy(lr_ctx* ctx) {
   cudaEventDestroy(ctx->ev_fork);
   cudaEventDestroy(ctx->ev_cf);
   cudaEventDestroy(ctx->ev_join);
+  cudaEventDestroy(ctx->ev_mf);
+  cudaEventDestroy(ctx->ev_dual);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   if (ctx->own_arena) cudaFree(ctx->arena);
   delete ctx;

@@ -77,7 +77,7 @@ struct lr_batch {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   cudaStream_t aux = nullptr;   // interface kernels, beside lb_mat_flux
-  cudaEvent_t ev_fork = nullptr, ev_cf = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_cf = nullptr, ev_join = nullptr, ev_mf = nullptr, ev_dual = nullptr;
   cudaGraphExec_t gexec[2];
   bool gvalid[2] = {false, false};
   int launches = 0;
@@ -338,8 +338,21 @@ cudaError_t enqueue_step(lr_batch* b, int from) {
   for (int k = 0; k < LRK_COUNT; ++k) {
     LrBatchArgs a = base_args(b);
     bool any_mixed = b->group_members[2] + b->group_members[3] > 0;
-    if (k == LRK_CELL_UPDATE && any_mixed) {
-      cudaError_t e = cudaStreamWaitEvent(b->stream, b->ev_join, 0);
+    cudaStream_t ks = b->stream;
+    if (k == LRK_CELL_UPDATE) {
+      // lb_dual_flux needs only the mass fluxes: it runs on the auxiliary
+      // stream beside lb_cell_update, joined before lb_node_update
+      cudaError_t e = cudaEventRecord(b->ev_mf, b->stream);
+      if (e == cudaSuccess && any_mixed) e = cudaStreamWaitEvent(b->stream, b->ev_join, 0);
+      if (e != cudaSuccess) return e;
+    }
+    if (k == LRK_DUAL_FLUX) {
+      cudaError_t e = cudaStreamWaitEvent(b->aux, b->ev_mf, 0);
+      if (e != cudaSuccess) return e;
+      ks = b->aux;
+    }
+    if (k == LRK_NODE_UPDATE) {
+      cudaError_t e = cudaStreamWaitEvent(b->stream, b->ev_dual, 0);
       if (e != cudaSuccess) return e;
     }
     if (k == LRK_MIXED) {
@@ -372,7 +385,11 @@ cudaError_t enqueue_step(lr_batch* b, int from) {
       a.tiles = b->d_tiles + r.start;
       a.ntiles = r.count;
       a.grid = grid_for_tiles(b, b->sch.bps[k], r.count);
-      cudaError_t e = launch_timed(b, k, a, cur, nxt, b->stream);
+      cudaError_t e = launch_timed(b, k, a, cur, nxt, ks);
+      if (e != cudaSuccess) return e;
+    }
+    if (k == LRK_DUAL_FLUX) {
+      cudaError_t e = cudaEventRecord(b->ev_dual, b->aux);
       if (e != cudaSuccess) return e;
     }
     if (k == LRK_CELL_LAG && any_mixed) {
@@ -531,7 +548,9 @@ lr_status lr_batch_create(const lr_batch_config* cfg, lr_batch** out) {
   if (lr_create_aux_stream(&b->aux) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&b->ev_cf, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_mf, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_dual, cudaEventDisableTiming) != cudaSuccess) {
     if (b->own_stream) cudaStreamDestroy(b->stream);
     cudaFree(b->arena);
     delete b;
@@ -566,6 +585,8 @@ void lr_batch_destroy(lr_batch* b) {
   cudaEventDestroy(b->ev_fork);
   cudaEventDestroy(b->ev_cf);
   cudaEventDestroy(b->ev_join);
+  cudaEventDestroy(b->ev_mf);
+  cudaEventDestroy(b->ev_dual);
   if (b->own_stream) cudaStreamDestroy(b->stream);
   cudaFree(b->arena);
   delete b;
