@@ -260,11 +260,15 @@ lr_status lr_cfl_dt_noalloc(const lr_config* cfg, const lr_material* mats, const
  *      off; b zero, subnormal, infinite, NaN or |b| >= 2^1020 take IEEE
  *      division.  The FP64 step uses it for every division except the
  *      reciprocals 1/x, which stay IEEE.
+ *   op LR_ARITH_SQRT: sqrt(a) (b unused, may equal a) by the same refinement
+ *      from a float reciprocal-square-root seed, correctly rounded except
+ *      near midpoints as above; a zero, subnormal, negative, infinite, NaN or
+ *      >= 2^1023 takes the IEEE square root.
  * a, b, out: device pointers to n doubles (out may alias a or b).
  * cuda_stream: cudaStream_t, NULL = the legacy default stream; the work is
  * enqueued, nothing is synchronised.  LR_ERR_ARG: unknown op, or n > 0 with
  * a NULL pointer; LR_ERR_CUDA: the launch failed. */
-enum { LR_ARITH_DIV = 0 };
+enum { LR_ARITH_DIV = 0, LR_ARITH_SQRT = 1 };
 lr_status lr_arith_check(int op, const double* a, const double* b, double* out, size_t n, void* cuda_stream);
 
 #ifdef __cplusplus

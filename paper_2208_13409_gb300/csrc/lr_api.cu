@@ -174,7 +174,7 @@ cudaError_t lr_field_view(const LrGrid& g, const LrState& s, const LrState& prev
 
 extern "C" lr_status lr_arith_check(int op, const double* a, const double* b, double* out, size_t n,
                                    void* cuda_stream) {
-  if (op != LR_ARITH_DIV) return LR_ERR_ARG;
+  if (op != LR_ARITH_DIV && op != LR_ARITH_SQRT) return LR_ERR_ARG;
   if (n > 0 && (!a || !b || !out)) return LR_ERR_ARG;
   return lr_launch_arith(op, a, b, out, n, static_cast<cudaStream_t>(cuda_stream)) == cudaSuccess ? LR_OK
                                                                                                    : LR_ERR_CUDA;

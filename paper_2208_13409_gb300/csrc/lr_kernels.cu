@@ -30,16 +30,30 @@ constexpr double EPS_K = 1e-12;  // material dropped when its volume <= EPS_K dx
 constexpr double EPS_K_FP32 = 1e-6;  // the same in the FP32 bulk mode (above float round-off)
 constexpr double EPS_C = 1e-3;   // sound-speed weight min(1, k / EPS_C)
 constexpr int BX = 32, BY = 8;
-// Register caps of the float and double-float kernels (MinBlocks below),
-// from a sweep on the 1400x600 triple point: 6 and 4 resident 256-thread
+// Register caps (MinBlocks below), from sweeps on the 1400x600 triple
+// point: the float and double-float kernels at 6 and 4 resident 256-thread
 // blocks per SM (42 and 64 registers) cut the FP32 step by 11 % and the
-// double-float step by 8 % against the compiler's choice, without spills in
-// the step kernels.
+// double-float step by 8 % against the compiler's choice; in native FP64 the
+// material-flux, cell-update, dual-flux and node-update kernels at 4 blocks
+// (64 registers) keep the FP64 pipe fed through their loads (-5 % on the
+// step), without spills in the single-simulation kernels.
 #ifndef LR_MINB_F32
 #define LR_MINB_F32 6
 #endif
 #ifndef LR_DEFAULT_LANES
 #define LR_DEFAULT_LANES 8
+#endif
+#ifndef LR_MINB_D_MATFLUX
+#define LR_MINB_D_MATFLUX 4
+#endif
+#ifndef LR_MINB_D_UPDATE
+#define LR_MINB_D_UPDATE 4
+#endif
+#ifndef LR_MINB_D_DUAL
+#define LR_MINB_D_DUAL 4
+#endif
+#ifndef LR_MINB_D_NODE
+#define LR_MINB_D_NODE 4
 #endif
 #ifndef LR_MINB_DF64
 #define LR_MINB_DF64 4
@@ -1322,8 +1336,11 @@ __device__ __forceinline__ void cell_update_at(const LrGrid& g, const KC<R>& kc,
     ee.add(w.xE[a][fl] - w.xE[a][fr]); ee.add(w.yE[a][fb] - w.yE[a][ft]);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      if (cs[q] == 1) { vv.add(w.cA[a][cn[q]]); mm.add(w.cMm[a][cn[q]]); ee.add(w.cE[a][cn[q]]); }
-      if (cs[q] == -1) { vv.add(-w.cA[a][cn[q]]); mm.add(-w.cMm[a][cn[q]]); ee.add(-w.cE[a][cn[q]]); }
+      // every corner added (zero when it does not involve the cell): one
+      // instruction stream for a warp whatever its cells' corner patterns
+      bool on = cs[q] != 0, ng = cs[q] < 0;
+      R ca = w.cA[a][cn[q]], cm = w.cMm[a][cn[q]], ce = w.cE[a][cn[q]];
+      vv.add(on ? O::flip(ng, ca) : Z); mm.add(on ? O::flip(ng, cm) : Z); ee.add(on ? O::flip(ng, ce) : Z);
     }
     vol[a] = vv.get(); mas[a] = mm.get(); ene[a] = ee.get();
   }
@@ -1465,38 +1482,45 @@ __device__ __forceinline__ void dual_flux_at(const LrGrid& g, const KC<R>& kc, c
                   nodeX(g, w.ddx, i + 1, j + 1));
     R cdy = Q4 * (nodeY(g, w.ddy, i, j) + nodeY(g, w.ddy, i + 1, j) + nodeY(g, w.ddy, i, j + 1) +
                   nodeY(g, w.ddy, i + 1, j + 1));
-    for (int kind = 0; kind < 2; ++kind) {
-      bool pp = kind == 0;
-      R Dm = pp ? Q4 * (p0 + p1 + p2 + p3) : Q4 * (m0 + m1 + m2 + m3);
-      R px = Z, py = Z;
-      if (!O::zero(Dm)) {
-        bool fwd = O::pos(Dm);
-        int ai = i, aj = pp ? j : j + 1, bi = i + 1, bj = pp ? j + 1 : j;
-        int qi = fwd ? ai : bi, qj = fwd ? aj : bj;
-        R vx = nodeX(g, w.ulx, qi, qj), vy = nodeY(g, w.uly, qi, qj);
-        if (g.corner_o2) {
-          int sj = pp ? 1 : -1;
-          R sdy = O::flip(!pp, kc.dy);
-          R dx0 = nodeX(g, w.ddx, qi, qj), dy0 = nodeY(g, w.ddy, qi, qj);
-          R dxp = nodeX(g, w.ddx, qi + 1, qj + sj), dyp = nodeY(g, w.ddy, qi + 1, qj + sj);
-          R dxm = nodeX(g, w.ddx, qi - 1, qj - sj), dym = nodeY(g, w.ddy, qi - 1, qj - sj);
-          // spacings and offset along v, all scaled by |v|^2 = dx^2 + dy^2
-          R hp = (kc.dx + dxp - dx0) * kc.dx + (sdy + dyp - dy0) * sdy;
-          R hm = (kc.dx + dx0 - dxm) * kc.dx + (sdy + dy0 - dym) * sdy;
-          R wxq = kc.dx + H * (nodeX(g, w.ddx, qi + 1, qj) - nodeX(g, w.ddx, qi - 1, qj));
-          R wyq = kc.dy + H * (nodeY(g, w.ddy, qi, qj + 1) - nodeY(g, w.ddy, qi, qj - 1));
-          R wsum = wxq * kc.dx + wyq * kc.dy;
-          R X = O::flip(!fwd, wsum) - (cdx * kc.dx + cdy * sdy);
-          R uxp = nodeX(g, w.ulx, qi + 1, qj + sj), uxm = nodeX(g, w.ulx, qi - 1, qj - sj);
-          R uyp = nodeY(g, w.uly, qi + 1, qj + sj), uym = nodeY(g, w.uly, qi - 1, qj - sj);
-          vx = vx + vl_term(vx - uxm, uxp - vx, hm, hp, X);
-          vy = vy + vl_term(vy - uym, uyp - vy, hm, hp, X);
-        }
-        px = Dm * vx; py = Dm * vy;
+    R D0 = Q4 * (p0 + p1 + p2 + p3), D1 = Q4 * (m0 + m1 + m2 + m3);  // ++ and +- kinds
+    bool on0 = !O::zero(D0), on1 = !O::zero(D1);
+    R px0 = Z, py0 = Z, px1 = Z, py1 = Z;
+    // One reconstruction per pass, the kind a lane data: the first pass
+    // takes each dual corner's first non-zero kind, the second the +- kind
+    // where both are non-zero (rare), so lanes of a warp whose corners flow
+    // along different diagonals share one instruction stream.
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+      if (!(pass == 0 ? (on0 || on1) : (on0 && on1))) continue;
+      bool pp = pass == 0 && on0;
+      R Dm = pp ? D0 : D1;
+      bool fwd = O::pos(Dm);
+      int ai = i, aj = pp ? j : j + 1, bi = i + 1, bj = pp ? j + 1 : j;
+      int qi = fwd ? ai : bi, qj = fwd ? aj : bj;
+      R vx = nodeX(g, w.ulx, qi, qj), vy = nodeY(g, w.uly, qi, qj);
+      if (g.corner_o2) {
+        int sj = pp ? 1 : -1;
+        R sdy = O::flip(!pp, kc.dy);
+        R dx0 = nodeX(g, w.ddx, qi, qj), dy0 = nodeY(g, w.ddy, qi, qj);
+        R dxp = nodeX(g, w.ddx, qi + 1, qj + sj), dyp = nodeY(g, w.ddy, qi + 1, qj + sj);
+        R dxm = nodeX(g, w.ddx, qi - 1, qj - sj), dym = nodeY(g, w.ddy, qi - 1, qj - sj);
+        // spacings and offset along v, all scaled by |v|^2 = dx^2 + dy^2
+        R hp = (kc.dx + dxp - dx0) * kc.dx + (sdy + dyp - dy0) * sdy;
+        R hm = (kc.dx + dx0 - dxm) * kc.dx + (sdy + dy0 - dym) * sdy;
+        R wxq = kc.dx + H * (nodeX(g, w.ddx, qi + 1, qj) - nodeX(g, w.ddx, qi - 1, qj));
+        R wyq = kc.dy + H * (nodeY(g, w.ddy, qi, qj + 1) - nodeY(g, w.ddy, qi, qj - 1));
+        R wsum = wxq * kc.dx + wyq * kc.dy;
+        R X = O::flip(!fwd, wsum) - (cdx * kc.dx + cdy * sdy);
+        R uxp = nodeX(g, w.ulx, qi + 1, qj + sj), uxm = nodeX(g, w.ulx, qi - 1, qj - sj);
+        R uyp = nodeY(g, w.uly, qi + 1, qj + sj), uym = nodeY(g, w.uly, qi - 1, qj - sj);
+        vx = vx + vl_term(vx - uxm, uxp - vx, hm, hp, X);
+        vy = vy + vl_term(vy - uym, uyp - vy, hm, hp, X);
       }
-      if (pp) { w.dPP[0][o] = Dm; w.dPP[1][o] = px; w.dPP[2][o] = py; }
-      else { w.dPM[0][o] = Dm; w.dPM[1][o] = px; w.dPM[2][o] = py; }
+      R px = Dm * vx, py = Dm * vy;
+      if (pp) { px0 = px; py0 = py; } else { px1 = px; py1 = py; }
     }
+    w.dPP[0][o] = D0; w.dPP[1][o] = px0; w.dPP[2][o] = py0;
+    w.dPM[0][o] = D1; w.dPM[1][o] = px1; w.dPM[2][o] = py1;
   }
 }
 
@@ -1954,22 +1978,21 @@ static_assert(sizeof(KC<float>) % 4 == 0 && sizeof(KC<double>) % 8 == 0 && sizeo
               alignof(KC<double>) <= 16 && alignof(KC<df64>) <= 16, "constants copied in words");
 
 // Minimum resident blocks per SM the compiler must allow (register cap):
-// the FP64 kernels are bound by the FP64 pipe and keep the compiler's
-// choice; the float and double-float ones are latency bound and gain from
-// more resident warps.
-template <class R> struct MinBlocks { static constexpr int value = 1; };
-template <> struct MinBlocks<float> { static constexpr int value = LR_MINB_F32; };
-template <> struct MinBlocks<df64> { static constexpr int value = LR_MINB_DF64; };
+// D for the native-double instantiation of a kernel, the float and
+// double-float ones from their own settings.
+template <class R, int D> struct MinBlocks { static constexpr int value = D; };
+template <int D> struct MinBlocks<float, D> { static constexpr int value = LR_MINB_F32; };
+template <int D> struct MinBlocks<df64, D> { static constexpr int value = LR_MINB_DF64; };
 
-#define LR_KERNEL_PAIR(NAME, OP)                                                                          \
+#define LR_KERNEL_PAIR(NAME, OP, MBD)                                                                     \
   template <class R, int M>                                                                               \
-  __global__ void __launch_bounds__(256, MinBlocks<R>::value) lr_##NAME(LrGrid g, KC<R> kc, LrStateT<R> cur, LrStateT<R> nxt,  \
+  __global__ void __launch_bounds__(256, MinBlocks<R, MBD>::value) lr_##NAME(LrGrid g, KC<R> kc, LrStateT<R> cur, LrStateT<R> nxt,  \
                                                    LrWorkT<R> w) {                                        \
     OP::template at<R, M>(g, kc, cur, nxt, w, blockIdx.x * BX + threadIdx.x, blockIdx.y * BY + threadIdx.y, \
                           (unsigned long long)gridDim.x * gridDim.y);                                     \
   }                                                                                                       \
   template <class R, int M>                                                                               \
-  __global__ void __launch_bounds__(256, MinBlocks<R>::value) lb_##NAME(const LrGrid* __restrict__ gs, const KC<R>* __restrict__ kcs, \
+  __global__ void __launch_bounds__(256, MinBlocks<R, MBD>::value) lb_##NAME(const LrGrid* __restrict__ gs, const KC<R>* __restrict__ kcs, \
                                                    const LrTile* __restrict__ tl, int nt, LrStateT<R> cur,   \
                                                    LrStateT<R> nxt, LrWorkT<R> w) {                         \
     __shared__ Staged<R> sd;                                                                              \
@@ -1987,16 +2010,16 @@ template <> struct MinBlocks<df64> { static constexpr int value = LR_MINB_DF64; 
                             T.j0 + (int)threadIdx.y, (unsigned long long)T.n);                            \
     }                                                                                                     \
   }
-LR_KERNEL_PAIR(cell_pre, OpCellPre)
-LR_KERNEL_PAIR(node_half, OpNodeHalf)
-LR_KERNEL_PAIR(cell_lag, OpCellLag)
-LR_KERNEL_PAIR(cell_cf, OpCellCf)
-LR_KERNEL_PAIR(mat_flux, OpMatFlux)
-LR_KERNEL_PAIR(cell_update, OpCellUpdate)
-LR_KERNEL_PAIR(dual_flux, OpDualFlux)
-LR_KERNEL_PAIR(node_update, OpNodeUpdate)
-LR_KERNEL_PAIR(cfl_only, OpCflOnly)
-LR_KERNEL_PAIR(prepare, OpPrepare)
+LR_KERNEL_PAIR(cell_pre, OpCellPre, 1)
+LR_KERNEL_PAIR(node_half, OpNodeHalf, 1)
+LR_KERNEL_PAIR(cell_lag, OpCellLag, 1)
+LR_KERNEL_PAIR(cell_cf, OpCellCf, 1)
+LR_KERNEL_PAIR(mat_flux, OpMatFlux, LR_MINB_D_MATFLUX)
+LR_KERNEL_PAIR(cell_update, OpCellUpdate, LR_MINB_D_UPDATE)
+LR_KERNEL_PAIR(dual_flux, OpDualFlux, LR_MINB_D_DUAL)
+LR_KERNEL_PAIR(node_update, OpNodeUpdate, LR_MINB_D_NODE)
+LR_KERNEL_PAIR(cfl_only, OpCflOnly, 1)
+LR_KERNEL_PAIR(prepare, OpPrepare, 1)
 #undef LR_KERNEL_PAIR
 
 template <class R, int M>
@@ -2243,6 +2266,7 @@ __global__ void lr_arith_k(int op, const double* a, const double* b, double* out
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   if (op == LR_ARITH_DIV) out[t] = RealOps<double>::div(a[t], b[t]);
+  else if (op == LR_ARITH_SQRT) out[t] = RealOps<double>::sqrt(a[t]);
 }
 cudaError_t lr_launch_arith(int op, const double* a, const double* b, double* out, size_t n, cudaStream_t s) {
   if (n == 0) return cudaSuccess;

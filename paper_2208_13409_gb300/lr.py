@@ -29,7 +29,7 @@ FP64, DF64, FP32 = 0, 1, 2
 F_K, F_RHO_MAT, F_E_MAT, F_P, F_RHO, F_E, F_UX, F_UY, F_CONS, F_C = range(10)
 F_UHX, F_UHY, F_VOL_LAGCF, F_E_LAG, F_FX, F_FY, F_FC, F_MX, F_MY, F_MC, F_Q, F_DT = range(20, 32)
 F_CUTS, F_XA, F_YA, F_CA, F_NMIXED = range(32, 37)
-ARITH_DIV = 0
+ARITH_DIV, ARITH_SQRT = 0, 1
 
 
 class LrError(RuntimeError):

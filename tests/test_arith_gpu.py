@@ -94,3 +94,45 @@ def test_zero_numerator_and_quotients_near_underflow():
         ref = a2 / b2
     got2 = _gpu_div(a2, b2)
     assert np.all(np.abs(got2 - ref) <= 4 * 5e-324)
+
+
+def _gpu_sqrt(a: np.ndarray) -> np.ndarray:
+    from paper_2208_13409_gb300 import lr
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ta = torch.from_numpy(a).cuda()
+    out = torch.empty_like(ta)
+    lr.arith_check(lr.ARITH_SQRT, ta, ta, out, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def test_square_roots_correctly_rounded_but_rarely():
+    rng = np.random.default_rng(1340913)
+    n = 1 << 21
+    x = np.abs(_random(rng, n, -1020, 1020))
+    x[: n // 4] = rng.uniform(0.0, 1.0, n // 4) * 10.0 ** rng.integers(-8, 12, n // 4)  # c^2, |u|^2 scales
+    x[n // 4: n // 4 + 1000] = np.arange(1, 1001, dtype=np.float64) ** 2                 # perfect squares
+    ref = np.sqrt(x)
+    got = _gpu_sqrt(x)
+    d = _ulps(got, ref)
+    assert d.max() <= 1.0, d.max()
+    assert np.mean(d == 0) >= 0.9999
+    assert np.array_equal(got[n // 4: n // 4 + 1000], np.arange(1, 1001, dtype=np.float64))
+
+
+def test_square_root_handover_cases():
+    x = np.array([0.0, -0.0, 5e-324, 1e-310, -1.0, np.inf, np.nan, np.ldexp(1.5, 1023),
+                  np.ldexp(1.0, -1022), np.ldexp(1.0, 1022), 2.0, 0.25])
+    with np.errstate(all="ignore"):
+        ref = np.sqrt(x)
+    got = _gpu_sqrt(x)
+    ex = (x.view(np.uint64) >> np.uint64(52)).astype(np.int64)  # sign bit included
+    handled = (ex >= 1) & (ex <= 2045)
+    hb = ~handled
+    assert np.array_equal(np.isnan(got[hb]), np.isnan(ref[hb]))
+    fin = hb & ~np.isnan(ref)
+    assert np.array_equal(got[fin].view(np.int64), ref[fin].view(np.int64))
+    assert _ulps(got[handled], ref[handled]).max() <= 1.0
+    # even powers of two have exact roots
+    assert got[8] == np.ldexp(1.0, -511) and got[9] == np.ldexp(1.0, 511) and got[11] == 0.5
