@@ -130,17 +130,18 @@ def load_peaks():
         return {}
 
 
-# FP64 operations per unit of each kernel, counted on the source for the
-# single-material path with every flux active (kernel table): adds,
-# multiplies, FMAs, divisions and square roots count 1 each.
+# Algorithmic FP64 flops per unit of each kernel, counted on the source for
+# the single-material path with every flux active: an addition, subtraction
+# or multiplication is one flop (a fused multiply-add two), a division or a
+# square root one; comparisons, selects and sign flips none.
 FLOPS_PER_UNIT = {
-    "lr_cell_pre": 79.0,      # per cell
+    "lr_cell_pre": 68.0,      # per cell
     "lr_node_half": 25.0,     # per node
-    "lr_cell_lag": 74.0,      # per node-grid point (one cell, one X face, one Y face)
+    "lr_cell_lag": 73.0,      # per node-grid point (one cell, one X face, one Y face)
     "lr_cell_cf": 14.0,       # per cell
-    "lr_mat_flux": 152.0,     # per node-grid point (one X face, one Y face, one corner)
-    "lr_cell_update": 41.0,   # per cell
-    "lr_dual_flux": 210.0,    # per dual index (dual X face, dual Y face, two dual corners)
+    "lr_mat_flux": 99.0,      # per node-grid point (one X face, one Y face, one corner)
+    "lr_cell_update": 45.0,   # per cell
+    "lr_dual_flux": 178.0,    # per dual index (dual X face, dual Y face, two dual corners)
     "lr_node_update": 38.0,   # per node
 }
 
@@ -153,15 +154,23 @@ def units_per_launch(kernel, nx, ny):
     return (nx + 1) * (ny + 1)
 
 
+def kernel_source_hash():
+    """sha256 prefix of the device code the counters describe: the kernels
+    and the arithmetic and layout headers they include."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("lr_kernels.cu", "lr_real.cuh", "lr_dev.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2208_13409_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def kernel_counters(kernel):
     """DRAM bytes per launch and FP64-pipe activity of `kernel` from the
     committed ncu summary, or (None, None) when the kernel source has changed
     since the counters were taken."""
-    import hashlib
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        src = open(os.path.join(ROOT, "paper_2208_13409_gb300", "csrc", "lr_kernels.cu"), "rb").read()
-        if hashlib.sha256(src).hexdigest()[:16] != rec["kernel_source_sha256_prefix"]:
+        if kernel_source_hash() != rec["kernel_source_sha256_prefix"]:
             return None, None
         k = kernel.split("<")[0]
         return rec["dram_bytes_per_launch"].get(k), rec.get("fp64_pipe_active_pct", {}).get(k)

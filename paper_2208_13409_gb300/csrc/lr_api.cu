@@ -355,27 +355,30 @@ cudaError_t launch_on(lr_ctx* ctx, int k, const LrGrid& g, const LrState& cur, c
 // beside lr_cell_update, joined before lr_node_update.
 cudaError_t launch_one(lr_ctx* ctx, int k, const LrGrid& g, const LrState& cur, const LrState& nxt) {
   cudaError_t e;
+  // profiling mode times every kernel alone: the second stream's kernels
+  // run on the main stream, in the same order
+  cudaStream_t side = ctx->prof ? ctx->stream : ctx->aux;
   if (k == LRK_CELL_LAG && g.M > 1) {
     if ((e = launch_on(ctx, k, g, cur, nxt, ctx->stream)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(ctx->ev_fork, ctx->stream)) != cudaSuccess) return e;
-    if ((e = cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0)) != cudaSuccess) return e;
-    return launch_on(ctx, LRK_MIXED_PLACE, g, cur, nxt, ctx->aux);
+    if ((e = cudaStreamWaitEvent(side, ctx->ev_fork, 0)) != cudaSuccess) return e;
+    return launch_on(ctx, LRK_MIXED_PLACE, g, cur, nxt, side);
   }
   if (k == LRK_MIXED) {
     if (g.M == 1) return cudaSuccess;
     if ((e = cudaEventRecord(ctx->ev_cf, ctx->stream)) != cudaSuccess) return e;
-    if ((e = cudaStreamWaitEvent(ctx->aux, ctx->ev_cf, 0)) != cudaSuccess) return e;
-    if ((e = launch_on(ctx, k, g, cur, nxt, ctx->aux)) != cudaSuccess) return e;
-    return cudaEventRecord(ctx->ev_join, ctx->aux);
+    if ((e = cudaStreamWaitEvent(side, ctx->ev_cf, 0)) != cudaSuccess) return e;
+    if ((e = launch_on(ctx, k, g, cur, nxt, side)) != cudaSuccess) return e;
+    return cudaEventRecord(ctx->ev_join, side);
   }
   if (k == LRK_CELL_UPDATE) {
     if ((e = cudaEventRecord(ctx->ev_mf, ctx->stream)) != cudaSuccess) return e;  // lr_mat_flux done
     if (g.M > 1 && (e = cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0)) != cudaSuccess) return e;
   }
   if (k == LRK_DUAL_FLUX) {
-    if ((e = cudaStreamWaitEvent(ctx->aux, ctx->ev_mf, 0)) != cudaSuccess) return e;
-    if ((e = launch_on(ctx, k, g, cur, nxt, ctx->aux)) != cudaSuccess) return e;
-    return cudaEventRecord(ctx->ev_dual, ctx->aux);
+    if ((e = cudaStreamWaitEvent(side, ctx->ev_mf, 0)) != cudaSuccess) return e;
+    if ((e = launch_on(ctx, k, g, cur, nxt, side)) != cudaSuccess) return e;
+    return cudaEventRecord(ctx->ev_dual, side);
   }
   if (k == LRK_NODE_UPDATE && (e = cudaStreamWaitEvent(ctx->stream, ctx->ev_dual, 0)) != cudaSuccess) return e;
   return launch_on(ctx, k, g, cur, nxt, ctx->stream);

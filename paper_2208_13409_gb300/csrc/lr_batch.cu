@@ -335,6 +335,9 @@ cudaError_t enqueue_step(lr_batch* b, int from) {
   const LrState& cur = b->st[from];
   const LrState& nxt = b->st[1 - from];
   b->launches = 0;
+  // profiling mode times every kernel alone: the second stream's kernels
+  // run on the main stream, in the same order
+  cudaStream_t side = b->prof ? b->stream : b->aux;
   for (int k = 0; k < LRK_COUNT; ++k) {
     LrBatchArgs a = base_args(b);
     bool any_mixed = b->group_members[2] + b->group_members[3] > 0;
@@ -347,9 +350,9 @@ cudaError_t enqueue_step(lr_batch* b, int from) {
       if (e != cudaSuccess) return e;
     }
     if (k == LRK_DUAL_FLUX) {
-      cudaError_t e = cudaStreamWaitEvent(b->aux, b->ev_mf, 0);
+      cudaError_t e = cudaStreamWaitEvent(side, b->ev_mf, 0);
       if (e != cudaSuccess) return e;
-      ks = b->aux;
+      ks = side;
     }
     if (k == LRK_NODE_UPDATE) {
       cudaError_t e = cudaStreamWaitEvent(b->stream, b->ev_dual, 0);
@@ -361,15 +364,15 @@ cudaError_t enqueue_step(lr_batch* b, int from) {
       // before lb_cell_update
       if (!any_mixed) continue;
       cudaError_t e = cudaEventRecord(b->ev_cf, b->stream);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->aux, b->ev_cf, 0);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(side, b->ev_cf, 0);
       if (e != cudaSuccess) return e;
       for (int M = 2; M <= LR_MAXM; ++M) {
         if (b->group_members[M] == 0) continue;
         set_mixed_args(b, M, b->sch.lanes, a);
-        e = launch_timed(b, k, a, cur, nxt, b->aux);
+        e = launch_timed(b, k, a, cur, nxt, side);
         if (e != cudaSuccess) return e;
       }
-      e = cudaEventRecord(b->ev_join, b->aux);
+      e = cudaEventRecord(b->ev_join, side);
       if (e != cudaSuccess) return e;
       continue;
     }
@@ -389,20 +392,20 @@ cudaError_t enqueue_step(lr_batch* b, int from) {
       if (e != cudaSuccess) return e;
     }
     if (k == LRK_DUAL_FLUX) {
-      cudaError_t e = cudaEventRecord(b->ev_dual, b->aux);
+      cudaError_t e = cudaEventRecord(b->ev_dual, side);
       if (e != cudaSuccess) return e;
     }
     if (k == LRK_CELL_LAG && any_mixed) {
       // the interface lines of the mixed cells need the Lagrangian
       // rectangles: placed on the auxiliary stream beside lb_cell_cf
       cudaError_t e = cudaEventRecord(b->ev_fork, b->stream);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->aux, b->ev_fork, 0);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(side, b->ev_fork, 0);
       if (e != cudaSuccess) return e;
       for (int M = 2; M <= LR_MAXM; ++M) {
         if (b->group_members[M] == 0) continue;
         LrBatchArgs pa = base_args(b);
         set_mixed_args(b, M, 8, pa);
-        e = launch_timed(b, LRK_MIXED_PLACE, pa, cur, nxt, b->aux);
+        e = launch_timed(b, LRK_MIXED_PLACE, pa, cur, nxt, side);
         if (e != cudaSuccess) return e;
       }
     }
