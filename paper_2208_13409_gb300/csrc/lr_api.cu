@@ -552,8 +552,7 @@ lr_status lr_init(lr_ctx* ctx, const double* k, const double* rho, const double*
   size_t nc = (size_t)g.nx * g.ny, nn = (size_t)(g.nx + 1) * (g.ny + 1);
   ctx->cur = 0;
   LrState& s = ctx->st[0];
-  double* sk = ctx->w.stage;
-  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  double* sk = ctx->w.stage;  // stream-ordered after any step still in flight
   CK(cudaMemcpyAsync(sk, k, g.M * nc * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload k");
   CK(cudaMemcpyAsync(sk + g.M * nc, rho, g.M * nc * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload rho");
   CK(cudaMemcpyAsync(sk + 2 * g.M * nc, p, g.M * nc * sizeof(double), cudaMemcpyHostToDevice, ctx->stream), "upload p");
@@ -664,9 +663,18 @@ lr_status lr_get_fields(lr_ctx* ctx, int field, double* host_out, size_t n_elems
   size_t need = lr_field_size(ctx, field);
   if (need == 0 || n_elems < need) { setmsg(ctx, "lr_get_fields: field %d needs %zu elements", field, need); return LR_ERR_ARG; }
   if (!ctx->inited) { setmsg(ctx, "lr_get_fields before lr_init"); return LR_ERR_STATE; }
-  lr_status s = field_to_device(ctx, field, ctx->tmp);
-  if (s != LR_OK) return s;
-  CK(cudaMemcpyAsync(host_out, ctx->tmp, need * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "download");
+  // pinned (page-locked, mapped) host memory: the view kernel writes it
+  // directly over the host link, no device staging and no separate copy
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, host_out) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer) {
+    lr_status s = field_to_device(ctx, field, static_cast<double*>(at.devicePointer));
+    if (s != LR_OK) return s;
+  } else {
+    cudaGetLastError();  // a failed query leaves an error state behind: clear it
+    lr_status s = field_to_device(ctx, field, ctx->tmp);
+    if (s != LR_OK) return s;
+    CK(cudaMemcpyAsync(host_out, ctx->tmp, need * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "download");
+  }
   CK(cudaStreamSynchronize(ctx->stream), "sync");
   return LR_OK;
 }
