@@ -136,36 +136,67 @@ __device__ __forceinline__ bool lt(double a, double b) {
   bool zz = ((u | v) << 1) == 0;
   return ord & !zz & (okey(u) < okey(v));
 }
-// n / d by Newton-Raphson refinement of the quotient with fused
-// multiply-add residuals (P. W. Markstein, IBM J. Res. Dev. 34(1), 1990):
-// a float reciprocal r of d's significand, scaled to d's exponent, seeds
-// q = n r, and each step adds e r to q, with e = n - d q from one fused
-// multiply-add.  The seed is within about 2^-22 of 1/d, so two steps leave
-// a relative error near 2^-66 before the last rounding: the result is the
-// correctly rounded quotient unless n/d lies that close to a rounding
-// midpoint (then it is one ulp off).  Five FP64 operations against about
-// seven for the division instruction sequence, which still handles d zero,
-// subnormal, infinite, NaN or of magnitude >= 2^1020.  Other differences
-// from IEEE division: a quotient that overflows, or n infinite, gives NaN
-// rather than an infinity, and -0 / d gives +0.
+// Exact double of a float that is normal or zero, from its bits (integer
+// units; a subnormal float, which the seeds below never produce, reads as 0).
+__device__ __forceinline__ double f2d_exact(float f) {
+  unsigned b = __float_as_uint(f), e8 = (b >> 23) & 0xffu;
+  unsigned hi = e8 ? (b & 0x80000000u) | ((e8 + 896u) << 20) | ((b & 0x7fffffu) >> 3) : (b & 0x80000000u);
+  return __hiloint2double((int)hi, (int)(e8 ? b << 29 : 0u));
+}
+// n / d with three FP64 operations.  The significands of n and d (in [1, 2))
+// are split into float pairs hi + lo (24 + about 24 bits); on the float pipe
+// a reciprocal seed r of d's (rcp.approx) takes one Newton-Raphson step in
+// double-float arithmetic, r (1 + e) with e = 1 - d r from fused
+// multiply-adds (about 2^-44), and the significand quotient q0 = n r (1 + e)
+// is formed as an unevaluated float pair by Dekker's exact product with a
+// fused multiply-add (T. J. Dekker, Numer. Math. 18, 1971).  In FP64: one
+// exact addition joins the pair, the exponents are applied on the integer
+// units, and one Markstein correction q0 + (n - d q0) r with its residual
+// from a fused multiply-add (P. W. Markstein, IBM J. Res. Dev. 34(1), 1990)
+// takes the relative error to about 2^-66 before the last rounding: the
+// result is the correctly rounded quotient unless n/d lies that close to a
+// rounding midpoint (then it is one ulp off).  About seven FP64 operations
+// for the division instruction sequence, which still handles d zero,
+// subnormal, infinite, NaN or of magnitude >= 2^1020, n subnormal, infinite
+// or NaN, and quotients outside the normal range; n = +-0 gives the IEEE
+// signed zero.
 __device__ __forceinline__ double ddiv(double n, double d) {
+  unsigned hn = (unsigned)__double2hiint(n), ln = (unsigned)__double2loint(n);
   unsigned hd = (unsigned)__double2hiint(d), ld = (unsigned)__double2loint(d);
-  unsigned ed = (hd >> 20) & 0x7ffu;
-  if (ed - 1u >= 2043u) return n / d;
-  // |d|'s significand in [1, 2) to float precision (truncated), its reciprocal
-  float m = __uint_as_float(0x3f800000u | ((hd & 0xfffffu) << 3) | (ld >> 29));
-  float rf;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(m));
-  // r = sign(d) rf 2^(1023 - ed): rf's exponent field fe (126 or 127) gives
-  // r's as fe - 127 + 2046 - ed, within [2, 2045] for ed in [1, 2043]
-  unsigned fb = __float_as_uint(rf);
+  unsigned en = (hn >> 20) & 0x7ffu, ed = (hd >> 20) & 0x7ffu;
+  if (ed - 1u >= 2043u || en - 1u >= 2046u) {
+    if (en == 0u && ((hn << 1) | ln) == 0u && ed - 1u < 2043u)
+      return __hiloint2double((int)((hn ^ hd) & 0x80000000u), 0);
+    return n / d;
+  }
+  // significands: hi = the top 23 fraction bits (exact), lo = the other 29
+  // (rounded to float)
+  float nh = __uint_as_float(0x3f800000u | ((hn & 0xfffffu) << 3) | (ln >> 29));
+  float nl = __uint2float_rn(ln & 0x1fffffffu) * 0x1p-52f;
+  float dh = __uint_as_float(0x3f800000u | ((hd & 0xfffffu) << 3) | (ld >> 29));
+  float dl = __uint2float_rn(ld & 0x1fffffffu) * 0x1p-52f;
+  float r0;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(dh));  // in (0.5, 1]
+  float e = __fmaf_rn(-dh, r0, 1.0f);
+  e = __fmaf_rn(-dl, r0, e);
+  float c = __fmul_rn(r0, e);             // 1/(dh + dl) = r0 + c to about 2^-44
+  float p = __fmul_rn(nh, r0);
+  float pe = __fmaf_rn(nh, r0, -p);       // nh r0 = p + pe exactly
+  pe = __fmaf_rn(nh, c, pe);
+  pe = __fmaf_rn(nl, r0, pe);
+  double q0 = f2d_exact(p) + f2d_exact(pe);  // exact: the pair fits in 53 bits; q0 in (0.25, 2)
+  // q = sign q0 2^(en - ed)
+  unsigned hq = (unsigned)__double2hiint(q0);
+  int fq = (int)((hq >> 20) & 0x7ffu) + (int)en - (int)ed;
+  if (fq < 1 || fq > 2046) return n / d;
+  hq = ((hn ^ hd) & 0x80000000u) | ((unsigned)fq << 20) | (hq & 0xfffffu);
+  double q = __hiloint2double((int)hq, __double2loint(q0));
+  // r = sign(d) r0 2^(1023 - ed): r0's exponent field (126 or 127) gives r's
+  // as fe - 127 + 2046 - ed, within [2, 2045] for ed in [1, 2043]
+  unsigned fb = __float_as_uint(r0);
   unsigned hr = (hd & 0x80000000u) | (((fb >> 23) + 1919u - ed) << 20) | ((fb & 0x7fffffu) >> 3);
   double r = __hiloint2double((int)hr, (int)(fb << 29));
-  double q = n * r;
-  double e = fma(-d, q, n);
-  q = fma(e, r, q);
-  e = fma(-d, q, n);
-  return fma(e, r, q);
+  return fma(fma(-d, q, n), r, q);
 }
 // sqrt(x) by the same refinement with a reciprocal-square-root seed: y, a
 // float approximation of 1/sqrt(x) (from x's significand, with the
