@@ -198,13 +198,15 @@ __device__ __forceinline__ double ddiv(double n, double d) {
   double r = __hiloint2double((int)hr, (int)(fb << 29));
   return fma(fma(-d, q, n), r, q);
 }
-// sqrt(x) by the same refinement with a reciprocal-square-root seed: y, a
-// float approximation of 1/sqrt(x) (from x's significand, with the
-// exponent's parity folded in), gives s = x y and h = y/2; each step adds
-// (x - s s) h to s, the residual from one fused multiply-add.  The seed is
-// within about 2^-22, one step leaves about 2^-43 and the second about
-// 2^-66 before the last rounding (correctly rounded but near midpoints).
-// Five FP64 operations against about seven and a half for the square-root
+// sqrt(x) with three FP64 operations, the same way: x = m 4^k with m in
+// [1, 4) split into a float pair; on the float pipe a reciprocal-square-root
+// seed y of m's high part (rsqrt.approx) gives s = m y, and one Newton step
+// s + (m - s s) y/2, residual by a fused multiply-add, leaves sqrt(m) as an
+// unevaluated float pair to about 2^-44.  In FP64: one exact addition joins
+// the pair, 2^k is applied on the integer units, and one correction
+// s + (x - s s) y/2 (residual from a fused multiply-add) takes the error to
+// about 2^-66 before the last rounding (correctly rounded but near
+// midpoints).  About seven and a half FP64 operations for the square-root
 // instruction sequence, which still handles x zero, subnormal, negative,
 // infinite, NaN or in the top binade.
 __device__ __forceinline__ double dsqrt(double x) {
@@ -214,19 +216,23 @@ __device__ __forceinline__ double dsqrt(double x) {
   // x = m 2^e, m in [1, 2); e = 2k + p, p in {0, 1}: x = (m 2^p) 4^k
   int e = (int)ex - 1023;
   int p = e & 1, k = (e - p) / 2;
-  float mf = __uint_as_float(((127u + (unsigned)p) << 23) | ((hx & 0xfffffu) << 3) | (lx >> 29));
+  float mh = __uint_as_float(((127u + (unsigned)p) << 23) | ((hx & 0xfffffu) << 3) | (lx >> 29));
+  float ml = __uint2float_rn(lx & 0x1fffffffu) * (p ? 0x1p-51f : 0x1p-52f);
   float yf;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(mf));  // in (0.5, 1]
-  // y = yf 2^-k: exponent field (fe - 127) - k + 1023, within [511, 1534]
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(mh));  // in (0.5, 1]
+  float sh = __fmul_rn(mh, yf);
+  float t = __fmaf_rn(-sh, sh, mh);        // mh - sh^2, the square exact inside the fma
+  float sl = __fmul_rn(__fadd_rn(t, ml), __fmul_rn(0.5f, yf));
+  double s = f2d_exact(sh) + f2d_exact(sl);  // exact; sqrt(m) to about 2^-44, in [1, 2)
+  // s 2^k: s's exponent field (1023, or 1024 if it rounded up to 2) + k
+  unsigned hs = (unsigned)__double2hiint(s);
+  hs = (((hs >> 20) + (unsigned)k) << 20) | (hs & 0xfffffu);
+  s = __hiloint2double((int)hs, __double2loint(s));
+  // h = yf 2^(-k-1) = y/2: exponent field (fe - 127) - k - 1 + 1023, within [510, 1533]
   unsigned fb = __float_as_uint(yf);
-  unsigned hy = ((unsigned)((int)(fb >> 23) - 127 - k + 1023) << 20) | ((fb & 0x7fffffu) >> 3);
-  double y = __hiloint2double((int)hy, (int)(fb << 29));
-  double h = __hiloint2double((int)(hy - (1u << 20)), (int)(fb << 29));  // y / 2
-  double s = x * y;
-  double r = fma(-s, s, x);
-  s = fma(r, h, s);
-  r = fma(-s, s, x);
-  return fma(r, h, s);
+  unsigned hh = ((unsigned)((int)(fb >> 23) - 127 - k - 1 + 1023) << 20) | ((fb & 0x7fffffu) >> 3);
+  double h = __hiloint2double((int)hh, (int)(fb << 29));
+  return fma(fma(-s, s, x), h, s);
 }
 }  // namespace dbits
 
