@@ -253,16 +253,19 @@ lr_status lr_cfl_dt_noalloc(const lr_config* cfg, const lr_material* mats, const
 /* Arithmetic check: out[i] = a[i] op b[i], i < n, computed on the device by
  * the routine the FP64 step kernels use for that operation, so that a test
  * can compare it with IEEE 754 arithmetic.
- *   op LR_ARITH_DIV: the quotient a/b by Newton-Raphson refinement with
- *      fused multiply-add residuals (P. W. Markstein, IBM J. Res. Dev. 34(1),
- *      1990) from a float reciprocal seed; correctly rounded except within
- *      about 2^-66 (relative) of a rounding midpoint, where it is one ulp
- *      off; b zero, subnormal, infinite, NaN or |b| >= 2^1020 take IEEE
- *      division.  The FP64 step uses it for every division except the
- *      reciprocals 1/x, which stay IEEE.
- *   op LR_ARITH_SQRT: sqrt(a) (b unused, may equal a) by the same refinement
- *      from a float reciprocal-square-root seed, correctly rounded except
- *      near midpoints as above; a zero, subnormal, negative, infinite, NaN or
+ *   op LR_ARITH_DIV: the quotient a/b: the significand quotient to about
+ *      2^-44 as a float pair (a float reciprocal seed, one Newton-Raphson
+ *      step in double-float arithmetic, Dekker's exact product), then one
+ *      Markstein correction with a fused multiply-add residual in double
+ *      (P. W. Markstein, IBM J. Res. Dev. 34(1), 1990); correctly rounded
+ *      except within about 2^-66 (relative) of a rounding midpoint, where it
+ *      is one ulp off; a = +-0 gives the signed zero; b zero, subnormal,
+ *      infinite, NaN or |b| >= 2^1020, a subnormal, infinite or NaN, and
+ *      quotients outside the normal range take IEEE division.  The FP64 step
+ *      uses it for every division and reciprocal.
+ *   op LR_ARITH_SQRT: sqrt(a) (b unused, may equal a) the same way from a
+ *      float reciprocal-square-root seed, correctly rounded except near
+ *      midpoints as above; a zero, subnormal, negative, infinite, NaN or
  *      >= 2^1023 takes the IEEE square root.
  * a, b, out: device pointers to n doubles (out may alias a or b).
  * cuda_stream: cudaStream_t, NULL = the legacy default stream; the work is

@@ -243,7 +243,7 @@ template <> struct RealOps<double> {
   __device__ static __forceinline__ double abs(double x) { return dbits::absb(x); }
   __device__ static __forceinline__ double flip(bool f, double x) { return dbits::flip(f, x); }
   __device__ static __forceinline__ double sqrt(double x) { return dbits::dsqrt(x); }
-  __device__ static __forceinline__ double rcp(double x) { return 1.0 / x; }
+  __device__ static __forceinline__ double rcp(double x) { return dbits::ddiv(1.0, x); }
   __device__ static __forceinline__ double div(double a, double b) { return dbits::ddiv(a, b); }
   __device__ static __forceinline__ bool finite(double x) { return dbits::finite(x); }
   __device__ static __forceinline__ bool pos(double x) { return dbits::pos(x); }
