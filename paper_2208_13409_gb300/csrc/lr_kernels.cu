@@ -151,6 +151,16 @@ template <class R> __device__ __forceinline__ R cellOY(const LrGrid& g, const R*
   return RealOps<R>::flip(q.fy, a[q.idx]);
 }
 
+// Table entry a (< M) of a per-material array table, by selects rather than
+// an indexed read of the kernel parameter.
+template <int M, class T>
+__device__ __forceinline__ T* pick(T* const* arr, int a) {
+  T* p = arr[0];
+  if (M > 1 && a == 1) p = arr[1];
+  if (M > 2 && a == 2) p = arr[2];
+  return p;
+}
+
 __device__ __forceinline__ void set_err(int* err, int bit, int idx) {
   atomicOr(&err[0], bit);
   atomicCAS(&err[1], -1, idx);
@@ -959,45 +969,53 @@ __device__ __forceinline__ bool pure_in(const LrGrid& g, const unsigned char* ma
   return mask[cix(g, i, j).idx] == bit;
 }
 
-// Face value (section 2.1.1): a_d + slope/2 (sgn(dVol) wx_d - dt u_f).
+// Face values (section 2.1.1) a_d + slope/2 (sgn(dVol) wx_d - dt u_f) of two
+// cell quantities q1, q2 of donor (di, dj) along x (xdir) or y, sharing the
+// geometry: centre offsets ox (the x or y ones), width wx along the direction.
 template <class R>
-__device__ __forceinline__ R recon_face(const LrGrid& g, const KC<R>& kc, const R* q, const R* ox, const R* wx,
-                                       int di, int dj, bool fwd, R fdisp, bool xdir) {
+__device__ __forceinline__ void recon_face2(const LrGrid& g, const KC<R>& kc, const R* q1, const R* q2,
+                                            const R* ox, const R* wx, int di, int dj, bool fwd, R fdisp,
+                                            bool xdir, R& v1, R& v2) {
   using O = RealOps<R>;
+  int mi = xdir ? 1 : 0, mj = 1 - mi;
   int c = cix(g, di, dj).idx;
-  R a0 = q[c];
-  R am, ap, om, op;
-  if (xdir) {
-    am = cellS(g, q, di - 1, dj); ap = cellS(g, q, di + 1, dj);
-    om = cellOX(g, ox, di - 1, dj); op = cellOX(g, ox, di + 1, dj);
-  } else {
-    am = cellS(g, q, di, dj - 1); ap = cellS(g, q, di, dj + 1);
-    om = cellOY(g, ox, di, dj - 1); op = cellOY(g, ox, di, dj + 1);
-  }
+  Ix cm = cix(g, di - mi, dj - mj), cp = cix(g, di + mi, dj + mj);
   R o0 = ox[c];
+  R om = O::flip(xdir ? cm.fx : cm.fy, ox[cm.idx]), op = O::flip(xdir ? cp.fx : cp.fy, ox[cp.idx]);
   R h = xdir ? kc.dx : kc.dy;
-  return a0 + vl_term(a0 - am, ap - a0, h + o0 - om, h + op - o0, O::flip(!fwd, wx[c]) - fdisp);
+  R hm = h + o0 - om, hp = h + op - o0;
+  R X = O::flip(!fwd, wx[c]) - fdisp;
+  R a0 = q1[c];
+  v1 = a0 + vl_term(a0 - q1[cm.idx], q1[cp.idx] - a0, hm, hp, X);
+  R b0 = q2[c];
+  v2 = b0 + vl_term(b0 - q2[cm.idx], q2[cp.idx] - b0, hm, hp, X);
 }
 // Corner value, diagonal limited reconstruction (section 3.3): along v (or
 // v_perp when dx dy < 0), slope over the diagonal neighbours' Lagrangian
 // centres, evaluated at 1/2 (sgn(dx) (wx, +-wy) - (dx, dy)) . v from the
 // donor's centre.
+// Two cell quantities q1, q2 at once, sharing the geometry.
 template <class R>
-__device__ __forceinline__ R recon_corner(const LrGrid& g, const KC<R>& kc, const R* q, const LrWorkT<R>& w,
-                                         int di, int dj, R ddx, R ddy, int sj) {
+__device__ __forceinline__ void recon_corner2(const LrGrid& g, const KC<R>& kc, const R* q1, const R* q2,
+                                              const LrWorkT<R>& w, int di, int dj, R ddx, R ddy, int sj, R& v1,
+                                              R& v2) {
   using O = RealOps<R>;
   int c = cix(g, di, dj).idx;
-  R a0 = q[c], ox0 = w.ox[c], oy0 = w.oy[c];
-  R ap = cellS(g, q, di + 1, dj + sj), am = cellS(g, q, di - 1, dj - sj);
-  R oxp = cellOX(g, w.ox, di + 1, dj + sj), oyp = cellOY(g, w.oy, di + 1, dj + sj);
-  R oxm = cellOX(g, w.ox, di - 1, dj - sj), oym = cellOY(g, w.oy, di - 1, dj - sj);
+  Ix cp = cix(g, di + 1, dj + sj), cm = cix(g, di - 1, dj - sj);
+  R ox0 = w.ox[c], oy0 = w.oy[c];
+  R oxp = O::flip(cp.fx, w.ox[cp.idx]), oyp = O::flip(cp.fy, w.oy[cp.idx]);
+  R oxm = O::flip(cm.fx, w.ox[cm.idx]), oym = O::flip(cm.fy, w.oy[cm.idx]);
   R sdy = O::flip(sj < 0, kc.dy);
   // spacings and offset along v, all scaled by |v|^2 = dx^2 + dy^2
   R hp = (kc.dx + oxp - ox0) * kc.dx + (sdy + oyp - oy0) * sdy;
   R hm = (kc.dx + ox0 - oxm) * kc.dx + (sdy + oy0 - oym) * sdy;
   R wsum = w.wx[c] * kc.dx + w.wy[c] * kc.dy;
   R dsum = ddx * kc.dx + ddy * sdy;
-  return a0 + vl_term(a0 - am, ap - a0, hm, hp, O::flip(!O::pos(ddx), wsum) - dsum);
+  R X = O::flip(!O::pos(ddx), wsum) - dsum;
+  R a0 = q1[c];
+  v1 = a0 + vl_term(a0 - q1[cm.idx], q1[cp.idx] - a0, hm, hp, X);
+  R b0 = q2[c];
+  v2 = b0 + vl_term(b0 - q2[cm.idx], q2[cp.idx] - b0, hm, hp, X);
 }
 
 // Van Leer limited slopes of q in cell (di,dj): along x or y over the
@@ -1111,114 +1129,74 @@ __device__ __forceinline__ void mat_flux_at(const LrGrid& g, const KC<R>& kc, co
   using O = RealOps<R>;
   if (i >= g.nxu || j >= g.nyu) return;
   if (!step_live(g, w.scal)) return;
-  const R Z = O::c(0.0f), H = O::c(0.5f), ONE = O::c(1.0f);
+  const R Z = O::c(0.0f), H = O::c(0.5f);
   int nn = g.nx + 1, nb = g.noff;
   int j1 = (g.pery && j + 1 == g.ny) ? 0 : j + 1;
   int i1 = (g.perx && i + 1 == g.nx) ? 0 : i + 1;
-  // ---- X face (i, j)
-  if (j < g.ny) {
-    int f = nb + j * nn + i;
-    R v = w.fx[f];
-    R mt = Z;
+  // ---- X face (i, j) and Y face (i, j): one code path, the direction a
+  // runtime value (the kernel stays small enough for the instruction cache)
+#pragma unroll 1
+  for (int xf = 1; xf >= 0; --xf) {
+    if (xf ? j >= g.ny : i >= g.nx) continue;
+    int f = xf ? nb + j * nn + i : nb + j * g.nx + i;
+    R v = (xf ? w.fx : w.fy)[f];
     unsigned dm = 0u;
-    int di = 0, dc = 0;
-    bool left = O::pos(v);
+    int dc = 0;
+    bool fwd = O::pos(v);
+    int di = xf ? (fwd ? i - 1 : i) : i, dj = xf ? j : (fwd ? j - 1 : j);
     R fd = Z;
     if (!O::zero(v)) {
-      di = left ? i - 1 : i;
-      dc = cix(g, di, j).idx;
+      dc = cix(g, di, dj).idx;
       dm = w.mask[dc];
-      fd = H * (w.ddx[nb + j * nn + i] + w.ddx[nb + j1 * nn + i]);
+      const R* dd = xf ? w.ddx : w.ddy;
+      fd = H * (dd[nb + j * nn + i] + dd[xf ? nb + j1 * nn + i : nb + j * nn + i1]);
     }
-    bool mixed = (dm & (dm - 1u)) != 0u;
-    if (!mixed) {  // a mixed donor's objects are finished by lr_mixed
-#pragma unroll
-    for (int a = 0; a < M; ++a) {
-      unsigned bit = 1u << a;
-      if (!(dm & bit)) { w.xA[a][f] = Z; w.xMm[a][f] = Z; w.xE[a][f] = Z; continue; }
-      R Aa = mixed ? w.xAm[a][f] : O::abs(v);
-      R Ma = Z, Ea = Z;
-      if (!mixed || O::pos(Aa)) {
-        R rf = w.rcf[a][dc], ef = w.elag[a][dc];
-        if (VAR && !mixed && g.face_o2 && g.corner_kind == LR_CORNER_LSQ) {
-          if (pure_stencil(g, w.mask, di, j, bit)) {
+    if (dm & (dm - 1u)) continue;  // a mixed donor's objects are finished by lr_mixed
+    // a pure donor holds one material (none for a zero flux)
+    int as = dm ? __ffs(dm) - 1 : -1;
+    R Aa = O::abs(v), Ma = Z, Ea = Z;
+    if (as >= 0) {
+      unsigned bit = 1u << as;
+      const R* rq = pick<M>(w.rcf, as);
+      const R* eq = pick<M>(w.elag, as);
+      R rf = rq[dc], ef = eq[dc];
+      if (VAR && g.face_o2 && g.corner_kind == LR_CORNER_LSQ) {
+        if (pure_stencil(g, w.mask, di, dj, bit)) {
+          R px, py;
+          if (xf) {
             R xb = w.fxb[f];
-            R r0 = left ? kc.dx : xb, r1 = left ? kc.dx + xb : Z;
-            R px = H * (r0 + r1), py = H * (w.fxlo[f] + w.fxhi[f]);
-            rf = recon_lsq(g, kc, w.rcf[a], w, di, j, px, py);
-            ef = recon_lsq(g, kc, w.elag[a], w, di, j, px, py);
+            R r0 = fwd ? kc.dx : xb, r1 = fwd ? kc.dx + xb : Z;
+            px = H * (r0 + r1); py = H * (w.fxlo[f] + w.fxhi[f]);
+          } else {
+            R yb = w.fyb[f];
+            R r2 = fwd ? kc.dy : yb, r3 = fwd ? kc.dy + yb : Z;
+            px = H * (w.fylo[f] + w.fyhi[f]); py = H * (r2 + r3);
           }
-        } else if (!mixed && g.face_o2 && pure_in(g, w.mask, di - 1, j, bit) && pure_in(g, w.mask, di + 1, j, bit)) {
-          rf = recon_face(g, kc, w.rcf[a], w.ox, w.wx, di, j, left, fd, true);
-          ef = recon_face(g, kc, w.elag[a], w.ox, w.wx, di, j, left, fd, true);
+          rf = recon_lsq(g, kc, rq, w, di, dj, px, py);
+          ef = recon_lsq(g, kc, eq, w, di, dj, px, py);
         }
-        Ma = O::mul(rf, Aa);
-        Ea = O::mul(Ma, ef);
-      } else {
-        Aa = Z;
+      } else if (g.face_o2 && pure_in(g, w.mask, di - xf, dj - (1 - xf), bit) &&
+                 pure_in(g, w.mask, di + xf, dj + (1 - xf), bit)) {
+        recon_face2(g, kc, rq, eq, xf ? w.ox : w.oy, xf ? w.wx : w.wy, di, dj, fwd, fd, xf != 0, rf, ef);
       }
-      R sMa = O::flip(!left, Ma);
-      w.xA[a][f] = O::flip(!left, Aa); w.xMm[a][f] = sMa; w.xE[a][f] = O::flip(!left, Ea);
-      mt = O::add(mt, sMa);
+      Ma = O::mul(rf, Aa);
+      Ea = O::mul(Ma, ef);
     }
-    w.MX[f] = mt;
-    }
-  }
-  // ---- Y face (i, j)
-  if (i < g.nx) {
-    int f = nb + j * g.nx + i;
-    R v = w.fy[f];
-    R mt = Z;
-    unsigned dm = 0u;
-    int dj = 0, dc = 0;
-    bool below = O::pos(v);
-    R fd = Z;
-    if (!O::zero(v)) {
-      dj = below ? j - 1 : j;
-      dc = cix(g, i, dj).idx;
-      dm = w.mask[dc];
-      fd = H * (w.ddy[nb + j * nn + i] + w.ddy[nb + j * nn + i1]);
-    }
-    bool mixed = (dm & (dm - 1u)) != 0u;
-    if (!mixed) {
+    R sA = O::flip(!fwd, Aa), sM = O::flip(!fwd, Ma), sE = O::flip(!fwd, Ea);
 #pragma unroll
     for (int a = 0; a < M; ++a) {
-      unsigned bit = 1u << a;
-      if (!(dm & bit)) { w.yA[a][f] = Z; w.yMm[a][f] = Z; w.yE[a][f] = Z; continue; }
-      R Aa = mixed ? w.yAm[a][f] : O::abs(v);
-      R Ma = Z, Ea = Z;
-      if (!mixed || O::pos(Aa)) {
-        R rf = w.rcf[a][dc], ef = w.elag[a][dc];
-        if (VAR && !mixed && g.face_o2 && g.corner_kind == LR_CORNER_LSQ) {
-          if (pure_stencil(g, w.mask, i, dj, bit)) {
-            R yb = w.fyb[f];
-            R r2 = below ? kc.dy : yb, r3 = below ? kc.dy + yb : Z;
-            R px = H * (w.fylo[f] + w.fyhi[f]), py = H * (r2 + r3);
-            rf = recon_lsq(g, kc, w.rcf[a], w, i, dj, px, py);
-            ef = recon_lsq(g, kc, w.elag[a], w, i, dj, px, py);
-          }
-        } else if (!mixed && g.face_o2 && pure_in(g, w.mask, i, dj - 1, bit) && pure_in(g, w.mask, i, dj + 1, bit)) {
-          rf = recon_face(g, kc, w.rcf[a], w.oy, w.wy, i, dj, below, fd, false);
-          ef = recon_face(g, kc, w.elag[a], w.oy, w.wy, i, dj, below, fd, false);
-        }
-        Ma = O::mul(rf, Aa);
-        Ea = O::mul(Ma, ef);
-      } else {
-        Aa = Z;
-      }
-      R sMa = O::flip(!below, Ma);
-      w.yA[a][f] = O::flip(!below, Aa); w.yMm[a][f] = sMa; w.yE[a][f] = O::flip(!below, Ea);
-      mt = O::add(mt, sMa);
+      bool on = a == as;
+      (xf ? w.xA[a] : w.yA[a])[f] = on ? sA : Z;
+      (xf ? w.xMm[a] : w.yMm[a])[f] = on ? sM : Z;
+      (xf ? w.xE[a] : w.yE[a])[f] = on ? sE : Z;
     }
-    w.MY[f] = mt;
-    }
+    (xf ? w.MX : w.MY)[f] = as >= 0 ? O::add(Z, sM) : Z;
   }
   // ---- corner at node (i, j)
   {
     int n = nb + j * nn + i;
     R ddx = w.ddx[n], ddy = w.ddy[n];
-    R mt = Z;
-    int di = 0, dj = 0, ri, rj, dc = 0, sj = 1;
+    int di = 0, dj = 0, ri = 0, rj = 0, dc = 0, sj = 1;
     unsigned dm = 0u;
     R fv = Z;
     bool pp = false;
@@ -1229,50 +1207,49 @@ __device__ __forceinline__ void mat_flux_at(const LrGrid& g, const KC<R>& kc, co
       pp = O::pos(ddx) == O::pos(ddy);
       sj = pp ? 1 : -1;
     }
-    bool mixed = (dm & (dm - 1u)) != 0u;
-    if (!mixed) {
-#pragma unroll
-    for (int a = 0; a < M; ++a) {
-      unsigned bit = 1u << a;
-      if (!(dm & bit)) { w.cA[a][n] = Z; w.cMm[a][n] = Z; w.cE[a][n] = Z; continue; }
-      R Aa = mixed ? w.cAm[a][n] : fv;
-      R Ma = Z, Ea = Z;
-      if (!mixed || O::pos(Aa)) {
-        R rf = w.rcf[a][dc], ef = w.elag[a][dc];
-        int ck = mixed ? LR_CORNER_UPWIND : g.corner_kind;
+    if (!(dm & (dm - 1u))) {  // a mixed donor's corner is finished by lr_mixed
+      int as = dm ? __ffs(dm) - 1 : -1;
+      R Aa = Z, Ma = Z, Ea = Z;
+      if (as >= 0) {
+        Aa = fv;
+        unsigned bit = 1u << as;
+        const R* rq = pick<M>(w.rcf, as);
+        const R* eq = pick<M>(w.elag, as);
+        R rf = rq[dc], ef = eq[dc];
+        int ck = g.corner_kind;
         if (ck == LR_CORNER_DIAG && pure_in(g, w.mask, di - 1, dj - sj, bit) &&
             pure_in(g, w.mask, di + 1, dj + sj, bit)) {
-          rf = recon_corner(g, kc, w.rcf[a], w, di, dj, ddx, ddy, sj);
-          ef = recon_corner(g, kc, w.elag[a], w, di, dj, ddx, ddy, sj);
+          recon_corner2(g, kc, rq, eq, w, di, dj, ddx, ddy, sj, rf, ef);
         } else if (VAR && ck == LR_CORNER_AVG && pure_in(g, w.mask, ri, rj, bit)) {
           // 1/2 (donor + receiver), clamped to the donor value (section 3.3)
           int rc = cix(g, ri, rj).idx;
-          R ra = H * (w.rcf[a][dc] + w.rcf[a][rc]), ea = H * (w.elag[a][dc] + w.elag[a][rc]);
+          R ra = H * (rq[dc] + rq[rc]), ea = H * (eq[dc] + eq[rc]);
           rf = rmin(ra, rf);
           ef = rmin(ea, ef);
-        } else if (VAR && ck == LR_CORNER_XY && pure_in(g, w.mask, di - 1, dj, bit) && pure_in(g, w.mask, di + 1, dj, bit) &&
-                   pure_in(g, w.mask, di, dj - 1, bit) && pure_in(g, w.mask, di, dj + 1, bit)) {
-          rf = recon_corner_xy(g, kc, w.rcf[a], w, di, dj, ddx, ddy);
-          ef = recon_corner_xy(g, kc, w.elag[a], w, di, dj, ddx, ddy);
+        } else if (VAR && ck == LR_CORNER_XY && pure_in(g, w.mask, di - 1, dj, bit) &&
+                   pure_in(g, w.mask, di + 1, dj, bit) && pure_in(g, w.mask, di, dj - 1, bit) &&
+                   pure_in(g, w.mask, di, dj + 1, bit)) {
+          rf = recon_corner_xy(g, kc, rq, w, di, dj, ddx, ddy);
+          ef = recon_corner_xy(g, kc, eq, w, di, dj, ddx, ddy);
         } else if (VAR && ck == LR_CORNER_LSQ && pure_stencil(g, w.mask, di, dj, bit)) {
           R nxp = O::pos(ddx) ? kc.dx : Z, nyp = O::pos(ddy) ? kc.dy : Z;
           R r0 = O::pos(ddx) ? nxp : nxp + ddx, r1 = O::pos(ddx) ? nxp + ddx : nxp;
           R r2 = O::pos(ddy) ? nyp : nyp + ddy, r3 = O::pos(ddy) ? nyp + ddy : nyp;
           R px = H * (r0 + r1), py = H * (r2 + r3);
-          rf = recon_lsq(g, kc, w.rcf[a], w, di, dj, px, py);
-          ef = recon_lsq(g, kc, w.elag[a], w, di, dj, px, py);
+          rf = recon_lsq(g, kc, rq, w, di, dj, px, py);
+          ef = recon_lsq(g, kc, eq, w, di, dj, px, py);
         }
         Ma = O::mul(rf, Aa);
         Ea = O::mul(Ma, ef);
-      } else {
-        Aa = Z;
       }
-      w.cA[a][n] = Aa; w.cMm[a][n] = Ma; w.cE[a][n] = Ea;
-      mt = O::add(mt, Ma);
-    }
-    R sgm = O::flip(!O::pos(ddx), mt);  // signed along +x
-    w.Mpp[n] = (dm && pp) ? sgm : Z;
-    w.Mpm[n] = (dm && !pp) ? sgm : Z;
+#pragma unroll
+      for (int a = 0; a < M; ++a) {
+        bool on = a == as;
+        w.cA[a][n] = on ? Aa : Z; w.cMm[a][n] = on ? Ma : Z; w.cE[a][n] = on ? Ea : Z;
+      }
+      R sgm = O::flip(!O::pos(ddx), as >= 0 ? O::add(Z, Ma) : Z);  // signed along +x
+      w.Mpp[n] = (dm && pp) ? sgm : Z;
+      w.Mpm[n] = (dm && !pp) ? sgm : Z;
     }
   }
 }
@@ -1393,21 +1370,28 @@ __device__ __forceinline__ void cell_update_at(const LrGrid& g, const KC<R>& kc,
   w.cc[c] = cmax;
 }
 
-// Dual reconstruction of a node velocity component along x or y: the
-// primary formula with nodes as centres (Lagrangian positions x + d, dual
-// width dx + (d_{q+1} - d_{q-1})/2, face displacement fdisp).
+// Dual reconstruction of the node velocity u^{lag} (both components) along
+// x (xdir) or y at upwind node (qi, qj): the primary formula with nodes as
+// centres (Lagrangian positions x + d, dual width dx + (d_{q+1} - d_{q-1})/2,
+// face displacement fdisp); the geometry is shared by the two components.
 template <class R>
-__device__ __forceinline__ R recon_dual_face(const LrGrid& g, const KC<R>& kc, const R* u, bool ucomp_x,
-                                            const R* dd, int qi, int qj, bool xdir, bool fwd, R fdisp) {
+__device__ __forceinline__ void recon_dual_face2(const LrGrid& g, const KC<R>& kc, const LrWorkT<R>& w, int qi,
+                                                 int qj, bool xdir, bool fwd, R fdisp, R& vx, R& vy) {
   using O = RealOps<R>;
-  auto U = [&](int a, int b) { return ucomp_x ? nodeX(g, u, a, b) : nodeY(g, u, a, b); };
-  auto Dd = [&](int a, int b) { return xdir ? nodeX(g, dd, a, b) : nodeY(g, dd, a, b); };
-  int mi = xdir ? 1 : 0, mj = xdir ? 0 : 1;
-  R u0 = U(qi, qj), up = U(qi + mi, qj + mj), um = U(qi - mi, qj - mj);
-  R d0 = Dd(qi, qj), dp = Dd(qi + mi, qj + mj), dm = Dd(qi - mi, qj - mj);
+  int mi = xdir ? 1 : 0, mj = 1 - mi;
+  Ix n0 = nix(g, qi, qj), np = nix(g, qi + mi, qj + mj), nm = nix(g, qi - mi, qj - mj);
+  const R* dd = xdir ? w.ddx : w.ddy;
+  R d0 = O::flip(xdir ? n0.fx : n0.fy, dd[n0.idx]);
+  R dp = O::flip(xdir ? np.fx : np.fy, dd[np.idx]);
+  R dm = O::flip(xdir ? nm.fx : nm.fy, dd[nm.idx]);
   R h = xdir ? kc.dx : kc.dy;
   R wd = h + O::c(0.5f) * (dp - dm);
-  return u0 + vl_term(u0 - um, up - u0, h + d0 - dm, h + dp - d0, O::flip(!fwd, wd) - fdisp);
+  R hm = h + d0 - dm, hp = h + dp - d0;
+  R X = O::flip(!fwd, wd) - fdisp;
+  R u0 = O::flip(n0.fx, w.ulx[n0.idx]), up = O::flip(np.fx, w.ulx[np.idx]), um = O::flip(nm.fx, w.ulx[nm.idx]);
+  vx = u0 + vl_term(u0 - um, up - u0, hm, hp, X);
+  R v0 = O::flip(n0.fy, w.uly[n0.idx]), vp = O::flip(np.fy, w.uly[np.idx]), vm = O::flip(nm.fy, w.uly[nm.idx]);
+  vy = v0 + vl_term(v0 - vm, vp - v0, hm, hp, X);
 }
 
 // K7a: dual-mesh fluxes (sections 2.1.1 and 2.3).  Dual X face between nodes
@@ -1439,41 +1423,31 @@ __device__ __forceinline__ void dual_flux_at(const LrGrid& g, const KC<R>& kc, c
     pp = O::flip(q.fx, sw ? y : x);
     pm = O::flip(q.fx, sw ? x : y);
   };
-  if (xdual && ynode) {  // dual X face between nodes (i,j), (i+1,j)
-    R Dm = Q4 * (MXr(i, j - 1) + MXr(i + 1, j - 1) + MXr(i, j) + MXr(i + 1, j));
+  // dual X face between nodes (i,j), (i+1,j) and dual Y face between (i,j),
+  // (i,j+1): one code path, the direction a runtime value
+#pragma unroll 1
+  for (int xf = 1; xf >= 0; --xf) {
+    if (!(xf ? xdual && ynode : xnode && ydual)) continue;
+    R Dm = xf ? Q4 * (MXr(i, j - 1) + MXr(i + 1, j - 1) + MXr(i, j) + MXr(i + 1, j))
+              : Q4 * (MYr(i - 1, j) + MYr(i - 1, j + 1) + MYr(i, j) + MYr(i, j + 1));
     R px = Z, py = Z;
     if (!O::zero(Dm)) {
       bool fwd = O::pos(Dm);
-      int qi = fwd ? i : i + 1;
-      R fd = H * (nodeX(g, w.ddx, i, j) + nodeX(g, w.ddx, i + 1, j));
+      int qi = xf ? (fwd ? i : i + 1) : i, qj = xf ? j : (fwd ? j : j + 1);
+      Ix a = nix(g, i, j), b = nix(g, i + xf, j + 1 - xf);
+      const R* dd = xf ? w.ddx : w.ddy;
+      R fd = H * (O::flip(xf ? a.fx : a.fy, dd[a.idx]) + O::flip(xf ? b.fx : b.fy, dd[b.idx]));
       R vx, vy;
       if (g.face_o2) {
-        vx = recon_dual_face(g, kc, w.ulx, true, w.ddx, qi, j, true, fwd, fd);
-        vy = recon_dual_face(g, kc, w.uly, false, w.ddx, qi, j, true, fwd, fd);
+        recon_dual_face2(g, kc, w, qi, qj, xf != 0, fwd, fd, vx, vy);
       } else {
-        vx = nodeX(g, w.ulx, qi, j); vy = nodeY(g, w.uly, qi, j);
+        Ix q = nix(g, qi, qj);
+        vx = O::flip(q.fx, w.ulx[q.idx]); vy = O::flip(q.fy, w.uly[q.idx]);
       }
       px = Dm * vx; py = Dm * vy;
     }
-    w.dX[0][o] = Dm; w.dX[1][o] = px; w.dX[2][o] = py;
-  }
-  if (xnode && ydual) {  // dual Y face between nodes (i,j), (i,j+1)
-    R Dm = Q4 * (MYr(i - 1, j) + MYr(i - 1, j + 1) + MYr(i, j) + MYr(i, j + 1));
-    R px = Z, py = Z;
-    if (!O::zero(Dm)) {
-      bool fwd = O::pos(Dm);
-      int qj = fwd ? j : j + 1;
-      R fd = H * (nodeY(g, w.ddy, i, j) + nodeY(g, w.ddy, i, j + 1));
-      R vx, vy;
-      if (g.face_o2) {
-        vx = recon_dual_face(g, kc, w.ulx, true, w.ddy, i, qj, false, fwd, fd);
-        vy = recon_dual_face(g, kc, w.uly, false, w.ddy, i, qj, false, fwd, fd);
-      } else {
-        vx = nodeX(g, w.ulx, i, qj); vy = nodeY(g, w.uly, i, qj);
-      }
-      px = Dm * vx; py = Dm * vy;
-    }
-    w.dY[0][o] = Dm; w.dY[1][o] = px; w.dY[2][o] = py;
+    R* const* dst = xf ? w.dX : w.dY;
+    dst[0][o] = Dm; dst[1][o] = px; dst[2][o] = py;
   }
   if (xdual && ydual) {  // dual corners at the centre of cell (i,j)
     R p0, m0, p1, m1, p2, m2, p3, m3;
