@@ -285,3 +285,39 @@ def test_least_squares_faces_with_comparator_remaps(remap):
     sim, orc = _pair(pr)
     _steps(sim, orc, 6)
     _assert_close(compare(sim, orc), 1e-10, f"lsq {remap} 6 steps")
+
+
+@pytest.mark.parametrize("prec", [lr.FP64, lr.DF64, lr.FP32])
+def test_two_stream_schedule_matches_serial(prec):
+    """The step's second stream (interface kernels beside lr_cell_cf and
+    lr_mat_flux, lr_dual_flux beside lr_cell_update) gives the same bits as
+    the profiling mode, which runs every kernel on one stream in order: the
+    kernels that run side by side write disjoint arrays."""
+    pr = P.triple_point(280, 120)
+    a, b = lr.Sim(pr, precision=prec), lr.Sim(pr, precision=prec)
+    b.set_profiling(True)
+    for _ in range(40):
+        a.step()                    # two streams
+        b.step()                    # one stream, kernel by kernel
+    for f in (lr.F_K, lr.F_RHO_MAT, lr.F_E_MAT, lr.F_UX, lr.F_UY):
+        assert np.array_equal(a.get(f), b.get(f)), f
+    assert a.t == b.t
+    a.close(); b.close()
+
+
+def test_fields_into_page_locked_memory():
+    """lr_get_fields into page-locked host memory (the view kernel writes it
+    directly) gives the same values as into pageable memory."""
+    torch = pytest.importorskip("torch")
+    import ctypes
+    pr = P.random_box(31, nx=91, ny=57, nmat=3, velocity=0.3)
+    sim = lr.Sim(pr)
+    sim.run(5)
+    L = lr.load()
+    for f in (lr.F_K, lr.F_RHO_MAT, lr.F_E_MAT, lr.F_UX, lr.F_UY, lr.F_P, lr.F_C):
+        ref = sim.get(f).ravel()
+        pinned = torch.zeros(ref.size, dtype=torch.float64).pin_memory().numpy()
+        rc = L.lr_get_fields(sim._h, f, pinned.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), pinned.size)
+        assert rc == 0
+        assert np.array_equal(pinned, ref), f
+    sim.close()
