@@ -17,8 +17,9 @@
  * a later phase reads outside the interior (the analogue of a halo exchange
  * between phases).  No blocking, fusion or reordering.
  *
- * Readings of points the paper leaves open are the ones listed in the design doc
- * of this repository and restated at each use below.  Pins (tests/) cover:
+ * Readings of points the paper leaves open (garbled formulas, unstated
+ * constants, inconsistent signs) are stated at each use below.  Pins
+ * (tests/) cover:
  * EOS, cell volume F, Van Leer limiter, half-plane clipping and PLIC
  * placement, face/corner volume fluxes (one-node displacement expansion,
  * uniform translation), order-1 linear advection closed form, order-2 exact
