@@ -372,9 +372,10 @@ def run_lr(args, world, rank, local):
         sim.init(hp)
         sim.step(sync=False)
         for f, a in outs.items():
-            rc = L.lr_get_fields(sim._h, f, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), a.size)
+            rc = L.lr_get_fields_async(sim._h, f, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), a.size)
             if rc != 0:
-                raise RuntimeError("lr_get_fields failed")
+                raise RuntimeError("lr_get_fields_async failed")
+        sim.sync()
     e2e_s = (time.perf_counter() - t0) / n_e2e
     e2e_val = world * cells / e2e_s
     sim.close()

@@ -203,6 +203,13 @@ size_t lr_field_size(const lr_ctx* ctx, int field);
  * be at least lr_field_size). */
 lr_status lr_get_fields(lr_ctx* ctx, int field, double* host_out, size_t n_elems);
 
+/* Same without synchronising: the copy is enqueued on the context's stream
+ * and host_out must stay valid and unread until lr_sync returns.  Page-locked
+ * (pinned) host memory is written by the device directly; pageable memory is
+ * copied before the call returns.  LR_F_CONS is not available here.  Several
+ * fields read this way cost one synchronisation. */
+lr_status lr_get_fields_async(lr_ctx* ctx, int field, double* host_out, size_t n_elems);
+
 /* Same, into caller-owned device memory on the context's stream (no host
  * synchronisation).  LR_F_CONS is not available here. */
 lr_status lr_get_fields_device(lr_ctx* ctx, int field, double* dev_out, size_t n_elems);

@@ -658,25 +658,42 @@ lr_status lr_sync(lr_ctx* ctx) {
 
 size_t lr_field_size(const lr_ctx* ctx, int field) { return ctx ? lr_field_count(ctx->g, field) : 0; }
 
-lr_status lr_get_fields(lr_ctx* ctx, int field, double* host_out, size_t n_elems) {
+// Field into host memory, enqueued: pinned (page-locked, mapped) memory is
+// written by the view kernel directly over the host link (no device staging,
+// no separate copy); pageable memory through the staging buffer, the copy
+// finishing before the call returns.
+static lr_status field_to_host(lr_ctx* ctx, int field, double* host_out, size_t n_elems, const char* who) {
   if (!ctx || !host_out) return LR_ERR_ARG;
   size_t need = lr_field_size(ctx, field);
-  if (need == 0 || n_elems < need) { setmsg(ctx, "lr_get_fields: field %d needs %zu elements", field, need); return LR_ERR_ARG; }
-  if (!ctx->inited) { setmsg(ctx, "lr_get_fields before lr_init"); return LR_ERR_STATE; }
-  // pinned (page-locked, mapped) host memory: the view kernel writes it
-  // directly over the host link, no device staging and no separate copy
+  if (need == 0 || n_elems < need) { setmsg(ctx, "%s: field %d needs %zu elements", who, field, need); return LR_ERR_ARG; }
+  if (!ctx->inited) { setmsg(ctx, "%s before lr_init", who); return LR_ERR_STATE; }
   cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, host_out) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer) {
-    lr_status s = field_to_device(ctx, field, static_cast<double*>(at.devicePointer));
-    if (s != LR_OK) return s;
-  } else {
-    cudaGetLastError();  // a failed query leaves an error state behind: clear it
-    lr_status s = field_to_device(ctx, field, ctx->tmp);
-    if (s != LR_OK) return s;
-    CK(cudaMemcpyAsync(host_out, ctx->tmp, need * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "download");
+  bool by_kernel = field != LR_F_DT && field != LR_F_NMIXED;  // the other fields are written by a kernel
+  if (by_kernel && cudaPointerGetAttributes(&at, host_out) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+      at.devicePointer) {
+    return field_to_device(ctx, field, static_cast<double*>(at.devicePointer));
   }
+  cudaGetLastError();  // a failed query leaves an error state behind: clear it
+  lr_status s = field_to_device(ctx, field, ctx->tmp);
+  if (s != LR_OK) return s;
+  CK(cudaMemcpyAsync(host_out, ctx->tmp, need * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "download");
+  CK(cudaStreamSynchronize(ctx->stream), "sync");  // the staging buffer is reused by the next call
+  return LR_OK;
+}
+
+lr_status lr_get_fields(lr_ctx* ctx, int field, double* host_out, size_t n_elems) {
+  lr_status s = field_to_host(ctx, field, host_out, n_elems, "lr_get_fields");
+  if (s != LR_OK) return s;
   CK(cudaStreamSynchronize(ctx->stream), "sync");
   return LR_OK;
+}
+
+lr_status lr_get_fields_async(lr_ctx* ctx, int field, double* host_out, size_t n_elems) {
+  if (field == LR_F_CONS) {
+    if (ctx) setmsg(ctx, "lr_get_fields_async: LR_F_CONS is read with lr_get_fields");
+    return LR_ERR_ARG;
+  }
+  return field_to_host(ctx, field, host_out, n_elems, "lr_get_fields_async");
 }
 
 lr_status lr_get_fields_device(lr_ctx* ctx, int field, double* dev_out, size_t n_elems) {

@@ -130,6 +130,8 @@ def load(build_if_missing: bool = True):
     L.lr_last_error.restype = ctypes.c_char_p
     L.lr_cfl_dt_noalloc.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(Material), vp, vp, vp, vp, vp, vp]
     L.lr_cfl_dt_noalloc.restype = ctypes.c_int
+    L.lr_get_fields_async.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_size_t]
+    L.lr_get_fields_async.restype = ctypes.c_int
     L.lr_arith_check.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.c_size_t, vp]
     L.lr_arith_check.restype = ctypes.c_int
     bp = ctypes.POINTER(BatchConfig)

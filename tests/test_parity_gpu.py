@@ -314,10 +314,23 @@ def test_fields_into_page_locked_memory():
     sim = lr.Sim(pr)
     sim.run(5)
     L = lr.load()
-    for f in (lr.F_K, lr.F_RHO_MAT, lr.F_E_MAT, lr.F_UX, lr.F_UY, lr.F_P, lr.F_C):
+    fields = (lr.F_K, lr.F_RHO_MAT, lr.F_E_MAT, lr.F_UX, lr.F_UY, lr.F_P, lr.F_C, lr.F_DT, lr.F_NMIXED, lr.F_CONS)
+    P_ = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    for f in fields:
         ref = sim.get(f).ravel()
         pinned = torch.zeros(ref.size, dtype=torch.float64).pin_memory().numpy()
-        rc = L.lr_get_fields(sim._h, f, pinned.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), pinned.size)
-        assert rc == 0
+        assert L.lr_get_fields(sim._h, f, P_(pinned), pinned.size) == 0
         assert np.array_equal(pinned, ref), f
+    # several fields enqueued, one synchronisation
+    outs = {f: torch.zeros(sim.get(f).size, dtype=torch.float64).pin_memory().numpy()
+            for f in fields if f != lr.F_CONS}
+    for f, a in outs.items():
+        assert L.lr_get_fields_async(sim._h, f, P_(a), a.size) == 0
+    sim.sync()
+    for f, a in outs.items():
+        assert np.array_equal(a, sim.get(f).ravel()), f
+    plain = np.zeros(sim.get(lr.F_K).size)
+    assert L.lr_get_fields_async(sim._h, lr.F_K, P_(plain), plain.size) == 0  # pageable: copied on return
+    assert np.array_equal(plain, sim.get(lr.F_K).ravel())
+    assert L.lr_get_fields_async(sim._h, lr.F_CONS, P_(plain), plain.size) != 0
     sim.close()
