@@ -222,7 +222,11 @@ def run_reference(args, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / n,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "nx": pr.nx, "ny": pr.ny, "nmat": 3},
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": pr.nx, "ny": pr.ny, "nmat": 3, "precision": "fp64",
+                       "t_start": 0.0, "parallelism": "one CPU thread",
+                       "note": "the oracle evaluates every cell and flux object each step, so its cost per "
+                               "step does not depend on the flow state: sampled from the initial state"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
