@@ -278,6 +278,23 @@ def kernel_profile(sim, K, flush, torch):
     return {k: v[1] / max(v[0], 1) for k, v in kt.items() if v[0] > 0}
 
 
+def max_over_ranks(x, dist, device):
+    """The largest of every rank's x (x itself on one rank): the job's time
+    is its slowest rank's."""
+    if not dist:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, seconds_max):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (weak scaling: every rank processes the same units)."""
+    return world * units_per_rank / seconds_max
+
+
 def run_lr(args, world, rank, local):
     import numpy as np
     import torch
@@ -320,11 +337,8 @@ def run_lr(args, world, rank, local):
     if dist:
         dist.barrier()
     clocks = sampler.stop()
-    tmax = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    ms_max = float(tmax.item())
-    value = world * cells * K / (ms_max * 1e-3)
+    ms_max = max_over_ranks(ms, dist, "cuda")
+    value = job_rate(world, cells * K, ms_max * 1e-3)
     step_ms = ms_max / K
 
     # ---- per-kernel durations: a second simulation replays the same steps
@@ -380,8 +394,8 @@ def run_lr(args, world, rank, local):
             if rc != 0:
                 raise RuntimeError("lr_get_fields_async failed")
         sim.sync()
-    e2e_s = (time.perf_counter() - t0) / n_e2e
-    e2e_val = world * cells / e2e_s
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / n_e2e, dist, "cuda")
+    e2e_val = job_rate(world, cells, e2e_s)
     sim.close()
 
     # ---- the other arithmetic modes: same workload, short timed runs, and
