@@ -156,11 +156,16 @@ def units_per_launch(kernel, nx, ny):
 
 def kernel_source_hash():
     """sha256 prefix of the device code the counters describe: the kernels
-    and the arithmetic and layout headers they include."""
+    and the arithmetic and layout headers they include, comments and blank
+    space removed (an edit to a comment does not change the counters)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in ("lr_kernels.cu", "lr_real.cuh", "lr_dev.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2208_13409_gb300", "csrc", f), "rb").read())
+        src = open(os.path.join(ROOT, "paper_2208_13409_gb300", "csrc", f)).read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -1020,8 +1020,8 @@ __device__ __forceinline__ void recon_corner2(const LrGrid& g, const KC<R>& kc, 
 
 // Van Leer limited slopes of q in cell (di,dj): along x or y over the
 // Lagrangian centres of the two neighbours, and along v (pp) or v_perp over
-// the diagonal neighbours' centres projected on v (as recon_face and
-// recon_corner compute them).
+// the diagonal neighbours' centres projected on v (as recon_face2 and
+// recon_corner2 compute them).
 template <class R>
 __device__ __forceinline__ R slope_axis(const LrGrid& g, const KC<R>& kc, const R* q, const LrWorkT<R>& w, int di,
                                         int dj, bool xdir) {
