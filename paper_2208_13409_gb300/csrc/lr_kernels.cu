@@ -161,6 +161,16 @@ __device__ __forceinline__ T* pick(T* const* arr, int a) {
   return p;
 }
 
+// Programmatic dependent launch (the lone step's kernels are launched with
+// it): a kernel lets its successor's blocks be scheduled once every block of
+// its own has started, and waits for its predecessor grid to complete (and
+// its writes to be visible) before reading anything; both are no-ops for a
+// kernel launched without the attribute.
+__device__ __forceinline__ void lr_pdl_enter() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 __device__ __forceinline__ void set_err(int* err, int bit, int idx) {
   atomicOr(&err[0], bit);
   atomicCAS(&err[1], -1, idx);
@@ -1764,6 +1774,7 @@ __device__ __forceinline__ void prepare_at(const LrGrid& g, const KC<R>& kc, con
 // t_end of this call and the dt of the next step (one thread).
 template <class R>
 __global__ void lr_set_tend_k(LrGrid g, LrWorkT<R> w, double t_end) {
+  lr_pdl_enter();
   double* sc = scal_of(g, w.scal);
   sc[3] = t_end;
   double t = sc[0];
@@ -1962,6 +1973,7 @@ template <int D> struct MinBlocks<df64, D> { static constexpr int value = LR_MIN
   template <class R, int M>                                                                               \
   __global__ void __launch_bounds__(256, MinBlocks<R, MBD>::value) lr_##NAME(LrGrid g, KC<R> kc, LrStateT<R> cur, LrStateT<R> nxt,  \
                                                    LrWorkT<R> w) {                                        \
+    lr_pdl_enter();                                                                                       \
     OP::template at<R, M>(g, kc, cur, nxt, w, blockIdx.x * BX + threadIdx.x, blockIdx.y * BY + threadIdx.y, \
                           (unsigned long long)gridDim.x * gridDim.y);                                     \
   }                                                                                                       \
@@ -1999,12 +2011,14 @@ LR_KERNEL_PAIR(prepare, OpPrepare, 1)
 template <class R, int M>
 __global__ void __launch_bounds__(256) lr_mat_flux_var(LrGrid g, KC<R> kc, LrStateT<R> cur, LrStateT<R> nxt,
                                                        LrWorkT<R> w) {
+  lr_pdl_enter();
   mat_flux_at<R, M, true>(g, kc, cur, w, blockIdx.x * BX + threadIdx.x, blockIdx.y * BY + threadIdx.y);
 }
 
 template <class R, int M>
 __global__ void __launch_bounds__(256) lr_sweep_prep(LrGrid g, KC<R> kc, LrStateT<R> cur, LrStateT<R> nxt,
                                                      LrWorkT<R> w) {
+  lr_pdl_enter();
   sweep_prep_at<R, M>(g, kc, cur, w, blockIdx.x * BX + threadIdx.x, blockIdx.y * BY + threadIdx.y);
 }
 
@@ -2016,6 +2030,7 @@ __global__ void __launch_bounds__(256) lr_sweep_prep(LrGrid g, KC<R> kc, LrState
 template <class R, int M>
 __global__ void __launch_bounds__(128) lb_mixed_place(const LrGrid* __restrict__ gs, LrStateT<R> cur,
                                                       LrWorkT<R> w, int mslot, int moff) {
+  lr_pdl_enter();
   int count = (int)w.red[mslot];
   int lane = threadIdx.x & 7;
   int group = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 3);
@@ -2031,10 +2046,27 @@ __global__ void __launch_bounds__(128) lb_mixed_place(const LrGrid* __restrict__
 template <class R, int M>
 __global__ void __launch_bounds__(128) lb_mixed(const LrGrid* __restrict__ gs, LrStateT<R> cur, LrWorkT<R> w,
                                                 int lanes, int mslot, int moff) {
+  lr_pdl_enter();
   mixed_loop<R, M>([&](int e) -> const LrGrid& { return gs[w.minst[e]]; }, cur, w, lanes, mslot, moff);
 }
 
 inline dim3 grid_for(int nxr, int nyr) { return dim3((nxr + BX - 1) / BX, (nyr + BY - 1) / BY); }
+
+// Launch with programmatic stream serialisation (see lr_pdl_enter).
+template <class... KArgs, class... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
 
 template <class R>
 cudaError_t launch_t(int kid, const LrGrid& g, const LrState& cur0, const LrState& nxt0, const LrWork& w0,
@@ -2045,11 +2077,16 @@ cudaError_t launch_t(int kid, const LrGrid& g, const LrState& cur0, const LrStat
   dim3 b(BX, BY);
 #define LR_M(K, GRID)                                                                        \
   do {                                                                                       \
-    if (g.M == 1) K<R, 1><<<GRID, b, 0, s>>>(g, kc, cur, nxt, w);                            \
-    else if (g.M == 2) K<R, 2><<<GRID, b, 0, s>>>(g, kc, cur, nxt, w);                       \
-    else K<R, 3><<<GRID, b, 0, s>>>(g, kc, cur, nxt, w);                                     \
+    cudaError_t _e = g.M == 1   ? launch_pdl(K<R, 1>, GRID, b, s, g, kc, cur, nxt, w)        \
+                     : g.M == 2 ? launch_pdl(K<R, 2>, GRID, b, s, g, kc, cur, nxt, w)        \
+                                : launch_pdl(K<R, 3>, GRID, b, s, g, kc, cur, nxt, w);       \
+    if (_e != cudaSuccess) return _e;                                                        \
   } while (0)
-#define LR_1(K, GRID) K<R, 1><<<GRID, b, 0, s>>>(g, kc, cur, nxt, w)
+#define LR_1(K, GRID)                                                                        \
+  do {                                                                                       \
+    cudaError_t _e = launch_pdl(K<R, 1>, GRID, b, s, g, kc, cur, nxt, w);                    \
+    if (_e != cudaSuccess) return _e;                                                        \
+  } while (0)
   switch (kid) {
     case LRK_CELL_PRE: LR_M(lr_cell_pre, grid_for(g.nx, g.ny)); break;
     case LRK_NODE_HALF: LR_1(lr_node_half, grid_for(g.nxu, g.nyu)); break;
