@@ -52,18 +52,18 @@ __device__ __forceinline__ df64 mul(df64 x, df64 y) {
   fast_two_sum(p, e, r.hi, r.lo);
   return r;
 }
-// x / y: three quotient digits from an approximate reciprocal of y.hi, each
-// removing the remainder of the previous ones (long division in base 2^24).
+// x / y: two quotient digits from an approximate reciprocal of y.hi, the
+// second removing the remainder of the first (long division in base 2^24):
+// about 2^-46, the pair's own precision near 2^-48.
 __device__ __forceinline__ df64 div(df64 x, df64 y) {
-  float r0 = __frcp_rn(y.hi);
+  float r0;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(y.hi));
   float q1 = __fmul_rn(x.hi, r0);
   df64 rem = add(x, neg(mul(y, df64(q1))));
   float q2 = __fmul_rn(rem.hi, r0);
-  rem = add(rem, neg(mul(y, df64(q2))));
-  float q3 = __fmul_rn(rem.hi, r0);
   df64 q;
   fast_two_sum(q1, q2, q.hi, q.lo);
-  return add(q, df64(q3));
+  return q;
 }
 // sqrt(x): float square root, then one Newton correction in double length:
 // s' = s + (x - s^2) / (2 s).
@@ -259,8 +259,10 @@ template <> struct RealOps<float> {
   __device__ static __forceinline__ float abs(float x) { return fabsf(x); }
   __device__ static __forceinline__ float flip(bool f, float x) { return f ? -x : x; }
   __device__ static __forceinline__ float sqrt(float x) { return sqrtf(x); }
-  __device__ static __forceinline__ float rcp(float x) { return 1.0f / x; }
-  __device__ static __forceinline__ float div(float a, float b) { return a / b; }
+  // reciprocal and quotient to about two ulps (the bulk mode's accuracy is
+  // set by float storage, not by these)
+  __device__ static __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+  __device__ static __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
   __device__ static __forceinline__ bool finite(float x) { return isfinite(x); }
   __device__ static __forceinline__ bool pos(float x) { return x > 0.0f; }
   __device__ static __forceinline__ bool neg(float x) { return x < 0.0f; }
