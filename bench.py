@@ -434,6 +434,7 @@ def run_lr(args, world, rank, local):
         extras["ensemble"] = ensemble_bench(args)
         extras["serving"] = serving_bench(args)
         extras["variants"] = variants_bench(args)
+        extras["shock_bubble_2000"] = shock_bubble_modes(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.cpu_baseline_steps)
         accuracy = sod_accuracy()
@@ -531,6 +532,37 @@ def variants_bench(args, t_start=1.0, steps=200):
                      "launches_per_step": sim.launches_per_step()}
         sim.close()
     del flush
+    torch.cuda.empty_cache()
+    return out
+
+
+def shock_bubble_modes(args, steps=2000):
+    """The shock-bubble workload (4096 x 1024, air with a helium disc, Mach
+    1.22 shock) run 2000 steps in FP64 and in the FP32 bulk mode (and in
+    double-float): per-field L1 relative difference of each mode from the
+    FP64 run, and each run's rate (one lr_run, host-timed)."""
+    import torch
+    from paper_2208_13409_gb300 import lr, problems as P
+
+    pr = P.shock_bubble()
+    out = {"workload": f"shock_bubble_{pr.nx}x{pr.ny}", "steps": steps}
+    ref = None
+    for name in ("fp64", "fp32", "df64"):
+        sim = lr.Sim(pr, precision=MODES[name])
+        sim.run(3)
+        sim.sync()
+        t0 = time.perf_counter()
+        n, t = sim.run(steps - 3)
+        sim.sync()
+        el = time.perf_counter() - t0
+        fs = field_set(sim, lr)
+        rec = {"value": pr.cells * n / el, "unit": UNIT, "t": t}
+        if ref is None:
+            ref = fs
+        else:
+            rec["l1_vs_fp64"] = {k: l1_rel(fs[k], ref[k]) for k in fs}
+        out[name] = rec
+        sim.close()
     torch.cuda.empty_cache()
     return out
 
