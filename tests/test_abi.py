@@ -65,3 +65,14 @@ def test_batch_host_side_validation_without_gpu():
         setattr(c, field, bad)
         assert L.lr_batch_workspace_bytes(ctypes.byref(c), ctypes.byref(n)) == lr.ERR_ARG, field
     assert L.lr_batch_last_error(None) == b"null batch"
+
+
+def test_arith_check_and_async_reads_validate_without_gpu():
+    L = lr.load()
+    vp = ctypes.c_void_p
+    # unknown operation, or missing buffers: refused before any device call
+    assert L.lr_arith_check(7, vp(), vp(), vp(), 4, vp()) == lr.ERR_ARG
+    assert L.lr_arith_check(lr.ARITH_DIV, vp(), vp(), vp(), 4, vp()) == lr.ERR_ARG
+    assert L.lr_arith_check(lr.ARITH_SQRT, vp(), vp(), vp(), 0, vp()) == lr.OK  # nothing to do
+    buf = (ctypes.c_double * 4)()
+    assert L.lr_get_fields_async(None, lr.F_K, buf, 4) == lr.ERR_ARG
