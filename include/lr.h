@@ -97,7 +97,8 @@ typedef struct {
   int nmat;               /* 1..3 materials */
   double cfl;             /* CFL number of the time-step rule (0.25 default) */
   double a1, a2;          /* Wilkins linear / quadratic coefficients (0.5, 1.0) */
-  int bc[4];              /* xlo, xhi, ylo, yhi: LR_BC_REFLECT | LR_BC_PERIODIC;
+  int bc[4];              /* xlo, xhi, ylo, yhi: LR_BC_REFLECT | LR_BC_PERIODIC (a periodic
+                             direction needs at least 3 cells);
                              xlo == xhi and ylo == yhi */
   int precision;          /* LR_FP64 (default), LR_DF64 or LR_FP32 */
   int face_order;         /* 1 upwind or 2 Van Leer limited linear (default 2) */

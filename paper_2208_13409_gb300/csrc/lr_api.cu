@@ -49,6 +49,10 @@ bool lr_config_ok(const lr_config* c, char* why, size_t nwhy) {
   if (c->bc[0] != c->bc[1] || c->bc[2] != c->bc[3]) { snprintf(why, nwhy, "bc[0]==bc[1] and bc[2]==bc[3] required"); return false; }
   for (int q = 0; q < 4; ++q)
     if (c->bc[q] != LR_BC_REFLECT && c->bc[q] != LR_BC_PERIODIC) { snprintf(why, nwhy, "bad bc"); return false; }
+  if ((c->bc[0] == LR_BC_PERIODIC && c->nx < 3) || (c->bc[2] == LR_BC_PERIODIC && c->ny < 3)) {
+    snprintf(why, nwhy, "a periodic direction needs at least 3 cells");
+    return false;
+  }
   if (!(c->cfl > 0.0) || c->cfl > 1.0) { snprintf(why, nwhy, "cfl must be in (0,1]"); return false; }
   if (c->a1 < 0.0 || c->a2 < 0.0) { snprintf(why, nwhy, "negative viscosity coefficient"); return false; }
   if (c->face_order != 1 && c->face_order != 2) { snprintf(why, nwhy, "face_order must be 1 or 2"); return false; }

@@ -84,16 +84,20 @@ KC<R> make_kc(const LrGrid& g) {
 }
 
 // ------------------------------------------------------------ index maps
+// Stencil reads reach at most two cells or nodes beyond the grid, and a
+// periodic direction has at least three cells (lr_config check), so one
+// period added or removed brings every periodic index home.
+__host__ __device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 __host__ __device__ __forceinline__ int map_cell(int i, int n, int per, int& flip) {
   flip = 0;
   if (i >= 0 && i < n) return i;
-  if (per) return (i + n) % n;
+  if (per) return wrap1(i, n);
   flip = 1;
   return i < 0 ? -1 - i : 2 * n - 1 - i;
 }
 __host__ __device__ __forceinline__ int map_node(int i, int n, int per, int& flip) {
   flip = 0;
-  if (per) return (i + n) % n;
+  if (per) return wrap1(i, n);
   if (i >= 0 && i <= n) return i;
   flip = 1;
   return i < 0 ? -i : 2 * n - i;
@@ -126,8 +130,8 @@ __device__ __forceinline__ Ix yix(const LrGrid& g, int i, int j) {
 }
 // dual objects: i, j in [-1, n]; periodic directions wrap into [0, n)
 __device__ __forceinline__ int dix(const LrGrid& g, int i, int j) {
-  if (g.perx) i = (i + g.nx) % g.nx;
-  if (g.pery) j = (j + g.ny) % g.ny;
+  if (g.perx) i = wrap1(i, g.nx);
+  if (g.pery) j = wrap1(j, g.ny);
   return g.doff + (j + 1) * (g.nx + 2) + (i + 1);
 }
 // mirrored reads: node vector components, cell scalars, centre offsets
