@@ -11,8 +11,8 @@
 // arithmetic-bound on GB300 (FP64: ~0.6e12 DFMA/s against ~7 TB/s of HBM).
 // The kernels are templates over the arithmetic type R: native double, float
 // (the FP32 bulk mode) or df64 (double-float on the FP32 pipe, see
-// lr_real.cuh).  Interface geometry of mixed cells (lr_mixed) always runs in
-// double.  Boundary conditions are applied on read: an index outside the
+// lr_real.cuh).  Interface geometry of mixed cells (lb_mixed_place and
+// lb_mixed, timed together as lr_mixed) always runs in double.  Boundary conditions are applied on read: an index outside the
 // domain maps to its mirror image (reflective wall, with the sign of the
 // mirrored vector component or flux flipped) or wraps (periodic).
 #include "../../include/lr.h"
