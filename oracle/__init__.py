@@ -23,6 +23,8 @@ F_K, F_RHO_MAT, F_E_MAT, F_P, F_RHO, F_E, F_UX, F_UY, F_CONS, F_C = range(10)
 F_UHX, F_UHY, F_VOL_LAGCF, F_E_LAG, F_FX, F_FY, F_FC, F_MX, F_MY, F_MC, F_Q, F_DT = range(20, 32)
 F_CUTS, F_XA, F_YA, F_CA = range(32, 36)
 F_SCLIP = 37
+F_MP_NEW, F_DUAL = 38, 39
+DUAL_X, DUAL_Y, DUAL_PP, DUAL_PM = range(4)
 
 
 class Config(ctypes.Structure):
@@ -65,6 +67,8 @@ def lib():
         L.orc_init.argtypes = [ctypes.c_void_p, dp, dp, dp, dp, dp]
         L.orc_set_prescribed.restype = ctypes.c_int
         L.orc_set_prescribed.argtypes = [ctypes.c_void_p, dp, dp]
+        L.orc_set_remap_velocity.restype = ctypes.c_int
+        L.orc_set_remap_velocity.argtypes = [ctypes.c_void_p, dp, dp]
         L.orc_step.restype = ctypes.c_int
         L.orc_step.argtypes = [ctypes.c_void_p, ctypes.c_double, dp]
         L.orc_get.restype = ctypes.c_int
@@ -135,6 +139,13 @@ class Oracle:
         self._pv = (_c64(ux), _c64(uy))
         lib().orc_set_prescribed(self._h, _dp(self._pv[0]), _dp(self._pv[1]))
 
+    def set_remap_velocity(self, ux, uy):
+        """Test hook: with a prescribed velocity set, the dual remap carries
+        this node field as u^{lag} (the flux geometry still follows the
+        prescribed velocity)."""
+        self._rv = (_c64(ux), _c64(uy))
+        lib().orc_set_remap_velocity(self._h, _dp(self._rv[0]), _dp(self._rv[1]))
+
     def step(self, t_end: float = 1e300) -> float:
         dt = ctypes.c_double(0.0)
         rc = lib().orc_step(self._h, t_end, ctypes.byref(dt))
@@ -166,7 +177,7 @@ class Oracle:
             return out.reshape(M, ny, nx)
         if field in (F_P, F_RHO, F_E, F_C, F_VOL_LAGCF, F_Q):
             return out.reshape(ny, nx)
-        if field in (F_UX, F_UY, F_UHX, F_UHY, F_FC, F_MC):
+        if field in (F_UX, F_UY, F_UHX, F_UHY, F_FC, F_MC, F_MP_NEW):
             return out.reshape(ny + 1, nx + 1)
         if field in (F_FX, F_MX):
             return out.reshape(ny, nx + 1)
@@ -180,6 +191,8 @@ class Oracle:
             return out.reshape(M, ny + 1, nx)
         if field == F_CA:
             return out.reshape(M, ny + 1, nx + 1)
+        if field == F_DUAL:
+            return out.reshape(4, 3, ny + 1, nx + 1)
         return out
 
 

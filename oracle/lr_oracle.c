@@ -25,7 +25,13 @@
  * uniform translation), order-1 linear advection closed form, order-2 exact
  * translation of linear fields, uniform-state preservation, conservation,
  * Sod shock tube against the exact Riemann solution, translated planar
- * interfaces, volume-fraction bounds, mirror and transpose symmetry, CFL.
+ * interfaces, volume-fraction bounds, mirror and transpose symmetry, CFL,
+ * and the dual-mesh momentum remap: remapped nodal mass equal to a quarter
+ * of the four remapped cell masses, the order-1 box formula on the dual
+ * mesh, and exact dual face and corner fluxes of linear velocity fields
+ * under uniform and axis-preserving affine displacements (the hook
+ * orc_set_remap_velocity carries a given node field under a prescribed
+ * displacement).
  * Parity unpinned beyond those invariants: the flux clipping near k=0 and
  * the material-removal threshold (clip_and_split, cell_update), the
  * 3-material nested interface order and the sound-speed ramp for nearly
@@ -76,6 +82,10 @@ struct orc {
   double *fc;                   /* corner |dVol| */
   double *cA[MAXM], *cMm[MAXM], *cE[MAXM]; /* corner per-material (positive) */
   double *Mpp, *Mpm;
+  double *mpn;                  /* remapped nodal mass m_p' of the last step */
+  double *dual[4][3];           /* dual X face, Y face, ++ and +- corner: mass, x- and y-momentum flux */
+  int ruse;                     /* test hook: remap this node field under a prescribed velocity */
+  double *rux, *ruy;
   /* face intermediates */
   double *fx, *fxlo, *fxhi, *fxb; /* X-faces */
   double *fy, *fylo, *fyhi, *fyb; /* Y-faces */
@@ -333,6 +343,9 @@ orc* orc_create(const orc_config* cfg, const double* gamma, const double* pinf) 
   s->uhx = dalloc(nn); s->uhy = dalloc(nn); s->ulx = dalloc(nn); s->uly = dalloc(nn);
   s->ddx = dalloc(nn); s->ddy = dalloc(nn); s->fc = dalloc(nn);
   s->Mpp = dalloc(nn); s->Mpm = dalloc(nn);
+  s->mpn = dalloc(nn); s->rux = dalloc(nn); s->ruy = dalloc(nn);
+  for (int q = 0; q < 4; ++q)
+    for (int z = 0; z < 3; ++z) s->dual[q][z] = dalloc(nn);
   s->fx = dalloc(nfx); s->fxlo = dalloc(nfx); s->fxhi = dalloc(nfx); s->fxb = dalloc(nfx);
   s->fy = dalloc(nfy); s->fylo = dalloc(nfy); s->fyhi = dalloc(nfy); s->fyb = dalloc(nfy);
   s->MX = dalloc(nfx); s->MY = dalloc(nfy);
@@ -357,6 +370,9 @@ void orc_destroy(orc* s) {
   free(s->ox); free(s->oy); free(s->wx); free(s->wy);
   free(s->uhx); free(s->uhy); free(s->ulx); free(s->uly); free(s->ddx); free(s->ddy); free(s->fc);
   free(s->Mpp); free(s->Mpm);
+  free(s->mpn); free(s->rux); free(s->ruy);
+  for (int q = 0; q < 4; ++q)
+    for (int z = 0; z < 3; ++z) free(s->dual[q][z]);
   free(s->fx); free(s->fxlo); free(s->fxhi); free(s->fxb);
   free(s->fy); free(s->fylo); free(s->fyhi); free(s->fyb);
   free(s->MX); free(s->MY);
@@ -423,6 +439,17 @@ int orc_set_prescribed(orc* s, const double* ux, const double* uy) {
       s->puy[NI(s, i, j)] = uy[(long)j * (s->nx + 1) + i];
     }
   s->presc = 1;
+  return 0;
+}
+
+int orc_set_remap_velocity(orc* s, const double* ux, const double* uy) {
+  if (!ux || !uy) { s->ruse = 0; return 0; }
+  for (int j = 0; j <= s->ny; ++j)
+    for (int i = 0; i <= s->nx; ++i) {
+      s->rux[NI(s, i, j)] = ux[(long)j * (s->nx + 1) + i];
+      s->ruy[NI(s, i, j)] = uy[(long)j * (s->nx + 1) + i];
+    }
+  s->ruse = 1;
   return 0;
 }
 
@@ -539,7 +566,9 @@ static int lagrange(orc* s, double dt) {
       int n = NI(s, i, j);
       if (s->presc) {
         s->uhx[n] = s->pux[n]; s->uhy[n] = s->puy[n];
-        s->ulx[n] = s->pux[n]; s->uly[n] = s->puy[n];
+        /* test hook: the node field the dual remap carries */
+        s->ulx[n] = s->ruse ? s->rux[n] : s->pux[n];
+        s->uly[n] = s->ruse ? s->ruy[n] : s->puy[n];
         continue;
       }
       int A = CI(s, i - 1, j - 1), B = CI(s, i, j - 1), C = CI(s, i - 1, j), D = CI(s, i, j);
@@ -779,6 +808,8 @@ static void interfaces_in(orc* s, int rect, double* (*cn)[3]) {
       double xr = xl + s->wx[c];
       double yb = 0.5 * dy - 0.5 * s->wy[c] + s->oy[c];
       double yt = yb + s->wy[c];
+      /* the rectangle is kept as centre offset and widths (wx, wy); its
+       * area is the product of the widths (xr - xl would re-round wx) */
       double area = s->wx[c] * s->wy[c];
       if (rect == 1) { yb = 0.0; yt = dy; area = s->wx[c] * dy; }
       if (rect == 2) { xl = 0.0; xr = dx; area = dx * s->wy[c]; }
@@ -1288,11 +1319,17 @@ static void dual_remap(orc* s, double* nux, double* nuy) {
    * second-order corner choice (reading: section 3.3 defines the variants
    * for the cell-centred variables only) */
   int fo2 = s->c.face_order == 2, co2 = s->c.corner_recon != ORC_CORNER_UPWIND;
+  long nn = (long)s->nw * s->nh;
+  for (long v = 0; v < nn; ++v) {
+    s->mpn[v] = 0.0;
+    for (int q = 0; q < 4; ++q)
+      for (int z = 0; z < 3; ++z) s->dual[q][z][v] = 0.0;
+  }
   for (int j = 0; j <= ny; ++j)
     for (int i = 0; i <= nx; ++i) {
       if (!node_interior(i, nx, s->perx) || !node_interior(j, ny, s->pery)) continue;
       int p = NI(s, i, j);
-      if (s->presc) { nux[p] = s->pux[p]; nuy[p] = s->puy[p]; continue; }
+      if (s->presc && !s->ruse) { nux[p] = s->pux[p]; nuy[p] = s->puy[p]; continue; }
       double mp = 0.25 * (s->mc[CI(s, i - 1, j - 1)] + s->mc[CI(s, i, j - 1)]
                         + s->mc[CI(s, i - 1, j)] + s->mc[CI(s, i, j)]);
       double mnew = mp, px = mp * s->ulx[p], py = mp * s->uly[p];
@@ -1309,6 +1346,7 @@ static void dual_remap(orc* s, double* nux, double* nuy) {
         double vy = recon_dual_face(s, s->uly, qi, j, 1, sg, fd, fo2);
         double sgn = side == 0 ? -1.0 : 1.0;
         mnew += sgn * D; px += sgn * D * vx; py += sgn * D * vy;
+        if (side == 0) { s->dual[0][0][p] = D; s->dual[0][1][p] = D * vx; s->dual[0][2][p] = D * vy; }
       }
       /* dual Y-faces: top (tail p), bottom (head p) */
       for (int side = 0; side < 2; ++side) {
@@ -1323,6 +1361,7 @@ static void dual_remap(orc* s, double* nux, double* nuy) {
         double vy = recon_dual_face(s, s->uly, i, qj, 0, sg, fd, fo2);
         double sgn = side == 0 ? -1.0 : 1.0;
         mnew += sgn * D; px += sgn * D * vx; py += sgn * D * vy;
+        if (side == 0) { s->dual[1][0][p] = D; s->dual[1][1][p] = D * vx; s->dual[1][2][p] = D * vy; }
       }
       /* dual corners: ++ at cells (i,j) [tail p] and (i-1,j-1) [head p];
        * +- at cells (i,j-1) [tail p = its upper-left node] and (i-1,j)
@@ -1348,7 +1387,12 @@ static void dual_remap(orc* s, double* nux, double* nuy) {
         double vy = recon_dual_corner(s, s->uly, qi, qj, pp, sg, cdx, cdy, co2);
         double sgn = tail ? -1.0 : 1.0;
         mnew += sgn * D; px += sgn * D * vx; py += sgn * D * vy;
+        if (tail && cj >= 0) {  /* kept for the test hooks, at the cell's index */
+          int o = NI(s, ci, cj), q = pp ? 2 : 3;
+          s->dual[q][0][o] = D; s->dual[q][1][o] = D * vx; s->dual[q][2][o] = D * vy;
+        }
       }
+      s->mpn[p] = mnew;
       if (!(mnew > 0.0)) { nux[p] = NAN; nuy[p] = NAN; continue; }
       nux[p] = px / mnew;
       nuy[p] = py / mnew;
@@ -1485,6 +1529,8 @@ long orc_size(const orc* s, int field) {
     case ORC_F_XA: return (long)s->M * s->ny * (s->nx + 1);
     case ORC_F_YA: return (long)s->M * (s->ny + 1) * s->nx;
     case ORC_F_CA: return (long)s->M * n;
+    case ORC_F_MP_NEW: return n;
+    case ORC_F_DUAL: return 12 * n;
   }
   return -1;
 }
@@ -1555,6 +1601,17 @@ int orc_get(orc* s, int field, double* out, long n) {
           out[(long)j * (nx + 1) + i] = v;
         }
       return 0;
+    case ORC_F_MP_NEW: case ORC_F_DUAL: {
+      long nnode = (long)(nx + 1) * (ny + 1);
+      int nq = field == ORC_F_DUAL ? 12 : 1;
+      for (int q = 0; q < nq; ++q)
+        for (int j = 0; j <= ny; ++j)
+          for (int i = 0; i <= nx; ++i) {
+            int p = NI(s, i, j);
+            out[q * nnode + (long)j * (nx + 1) + i] = field == ORC_F_MP_NEW ? s->mpn[p] : s->dual[q / 3][q % 3][p];
+          }
+      return 0;
+    }
     case ORC_F_VOL_LAGCF: case ORC_F_Q:
       for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i)

@@ -73,8 +73,18 @@ enum {
   ORC_F_XA = 33,      /* [nmat][ny][nx+1] per-material X-face volume flux, signed */
   ORC_F_YA = 34,      /* [nmat][ny+1][nx] per-material Y-face volume flux, signed */
   ORC_F_CA = 35,      /* [nmat][(ny+1)][(nx+1)] per-material corner volume flux */
-  ORC_F_SCLIP = 37    /* [nmat][ny][nx] factor on material a's outgoing volume
+  ORC_F_SCLIP = 37,   /* [nmat][ny][nx] factor on material a's outgoing volume
                          in the last step (1 unless clipped to what it holds) */
+  ORC_F_MP_NEW = 38,  /* [(ny+1)][(nx+1)] remapped nodal mass m_p' of the last
+                         step: m_p plus the signed dual mass fluxes (sections
+                         2.1.1, 2.3); 0 at nodes the dual remap skipped */
+  ORC_F_DUAL = 39     /* [4][3][(ny+1)][(nx+1)] dual fluxes of the last step:
+                         kind 0 the dual X face between nodes (i,j),(i+1,j),
+                         1 the dual Y face between (i,j),(i,j+1), 2 the ++
+                         and 3 the +- dual corner at the centre of cell (i,j);
+                         per kind the mass flux (signed along +x, or +y for
+                         the Y face) and the x and y momentum fluxes (mass
+                         flux times the upwind reconstructed velocity) */
 };
 
 orc* orc_create(const orc_config* cfg, const double* gamma, const double* pinf);
@@ -84,6 +94,11 @@ int orc_init(orc* s, const double* k, const double* rho, const double* p,
              const double* ux, const double* uy);
 /* Prescribed node velocity (re-imposed every step), NULL to clear. */
 int orc_set_prescribed(orc* s, const double* ux, const double* uy);
+/* Test hook for the dual remap (only with a prescribed velocity set): the
+ * flux geometry still follows the prescribed velocity, but the dual remap
+ * runs and carries this node field ([(ny+1)][(nx+1)] each) as u^{lag}
+ * instead of the prescribed one.  NULL, NULL clears it. */
+int orc_set_remap_velocity(orc* s, const double* ux, const double* uy);
 /* One step, dt capped so that t does not pass t_end.  Returns 0 or <0. */
 int orc_step(orc* s, double t_end, double* dt_out);
 int orc_get(orc* s, int field, double* out, long n);
