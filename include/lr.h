@@ -141,6 +141,22 @@ lr_status lr_set_materials(lr_ctx* ctx, int nmat, const lr_material* mats);
 lr_status lr_init(lr_ctx* ctx, const double* k, const double* rho, const double* p,
                   const double* ux, const double* uy);
 
+/* Checkpoint and resume: lr_checkpoint_save copies the context's current
+ * state exactly (the state in the step's own arithmetic type, the cell
+ * sound speeds of the CFL rule, the time, the step count and the time step
+ * in flight) into the caller's host buffer of lr_checkpoint_bytes bytes
+ * (synchronises; LR_ERR_STATE before lr_init, LR_ERR_ARG if the buffer is
+ * too small; a sticky numeric error is returned instead of saving).
+ * lr_checkpoint_load restores such a buffer into a context of the same grid,
+ * material count, precision, remap and corner values (LR_ERR_ARG
+ * otherwise; materials must be set), after which lr_step continues exactly
+ * where the saved run would have: N steps, save, load (in this or a fresh
+ * context), N steps equal 2N steps bit for bit.  The buffer belongs to the
+ * caller; its layout is an 8-word header, the scalars, then the arrays. */
+size_t lr_checkpoint_bytes(const lr_ctx* ctx);
+lr_status lr_checkpoint_save(lr_ctx* ctx, void* host_buf, size_t bytes);
+lr_status lr_checkpoint_load(lr_ctx* ctx, const void* host_buf, size_t bytes);
+
 /* Prescribed node velocity (host arrays [(ny+1)][(nx+1)]), re-imposed every
  * step: the momentum equation and the dual remap are skipped and u^{n+1/2} =
  * u^{lag} = u^{n+1} = the given field (the imposed-velocity tests of section
@@ -230,6 +246,20 @@ int lr_launches_per_step(const lr_ctx* ctx);
 lr_status lr_set_profiling(lr_ctx* ctx, int on);
 int lr_kernel_times(lr_ctx* ctx, const char** names, long* launches, double* ms, int n);
 
+/* Tiled step (on = 1): kernel pairs of the step that otherwise exchange
+ * their intermediate results through device memory run as one kernel over
+ * tiles of the grid, each block staging its tile and a halo of inputs in
+ * shared memory (the stencils of sections 2.1.1, 2.3 and 3.3 reach two cells
+ * or nodes), with the boundary conditions applied once at staging.  The
+ * arithmetic is the same; the rounding differs only in the order of a few
+ * operations the compiler contracts.  Available for the DirectCF remap with
+ * upwind or diagonal corner values (LR_ERR_ARG otherwise); on by default in
+ * LR_FP32, off in LR_FP64 and LR_DF64.  Intermediate per-material flux
+ * fields (LR_F_XA, LR_F_YA, LR_F_CA) of a tiled step hold only the objects
+ * with a mixed donor.  lr_get_tiled returns the current setting. */
+lr_status lr_set_tiled(lr_ctx* ctx, int on);
+int lr_get_tiled(const lr_ctx* ctx);
+
 void lr_destroy(lr_ctx* ctx);
 const char* lr_last_error(const lr_ctx* ctx);
 
@@ -253,7 +283,16 @@ const char* lr_last_error(const lr_ctx* ctx);
  * first call on a device looks up the scratch address on that device (make
  * that first call before any stream capture).  All calls share the scratch,
  * so calls that overlap on the GPU (other streams, other host threads) race:
- * serialise them. */
+ * serialise them.  The scratch address is kept per device for the life of
+ * the process: no call may follow a cudaDeviceReset of that device.
+ * Validation follows lr_create's: LR_ERR_ARG for nx or ny < 2, nmat outside
+ * 1..3, an empty domain, cfl outside (0, 1], a bc other than LR_BC_REFLECT
+ * or LR_BC_PERIODIC, xlo != xhi or ylo != yhi, a periodic direction with
+ * fewer than 3 cells, or a NULL pointer.  A state that is not finite (NaN
+ * or infinite k, rho, e or u) or where a material of full weight has no
+ * real sound speed (c^2 <= 0) gives *dt_out = NaN, so a caller can tell a
+ * bad state from a quiet one (lr_step reports the same states through its
+ * error flags). */
 lr_status lr_cfl_dt_noalloc(const lr_config* cfg, const lr_material* mats, const double* k,
                             const double* rho, const double* e, const double* ux, const double* uy,
                             double* dt_out);
@@ -280,6 +319,16 @@ lr_status lr_cfl_dt_noalloc(const lr_config* cfg, const lr_material* mats, const
  * enqueued, nothing is synchronised.  LR_ERR_ARG: unknown op, or n > 0 with
  * a NULL pointer; LR_ERR_CUDA: the launch failed. */
 enum { LR_ARITH_DIV = 0, LR_ARITH_SQRT = 1 };
+
+/* FP64 throughput probe (a measurement hook; the paper has no counterpart):
+ * blocks x threads threads each run `iters` iterations of eight independent
+ * fused multiply-add chains in double, 16 * iters flops per thread, and
+ * store one double each to dev_out[blocks * threads] (device).  Timed by
+ * the caller (CUDA events on cuda_stream, NULL = the legacy default
+ * stream), it measures the FP64 rate the native-double step is bound by.
+ * LR_ERR_ARG: NULL dev_out, blocks < 1, threads not a multiple of 32 in
+ * [32, 1024], iters < 1; LR_ERR_CUDA: the launch failed. */
+lr_status lr_fp64_fma_probe(double* dev_out, int blocks, int threads, int iters, void* cuda_stream);
 lr_status lr_arith_check(int op, const double* a, const double* b, double* out, size_t n, void* cuda_stream);
 
 #ifdef __cplusplus

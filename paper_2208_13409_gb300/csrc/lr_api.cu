@@ -30,10 +30,11 @@ struct lr_ctx {
   cudaGraphExec_t gexec[2];
   bool gvalid[2];
   bool prof;
+  bool tiled;       // the tiled (fused, shared-memory) kernels replace kernel pairs of the step
   struct Pend { int kid; cudaEvent_t a, b; };
   std::vector<Pend> pend;
-  double acc_ms[LRK_COUNT];
-  long acc_n[LRK_COUNT];
+  double acc_ms[LRK_COUNT + 3];  // per kernel, then the tiled kernels
+  long acc_n[LRK_COUNT + 3];
   double* tmp;      // device scratch for field views (max field size)
   size_t tmp_elems;
   double* rows;     // device scratch for conservation partial sums
@@ -182,6 +183,13 @@ extern "C" lr_status lr_arith_check(int op, const double* a, const double* b, do
   if (n > 0 && (!a || !b || !out)) return LR_ERR_ARG;
   return lr_launch_arith(op, a, b, out, n, static_cast<cudaStream_t>(cuda_stream)) == cudaSuccess ? LR_OK
                                                                                                    : LR_ERR_CUDA;
+}
+
+extern "C" lr_status lr_fp64_fma_probe(double* dev_out, int blocks, int threads, int iters, void* cuda_stream) {
+  if (!dev_out || blocks < 1 || threads < 32 || threads > 1024 || (threads & 31) || iters < 1) return LR_ERR_ARG;
+  return lr_launch_dfma(dev_out, blocks, threads, iters, static_cast<cudaStream_t>(cuda_stream)) == cudaSuccess
+             ? LR_OK
+             : LR_ERR_CUDA;
 }
 
 cudaError_t lr_create_aux_stream(cudaStream_t* s) {
@@ -335,9 +343,34 @@ lr_status check_sticky(lr_ctx* ctx) {
   return LR_OK;
 }
 
+// Timing slots: the step's kernels, then the tiled kernels.
+enum { SLOT_T_LAG = LRK_COUNT, SLOT_T_CELL, SLOT_T_NODE, NSLOT };
+const char* slot_name(int k) {
+  switch (k) {
+    case SLOT_T_LAG: return "lr_t_lagrange";
+    case SLOT_T_CELL: return "lr_t_cell_remap";
+    case SLOT_T_NODE: return "lr_t_node_remap";
+    default: return lr_kernel_names[k];
+  }
+}
+int slot_of(int k) {
+  switch (k) {
+    case LRK_MIXED_PLACE: case LRK_T_MIXED: return LRK_MIXED;  // the interface kernels time as lr_mixed
+    case LRK_T_LAGRANGE: return SLOT_T_LAG;
+    case LRK_T_CELL_REMAP: return SLOT_T_CELL;
+    case LRK_T_NODE_REMAP: return SLOT_T_NODE;
+    default: return k < LRK_COUNT ? k : -1;
+  }
+}
+// The tiled kernels cover the one-step remap with corner fluxes and upwind or
+// diagonal corner values.
+bool tiled_ok(const LrGrid& g) {
+  return g.remap == LR_REMAP_DIRECTCF && (g.corner_kind == LR_CORNER_UPWIND || g.corner_kind == LR_CORNER_DIAG);
+}
+
 cudaError_t launch_on(lr_ctx* ctx, int k, const LrGrid& g, const LrState& cur, const LrState& nxt, cudaStream_t st) {
-  int slot = k == LRK_MIXED_PLACE ? (int)LRK_MIXED : k;  // both interface kernels time as lr_mixed
-  if (!ctx->prof || slot >= LRK_COUNT) return lr_launch(k, g, cur, nxt, ctx->w, st);
+  int slot = slot_of(k);
+  if (!ctx->prof || slot < 0) return lr_launch(k, g, cur, nxt, ctx->w, st);
   lr_ctx::Pend p;
   p.kid = slot;
   cudaEventCreate(&p.a);
@@ -396,6 +429,18 @@ cudaError_t launch_one(lr_ctx* ctx, int k, const LrGrid& g, const LrState& cur, 
 cudaError_t enqueue_step(lr_ctx* ctx, int from) {
   const LrState& cur = ctx->st[from];
   const LrState& nxt = ctx->st[1 - from];
+  if (ctx->tiled) {
+    // Tiled step on one stream: the Lagrange phase and remap geometry; the
+    // interface work of the mixed cells; the material fluxes and cell
+    // update; the dual remap and node update (it reads the new sound speeds
+    // for the CFL rule).
+    const LrGrid& g = ctx->g;
+    cudaError_t e;
+    if ((e = launch_on(ctx, LRK_T_LAGRANGE, g, cur, nxt, ctx->stream)) != cudaSuccess) return e;
+    if (g.M > 1 && (e = launch_on(ctx, LRK_T_MIXED, g, cur, nxt, ctx->stream)) != cudaSuccess) return e;
+    if ((e = launch_on(ctx, LRK_T_CELL_REMAP, g, cur, nxt, ctx->stream)) != cudaSuccess) return e;
+    return launch_on(ctx, LRK_T_NODE_REMAP, g, cur, nxt, ctx->stream);
+  }
   if (ctx->g.remap != LR_REMAP_AD) {
     for (int k = 0; k < LRK_COUNT; ++k) {
       cudaError_t e = launch_one(ctx, k, ctx->g, cur, nxt);
@@ -480,7 +525,9 @@ lr_status create_common(const lr_config* cfg, void* mem, size_t bytes, bool own,
     return LR_ERR_CUDA;
   }
   ctx->sticky = LR_OK;
-  if (cudaMemcpyAsync(const_cast<LrGrid*>(ctx->w.gdev), &ctx->g, sizeof(LrGrid), cudaMemcpyHostToDevice,
+  ctx->tiled = tiled_ok(ctx->g) && ctx->g.mode == LR_MODE_FP32;
+  if (lr_tiled_setup() != cudaSuccess ||
+      cudaMemcpyAsync(const_cast<LrGrid*>(ctx->w.gdev), &ctx->g, sizeof(LrGrid), cudaMemcpyHostToDevice,
                       ctx->stream) != cudaSuccess ||
       lr_launch_reset(ctx->g.mode, ctx->w, 1, ctx->stream) != cudaSuccess ||
       cudaMemsetAsync(ctx->w.pux, 0, lr_real_size(ctx->g.mode) * (cfg->nx + 1) * (cfg->ny + 1), ctx->stream) != cudaSuccess ||
@@ -572,6 +619,96 @@ lr_status lr_init(lr_ctx* ctx, const double* k, const double* rho, const double*
     ctx->sticky = LR_OK;
     return LR_ERR_ARG;
   }
+  ctx->inited = true;
+  return LR_OK;
+}
+
+// ---------------------------------------------------------- checkpoints
+// Layout of a checkpoint: a header of 8 int64 (magic, nx, ny, nmat,
+// precision, element size, remap, corner values), the scalars of the
+// simulation (LR_NSCAL doubles), then in the step's element type the state
+// (k, rho, e per material [nmat][ny][nx], ux, uy [(ny+1)][(nx+1)]), the cell
+// sound speeds [ny][nx] and the dt of the step in flight (one element).
+static const long long LR_CKPT_MAGIC = 0x4c52434b50543031ll;  // "LRCKPT01"
+static size_t ckpt_bytes(const lr_ctx* c) {
+  size_t es = lr_real_size(c->g.mode);
+  size_t nc = (size_t)c->g.nx * c->g.ny, nn = (size_t)(c->g.nx + 1) * (c->g.ny + 1);
+  return 8 * sizeof(long long) + LR_NSCAL * sizeof(double) + es * (3 * c->g.M * nc + 2 * nn + nc + 1);
+}
+
+size_t lr_checkpoint_bytes(const lr_ctx* ctx) { return ctx ? ckpt_bytes(ctx) : 0; }
+
+lr_status lr_checkpoint_save(lr_ctx* ctx, void* host_buf, size_t bytes) {
+  if (!ctx || !host_buf) return LR_ERR_ARG;
+  if (!ctx->inited) { setmsg(ctx, "lr_checkpoint_save before lr_init"); return LR_ERR_STATE; }
+  if (bytes < ckpt_bytes(ctx)) { setmsg(ctx, "checkpoint buffer too small"); return LR_ERR_ARG; }
+  lr_status st = check_sticky(ctx);
+  if (st != LR_OK) return st;
+  const LrGrid& g = ctx->g;
+  long long* h = static_cast<long long*>(host_buf);
+  h[0] = LR_CKPT_MAGIC; h[1] = g.nx; h[2] = g.ny; h[3] = g.M; h[4] = g.mode;
+  h[5] = (long long)lr_real_size(g.mode); h[6] = g.remap; h[7] = g.corner_kind;
+  char* p = static_cast<char*>(host_buf) + 8 * sizeof(long long);
+  size_t es = lr_real_size(g.mode);
+  size_t nc = (size_t)g.nx * g.ny, nn = (size_t)(g.nx + 1) * (g.ny + 1);
+  cudaStream_t s = ctx->stream;
+  CK(cudaMemcpyAsync(p, ctx->w.scal, LR_NSCAL * sizeof(double), cudaMemcpyDeviceToHost, s), "checkpoint");
+  p += LR_NSCAL * sizeof(double);
+  const LrState& cs = ctx->st[ctx->cur];
+  for (int a = 0; a < g.M; ++a) {
+    void* src[3] = {cs.k[a], cs.r[a], cs.e[a]};
+    for (int q = 0; q < 3; ++q) {
+      CK(cudaMemcpyAsync(p, src[q], es * nc, cudaMemcpyDeviceToHost, s), "checkpoint");
+      p += es * nc;
+    }
+  }
+  CK(cudaMemcpyAsync(p, cs.ux, es * nn, cudaMemcpyDeviceToHost, s), "checkpoint");
+  p += es * nn;
+  CK(cudaMemcpyAsync(p, cs.uy, es * nn, cudaMemcpyDeviceToHost, s), "checkpoint");
+  p += es * nn;
+  CK(cudaMemcpyAsync(p, ctx->w.cc, es * nc, cudaMemcpyDeviceToHost, s), "checkpoint");
+  p += es * nc;
+  CK(cudaMemcpyAsync(p, ctx->w.dtR, es, cudaMemcpyDeviceToHost, s), "checkpoint");
+  CK(cudaStreamSynchronize(s), "checkpoint");
+  return LR_OK;
+}
+
+lr_status lr_checkpoint_load(lr_ctx* ctx, const void* host_buf, size_t bytes) {
+  if (!ctx || !host_buf) return LR_ERR_ARG;
+  if (!ctx->have_mats) { setmsg(ctx, "lr_checkpoint_load before lr_set_materials"); return LR_ERR_STATE; }
+  const LrGrid& g = ctx->g;
+  const long long* h = static_cast<const long long*>(host_buf);
+  if (bytes < 8 * sizeof(long long) || h[0] != LR_CKPT_MAGIC) { setmsg(ctx, "not a checkpoint"); return LR_ERR_ARG; }
+  if (h[1] != g.nx || h[2] != g.ny || h[3] != g.M || h[4] != g.mode || h[5] != (long long)lr_real_size(g.mode) ||
+      h[6] != g.remap || h[7] != g.corner_kind || bytes < ckpt_bytes(ctx)) {
+    setmsg(ctx, "checkpoint of another configuration");
+    return LR_ERR_ARG;
+  }
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  const char* p = static_cast<const char*>(host_buf) + 8 * sizeof(long long);
+  size_t es = lr_real_size(g.mode);
+  size_t nc = (size_t)g.nx * g.ny, nn = (size_t)(g.nx + 1) * (g.ny + 1);
+  cudaStream_t s = ctx->stream;
+  CK(lr_launch_reset(g.mode, ctx->w, 1, s), "reset");
+  CK(cudaMemcpyAsync(ctx->w.scal, p, LR_NSCAL * sizeof(double), cudaMemcpyHostToDevice, s), "restore");
+  p += LR_NSCAL * sizeof(double);
+  const LrState& cs = ctx->st[ctx->cur];
+  for (int a = 0; a < g.M; ++a) {
+    void* dst[3] = {cs.k[a], cs.r[a], cs.e[a]};
+    for (int q = 0; q < 3; ++q) {
+      CK(cudaMemcpyAsync(dst[q], p, es * nc, cudaMemcpyHostToDevice, s), "restore");
+      p += es * nc;
+    }
+  }
+  CK(cudaMemcpyAsync(cs.ux, p, es * nn, cudaMemcpyHostToDevice, s), "restore");
+  p += es * nn;
+  CK(cudaMemcpyAsync(cs.uy, p, es * nn, cudaMemcpyHostToDevice, s), "restore");
+  p += es * nn;
+  CK(cudaMemcpyAsync(ctx->w.cc, p, es * nc, cudaMemcpyHostToDevice, s), "restore");
+  p += es * nc;
+  CK(cudaMemcpyAsync(ctx->w.dtR, p, es, cudaMemcpyHostToDevice, s), "restore");
+  CK(cudaStreamSynchronize(s), "restore");
+  ctx->sticky = LR_OK;
   ctx->inited = true;
   return LR_OK;
 }
@@ -724,15 +861,32 @@ int lr_launches_per_step(const lr_ctx* ctx) {
   if (!ctx) return 0;
   // the interface work is two kernels (placement, then the flux split)
   int one = (int)LRK_COUNT + (ctx->g.M == 1 ? -1 : 1);
+  // tiled: t_end/dt, Lagrange, interface work (two or more materials), cell
+  // remap, node remap
+  if (ctx->tiled) return ctx->g.M == 1 ? 4 : 5;
   return 1 + one + (ctx->g.remap == LR_REMAP_AD ? one - 1 : 0);
 }
+
+lr_status lr_set_tiled(lr_ctx* ctx, int on) {
+  if (!ctx) return LR_ERR_ARG;
+  if (on && !tiled_ok(ctx->g)) {
+    setmsg(ctx, "the tiled step covers the DirectCF remap with upwind or diagonal corners only");
+    return LR_ERR_ARG;
+  }
+  CK(cudaStreamSynchronize(ctx->stream), "sync");
+  ctx->tiled = on != 0;
+  drop_graphs(ctx);
+  return LR_OK;
+}
+
+int lr_get_tiled(const lr_ctx* ctx) { return ctx && ctx->tiled ? 1 : 0; }
 
 lr_status lr_set_profiling(lr_ctx* ctx, int on) {
   if (!ctx) return LR_ERR_ARG;
   CK(cudaStreamSynchronize(ctx->stream), "sync");
   for (auto& p : ctx->pend) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
   ctx->pend.clear();
-  for (int k = 0; k < LRK_COUNT; ++k) { ctx->acc_ms[k] = 0.0; ctx->acc_n[k] = 0; }
+  for (int k = 0; k < NSLOT; ++k) { ctx->acc_ms[k] = 0.0; ctx->acc_n[k] = 0; }
   ctx->prof = on != 0;
   return LR_OK;
 }
@@ -747,13 +901,13 @@ int lr_kernel_times(lr_ctx* ctx, const char** names, long* launches, double* ms,
     cudaEventDestroy(p.b);
   }
   ctx->pend.clear();
-  int m = n < (int)LRK_COUNT ? n : (int)LRK_COUNT;
+  int m = n < (int)NSLOT ? n : (int)NSLOT;
   for (int k = 0; k < m; ++k) {
-    if (names) names[k] = lr_kernel_names[k];
+    if (names) names[k] = slot_name(k);
     if (launches) launches[k] = ctx->acc_n[k];
     if (ms) ms[k] = ctx->acc_ms[k];
   }
-  return LRK_COUNT;
+  return NSLOT;
 }
 
 void lr_destroy(lr_ctx* ctx) {

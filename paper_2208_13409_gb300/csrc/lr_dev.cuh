@@ -153,8 +153,17 @@ enum LrKernelId {
   LRK_PREPARE = 100,   // initial state from the staging area
   LRK_CFL_ONLY = 101,  // CFL rule from the current state
   LRK_SWEEP_PREP = 102, // alternate directions: the first sweep's result as the second's input
-  LRK_MIXED_PLACE = 103 // interface lines of the mixed cells; LRK_MIXED then splits their fluxes
+  LRK_MIXED_PLACE = 103, // interface lines of the mixed cells; LRK_MIXED then splits their fluxes
+  // tiled step (lone simulations): fused kernel pairs over shared-memory tiles
+  LRK_T_NODE_REMAP = 110,  // lr_dual_flux + lr_node_update
+  LRK_T_CELL_REMAP = 111,  // lr_mat_flux + lr_cell_update
+  LRK_T_LAGRANGE = 112,    // lr_cell_pre + lr_node_half + lr_cell_lag + lr_cell_cf
+  LRK_T_MIXED = 113        // lb_mixed_place + lb_mixed (interface lines and flux split) in one launch
 };
+// Dynamic shared-memory limits of the tiled kernels (once per device, before
+// their first launch).
+cudaError_t lr_tiled_setup();
+
 // Iteration domains of the kernels (tile tables of a batch are per domain).
 enum { LR_DOM_CELLS = 0, LR_DOM_NODES, LR_DOM_DUAL, LR_DOM_NODES_ALL, LR_NDOM };
 int lr_kernel_domain(int kid);
@@ -190,6 +199,7 @@ cudaError_t lr_launch_view(const LrGrid& g, const void* src, double* dst, size_t
 cudaError_t lr_launch_mixture(const LrGrid& g, const LrState& st, double* dst, int which, cudaStream_t s);
 cudaError_t lr_launch_cons(const LrGrid& g, const LrState& st, double* rows, double* dst, cudaStream_t s);
 cudaError_t lr_launch_arith(int op, const double* a, const double* b, double* out, size_t n, cudaStream_t s);
+cudaError_t lr_launch_dfma(double* out, int blocks, int threads, int iters, cudaStream_t s);
 cudaError_t lr_launch_corner_debug(const LrGrid& g, const LrWork& w, double* fc_out, double* mc_out,
                                    cudaStream_t s);
 cudaError_t lr_launch_cuts(const LrGrid& g, const LrState& prev, const LrWork& w, double* dst, cudaStream_t s);

@@ -19,6 +19,7 @@
 #include "lr_dev.cuh"
 #include "lr_real.cuh"
 #include <math.h>
+#include <type_traits>
 
 const char* const lr_kernel_names[LRK_COUNT] = {
   "lr_cell_pre", "lr_node_half", "lr_cell_lag", "lr_cell_cf", "lr_mixed", "lr_mat_flux",
@@ -235,11 +236,16 @@ __device__ __forceinline__ R vl_term(R dm, R dp, R hm, R hp, R X) {
 }
 
 // --------------------------------------------------- half-plane geometry
+// The interface geometry runs in double in every arithmetic mode, with IEEE
+// divisions and square roots.
+__device__ __forceinline__ double gdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ double gsqrt(double x) { return sqrt(x); }
+
 // Area of the axis-aligned rectangle [x0,x1]x[y0,y1] on the side x.n <= d:
 // with a <= b the extents of x.n along the two edge directions and s the
 // distance of the line from the lowest corner, the area is s^2/(2|nx ny|)
 // (triangle), W H (2s-a)/(2b) (trapezoid) or W H - (a+b-s)^2/(2|nx ny|).
-__host__ __device__ double rect_half_area(double x0, double x1, double y0, double y1,
+__device__ double rect_half_area(double x0, double x1, double y0, double y1,
                                  double nx, double ny, double d) {
   double W = x1 - x0, H = y1 - y0;
   double ax = fabs(nx) * W, by = fabs(ny) * H;
@@ -248,37 +254,38 @@ __host__ __device__ double rect_half_area(double x0, double x1, double y0, doubl
   double A = W * H;
   if (s <= 0.0) return 0.0;
   if (s >= a + b) return A;
-  if (a <= 0.0) return A * (s / b);
+  if (a <= 0.0) return A * gdiv(s, b);
   double pq = fabs(nx) * fabs(ny);
-  if (s < a) return 0.5 * s * s / pq;
-  if (s <= b) return A * (2.0 * s - a) / (2.0 * b);
+  if (s < a) return gdiv(0.5 * s * s, pq);
+  if (s <= b) return gdiv(A * (2.0 * s - a), 2.0 * b);
   double r = a + b - s;
-  return A - 0.5 * r * r / pq;
+  return A - gdiv(0.5 * r * r, pq);
 }
 // Inverse of the above: the line constant d giving area fraction k (0<k<1).
-__host__ __device__ double rect_plic(double x0, double x1, double y0, double y1, double nx, double ny,
+__device__ double rect_plic(double x0, double x1, double y0, double y1, double nx, double ny,
                             double k) {
   double W = x1 - x0, H = y1 - y0;
   double ax = fabs(nx) * W, by = fabs(ny) * H;
   double a = fmin(ax, by), b = fmax(ax, by);
   double s0 = (nx >= 0.0 ? x0 : x1) * nx + (ny >= 0.0 ? y0 : y1) * ny;
   double s;
+  // branches: k <= a/(2b) (triangle), k <= 1 - a/(2b) (trapezoid), else
   if (a <= 0.0) s = k * b;
-  else if (k <= 0.5 * a / b) s = sqrt(2.0 * a * b * k);
-  else if (k <= 1.0 - 0.5 * a / b) s = k * b + 0.5 * a;
-  else s = a + b - sqrt(2.0 * a * b * (1.0 - k));
+  else if (2.0 * k * b <= a) s = gsqrt(2.0 * a * b * k);
+  else if (2.0 * (1.0 - k) * b >= a) s = k * b + 0.5 * a;
+  else s = a + b - gsqrt(2.0 * a * b * (1.0 - k));
   return s0 + s;
 }
 
 // Small convex polygons (three-material cells only).
 struct Poly { int n; double x[8], y[8]; };
-__host__ __device__ void poly_rect(Poly& p, double x0, double x1, double y0, double y1) {
+__device__ void poly_rect(Poly& p, double x0, double x1, double y0, double y1) {
   p.n = 4;
   p.x[0] = x0; p.y[0] = y0; p.x[1] = x1; p.y[1] = y0;
   p.x[2] = x1; p.y[2] = y1; p.x[3] = x0; p.y[3] = y1;
 }
 // keep the part with sgn * (x.n - d) <= 0
-__host__ __device__ void poly_clip(const Poly& in, double nx, double ny, double d, double sgn, Poly& out) {
+__device__ void poly_clip(const Poly& in, double nx, double ny, double d, double sgn, Poly& out) {
   out.n = 0;
   for (int a = 0; a < in.n; ++a) {
     int b = a + 1 == in.n ? 0 : a + 1;
@@ -286,14 +293,14 @@ __host__ __device__ void poly_clip(const Poly& in, double nx, double ny, double 
     double fb = sgn * (in.x[b] * nx + in.y[b] * ny - d);
     if (fa <= 0.0 && out.n < 8) { out.x[out.n] = in.x[a]; out.y[out.n] = in.y[a]; ++out.n; }
     if (((fa < 0.0 && fb > 0.0) || (fa > 0.0 && fb < 0.0)) && out.n < 8) {
-      double t = fa / (fa - fb);
+      double t = gdiv(fa, fa - fb);
       out.x[out.n] = in.x[a] + t * (in.x[b] - in.x[a]);
       out.y[out.n] = in.y[a] + t * (in.y[b] - in.y[a]);
       ++out.n;
     }
   }
 }
-__host__ __device__ double poly_area(const Poly& p) {
+__device__ double poly_area(const Poly& p) {
   if (p.n < 3) return 0.0;
   double s = 0.0;
   for (int a = 0; a < p.n; ++a) {
@@ -302,7 +309,7 @@ __host__ __device__ double poly_area(const Poly& p) {
   }
   return 0.5 * fabs(s);
 }
-__host__ __device__ double poly_half_area(const Poly& p, double nx, double ny, double d) {
+__device__ double poly_half_area(const Poly& p, double nx, double ny, double d) {
   Poly q;
   poly_clip(p, nx, ny, d, 1.0, q);
   return poly_area(q);
@@ -346,12 +353,12 @@ __device__ __noinline__ double poly_plic8(const Poly& p, double nx, double ny, d
   double T = target - alo;
   double t;
   if (fabs(c2) <= 1e-14 * fabs(c1)) {
-    t = c1 != 0.0 ? T / c1 : 0.0;
+    t = c1 != 0.0 ? gdiv(T, c1) : 0.0;
   } else {
     double disc = c1 * c1 + 4.0 * c2 * T;
     disc = disc > 0.0 ? disc : 0.0;
-    double sq = sqrt(disc);
-    t = c1 >= 0.0 ? 2.0 * T / (c1 + sq) : (-c1 + sq) / (2.0 * c2);
+    double sq = gsqrt(disc);
+    t = c1 >= 0.0 ? gdiv(2.0 * T, c1 + sq) : gdiv(-c1 + sq, 2.0 * c2);
   }
   t = fmin(fmax(t, 0.0), 1.0);
   return blo + t * h;
@@ -367,8 +374,8 @@ __device__ void youngs(const LrGrid& g, const R* K, int i, int j, double& nxv, d
   double k0p = k(0, 1), k0m = k(0, -1);
   double gx = ((kpp + 2.0 * kp0 + kpm) - (kmp + 2.0 * km0 + kmm)) * g.inv8dx;
   double gy = ((kpp + 2.0 * k0p + kmp) - (kpm + 2.0 * k0m + kmm)) * g.inv8dy;
-  double gn = sqrt(gx * gx + gy * gy);
-  if (gn > 0.0) { nxv = -gx / gn; nyv = -gy / gn; } else { nxv = 1.0; nyv = 0.0; }
+  double gn = gsqrt(gx * gx + gy * gy);
+  if (gn > 0.0) { nxv = gdiv(-gx, gn); nyv = gdiv(-gy, gn); } else { nxv = 1.0; nyv = 0.0; }
 }
 
 // Corner donor table (section 3.3): returns 0 when the corner carries no flux.
@@ -789,6 +796,51 @@ __device__ __forceinline__ void place_at(const LrGrid& g, const LrStateT<R>& cur
   }
 }
 
+// The same interface lines as place_at (DirectCF remap: the Lagrangian
+// rectangle), with the eight lanes of the group sharing the work instead of
+// repeating it: lane 0 (and lane 1 for a second cut) forms a Youngs normal,
+// lane 0 the first line constant, broadcast to the group; the nested cut of a
+// three-material cell spreads its vertex levels over the lanes as before.
+template <class R, int M>
+__device__ __forceinline__ void place_lanes(const LrGrid& g, const LrStateT<R>& cur, const LrWorkT<R>& w, int c,
+                                            bool valid, int lane) {
+  using O = RealOps<R>;
+  const unsigned gm = 0xffu << (threadIdx.x & 24u);
+  int i = (c - g.coff) % g.nx, j = (c - g.coff) / g.nx;
+  double kk[M];
+  int np = 0, order[LR_MAXM] = {0, 0, 0};
+  unsigned msk = w.mask[c];
+#pragma unroll
+  for (int a = 0; a < M; ++a) {
+    kk[a] = (msk & (1u << a)) ? O::todouble(cur.k[a][c]) : 0.0;
+    if (msk & (1u << a)) order[np++] = a;
+  }
+  double wxc = O::todouble(w.wx[c]), wyc = O::todouble(w.wy[c]);
+  double xl = 0.5 * g.dx - 0.5 * wxc + O::todouble(w.ox[c]), xr = xl + wxc;
+  double yb = 0.5 * g.dy - 0.5 * wyc + O::todouble(w.oy[c]), yt = yb + wyc;
+  int ncut = np - 1;
+  double nxv = 1.0, nyv = 0.0, d0 = 0.0;
+  if (lane < ncut) youngs(g, cur.k[order[lane]], i, j, nxv, nyv);
+  if (lane == 0) d0 = rect_plic(xl, xr, yb, yt, nxv, nyv, kk[order[0]]);
+  double n0x = __shfl_sync(gm, nxv, 0, 8), n0y = __shfl_sync(gm, nyv, 0, 8);
+  double n1x = __shfl_sync(gm, nxv, 1, 8), n1y = __shfl_sync(gm, nyv, 1, 8);
+  d0 = __shfl_sync(gm, d0, 0, 8);
+  double d1 = 0.0;
+  if (ncut == 2) {  // uniform over the group
+    Poly rect, rest;
+    poly_rect(rect, xl, xr, yb, yt);
+    poly_clip(rect, n0x, n0y, d0, -1.0, rest);
+    double target = kk[order[1]] * (wxc * wyc);
+    double ra = poly_area(rest);
+    if (target > ra) target = ra;
+    d1 = poly_plic8(rest, n1x, n1y, target, lane);
+  }
+  if (valid && lane == 0) {
+    w.cut[0][c] = n0x; w.cut[1][c] = n0y; w.cut[2][c] = d0;
+    if (ncut == 2) { w.cut[3][c] = n1x; w.cut[4][c] = n1y; w.cut[5][c] = d1; }
+  }
+}
+
 template <class R, int M>
 __device__ __forceinline__ void mixed_at(const LrGrid& g, const LrStateT<R>& cur, const LrWorkT<R>& w, int c,
                                          bool valid, int lane, int L) {
@@ -863,7 +915,7 @@ __device__ __forceinline__ void mixed_at(const LrGrid& g, const LrStateT<R>& cur
       sc[a] = 1.0;
       if (a == dom) continue;
       double avail = kk[a] * v;
-      if (o[a] > avail) { sc[a] = avail / o[a]; clip = true; }
+      if (o[a] > avail) { sc[a] = gdiv(avail, o[a]); clip = true; }
     }
     if (!valid) return;
     // ---- final fluxes of this donor's objects (lr_mat_flux leaves objects
@@ -1887,11 +1939,8 @@ __global__ void lr_corner_dbg(LrGrid g, LrWorkT<R> w, double* fc, double* mcn) {
   int o = j * (g.nx + 1) + i;
   int n = nix(g, i, j).idx;
   if (fc) fc[o] = fabs(O::todouble(w.ddx[n]) * O::todouble(w.ddy[n]));
-  if (mcn) {
-    double m = 0.0;
-    for (int a = 0; a < g.M; ++a) m += O::todouble(w.cMm[a][n]);
-    mcn[o] = m;
-  }
+  if (mcn)  // total corner mass: one of the two signed diagonal fluxes is zero
+    mcn[o] = fabs(O::todouble(w.Mpp[n])) + fabs(O::todouble(w.Mpm[n]));
 }
 // Interface lines of the last step, masked to the cells that were mixed
 // (the pre-step state is still in the other half of the double buffer).
@@ -2054,15 +2103,939 @@ __global__ void __launch_bounds__(128) lb_mixed(const LrGrid* __restrict__ gs, L
   mixed_loop<R, M>([&](int e) -> const LrGrid& { return gs[w.minst[e]]; }, cur, w, lanes, mslot, moff);
 }
 
+// ============================================================ tiled step
+// The tiled step fuses kernel pairs that the unfused step links through HBM
+// workspace arrays.  A block owns a tile of TX x TY points; it first stages
+// every input its stencils reach (the tile plus a halo) in shared memory,
+// applying the boundary conditions once per staged value (mirror with the
+// sign of mirrored vector components and signed fluxes flipped, or wrap),
+// then evaluates the flux objects its points need into shared memory (an
+// object on the tile's edge is evaluated by both tiles that share it), and
+// finally updates its own points.  Staging and object loops run over the
+// block's threads linearly; the update runs one thread per point.
+constexpr int TTX = 32, TTY = 8, TTHREADS = TTX * TTY;
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+// Staging coordinates beyond the reach of any live point are clamped to the
+// band the index maps handle (two cells or nodes beyond the grid); values
+// staged there are never used by a live output.
+__device__ __forceinline__ int nclamp(int i, int n) { return clampi(i, -2, n + 2); }
+__device__ __forceinline__ int cclamp(int i, int n) { return clampi(i, -2, n + 1); }
+
+// Index maps for staging: a block whose staged region (two cells or nodes
+// beyond its tile) lies inside the grid reads with plain indices (IN);
+// other blocks clamp to the band the maps handle and map.
+__device__ __forceinline__ bool tile_interior(const LrGrid& g, int i0, int j0) {
+  return i0 >= 2 && i0 + TTX + 1 <= g.nx - 1 && j0 >= 2 && j0 + TTY + 1 <= g.ny - 1;
+}
+template <bool IN> __device__ __forceinline__ Ix snix(const LrGrid& g, int i, int j) {
+  if (IN) return Ix{g.noff + j * (g.nx + 1) + i, 0, 0};
+  return nix(g, nclamp(i, g.nx), nclamp(j, g.ny));
+}
+template <bool IN> __device__ __forceinline__ Ix scix(const LrGrid& g, int i, int j) {
+  if (IN) return Ix{g.coff + j * g.nx + i, 0, 0};
+  return cix(g, cclamp(i, g.nx), cclamp(j, g.ny));
+}
+template <bool IN> __device__ __forceinline__ Ix sxix(const LrGrid& g, int i, int j) {
+  if (IN) return Ix{g.noff + j * (g.nx + 1) + i, 0, 0};
+  return xix(g, nclamp(i, g.nx), cclamp(j, g.ny));
+}
+template <bool IN> __device__ __forceinline__ Ix syix(const LrGrid& g, int i, int j) {
+  if (IN) return Ix{g.noff + j * g.nx + i, 0, 0};
+  return yix(g, cclamp(i, g.nx), nclamp(j, g.ny));
+}
+
+// Data a dual object reads, with the boundary conditions applied, from a
+// staged tile: primary X- and Y-face mass fluxes (signed along +x, +y),
+// the node corner mass fluxes (pp, pm), node displacements and u^{lag}.
+template <class R>
+struct DualTile {
+  const R *ux, *uy, *dx_, *dy_, *mx_, *my_, *pp_, *pm_;
+  int oi, oj, sw;  // grid index of the staged slot 0 and the staged row width
+  __device__ __forceinline__ int at(int a, int b) const { return (b - oj) * sw + (a - oi); }
+  __device__ __forceinline__ R mx(int a, int b) const { return mx_[at(a, b)]; }
+  __device__ __forceinline__ R my(int a, int b) const { return my_[at(a, b)]; }
+  __device__ __forceinline__ void cp(int a, int b, R& pp, R& pm) const { pp = pp_[at(a, b)]; pm = pm_[at(a, b)]; }
+  __device__ __forceinline__ R dx(int a, int b) const { return dx_[at(a, b)]; }
+  __device__ __forceinline__ R dy(int a, int b) const { return dy_[at(a, b)]; }
+  __device__ __forceinline__ R vx(int a, int b) const { return ux[at(a, b)]; }
+  __device__ __forceinline__ R vy(int a, int b) const { return uy[at(a, b)]; }
+};
+
+// Dual X face (xf = 1) between nodes (i,j),(i+1,j) or dual Y face (xf = 0)
+// between (i,j),(i,j+1) (sections 2.1.1 and 2.3): mass flux Dm = 1/4 of the
+// four primary face mass fluxes around it, momentum fluxes Dm u with u^{lag}
+// of the upwind node reconstructed on the dual mesh (the arithmetic of
+// dual_flux_at and recon_dual_face2, through an accessor).
+template <class R, class A>
+__device__ __forceinline__ void dual_face_obj(const LrGrid& g, const KC<R>& kc, const A& ax, int i, int j, int xf,
+                                              R& Dm, R& px, R& py) {
+  using O = RealOps<R>;
+  const R Z = O::c(0.0f), H = O::c(0.5f), Q4 = O::c(0.25f);
+  Dm = xf ? Q4 * (ax.mx(i, j - 1) + ax.mx(i + 1, j - 1) + ax.mx(i, j) + ax.mx(i + 1, j))
+          : Q4 * (ax.my(i - 1, j) + ax.my(i - 1, j + 1) + ax.my(i, j) + ax.my(i, j + 1));
+  px = Z; py = Z;
+  if (O::zero(Dm)) return;
+  bool fwd = O::pos(Dm);
+  int qi = xf ? (fwd ? i : i + 1) : i, qj = xf ? j : (fwd ? j : j + 1);
+  R fd = xf ? H * (ax.dx(i, j) + ax.dx(i + 1, j)) : H * (ax.dy(i, j) + ax.dy(i, j + 1));
+  R vx, vy;
+  if (g.face_o2) {
+    int mi = xf, mj = 1 - xf;
+    R d0 = xf ? ax.dx(qi, qj) : ax.dy(qi, qj);
+    R dp = xf ? ax.dx(qi + mi, qj + mj) : ax.dy(qi + mi, qj + mj);
+    R dm = xf ? ax.dx(qi - mi, qj - mj) : ax.dy(qi - mi, qj - mj);
+    R h = xf ? kc.dx : kc.dy;
+    R wd = h + H * (dp - dm);
+    R hm = h + d0 - dm, hp = h + dp - d0;
+    R X = O::flip(!fwd, wd) - fd;
+    R u0 = ax.vx(qi, qj), up = ax.vx(qi + mi, qj + mj), um = ax.vx(qi - mi, qj - mj);
+    vx = u0 + vl_term(u0 - um, up - u0, hm, hp, X);
+    R v0 = ax.vy(qi, qj), vp = ax.vy(qi + mi, qj + mj), vm = ax.vy(qi - mi, qj - mj);
+    vy = v0 + vl_term(v0 - vm, vp - v0, hm, hp, X);
+  } else {
+    vx = ax.vx(qi, qj);
+    vy = ax.vy(qi, qj);
+  }
+  px = Dm * vx;
+  py = Dm * vy;
+}
+
+// The two dual corners at the centre of cell (i,j): ++ (nodes (i,j),
+// (i+1,j+1)) and +- (nodes (i,j+1), (i+1,j)), each 1/4 of its four nodes'
+// corner mass fluxes along that diagonal, momentum with the diagonal
+// reconstruction on the dual mesh (the arithmetic of dual_flux_at).
+template <class R, class A>
+__device__ __forceinline__ void dual_corner_obj(const LrGrid& g, const KC<R>& kc, const A& ax, int i, int j,
+                                                R* opp, R* opm) {
+  using O = RealOps<R>;
+  const R Z = O::c(0.0f), H = O::c(0.5f), Q4 = O::c(0.25f);
+  R p0, m0, p1, m1, p2, m2, p3, m3;
+  ax.cp(i, j, p0, m0); ax.cp(i + 1, j, p1, m1); ax.cp(i, j + 1, p2, m2); ax.cp(i + 1, j + 1, p3, m3);
+  R cdx = Q4 * (ax.dx(i, j) + ax.dx(i + 1, j) + ax.dx(i, j + 1) + ax.dx(i + 1, j + 1));
+  R cdy = Q4 * (ax.dy(i, j) + ax.dy(i + 1, j) + ax.dy(i, j + 1) + ax.dy(i + 1, j + 1));
+  R D0 = Q4 * (p0 + p1 + p2 + p3), D1 = Q4 * (m0 + m1 + m2 + m3);
+  bool on0 = !O::zero(D0), on1 = !O::zero(D1);
+  R px0 = Z, py0 = Z, px1 = Z, py1 = Z;
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    if (!(pass == 0 ? (on0 || on1) : (on0 && on1))) continue;
+    bool pp = pass == 0 && on0;
+    R Dm = pp ? D0 : D1;
+    bool fwd = O::pos(Dm);
+    int ai = i, aj = pp ? j : j + 1, bi = i + 1, bj = pp ? j + 1 : j;
+    int qi = fwd ? ai : bi, qj = fwd ? aj : bj;
+    R vx = ax.vx(qi, qj), vy = ax.vy(qi, qj);
+    if (g.corner_o2) {
+      int sj = pp ? 1 : -1;
+      R sdy = O::flip(!pp, kc.dy);
+      R dx0 = ax.dx(qi, qj), dy0 = ax.dy(qi, qj);
+      R dxp = ax.dx(qi + 1, qj + sj), dyp = ax.dy(qi + 1, qj + sj);
+      R dxm = ax.dx(qi - 1, qj - sj), dym = ax.dy(qi - 1, qj - sj);
+      R hp = (kc.dx + dxp - dx0) * kc.dx + (sdy + dyp - dy0) * sdy;
+      R hm = (kc.dx + dx0 - dxm) * kc.dx + (sdy + dy0 - dym) * sdy;
+      R wxq = kc.dx + H * (ax.dx(qi + 1, qj) - ax.dx(qi - 1, qj));
+      R wyq = kc.dy + H * (ax.dy(qi, qj + 1) - ax.dy(qi, qj - 1));
+      R wsum = wxq * kc.dx + wyq * kc.dy;
+      R X = O::flip(!fwd, wsum) - (cdx * kc.dx + cdy * sdy);
+      R uxp = ax.vx(qi + 1, qj + sj), uxm = ax.vx(qi - 1, qj - sj);
+      R uyp = ax.vy(qi + 1, qj + sj), uym = ax.vy(qi - 1, qj - sj);
+      vx = vx + vl_term(vx - uxm, uxp - vx, hm, hp, X);
+      vy = vy + vl_term(vy - uym, uyp - vy, hm, hp, X);
+    }
+    R px = Dm * vx, py = Dm * vy;
+    if (pp) { px0 = px; py0 = py; } else { px1 = px; py1 = py; }
+  }
+  opp[0] = D0; opp[1] = px0; opp[2] = py0;
+  opm[0] = D1; opm[1] = px1; opm[2] = py1;
+}
+
+// Shared-memory sizes of the tiled kernels (elements of the step's type).
+constexpr int NR_SW = TTX + 4, NR_SH = TTY + 4, NR_OW = TTX + 1, NR_OH = TTY + 1;
+constexpr int NR_STAGED = 10, NR_OBJ = 12;
+template <class R> constexpr size_t node_remap_smem() {
+  return sizeof(R) * ((size_t)NR_STAGED * NR_SW * NR_SH + (size_t)NR_OBJ * NR_OW * NR_OH);
+}
+
+// Tiled dual remap and node update (fuses lr_dual_flux and lr_node_update):
+// a tile of TX x TY nodes stages u^{lag}, displacements, the primary mass
+// fluxes, cell masses and sound speeds over the nodes [i0-2, i0+TX+1] x
+// [j0-2, j0+TY+1]; evaluates the dual X faces, dual Y faces and dual
+// corners around its nodes into shared memory; then m_p' u_p' = m_p
+// u_p^{lag} + signed dual momentum fluxes for its nodes and the CFL rule of
+// the next step (node_update_at's arithmetic).
+template <class R>
+__global__ void __launch_bounds__(TTHREADS, MinBlocks<R, LR_MINB_D_DUAL>::value)
+    lr_t_node_remap(LrGrid g, KC<R> kc, LrStateT<R> cur, LrStateT<R> nxt, LrWorkT<R> w) {
+  using O = RealOps<R>;
+  lr_pdl_enter();
+  extern __shared__ __align__(16) unsigned char lr_smem[];
+  R* sm = reinterpret_cast<R*>(lr_smem);
+  constexpr int SN = NR_SW * NR_SH, ON = NR_OW * NR_OH;
+  R *sUX = sm, *sUY = sm + SN, *sDX = sm + 2 * SN, *sDY = sm + 3 * SN, *sMX = sm + 4 * SN, *sMY = sm + 5 * SN;
+  R *sPP = sm + 6 * SN, *sPM = sm + 7 * SN, *sMC = sm + 8 * SN, *sCC = sm + 9 * SN;
+  R* so = sm + NR_STAGED * SN;  // objects: dX[3], dY[3], dPP[3], dPM[3]
+  const int tid = threadIdx.x;
+  const int i0 = blockIdx.x * TTX, j0 = blockIdx.y * TTY;
+  const int ta = tid % TTX, tb = tid / TTX;
+  const int i = i0 + ta, j = j0 + tb;
+  const bool act = i < g.nxu && j < g.nyu;
+  if (!step_live(g, w.scal)) {  // uniform over the grid
+    if (act) { int n = g.noff + j * (g.nx + 1) + i; nxt.ux[n] = cur.ux[n]; nxt.uy[n] = cur.uy[n]; }
+    if (i == 0 && j == 0) scal_of(g, w.scal)[2] = 0.0;
+    return;
+  }
+  const R Z = O::c(0.0f);
+  // ---- stage (boundary conditions applied here, once per value)
+  auto stage = [&](auto in) {
+    constexpr bool IN = decltype(in)::value;
+    for (int t = tid; t < SN; t += TTHREADS) {
+      int gi = i0 - 2 + t % NR_SW, gj = j0 - 2 + t / NR_SW;
+      Ix n = snix<IN>(g, gi, gj);
+      sUX[t] = O::flip(n.fx, w.ulx[n.idx]);
+      sUY[t] = O::flip(n.fy, w.uly[n.idx]);
+      sDX[t] = O::flip(n.fx, w.ddx[n.idx]);
+      sDY[t] = O::flip(n.fy, w.ddy[n.idx]);
+      R x = w.Mpp[n.idx], y = w.Mpm[n.idx];
+      bool swp = n.fx != n.fy;  // a mirror in x maps (pp, pm) to (-pm, -pp), one in y to (pm, pp)
+      sPP[t] = O::flip(n.fx, swp ? y : x);
+      sPM[t] = O::flip(n.fx, swp ? x : y);
+      Ix qx = sxix<IN>(g, gi, gj);
+      sMX[t] = O::flip(qx.fx, w.MX[qx.idx]);
+      Ix qy = syix<IN>(g, gi, gj);
+      sMY[t] = O::flip(qy.fy, w.MY[qy.idx]);
+      int c = scix<IN>(g, gi, gj).idx;
+      sMC[t] = w.mc[c];
+      sCC[t] = w.cc[c];
+    }
+  };
+  if (tile_interior(g, i0, j0)) stage(std::true_type{});
+  else stage(std::false_type{});
+  __syncthreads();
+  // ---- dual objects around the tile's nodes, spread evenly over the
+  // block: the dual X faces of the tile's rows, the dual Y faces of its
+  // columns, the dual corners
+  DualTile<R> ax{sUX, sUY, sDX, sDY, sMX, sMY, sPP, sPM, i0 - 2, j0 - 2, NR_SW};
+  constexpr int NXF = NR_OW * TTY, NYF = TTX * NR_OH, NOBJ = NXF + NYF + ON;
+  for (int k = tid; k < NOBJ; k += TTHREADS) {
+    if (k < NXF + NYF) {
+      int xf = k < NXF;
+      int a = xf ? k % NR_OW : 1 + (k - NXF) % TTX, b = xf ? 1 + k / NR_OW : (k - NXF) / TTX;
+      int t = b * NR_OW + a;
+      R D, px, py;
+      dual_face_obj(g, kc, ax, i0 - 1 + a, j0 - 1 + b, xf, D, px, py);
+      R* o3 = so + (xf ? 0 : 3 * ON) + t;
+      o3[0] = D; o3[ON] = px; o3[2 * ON] = py;
+    } else {
+      int t = k - NXF - NYF;
+      R pp3[3], pm3[3];
+      dual_corner_obj(g, kc, ax, i0 - 1 + t % NR_OW, j0 - 1 + t / NR_OW, pp3, pm3);
+      so[6 * ON + t] = pp3[0]; so[7 * ON + t] = pp3[1]; so[8 * ON + t] = pp3[2];
+      so[9 * ON + t] = pm3[0]; so[10 * ON + t] = pm3[1]; so[11 * ON + t] = pm3[2];
+    }
+  }
+  __syncthreads();
+  // ---- node update (node_update_at's arithmetic)
+  R val = Z;
+  if (act) {
+    int n = g.noff + j * (g.nx + 1) + i;
+    int s0 = (tb + 2) * NR_SW + (ta + 2);  // staged slot of node (i, j) / cell (i, j)
+    R ux1, uy1;
+    if (g.presc) {
+      ux1 = w.pux[n]; uy1 = w.puy[n];
+    } else {
+      R mp = O::c(0.25f) * (sMC[s0 - NR_SW - 1] + sMC[s0 - NR_SW] + sMC[s0 - 1] + sMC[s0]);
+      R mnew = mp, px = mp * sUX[s0], py = mp * sUY[s0];
+      int oR = (tb + 1) * NR_OW + (ta + 1), oL = oR - 1, oT = oR, oB = oR - NR_OW;
+      mnew += so[oL] - so[oR]; px += so[ON + oL] - so[ON + oR]; py += so[2 * ON + oL] - so[2 * ON + oR];
+      mnew += so[3 * ON + oB] - so[3 * ON + oT]; px += so[4 * ON + oB] - so[4 * ON + oT];
+      py += so[5 * ON + oB] - so[5 * ON + oT];
+      int c0 = oR, c1 = oR - NR_OW - 1, c2 = oR - NR_OW, c3 = oR - 1;
+      mnew += (so[6 * ON + c1] - so[6 * ON + c0]) + (so[9 * ON + c3] - so[9 * ON + c2]);
+      px += (so[7 * ON + c1] - so[7 * ON + c0]) + (so[10 * ON + c3] - so[10 * ON + c2]);
+      py += (so[8 * ON + c1] - so[8 * ON + c0]) + (so[11 * ON + c3] - so[11 * ON + c2]);
+      if (!O::pos(mnew)) set_err(err_of(g, w.err), LR_DERR_MASS, n);
+      R im = O::rcp(mnew);
+      ux1 = px * im;
+      uy1 = py * im;
+      if (!O::finite(ux1) || !O::finite(uy1)) set_err(err_of(g, w.err), LR_DERR_NAN, n);
+    }
+    if (!g.perx && (i == 0 || i == g.nx)) ux1 = Z;
+    if (!g.pery && (j == 0 || j == g.ny)) uy1 = Z;
+    nxt.ux[n] = ux1;
+    nxt.uy[n] = uy1;
+    R cm = rmax(rmax(sCC[s0 - NR_SW - 1], sCC[s0 - NR_SW]), rmax(sCC[s0 - 1], sCC[s0]));
+    val = cm + O::sqrt(ux1 * ux1 + uy1 * uy1);
+  }
+  cfl_finalize(g, kc, w, val, true, (unsigned long long)gridDim.x * gridDim.y);
+}
+
+// Cell data a flux object reads, staged with the boundary conditions
+// applied: Lagrangian rectangle (centre offsets flipped under mirrors,
+// widths), rho^{lagCF} and e^{lag} per material, material masks, node
+// displacements.
+template <class R, int M>
+struct CellTile {
+  const R *ox, *oy, *wx, *wy, *dx_, *dy_;
+  const R* rq[LR_MAXM];
+  const R* eq[LR_MAXM];
+  const unsigned char* mk;
+  int oi, oj, sw;
+  __device__ __forceinline__ int at(int a, int b) const { return (b - oj) * sw + (a - oi); }
+  __device__ __forceinline__ R dx(int a, int b) const { return dx_[at(a, b)]; }
+  __device__ __forceinline__ R dy(int a, int b) const { return dy_[at(a, b)]; }
+  __device__ __forceinline__ bool pure(int a, int b, unsigned bit) const { return mk[at(a, b)] == bit; }
+};
+
+// Face value of the two quantities of material `as` (recon_face2's
+// arithmetic on a staged tile).
+template <class R, int M>
+__device__ __forceinline__ void recon_face2_t(const KC<R>& kc, const CellTile<R, M>& T, int as, int di, int dj,
+                                              bool fwd, R fdisp, bool xdir, R& v1, R& v2) {
+  using O = RealOps<R>;
+  int mi = xdir ? 1 : 0, mj = 1 - mi;
+  int c = T.at(di, dj), cm = T.at(di - mi, dj - mj), cp = T.at(di + mi, dj + mj);
+  const R* oa = xdir ? T.ox : T.oy;
+  const R* wa = xdir ? T.wx : T.wy;
+  R o0 = oa[c], om = oa[cm], op = oa[cp];
+  R h = xdir ? kc.dx : kc.dy;
+  R hm = h + o0 - om, hp = h + op - o0;
+  R X = O::flip(!fwd, wa[c]) - fdisp;
+  const R* q1 = pick<M>(T.rq, as);
+  const R* q2 = pick<M>(T.eq, as);
+  R a0 = q1[c];
+  v1 = a0 + vl_term(a0 - q1[cm], q1[cp] - a0, hm, hp, X);
+  R b0 = q2[c];
+  v2 = b0 + vl_term(b0 - q2[cm], q2[cp] - b0, hm, hp, X);
+}
+// Corner value, diagonal limited reconstruction (recon_corner2's arithmetic
+// on a staged tile).
+template <class R, int M>
+__device__ __forceinline__ void recon_corner2_t(const KC<R>& kc, const CellTile<R, M>& T, int as, int di, int dj,
+                                                R ddx, R ddy, int sj, R& v1, R& v2) {
+  using O = RealOps<R>;
+  int c = T.at(di, dj), cp = T.at(di + 1, dj + sj), cm = T.at(di - 1, dj - sj);
+  R ox0 = T.ox[c], oy0 = T.oy[c];
+  R oxp = T.ox[cp], oyp = T.oy[cp], oxm = T.ox[cm], oym = T.oy[cm];
+  R sdy = O::flip(sj < 0, kc.dy);
+  R hp = (kc.dx + oxp - ox0) * kc.dx + (sdy + oyp - oy0) * sdy;
+  R hm = (kc.dx + ox0 - oxm) * kc.dx + (sdy + oy0 - oym) * sdy;
+  R wsum = T.wx[c] * kc.dx + T.wy[c] * kc.dy;
+  R dsum = ddx * kc.dx + ddy * sdy;
+  R X = O::flip(!O::pos(ddx), wsum) - dsum;
+  const R* q1 = pick<M>(T.rq, as);
+  const R* q2 = pick<M>(T.eq, as);
+  R a0 = q1[c];
+  v1 = a0 + vl_term(a0 - q1[cm], q1[cp] - a0, hm, hp, X);
+  R b0 = q2[c];
+  v2 = b0 + vl_term(b0 - q2[cm], q2[cp] - b0, hm, hp, X);
+}
+
+// Node-like index i of a tile whose cells start at i0 is owned by that tile
+// (its total mass flux is stored by it) when the canonical index lies in
+// the tile's cell range, the last cell's tile also owning index n (walls).
+__device__ __forceinline__ bool owns(int i, int i0, int n, int nu) {
+  int c = i < n ? i : n - 1;
+  return i < nu && c >= i0 && c < i0 + TTX;
+}
+__device__ __forceinline__ bool owns_y(int j, int j0, int n, int nu) {
+  int c = j < n ? j : n - 1;
+  return j < nu && c >= j0 && c < j0 + TTY;
+}
+
+constexpr int CR_SW = TTX + 4, CR_SH = TTY + 4, CR_OW = TTX + 1, CR_OH = TTY + 1;
+template <class R, int M> constexpr size_t cell_remap_smem() {
+  return sizeof(R) * ((size_t)(6 + 2 * M) * CR_SW * CR_SH + (size_t)9 * CR_OW * CR_OH) +
+         (size_t)CR_SW * CR_SH + (size_t)3 * CR_OW * CR_OH;
+}
+
+// Tiled material fluxes and cell update (fuses lr_mat_flux and
+// lr_cell_update): a tile of TX x TY cells stages the Lagrangian
+// rectangles, rho^{lagCF}, e^{lag}, material masks (cells [i0-2, i0+TX+1] x
+// [j0-2, j0+TY+1]) and node displacements; evaluates the X faces, Y faces
+// and corners around its cells whose donor is pure (mat_flux_at's
+// arithmetic: the donor's material takes the whole flux, order-2 values
+// where the donor and its neighbours along the direction are pure) into
+// shared memory, storing the total mass fluxes of the objects it owns for
+// the dual remap; objects with a mixed donor were finished by the donor's
+// are read from the arrays lr_t_lagrange's interface phase stored.  Then the
+// cell update of cell_update_at.
+template <class R, int M>
+__global__ void __launch_bounds__(TTHREADS, MinBlocks<R, LR_MINB_D_UPDATE>::value)
+    lr_t_cell_remap(LrGrid g, KC<R> kc, LrStateT<R> cur, LrStateT<R> nxt, LrWorkT<R> w) {
+  using O = RealOps<R>;
+  lr_pdl_enter();
+  extern __shared__ __align__(16) unsigned char lr_smem[];
+  constexpr int SN = CR_SW * CR_SH, ON = CR_OW * CR_OH;
+  R* sm = reinterpret_cast<R*>(lr_smem);
+  R *sOX = sm, *sOY = sm + SN, *sWX = sm + 2 * SN, *sWY = sm + 3 * SN, *sDX = sm + 4 * SN, *sDY = sm + 5 * SN;
+  R* sQ = sm + 6 * SN;                        // rho^{lagCF} [M], then e^{lag} [M]
+  R* oA = sm + (6 + 2 * M) * SN;              // objects [kind][slot]: X face, Y face, corner
+  R* oM = oA + 3 * ON;
+  R* oE = oM + 3 * ON;
+  unsigned char* sMK = reinterpret_cast<unsigned char*>(oE + 3 * ON);
+  signed char* oMat = reinterpret_cast<signed char*>(sMK + SN);  // material, -1 none, -2 mixed donor
+  const int tid = threadIdx.x;
+  const int i0 = blockIdx.x * TTX, j0 = blockIdx.y * TTY;
+  const int ta = tid % TTX, tb = tid / TTX;
+  const int i = i0 + ta, j = j0 + tb;
+  const bool act = i < g.nx && j < g.ny;
+  if (!step_live(g, w.scal)) {
+    if (act) {
+      int c = g.coff + j * g.nx + i;
+#pragma unroll
+      for (int a = 0; a < M; ++a) { nxt.k[a][c] = cur.k[a][c]; nxt.r[a][c] = cur.r[a][c]; nxt.e[a][c] = cur.e[a][c]; }
+    }
+    return;
+  }
+  const R Z = O::c(0.0f), H = O::c(0.5f), ONE = O::c(1.0f);
+  // ---- stage
+  const bool inner = tile_interior(g, i0, j0);
+  auto stage = [&](auto in) {
+    constexpr bool IN = decltype(in)::value;
+    for (int t = tid; t < SN; t += TTHREADS) {
+      int gi = i0 - 2 + t % CR_SW, gj = j0 - 2 + t / CR_SW;
+      Ix c = scix<IN>(g, gi, gj);
+      sOX[t] = O::flip(c.fx, w.ox[c.idx]);
+      sOY[t] = O::flip(c.fy, w.oy[c.idx]);
+      sWX[t] = w.wx[c.idx];
+      sWY[t] = w.wy[c.idx];
+      sMK[t] = w.mask[c.idx];
+#pragma unroll
+      for (int a = 0; a < M; ++a) { sQ[a * SN + t] = w.rcf[a][c.idx]; sQ[(M + a) * SN + t] = w.elag[a][c.idx]; }
+      Ix n = snix<IN>(g, gi, gj);
+      sDX[t] = O::flip(n.fx, w.ddx[n.idx]);
+      sDY[t] = O::flip(n.fy, w.ddy[n.idx]);
+    }
+  };
+  if (inner) stage(std::true_type{});
+  else stage(std::false_type{});
+  __syncthreads();
+  CellTile<R, M> T;
+  T.ox = sOX; T.oy = sOY; T.wx = sWX; T.wy = sWY; T.dx_ = sDX; T.dy_ = sDY; T.mk = sMK;
+#pragma unroll
+  for (int a = 0; a < LR_MAXM; ++a) {
+    T.rq[a] = sQ + (a < M ? a : 0) * SN;
+    T.eq[a] = sQ + (M + (a < M ? a : 0)) * SN;
+  }
+  T.oi = i0 - 2; T.oj = j0 - 2; T.sw = CR_SW;
+  // ---- flux objects around the tile's cells (mat_flux_at's arithmetic),
+  // spread evenly over the block: X faces of the tile's rows, Y faces of
+  // its columns, corners
+  constexpr int NXF = CR_OW * TTY, NYF = TTX * CR_OH, NOBJ = NXF + NYF + ON;
+  for (int k = tid; k < NOBJ; k += TTHREADS) {
+    if (k < NXF + NYF) {  // X face (oi, oj) or Y face (oi, oj)
+      int xf = k < NXF;
+      int a = xf ? k % CR_OW : (k - NXF) % TTX, b = xf ? k / CR_OW : (k - NXF) / TTX;
+      int t = b * CR_OW + a;
+      int oi = i0 + a, oj = j0 + b;
+      int f;
+      R v;
+      if (inner) {
+        f = xf ? g.noff + oj * (g.nx + 1) + oi : g.noff + oj * g.nx + oi;
+        v = (xf ? w.fx : w.fy)[f];
+      } else if (xf) {
+        Ix q = xix(g, nclamp(oi, g.nx), cclamp(oj, g.ny));
+        f = q.idx; v = O::flip(q.fx, w.fx[f]);
+      } else {
+        Ix q = yix(g, cclamp(oi, g.nx), nclamp(oj, g.ny));
+        f = q.idx; v = O::flip(q.fy, w.fy[f]);
+      }
+      bool fwd = O::pos(v);
+      int di = xf ? (fwd ? oi - 1 : oi) : oi, dj = xf ? oj : (fwd ? oj - 1 : oj);
+      unsigned dm = 0u;
+      R fd = Z;
+      if (!O::zero(v)) {
+        dm = T.mk[T.at(di, dj)];
+        fd = xf ? H * (T.dx(oi, oj) + T.dx(oi, oj + 1)) : H * (T.dy(oi, oj) + T.dy(oi + 1, oj));
+      }
+      int slot = (1 - xf) * ON + t;
+      if (dm & (dm - 1u)) { oMat[slot] = -2; continue; }  // finished by lr_mixed
+      int as = dm ? __ffs(dm) - 1 : -1;
+      R Aa = O::abs(v), Ma = Z, Ea = Z;
+      if (as >= 0) {
+        unsigned bit = 1u << as;
+        int dc = T.at(di, dj);
+        R rf = pick<M>(T.rq, as)[dc], ef = pick<M>(T.eq, as)[dc];
+        if (g.face_o2 && T.pure(di - xf, dj - (1 - xf), bit) && T.pure(di + xf, dj + (1 - xf), bit))
+          recon_face2_t(kc, T, as, di, dj, fwd, fd, xf != 0, rf, ef);
+        Ma = O::mul(rf, Aa);
+        Ea = O::mul(Ma, ef);
+      }
+      R sM = O::flip(!fwd, Ma);
+      oMat[slot] = (signed char)as;
+      oA[slot] = O::flip(!fwd, Aa);
+      oM[slot] = sM;
+      oE[slot] = O::flip(!fwd, Ea);
+      bool own = xf ? (owns(oi, i0, g.nx, g.nxu) && oj < g.ny) : (owns_y(oj, j0, g.ny, g.nyu) && oi < g.nx);
+      if (own) (xf ? w.MX : w.MY)[f] = as >= 0 ? O::add(Z, sM) : Z;
+    } else {  // corner at node (oi, oj)
+      int t = k - NXF - NYF;
+      int oi = i0 + t % CR_OW, oj = j0 + t / CR_OW;
+      R ddx = T.dx(oi, oj), ddy = T.dy(oi, oj);
+      int di = 0, dj = 0, ri = 0, rj = 0, sj = 1;
+      unsigned dm = 0u;
+      R fv = Z;
+      bool pp = false;
+      if (corner_of(g, ddx, ddy, oi, oj, di, dj, ri, rj)) {
+        fv = O::abs(ddx * ddy);
+        dm = T.mk[T.at(di, dj)];
+        pp = O::pos(ddx) == O::pos(ddy);
+        sj = pp ? 1 : -1;
+      }
+      int slot = 2 * ON + t;
+      if (dm & (dm - 1u)) {
+        oMat[slot] = -2;
+      } else {
+        int as = dm ? __ffs(dm) - 1 : -1;
+        R Aa = Z, Ma = Z, Ea = Z;
+        if (as >= 0) {
+          Aa = fv;
+          unsigned bit = 1u << as;
+          int dc = T.at(di, dj);
+          R rf = pick<M>(T.rq, as)[dc], ef = pick<M>(T.eq, as)[dc];
+          if (g.corner_kind == LR_CORNER_DIAG && T.pure(di - 1, dj - sj, bit) && T.pure(di + 1, dj + sj, bit))
+            recon_corner2_t(kc, T, as, di, dj, ddx, ddy, sj, rf, ef);
+          Ma = O::mul(rf, Aa);
+          Ea = O::mul(Ma, ef);
+        }
+        oMat[slot] = (signed char)as;
+        oA[slot] = Aa; oM[slot] = Ma; oE[slot] = Ea;
+        if (owns(oi, i0, g.nx, g.nxu) && owns_y(oj, j0, g.ny, g.nyu)) {
+          int n = g.noff + oj * (g.nx + 1) + oi;
+          R sgm = O::flip(!O::pos(ddx), as >= 0 ? O::add(Z, Ma) : Z);  // signed along +x
+          w.Mpp[n] = (dm && pp) ? sgm : Z;
+          w.Mpm[n] = (dm && !pp) ? sgm : Z;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (!act) return;
+  // ---- cell update (cell_update_at's arithmetic)
+  int c = g.coff + j * g.nx + i;
+  int s0 = T.at(i, j);
+  unsigned own = sMK[s0], nb = own;
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    if (q == 4) continue;
+    nb |= sMK[s0 + (q / 3 - 1) * CR_SW + (q % 3 - 1)];
+  }
+  // object slots: X faces left/right, Y faces bottom/top, corners ll, lr, ul, ur
+  int o00 = tb * CR_OW + ta;
+  int sl[8] = {o00, o00 + 1, ON + o00, ON + o00 + CR_OW, 2 * ON + o00, 2 * ON + o00 + 1,
+               2 * ON + o00 + CR_OW, 2 * ON + o00 + CR_OW + 1};
+  int cs[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    int a = q & 1, b = q >> 1;
+    int di, dj, ri, rj;
+    cs[q] = 0;
+    if (corner_of(g, T.dx(i + a, j + b), T.dy(i + a, j + b), i + a, j + b, di, dj, ri, rj)) {
+      if (ri == i && rj == j) cs[q] = 1;
+      if (di == i && dj == j) cs[q] = -1;
+    }
+  }
+  // per-material values of object l: its own material's, the mixed donor's
+  // (lr_mixed's arrays), or zero
+  auto obj = [&](int l, int a, R& A, R& Mm, R& E) {
+    int sI = sl[l];
+    int m = oMat[sI];
+    if (m == a) { A = oA[sI]; Mm = oM[sI]; E = oE[sI]; return; }
+    A = Z; Mm = Z; E = Z;
+    if (m != -2) return;
+    if (l < 2) {
+      int f = xix(g, i + l, j).idx;
+      A = w.xA[a][f]; Mm = w.xMm[a][f]; E = w.xE[a][f];
+    } else if (l < 4) {
+      int f = yix(g, i, j + l - 2).idx;
+      A = w.yA[a][f]; Mm = w.yMm[a][f]; E = w.yE[a][f];
+    } else {
+      int q = l - 4;
+      int n = nix(g, i + (q & 1), j + (q >> 1)).idx;
+      A = w.cA[a][n]; Mm = w.cMm[a][n]; E = w.cE[a][n];
+    }
+  };
+  R vcf = w.vcf[c];
+  R vol[M], mas[M], ene[M];
+#pragma unroll
+  for (int a = 0; a < M; ++a) {
+    vol[a] = Z; mas[a] = Z; ene[a] = Z;
+    if (!(nb & (1u << a))) continue;
+    Acc<R> vv, mm, ee;
+    vv.init(Z); mm.init(Z); ee.init(Z);
+    if (own & (1u << a)) {
+      R ka = cur.k[a][c];
+      R m0 = cur.r[a][c] * ka * kc.V;
+      mm.init(m0);
+      vv.init(ka * vcf);
+      ee.init(m0 * pick<M>(T.eq, a)[s0]);
+    }
+    R Al, Ml, El, Ar, Mr, Er;
+    obj(0, a, Al, Ml, El); obj(1, a, Ar, Mr, Er);
+    R Ab, Mb, Eb, At, Mt, Et;
+    obj(2, a, Ab, Mb, Eb); obj(3, a, At, Mt, Et);
+    vv.add(Al - Ar); vv.add(Ab - At);
+    mm.add(Ml - Mr); mm.add(Mb - Mt);
+    ee.add(El - Er); ee.add(Eb - Et);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      bool on = cs[q] != 0, ng = cs[q] < 0;
+      R ca, cm, ce;
+      obj(4 + q, a, ca, cm, ce);
+      vv.add(on ? O::flip(ng, ca) : Z); mm.add(on ? O::flip(ng, cm) : Z); ee.add(on ? O::flip(ng, ce) : Z);
+    }
+    vol[a] = vv.get(); mas[a] = mm.get(); ene[a] = ee.get();
+  }
+  bool keep[M];
+  int big = -1, nkeep = 0;
+  R tot = Z, lm = Z, le = Z;
+#pragma unroll
+  for (int a = 0; a < M; ++a) {
+    keep[a] = (nb & (1u << a)) && O::lt(kc.epsKV, vol[a]);
+    if (keep[a]) {
+      tot += vol[a];
+      ++nkeep;
+      if (big < 0) big = a;
+      else if (O::lt(vol[big], vol[a])) big = a;
+    } else {
+      lm += mas[a];
+      le += ene[a];
+    }
+  }
+  if (big < 0) { set_err(err_of(g, w.err), LR_DERR_VOLUME, c); big = 0; tot = ONE; }
+#pragma unroll
+  for (int a = 0; a < M; ++a) {
+    if (a == big) { mas[a] += lm; ene[a] += le; }
+  }
+  R cmax = Z;
+#pragma unroll
+  for (int a = 0; a < M; ++a) {
+    R ka = Z, ra = Z, ea = Z;
+    if (keep[a]) {
+      ka = nkeep == 1 ? ONE : O::div(vol[a], tot);
+      if (!O::pos(mas[a])) set_err(err_of(g, w.err), LR_DERR_MASS, c);
+      R im = O::rcp(mas[a]);
+      R kV = ka * kc.V;
+      ra = nkeep == 1 ? mas[a] * kc.invV : O::div(mas[a], kV);
+      ea = ene[a] * im;
+      R pa = eos_p(kc.gm1[a], kc.pin[a], ra, ea);
+      R c2 = (kc.gam[a] * pa + kc.pin[a]) * (kV * im);
+      R wk = ka * kc.invEpsC;
+      bool thin = O::lt(wk, ONE);
+      R wgt = thin ? wk : ONE;
+      bool c2p = O::pos(c2);
+      if (!thin && !c2p) set_err(err_of(g, w.err), LR_DERR_SOUND, c);
+      R ca = c2p ? O::sqrt(c2) : Z;
+      R wc = wgt * ca;
+      if (O::lt(cmax, wc)) cmax = wc;
+      if (!O::finite(ra) || !O::finite(ea)) set_err(err_of(g, w.err), LR_DERR_NAN, c);
+    }
+    nxt.k[a][c] = ka; nxt.r[a][c] = ra; nxt.e[a][c] = ea;
+  }
+  w.cc[c] = cmax;
+}
+
+constexpr int LG_CW = TTX + 2, LG_CH = TTY + 2, LG_NW = TTX + 3, LG_NH = TTY + 3, LG_OW = TTX + 1,
+              LG_OH = TTY + 1;
+template <class R, int M> constexpr size_t lagrange_smem() {
+  return sizeof(R) * ((size_t)2 * LG_NW * LG_NH + (size_t)(2 + M) * LG_CW * LG_CH + (size_t)4 * LG_OW * LG_OH) +
+         (size_t)LG_CW * LG_CH;
+}
+
+// The cell part of lr_t_lagrange (phases 3b and 4) for cell (i, j), thread
+// (ta, tb) of the tile.
+template <class R, int M>
+__device__ __forceinline__ void lagrange_cell(const LrGrid& g, const KC<R>& kc, const LrStateT<R>& cur,
+                                              const LrWorkT<R>& w, int i, int j, int ta, int tb, const R* sDX,
+                                              const R* sDY, const R* sFX, const R* sFY, const R* sElc,
+                                              const unsigned char* sMK, int CN) {
+  using O = RealOps<R>;
+  const R Z = O::c(0.0f), H = O::c(0.5f);
+  int c = g.coff + j * g.nx + i;
+  int o = tb * LG_OW + ta;  // node (i, j) in the node/face grid
+  int ll = o, lr = o + 1, ul = o + LG_OW, ur = ul + 1;
+  R dxll = sDX[ll], dxlr = sDX[lr], dxul = sDX[ul], dxur = sDX[ur];
+  R dyll = sDY[ll], dylr = sDY[lr], dyul = sDY[ul], dyur = sDY[ur];
+  R vol = cell_F(dxll, dyll, kc.dx + dxlr, dylr, dxul, kc.dy + dyul, kc.dx + dxur, kc.dy + dyur);
+  if (!O::pos(vol)) set_err(err_of(g, w.err), LR_DERR_VOLUME, c);
+  R dv = vol - kc.V;
+  int sc = (tb + 1) * LG_CW + (ta + 1);
+  unsigned msk = sMK[sc];
+#pragma unroll
+  for (int q = 0; q < M; ++q) {
+    R el = Z;
+    if (msk & (1u << q)) el = cur.e[q][c] - sElc[q * CN + sc] * dv;
+    w.elag[q][c] = el;
+  }
+  R xl = H * (dxll + dxul), xr = kc.dx + H * (dxlr + dxur);
+  R yb = H * (dyll + dylr), yt = kc.dy + H * (dyul + dyur);
+  w.ox[c] = H * (xl + xr) - H * kc.dx;
+  w.oy[c] = H * (yb + yt) - H * kc.dy;
+  w.wx[c] = xr - xl;
+  w.wy[c] = yt - yb;
+  R v = kc.V + sFX[o + 1] - sFX[o] + sFY[o + LG_OW] - sFY[o];
+  const int nq[4] = {ll, lr, ul, ur};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    int qa = q & 1, qb = q >> 1;
+    R cx = sDX[nq[q]], cy = sDY[nq[q]];
+    int di, dj, ri, rj;
+    if (!corner_of(g, cx, cy, i + qa, j + qb, di, dj, ri, rj)) continue;
+    R f = O::abs(cx * cy);
+    if (di == i && dj == j) v += f;
+    if (ri == i && rj == j) v -= f;
+  }
+  if (!O::pos(v)) set_err(err_of(g, w.err), LR_DERR_VOLUME, c);
+  w.vcf[c] = v;
+  R vV = O::div(kc.V, v);
+#pragma unroll
+  for (int q = 0; q < M; ++q) w.rcf[q][c] = (msk & (1u << q)) ? cur.r[q][c] * vV : O::c(0.0f);
+}
+
+// Tiled Lagrange phase and remap geometry (fuses lr_cell_pre, lr_node_half,
+// lr_cell_lag and lr_cell_cf) for a tile of TX x TY cells:
+//  1. Q^n, the predictor and P^{n+1/2} (cell_pre_at) for the cells
+//     [i0-1, i0+TX] x [j0-1, j0+TY] from u^n staged over their nodes;
+//     across a reflective wall the mirrored cell's values are copied, so a
+//     ghost holds exactly its image's numbers;
+//  2. u^{n+1/2}, u^{lag} and the displacement d (node_half_at) for the
+//     nodes [i0, i0+TX] x [j0, j0+TY];
+//  3. Vol^{lag}, e^{lag}, the Lagrangian rectangle of the tile's cells and
+//     the X and Y face volume fluxes around them (cell_lag_at);
+//  4. Vol^{lagCF} and rho^{lagCF} (cell_cf_at).
+// Intermediates that only the next phase reads (P+Q, the e^{lag}
+// coefficients, the face volumes) stay in shared memory; the results later
+// kernels read are stored for the cells, nodes and faces the tile owns.
+// Mixed cells join the interface work list of lr_t_mixed.
+template <class R, int M>
+__global__ void __launch_bounds__(TTHREADS, MinBlocks<R, 1>::value)
+    lr_t_lagrange(LrGrid g, KC<R> kc, LrStateT<R> cur, LrStateT<R> nxt, LrWorkT<R> w) {
+  using O = RealOps<R>;
+  lr_pdl_enter();
+  extern __shared__ __align__(16) unsigned char lr_smem[];
+  constexpr int NN = LG_NW * LG_NH, CN = LG_CW * LG_CH, ON = LG_OW * LG_OH;
+  R* sm = reinterpret_cast<R*>(lr_smem);
+  R *sUX = sm, *sUY = sm + NN;
+  R *sPi = sm + 2 * NN, *sMC = sPi + CN, *sElc = sMC + CN;  // sElc: [M][CN]
+  R *sDX = sElc + M * CN, *sDY = sDX + ON, *sFX = sDY + ON, *sFY = sFX + ON;
+  unsigned char* sMK = reinterpret_cast<unsigned char*>(sFY + ON);
+  const int tid = threadIdx.x;
+  const int i0 = blockIdx.x * TTX, j0 = blockIdx.y * TTY;
+  if (!step_live(g, w.scal)) return;
+  const R Z = O::c(0.0f), H = O::c(0.5f);
+  const R dt = w.dtR[g.inst];
+  const int nn = g.nx + 1;
+  // ---- stage u^n over the nodes [i0-1, i0+TX+1] x [j0-1, j0+TY+1]
+  for (int t = tid; t < NN; t += TTHREADS) {
+    int gi = i0 - 1 + t % LG_NW, gj = j0 - 1 + t / LG_NW;
+    Ix n = nix(g, nclamp(gi, g.nx), nclamp(gj, g.ny));
+    sUX[t] = O::flip(n.fx, cur.ux[n.idx]);
+    sUY[t] = O::flip(n.fy, cur.uy[n.idx]);
+  }
+  __syncthreads();
+  // ---- 1. cell_pre over the cells [i0-1, i0+TX] x [j0-1, j0+TY]
+  for (int t = tid; t < CN; t += TTHREADS) {
+    int a = t % LG_CW, b = t / LG_CW;
+    int ci = i0 - 1 + a, cj = j0 - 1 + b;
+    bool gx = !g.perx && (ci < 0 || ci >= g.nx), gy = !g.pery && (cj < 0 || cj >= g.ny);
+    if (gx || gy) continue;  // a wall ghost: copied from its image below
+    int c = cix(g, cclamp(ci, g.nx), cclamp(cj, g.ny)).idx;
+    int ll = b * LG_NW + a, lr = ll + 1, ul = ll + LG_NW, ur = ul + 1;
+    R uxll = sUX[ll], uxlr = sUX[lr], uxul = sUX[ul], uxur = sUX[ur];
+    R uyll = sUY[ll], uylr = sUY[lr], uyul = sUY[ul], uyur = sUY[ur];
+    R kk[M], rr[M], ee[M], pa[M], ir[M];
+    R m = Z;
+    R cmax = w.cc[c];
+    unsigned msk = 0u;
+#pragma unroll
+    for (int q = 0; q < M; ++q) {
+      kk[q] = cur.k[q][c];
+      rr[q] = Z; ee[q] = Z; pa[q] = Z; ir[q] = Z;
+      if (O::pos(kk[q])) {
+        msk |= 1u << q;
+        rr[q] = cur.r[q][c];
+        ee[q] = cur.e[q][c];
+        ir[q] = O::rcp(rr[q]);
+        pa[q] = eos_p(kc.gm1[q], kc.pin[q], rr[q], ee[q]);
+        m += rr[q] * kk[q] * kc.V;
+      }
+    }
+    R div = ((uxlr + uxur) - (uxll + uxul)) * kc.inv2dx + ((uyul + uyur) - (uyll + uylr)) * kc.inv2dy;
+    R rc = m * kc.invV;
+    R Q = Z;
+    if (O::neg(div)) {
+      R ad = O::abs(div);
+      Q = rc * (kc.a1L * cmax * ad + kc.a2LL * div * div);
+    }
+    R h = H * dt;
+    R vol = cell_F(h * uxll, h * uyll, kc.dx + h * uxlr, h * uylr, h * uxul, kc.dy + h * uyul,
+                   kc.dx + h * uxur, kc.dy + h * uyur);
+    bool owned = a >= 1 && a <= TTX && b >= 1 && b <= TTY && ci < g.nx && cj < g.ny;
+    if (owned && !O::pos(vol)) set_err(err_of(g, w.err), LR_DERR_VOLUME, c);
+    R dv = vol - kc.V;
+    R vV = O::div(kc.V, vol);
+    R P = Z;
+#pragma unroll
+    for (int q = 0; q < M; ++q) {
+      R cl = Z;
+      if (msk & (1u << q)) {
+        R rh = rr[q] * vV;
+        R iv = ir[q] * kc.invV;
+        R eh = ee[q] - (pa[q] + Q) * (dv * iv);
+        R ph = eos_p(kc.gm1[q], kc.pin[q], rh, eh);
+        P += kk[q] * ph;
+        cl = (ph + Q) * iv;
+      }
+      sElc[q * CN + t] = cl;
+    }
+    sPi[t] = P + Q;
+    sMC[t] = m;
+    sMK[t] = (unsigned char)msk;
+    if (owned) {
+      w.mc[c] = m;
+      w.Q[c] = Q;
+      w.mask[c] = (unsigned char)msk;
+      if (msk & (msk - 1u)) {  // two or more materials: interface work list
+        int slot = g.moff + (int)atomicAdd(&w.red[g.mslot], 1ull);
+        w.mixed[slot] = c;
+        if (w.minst) w.minst[slot] = g.inst;
+      }
+    }
+  }
+  __syncthreads();
+  // wall ghosts: the values of their mirror images (scalars)
+  for (int t = tid; t < CN; t += TTHREADS) {
+    int a = t % LG_CW, b = t / LG_CW;
+    int ci = i0 - 1 + a, cj = j0 - 1 + b;
+    bool gx = !g.perx && (ci < 0 || ci >= g.nx), gy = !g.pery && (cj < 0 || cj >= g.ny);
+    if (!(gx || gy)) continue;
+    int mi = gx ? (ci < 0 ? -1 - ci : 2 * g.nx - 1 - ci) : ci;
+    int mj = gy ? (cj < 0 ? -1 - cj : 2 * g.ny - 1 - cj) : cj;
+    int ma = mi - (i0 - 1), mb = mj - (j0 - 1);
+    if (ma < 0 || ma >= LG_CW || mb < 0 || mb >= LG_CH) continue;  // beyond any live point's reach
+    int u = mb * LG_CW + ma;
+    sPi[t] = sPi[u];
+    sMC[t] = sMC[u];
+  }
+  __syncthreads();
+  // ---- 2. node_half over the nodes [i0, i0+TX] x [j0, j0+TY]
+  for (int t = tid; t < ON; t += TTHREADS) {
+    int a = t % LG_OW, b = t / LG_OW;
+    int ni = i0 + a, nj = j0 + b;
+    int A = b * LG_CW + a, B = A + 1, C = A + LG_CW, D = C + 1;  // cells around the node
+    int su = (b + 1) * LG_NW + (a + 1);                          // staged u^n of the node
+    R hx, hy, lx, ly;
+    if (g.presc) {
+      int n = nix(g, nclamp(ni, g.nx), nclamp(nj, g.ny)).idx;
+      hx = w.pux[n]; hy = w.puy[n]; lx = hx; ly = hy;
+    } else {
+      R gxp = ((sPi[B] + sPi[D]) - (sPi[A] + sPi[C])) * kc.inv2dx;
+      R gyp = ((sPi[C] + sPi[D]) - (sPi[A] + sPi[B])) * kc.inv2dy;
+      R mp = O::c(0.25f) * (sMC[A] + sMC[B] + sMC[C] + sMC[D]);
+      R f = O::div(O::c(0.5f) * dt * kc.V, mp);  // dt/2 / rho_p
+      R u0x = sUX[su], u0y = sUY[su];
+      hx = u0x - f * gxp;
+      hy = u0y - f * gyp;
+      if (!g.perx && (ni == 0 || ni == g.nx)) hx = Z;
+      if (!g.pery && (nj == 0 || nj == g.ny)) hy = Z;
+      lx = O::c(2.0f) * hx - u0x;
+      ly = O::c(2.0f) * hy - u0y;
+    }
+    if (!g.perx && (ni == 0 || ni == g.nx)) { hx = Z; lx = Z; }
+    if (!g.pery && (nj == 0 || nj == g.ny)) { hy = Z; ly = Z; }
+    R ddx = dt * hx, ddy = dt * hy;
+    sDX[t] = ddx;
+    sDY[t] = ddy;
+    if (owns(ni, i0, g.nx, g.nxu) && owns_y(nj, j0, g.ny, g.nyu)) {
+      int n = g.noff + nj * nn + ni;
+      w.uhx[n] = hx; w.uhy[n] = hy;
+      w.ulx[n] = lx; w.uly[n] = ly;
+      w.ddx[n] = ddx; w.ddy[n] = ddy;
+    }
+  }
+  __syncthreads();
+  // ---- 3a. face volume fluxes around the tile's cells (cell_lag_at)
+  for (int t = tid; t < ON; t += TTHREADS) {
+    int a = t % LG_OW, b = t / LG_OW;
+    int fi = i0 + a, fj = j0 + b;
+    if (b < TTY) {  // X face (fi, fj): nodes (fi, fj), (fi, fj+1)
+      int pm = t, pp = t + LG_OW;
+      R ax = sDX[pm], ay = sDY[pm], bx = sDX[pp], dyp = sDY[pp], by = kc.dy + dyp;
+      R ylo = O::pos(ay) ? ay : Z;
+      R yhi = kc.dy + (O::neg(dyp) ? dyp : Z);
+      bool own = owns(fi, i0, g.nx, g.nxu) && fj < g.ny;
+      if (own && !O::lt(ylo, yhi)) set_err(err_of(g, w.err), LR_DERR_GEOM, g.noff + fj * nn + fi);
+      R sl = O::div(bx - ax, by - ay);
+      R xlo = ax + sl * (ylo - ay), xhi = ax + sl * (yhi - ay);
+      R xb = H * (xlo + xhi);
+      R fv = xb * (yhi - ylo);
+      sFX[t] = fv;
+      if (own) {
+        int f = g.noff + fj * nn + fi;
+        w.fx[f] = fv; w.fxb[f] = xb; w.fxlo[f] = ylo; w.fxhi[f] = yhi;
+      }
+    }
+    if (a < TTX) {  // Y face (fi, fj): nodes (fi, fj), (fi+1, fj)
+      int pm = t, pp = t + 1;
+      R ax = sDX[pm], ay = sDY[pm], dxp = sDX[pp], bx = kc.dx + dxp, by = sDY[pp];
+      R xlo = O::pos(ax) ? ax : Z;
+      R xhi = kc.dx + (O::neg(dxp) ? dxp : Z);
+      bool own = owns_y(fj, j0, g.ny, g.nyu) && fi < g.nx;
+      if (own && !O::lt(xlo, xhi)) set_err(err_of(g, w.err), LR_DERR_GEOM, g.noff + fj * nn + fi);
+      R sl = O::div(by - ay, bx - ax);
+      R ylo = ay + sl * (xlo - ax), yhi = ay + sl * (xhi - ax);
+      R yb = H * (ylo + yhi);
+      R fv = yb * (xhi - xlo);
+      sFY[t] = fv;
+      if (own) {
+        int f = g.noff + fj * g.nx + fi;
+        w.fy[f] = fv; w.fyb[f] = yb; w.fylo[f] = xlo; w.fyhi[f] = xhi;
+      }
+    }
+  }
+  __syncthreads();
+  // ---- 3b, 4. the tile's cells: Vol^{lag}, e^{lag}, rectangle; Vol^{lagCF}, rho^{lagCF}
+  const int ta = tid % TTX, tb = tid / TTX;
+  const int i = i0 + ta, j = j0 + tb;
+  if (i < g.nx && j < g.ny) lagrange_cell<R, M>(g, kc, cur, w, i, j, ta, tb, sDX, sDY, sFX, sFY, sElc, sMK, CN);
+}
+
+// The interface work of the mixed cells lr_t_lagrange listed, in double,
+// eight lanes per cell (one launch instead of lb_mixed_place and lb_mixed):
+// the interface lines (place_lanes), then the split of every flux the cell
+// donates by those lines, the clipping of a material's outgoing volume to
+// what it holds and the donor's final material fluxes (mixed_at), which
+// lr_t_cell_remap reads.  A warp's groups iterate together (mixed_at's
+// shuffles span the warp); a group past the end of the list works on a copy
+// of the first entry and stores nothing.
+template <class R, int M>
+__global__ void __launch_bounds__(128) lr_t_mixed(LrGrid g, LrStateT<R> cur, LrWorkT<R> w) {
+  lr_pdl_enter();
+  int count = (int)w.red[g.mslot];
+  int lane = threadIdx.x & 7;
+  int group = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 3);
+  int ngroups = (int)((gridDim.x * blockDim.x) >> 3);
+  for (int k = 0;; ++k) {
+    if ((group & ~3) + k * ngroups >= count) break;  // uniform over the warp (four groups)
+    int t = group + k * ngroups;
+    bool valid = t < count;
+    int c = w.mixed[g.moff + (valid ? t : 0)];
+    place_lanes<R, M>(g, cur, w, c, valid, lane);
+    __syncwarp();
+    mixed_at<R, M>(g, cur, w, c, valid, lane, 8);
+  }
+}
+
 inline dim3 grid_for(int nxr, int nyr) { return dim3((nxr + BX - 1) / BX, (nyr + BY - 1) / BY); }
 
 // Launch with programmatic stream serialisation (see lr_pdl_enter).
 template <class... KArgs, class... Args>
-cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args... args) {
+cudaError_t launch_pdl_smem(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -2070,6 +3043,10 @@ cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, cudaStream_t 
   cfg.attrs = at;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k, args...);
+}
+template <class... KArgs, class... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args... args) {
+  return launch_pdl_smem(k, grid, block, 0, s, args...);
 }
 
 template <class R>
@@ -2125,6 +3102,45 @@ cudaError_t launch_t(int kid, const LrGrid& g, const LrState& cur0, const LrStat
     case LRK_PREPARE: LR_M(lr_prepare, grid_for(g.nx + 1, g.ny + 1)); break;
     case LRK_CFL_ONLY: LR_1(lr_cfl_only, grid_for(g.nxu, g.nyu)); break;
     case LRK_SWEEP_PREP: LR_M(lr_sweep_prep, grid_for(g.nxu, g.nyu)); break;
+    case LRK_T_CELL_REMAP: {
+      dim3 gr((g.nx + TTX - 1) / TTX, (g.ny + TTY - 1) / TTY);
+      cudaError_t e = g.M == 1 ? launch_pdl_smem(lr_t_cell_remap<R, 1>, gr, dim3(TTHREADS), cell_remap_smem<R, 1>(), s,
+                                                 g, kc, cur, nxt, w)
+                    : g.M == 2 ? launch_pdl_smem(lr_t_cell_remap<R, 2>, gr, dim3(TTHREADS), cell_remap_smem<R, 2>(), s,
+                                                 g, kc, cur, nxt, w)
+                               : launch_pdl_smem(lr_t_cell_remap<R, 3>, gr, dim3(TTHREADS), cell_remap_smem<R, 3>(), s,
+                                                 g, kc, cur, nxt, w);
+      if (e != cudaSuccess) return e;
+      break;
+    }
+    case LRK_T_MIXED: {
+      if (g.M == 1) break;
+      long long lanes = 8ll * g.nx * g.ny;
+      int nb = (int)((lanes + 127) / 128);
+      if (nb > 152 * 8) nb = 152 * 8;
+      cudaError_t e = g.M == 2 ? launch_pdl(lr_t_mixed<R, 2>, dim3(nb), dim3(128), s, g, cur, w)
+                               : launch_pdl(lr_t_mixed<R, 3>, dim3(nb), dim3(128), s, g, cur, w);
+      if (e != cudaSuccess) return e;
+      break;
+    }
+    case LRK_T_LAGRANGE: {
+      dim3 gr((g.nx + TTX - 1) / TTX, (g.ny + TTY - 1) / TTY);
+      cudaError_t e = g.M == 1 ? launch_pdl_smem(lr_t_lagrange<R, 1>, gr, dim3(TTHREADS), lagrange_smem<R, 1>(), s,
+                                                 g, kc, cur, nxt, w)
+                    : g.M == 2 ? launch_pdl_smem(lr_t_lagrange<R, 2>, gr, dim3(TTHREADS), lagrange_smem<R, 2>(), s,
+                                                 g, kc, cur, nxt, w)
+                               : launch_pdl_smem(lr_t_lagrange<R, 3>, gr, dim3(TTHREADS), lagrange_smem<R, 3>(), s,
+                                                 g, kc, cur, nxt, w);
+      if (e != cudaSuccess) return e;
+      break;
+    }
+    case LRK_T_NODE_REMAP: {
+      dim3 gr((g.nxu + TTX - 1) / TTX, (g.nyu + TTY - 1) / TTY);
+      cudaError_t e = launch_pdl_smem(lr_t_node_remap<R>, gr, dim3(TTHREADS), node_remap_smem<R>(), s, g, kc, cur,
+                                      nxt, w);
+      if (e != cudaSuccess) return e;
+      break;
+    }
     default: return cudaErrorInvalidValue;
   }
 #undef LR_M
@@ -2189,6 +3205,37 @@ __global__ void lr_reset_k(LrWorkT<R> w, int nsim) {
 }  // namespace
 
 int lr_default_mixed_lanes(int mode) { return LR_DEFAULT_LANES; }
+
+cudaError_t lr_tiled_setup() {
+  cudaError_t e;
+#define LR_SMEM(K, BYTES)                                                                          \
+  if ((e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(BYTES))) != \
+      cudaSuccess)                                                                                 \
+    return e;
+  LR_SMEM(lr_t_node_remap<double>, node_remap_smem<double>());
+  LR_SMEM(lr_t_node_remap<float>, node_remap_smem<float>());
+  LR_SMEM(lr_t_node_remap<df64>, node_remap_smem<df64>());
+  LR_SMEM((lr_t_cell_remap<double, 1>), (cell_remap_smem<double, 1>()));
+  LR_SMEM((lr_t_cell_remap<double, 2>), (cell_remap_smem<double, 2>()));
+  LR_SMEM((lr_t_cell_remap<double, 3>), (cell_remap_smem<double, 3>()));
+  LR_SMEM((lr_t_cell_remap<float, 1>), (cell_remap_smem<float, 1>()));
+  LR_SMEM((lr_t_cell_remap<float, 2>), (cell_remap_smem<float, 2>()));
+  LR_SMEM((lr_t_cell_remap<float, 3>), (cell_remap_smem<float, 3>()));
+  LR_SMEM((lr_t_cell_remap<df64, 1>), (cell_remap_smem<df64, 1>()));
+  LR_SMEM((lr_t_cell_remap<df64, 2>), (cell_remap_smem<df64, 2>()));
+  LR_SMEM((lr_t_cell_remap<df64, 3>), (cell_remap_smem<df64, 3>()));
+  LR_SMEM((lr_t_lagrange<double, 1>), (lagrange_smem<double, 1>()));
+  LR_SMEM((lr_t_lagrange<double, 2>), (lagrange_smem<double, 2>()));
+  LR_SMEM((lr_t_lagrange<double, 3>), (lagrange_smem<double, 3>()));
+  LR_SMEM((lr_t_lagrange<float, 1>), (lagrange_smem<float, 1>()));
+  LR_SMEM((lr_t_lagrange<float, 2>), (lagrange_smem<float, 2>()));
+  LR_SMEM((lr_t_lagrange<float, 3>), (lagrange_smem<float, 3>()));
+  LR_SMEM((lr_t_lagrange<df64, 1>), (lagrange_smem<df64, 1>()));
+  LR_SMEM((lr_t_lagrange<df64, 2>), (lagrange_smem<df64, 2>()));
+  LR_SMEM((lr_t_lagrange<df64, 3>), (lagrange_smem<df64, 3>()));
+#undef LR_SMEM
+  return cudaSuccess;
+}
 
 size_t lr_real_size(int mode) { return mode == LR_MODE_FP32 ? sizeof(float) : mode == LR_MODE_DF64 ? sizeof(df64) : sizeof(double); }
 
@@ -2288,6 +3335,24 @@ cudaError_t lr_launch_arith(int op, const double* a, const double* b, double* ou
   size_t nb = (n + 255) / 256;
   if (nb > 0x7fffffffull) return cudaErrorInvalidValue;
   lr_arith_k<<<(unsigned)nb, 256, 0, s>>>(op, a, b, out, n);
+  return cudaGetLastError();
+}
+
+// FP64 fused multiply-add throughput (lr_fp64_fma_probe): eight independent
+// chains a <- a x + y per thread, so the FP64 pipe rather than the FMA
+// latency bounds the rate; the sum is stored so no chain is dead code.
+__global__ void lr_dfma_k(double* out, int iters, double x, double y) {
+  double a0 = 1e-3 * threadIdx.x, a1 = a0 + 1.0, a2 = a0 + 2.0, a3 = a0 + 3.0;
+  double a4 = a0 + 4.0, a5 = a0 + 5.0, a6 = a0 + 6.0, a7 = a0 + 7.0;
+#pragma unroll 4
+  for (int q = 0; q < iters; ++q) {
+    a0 = fma(a0, x, y); a1 = fma(a1, x, y); a2 = fma(a2, x, y); a3 = fma(a3, x, y);
+    a4 = fma(a4, x, y); a5 = fma(a5, x, y); a6 = fma(a6, x, y); a7 = fma(a7, x, y);
+  }
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7));
+}
+cudaError_t lr_launch_dfma(double* out, int blocks, int threads, int iters, cudaStream_t s) {
+  lr_dfma_k<<<blocks, threads, 0, s>>>(out, iters, 0.9999999, 1e-7);
   return cudaGetLastError();
 }
 

@@ -121,6 +121,15 @@ def load(build_if_missing: bool = True):
     L.lr_launches_per_step.argtypes = [vp]
     L.lr_launches_per_step.restype = ctypes.c_int
     L.lr_set_profiling.argtypes = [vp, ctypes.c_int]
+    L.lr_checkpoint_bytes.argtypes = [vp]
+    L.lr_checkpoint_bytes.restype = ctypes.c_size_t
+    L.lr_checkpoint_save.argtypes = [vp, vp, ctypes.c_size_t]
+    L.lr_checkpoint_save.restype = ctypes.c_int
+    L.lr_checkpoint_load.argtypes = [vp, vp, ctypes.c_size_t]
+    L.lr_checkpoint_load.restype = ctypes.c_int
+    L.lr_set_tiled.argtypes = [vp, ctypes.c_int]
+    L.lr_get_tiled.argtypes = [vp]
+    L.lr_get_tiled.restype = ctypes.c_int
     L.lr_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_long),
                                   _dp, ctypes.c_int]
     L.lr_kernel_times.restype = ctypes.c_int
@@ -134,6 +143,8 @@ def load(build_if_missing: bool = True):
     L.lr_get_fields_async.restype = ctypes.c_int
     L.lr_arith_check.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.c_size_t, vp]
     L.lr_arith_check.restype = ctypes.c_int
+    L.lr_fp64_fma_probe.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]
+    L.lr_fp64_fma_probe.restype = ctypes.c_int
     bp = ctypes.POINTER(BatchConfig)
     L.lr_batch_config_default.argtypes = [bp]
     L.lr_batch_config_default.restype = None
@@ -193,7 +204,7 @@ def load(build_if_missing: bool = True):
         getattr(L, name).restype = ctypes.c_int
     for name in ("lr_workspace_bytes", "lr_create", "lr_create_in", "lr_set_materials", "lr_init",
                  "lr_set_prescribed_velocity", "lr_step", "lr_run", "lr_sync", "lr_get_fields",
-                 "lr_get_fields_device", "lr_time", "lr_set_profiling"):
+                 "lr_get_fields_device", "lr_time", "lr_set_profiling", "lr_set_tiled"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -205,11 +216,23 @@ def arith_check(op: int, a, b, out, stream: int = 0) -> None:
     L = load()
     n = out.numel()
     if a.numel() != n or b.numel() != n:
-        raise LrError("lr_arith_check: a, b and out differ in size")
+        raise LrError(ERR_ARG, "lr_arith_check: a, b and out differ in size")
     rc = L.lr_arith_check(op, ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()),
                           ctypes.c_void_p(out.data_ptr()), n, ctypes.c_void_p(stream))
     if rc != OK:
-        raise LrError(f"lr_arith_check failed ({rc})")
+        raise LrError(rc, "lr_arith_check failed")
+
+
+def fp64_fma_probe(out, blocks: int, threads: int, iters: int, stream: int = 0) -> float:
+    """Enqueue lr_fp64_fma_probe into the float64 CUDA tensor ``out`` (at
+    least blocks * threads elements) on ``stream``; returns the flops it
+    performs (16 per thread and iteration)."""
+    if out.numel() < blocks * threads:
+        raise LrError(ERR_ARG, "lr_fp64_fma_probe: output too small")
+    rc = load().lr_fp64_fma_probe(ctypes.c_void_p(out.data_ptr()), blocks, threads, iters, ctypes.c_void_p(stream))
+    if rc != OK:
+        raise LrError(rc, "lr_fp64_fma_probe failed")
+    return 16.0 * iters * blocks * threads
 
 
 def _c64(a) -> np.ndarray:
@@ -365,6 +388,27 @@ class Sim:
 
     def set_profiling(self, on: bool):
         self._check(load().lr_set_profiling(self._h, 1 if on else 0))
+
+    def checkpoint(self) -> np.ndarray:
+        """The exact state (lr_checkpoint_save) as a byte array."""
+        L = load()
+        n = L.lr_checkpoint_bytes(self._h)
+        buf = np.empty(n, dtype=np.uint8)
+        self._check(L.lr_checkpoint_save(self._h, buf.ctypes.data_as(ctypes.c_void_p), n))
+        return buf
+
+    def restore(self, buf: np.ndarray):
+        """Continue from a checkpoint of the same configuration."""
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        self._check(load().lr_checkpoint_load(self._h, buf.ctypes.data_as(ctypes.c_void_p), buf.size))
+
+    def set_tiled(self, on: bool):
+        """Switch the tiled (fused, shared-memory) step kernels on or off."""
+        self._check(load().lr_set_tiled(self._h, 1 if on else 0))
+
+    @property
+    def tiled(self) -> bool:
+        return bool(load().lr_get_tiled(self._h))
 
     def kernel_times(self):
         L = load()
