@@ -115,6 +115,27 @@ lr_status lr_batch_schedule(const lr_batch* b, int* tile_shape, int* blocks_per_
 /* Kernel launches the last step enqueued (all groups). */
 int lr_batch_launches_per_step(const lr_batch* b);
 
+/* Persistent step (on by default where the device can hold it resident):
+ * each step is one cooperative launch of co-resident blocks that walk every
+ * member's 32 x 8 cell tiles and node tiles through the phases of the tiled
+ * step (the Lagrange phase and remap geometry of section 1.2 and 2.3; the
+ * interface lines and material fluxes of the mixed cells, section 4.4; the
+ * material fluxes and cell update; the dual remap and node update of
+ * section 2.1.1 with each member's own CFL time step), separated by grid-wide
+ * barriers.  Every barrier wait has a limit (1 s); a wait that runs out
+ * abandons the step, and lr_batch_sync then returns LR_ERR_TIMEOUT, as does
+ * every later call that steps the batch (the batch has to be destroyed).
+ * Off: one launch per kernel and material-count group, with the schedule
+ * lr_batch_autotune picks (the autotuner times that path).
+ * lr_batch_get_persistent returns 1 when the persistent step is in use. */
+lr_status lr_batch_set_persistent(lr_batch* b, int on);
+int lr_batch_get_persistent(const lr_batch* b);
+
+/* Test hook of the persistent step's barrier: each barrier waits for
+ * extra_arrivals arrivals that no block makes (0: none, the normal
+ * setting), and gives up after limit_s seconds (default 1; at most 10). */
+lr_status lr_batch_test_barrier(lr_batch* b, unsigned int extra_arrivals, double limit_s);
+
 /* Per-kernel timing with CUDA events around every launch (profiling mode
  * launches without the graph); as lr_set_profiling / lr_kernel_times. */
 lr_status lr_batch_set_profiling(lr_batch* b, int on);

@@ -431,13 +431,16 @@ cudaError_t enqueue_step(lr_ctx* ctx, int from) {
   const LrState& nxt = ctx->st[1 - from];
   if (ctx->tiled) {
     // Tiled step on one stream: the Lagrange phase and remap geometry; the
-    // interface work of the mixed cells; the material fluxes and cell
+    // interface kernels of the mixed cells; the material fluxes and cell
     // update; the dual remap and node update (it reads the new sound speeds
     // for the CFL rule).
     const LrGrid& g = ctx->g;
     cudaError_t e;
     if ((e = launch_on(ctx, LRK_T_LAGRANGE, g, cur, nxt, ctx->stream)) != cudaSuccess) return e;
-    if (g.M > 1 && (e = launch_on(ctx, LRK_T_MIXED, g, cur, nxt, ctx->stream)) != cudaSuccess) return e;
+    if (g.M > 1) {  // the interface lines, then the split of the fluxes mixed cells donate
+      if ((e = launch_on(ctx, LRK_MIXED_PLACE, g, cur, nxt, ctx->stream)) != cudaSuccess) return e;
+      if ((e = launch_on(ctx, LRK_MIXED, g, cur, nxt, ctx->stream)) != cudaSuccess) return e;
+    }
     if ((e = launch_on(ctx, LRK_T_CELL_REMAP, g, cur, nxt, ctx->stream)) != cudaSuccess) return e;
     return launch_on(ctx, LRK_T_NODE_REMAP, g, cur, nxt, ctx->stream);
   }
@@ -861,9 +864,9 @@ int lr_launches_per_step(const lr_ctx* ctx) {
   if (!ctx) return 0;
   // the interface work is two kernels (placement, then the flux split)
   int one = (int)LRK_COUNT + (ctx->g.M == 1 ? -1 : 1);
-  // tiled: t_end/dt, Lagrange, interface work (two or more materials), cell
-  // remap, node remap
-  if (ctx->tiled) return ctx->g.M == 1 ? 4 : 5;
+  // tiled: t_end/dt, Lagrange, interface lines and flux split (two or more
+  // materials), cell remap, node remap
+  if (ctx->tiled) return ctx->g.M == 1 ? 4 : 6;
   return 1 + one + (ctx->g.remap == LR_REMAP_AD ? one - 1 : 0);
 }
 

@@ -82,10 +82,17 @@ struct lr_batch {
   bool gvalid[2] = {false, false};
   int launches = 0;
   bool prof = false;
+  // persistent step: one cooperative launch per step (lb_t_step)
+  bool persistent = true;
+  int pers_bps = 0;                 // resident blocks per SM of lb_t_step
+  LrGridBar* bar = nullptr;         // its grid barrier (count, generation, status)
+  unsigned int bar_extra = 0;       // test hook: arrivals no block makes
+  unsigned long long bar_limit_ns = 1000000000ull;
+  int sticky = LR_OK;               // LR_ERR_TIMEOUT after a barrier gave up
   struct Pend { int kid; cudaEvent_t a, b; };
   std::vector<Pend> pend;
-  double acc_ms[LRK_COUNT];
-  long acc_n[LRK_COUNT];
+  double acc_ms[LRK_COUNT + 1];     // per kernel; the last slot: the persistent step kernel
+  long acc_n[LRK_COUNT + 1];
   char msg[512];
 };
 
@@ -183,6 +190,7 @@ size_t layout(const lr_batch_config* c, char* base, lr_batch* b) {
   }
   W.MX = R(P); W.MY = R(P); W.Mpp = R(P); W.Mpm = R(P);
   for (int q = 0; q < 3; ++q) { W.dX[q] = R(P); W.dY[q] = R(P); W.dPP[q] = R(P); W.dPM[q] = R(P); }
+  LrGridBar* bar = m.take<LrGridBar>(1);
   LrGrid* gs = m.take<LrGrid>(S);
   size_t kcb = lr_kc_bytes(mode_of(c->precision));
   char* kcs = m.take<char>(S * kcb);
@@ -194,6 +202,7 @@ size_t layout(const lr_batch_config* c, char* base, lr_batch* b) {
     b->scal_bytes = sc1 - sc0;
     b->cc_bytes = P * es;
     b->d_gs = gs; b->d_kcs = kcs; b->kcb = kcb;
+    b->bar = bar;
     b->tmp = tmp; b->rows = rows;
   }
   return m.off + 256;
@@ -254,6 +263,8 @@ lr_status rebuild(lr_batch* b) {
   memset(use, 0, sizeof(use));
   for (int k = 0; k < LRK_COUNT; ++k)
     if (k != LRK_MIXED) use[b->sch.shape[k]][lr_kernel_domain(k)] = true;
+  // the persistent step walks 32 x 8 cell tiles and node tiles
+  use[0][LR_DOM_CELLS] = use[0][LR_DOM_NODES] = true;
   std::vector<LrTile> all;
   memset(b->rng, 0, sizeof(b->rng));
   for (int M = 0; M <= LR_MAXM; ++M) { b->group_units[M] = 0; b->group_members[M] = 0; }
@@ -329,9 +340,52 @@ void set_mixed_args(const lr_batch* b, int M, int lanes, LrBatchArgs& a) {
   a.grid = (int)(nb < (long)b->nsm * 16 ? nb : (long)b->nsm * 16);
 }
 
+bool persistent_on(const lr_batch* b) { return b->persistent && b->pers_bps > 0; }
+
+// One step of every member in one cooperative launch (lb_t_step), after the
+// barrier words are cleared.
+cudaError_t enqueue_persistent(lr_batch* b, int from) {
+  const LrState& cur = b->st[from];
+  const LrState& nxt = b->st[1 - from];
+  const Range& rc = b->rng[0][LR_DOM_CELLS][0];
+  const Range& rn = b->rng[0][LR_DOM_NODES][0];
+  b->launches = 0;
+  if (rc.count == 0) return cudaSuccess;
+  LrPersistArgs p;
+  memset(&p, 0, sizeof(p));
+  p.gs = b->d_gs;
+  p.kcs = b->d_kcs;
+  p.ctiles = b->d_tiles + rc.start;
+  p.nct = rc.count;
+  p.ntiles = b->d_tiles + rn.start;
+  p.nnt = rn.count;
+  p.bar = b->bar;
+  p.extra = b->bar_extra;
+  p.limit_ns = b->bar_limit_ns;
+  p.groups = (b->group_members[2] > 0 ? 4 : 0) | (b->group_members[3] > 0 ? 8 : 0);
+  p.P = (int)b->P;
+  int most = b->nsm * b->pers_bps;
+  p.grid = rc.count < most ? rc.count : most;
+  if (rn.count < p.grid) p.grid = rn.count > 0 ? rn.count : 1;
+  cudaError_t e = cudaMemsetAsync(b->bar, 0, sizeof(LrGridBar), b->stream);
+  if (e != cudaSuccess) return e;
+  b->launches = 1;
+  if (!b->prof) return lr_launch_batch_persistent(b->mode, p, cur, nxt, b->w, b->stream);
+  lr_batch::Pend pe;
+  pe.kid = LRK_COUNT;
+  cudaEventCreate(&pe.a);
+  cudaEventCreate(&pe.b);
+  cudaEventRecord(pe.a, b->stream);
+  e = lr_launch_batch_persistent(b->mode, p, cur, nxt, b->w, b->stream);
+  cudaEventRecord(pe.b, b->stream);
+  b->pend.push_back(pe);
+  return e;
+}
+
 // One step of every member: for each kernel, one launch per material-count
 // group (kernels that do not depend on it: one launch over all groups).
 cudaError_t enqueue_step(lr_batch* b, int from) {
+  if (persistent_on(b)) return enqueue_persistent(b, from);
   const LrState& cur = b->st[from];
   const LrState& nxt = b->st[1 - from];
   b->launches = 0;
@@ -428,7 +482,25 @@ lr_status ensure_graph(lr_batch* b, int from) {
   return LR_OK;
 }
 
+// The persistent step's barrier status: a wait that gave up leaves the
+// batch in error (LR_ERR_TIMEOUT) until it is destroyed.
+lr_status check_barrier(lr_batch* b) {
+  if (b->sticky != LR_OK) return (lr_status)b->sticky;
+  if (!persistent_on(b)) return LR_OK;
+  LrGridBar h;
+  CK(cudaMemcpyAsync(&h, b->bar, sizeof(h), cudaMemcpyDeviceToHost, b->stream), "barrier status");
+  CK(cudaStreamSynchronize(b->stream), "sync");
+  if (h.status != 0) {
+    b->sticky = LR_ERR_TIMEOUT;
+    setmsg(b, "persistent step: a grid barrier waited longer than %.3f s and the step was abandoned",
+           (double)b->bar_limit_ns * 1e-9);
+    return LR_ERR_TIMEOUT;
+  }
+  return LR_OK;
+}
+
 lr_status run_steps(lr_batch* b, int nsteps) {
+  if (b->sticky != LR_OK) return (lr_status)b->sticky;
   if (b->need_rebuild) {
     lr_status s = rebuild(b);
     if (s != LR_OK) return s;
@@ -562,7 +634,10 @@ lr_status lr_batch_create(const lr_batch_config* cfg, lr_batch** out) {
   b->mem.resize(b->S);
   b->freel.push_back(std::make_pair(0L, b->P));
   default_schedule(b);
-  for (int k = 0; k < LRK_COUNT; ++k) { b->acc_ms[k] = 0.0; b->acc_n[k] = 0; }
+  for (int k = 0; k <= LRK_COUNT; ++k) { b->acc_ms[k] = 0.0; b->acc_n[k] = 0; }
+  if (lr_tiled_setup() != cudaSuccess) cudaGetLastError();
+  b->pers_bps = lr_persistent_blocks_per_sm(b->mode);
+  if (b->pers_bps > 4) b->pers_bps = 4;
   b->msg[0] = 0;
   if (lr_launch_reset(b->mode, b->w, b->S, b->stream) != cudaSuccess ||
       cudaStreamSynchronize(b->stream) != cudaSuccess) {
@@ -728,6 +803,27 @@ lr_status lr_batch_step(lr_batch* b, int nsteps) {
 lr_status lr_batch_sync(lr_batch* b) {
   if (!b) return LR_ERR_ARG;
   CK(cudaStreamSynchronize(b->stream), "sync");
+  return check_barrier(b);
+}
+
+lr_status lr_batch_set_persistent(lr_batch* b, int on) {
+  if (!b) return LR_ERR_ARG;
+  if (on && b->pers_bps <= 0) { setmsg(b, "the persistent step cannot be resident on this device"); return LR_ERR_ARG; }
+  CK(cudaStreamSynchronize(b->stream), "sync");
+  b->persistent = on != 0;
+  b->need_rebuild = true;
+  return LR_OK;
+}
+
+int lr_batch_get_persistent(const lr_batch* b) { return b && persistent_on(b) ? 1 : 0; }
+
+lr_status lr_batch_test_barrier(lr_batch* b, unsigned int extra_arrivals, double limit_s) {
+  if (!b || !(limit_s > 0.0) || limit_s > 10.0) return LR_ERR_ARG;
+  CK(cudaStreamSynchronize(b->stream), "sync");
+  b->bar_extra = extra_arrivals;
+  b->bar_limit_ns = (unsigned long long)(limit_s * 1e9);
+  for (int q = 0; q < 2; ++q)
+    if (b->gvalid[q]) { cudaGraphExecDestroy(b->gexec[q]); b->gvalid[q] = false; }
   return LR_OK;
 }
 
@@ -801,6 +897,7 @@ lr_status lr_batch_get_fields(lr_batch* b, int m, int field, double* host_out, s
 
 int lr_batch_launches_per_step(const lr_batch* b) {
   if (!b) return 0;
+  if (persistent_on(b)) return 1;
   int n = 0;
   for (int k = 0; k < LRK_COUNT; ++k) {
     if (k == LRK_MIXED) {  // placement and flux split: two kernels per group
@@ -824,7 +921,7 @@ lr_status lr_batch_set_profiling(lr_batch* b, int on) {
   CK(cudaStreamSynchronize(b->stream), "sync");
   for (auto& p : b->pend) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
   b->pend.clear();
-  for (int k = 0; k < LRK_COUNT; ++k) { b->acc_ms[k] = 0.0; b->acc_n[k] = 0; }
+  for (int k = 0; k <= LRK_COUNT; ++k) { b->acc_ms[k] = 0.0; b->acc_n[k] = 0; }
   b->prof = on != 0;
   return LR_OK;
 }
@@ -839,13 +936,13 @@ int lr_batch_kernel_times(lr_batch* b, const char** names, long* launches, doubl
     cudaEventDestroy(p.b);
   }
   b->pend.clear();
-  int m = n < (int)LRK_COUNT ? n : (int)LRK_COUNT;
+  int m = n < (int)LRK_COUNT + 1 ? n : (int)LRK_COUNT + 1;
   for (int k = 0; k < m; ++k) {
-    if (names) names[k] = lr_kernel_names[k];
+    if (names) names[k] = k < LRK_COUNT ? lr_kernel_names[k] : "lb_t_step";
     if (launches) launches[k] = b->acc_n[k];
     if (ms) ms[k] = b->acc_ms[k];
   }
-  return LRK_COUNT;
+  return LRK_COUNT + 1;
 }
 
 lr_status lr_batch_schedule(const lr_batch* b, int* shape, int* bps, int* lanes) {
@@ -864,7 +961,12 @@ lr_status lr_batch_autotune(lr_batch* b, int trial_steps) {
   bool any = false;
   for (auto& m : b->mem) any |= m.used;
   if (!any) { setmsg(b, "lr_batch_autotune: no members"); return LR_ERR_STATE; }
+  if (b->sticky != LR_OK) return (lr_status)b->sticky;
   CK(cudaStreamSynchronize(b->stream), "sync");
+  // the schedule belongs to the per-kernel step; the persistent step is off
+  // while the trials run
+  const bool pers0 = b->persistent;
+  b->persistent = false;
   // snapshot of the current state buffer, the scalars and the sound-speed
   // term the next step's lb_cell_pre reads
   char* snap = nullptr;
@@ -935,6 +1037,7 @@ lr_status lr_batch_autotune(lr_batch* b, int trial_steps) {
   }
   cudaFree(snap);
   b->sch = best;
+  b->persistent = pers0;
   b->need_rebuild = true;
   if (rs != LR_OK) return rs;
   // the members' grids carry the lanes of lr_mixed only through the launch

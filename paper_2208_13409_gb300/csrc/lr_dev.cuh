@@ -190,6 +190,30 @@ struct LrBatchArgs {
 };
 cudaError_t lr_launch_batch(int kid, const LrBatchArgs& a, const LrState& cur, const LrState& nxt,
                             const LrWork& w, cudaStream_t s);
+// Persistent batch step (lb_t_step): one cooperative launch of `grid`
+// blocks per step over the cell tiles (32 x 8, every member) and the node
+// tiles, with grid barriers between the phases (bar: count, generation,
+// status; status LR_BAR_TIMEOUT after a wait of limit_ns).  groups: bit 2
+// set when two-material members are present, bit 3 three-material ones; P
+// the pool size (the three-material list starts at P).
+struct LrGridBar { unsigned int count, gen; int status, pad; };
+enum { LR_BAR_TIMEOUT = 1 };
+struct LrPersistArgs {
+  const LrGrid* gs;
+  const void* kcs;
+  const LrTile* ctiles;
+  int nct;
+  const LrTile* ntiles;
+  int nnt;
+  LrGridBar* bar;
+  unsigned int extra;
+  unsigned long long limit_ns;
+  int groups, P, grid;
+};
+cudaError_t lr_launch_batch_persistent(int mode, const LrPersistArgs& p, const LrState& cur, const LrState& nxt,
+                                       const LrWork& w, cudaStream_t s);
+// Resident blocks of lb_t_step per SM (0 when it cannot run).
+int lr_persistent_blocks_per_sm(int mode);
 size_t lr_kc_bytes(int mode);
 void lr_make_kc(const LrGrid& g, void* out);
 // Field views: convert a real array (element type from g.mode) to double,

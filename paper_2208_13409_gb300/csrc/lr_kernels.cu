@@ -2265,18 +2265,16 @@ template <class R> constexpr size_t node_remap_smem() {
 // u_p^{lag} + signed dual momentum fluxes for its nodes and the CFL rule of
 // the next step (node_update_at's arithmetic).
 template <class R>
-__global__ void __launch_bounds__(TTHREADS, MinBlocks<R, LR_MINB_D_DUAL>::value)
-    lr_t_node_remap(LrGrid g, KC<R> kc, LrStateT<R> cur, LrStateT<R> nxt, LrWorkT<R> w) {
+__device__ __forceinline__ void t_node_tile(const LrGrid& g, const KC<R>& kc, const LrStateT<R>& cur,
+                                            const LrStateT<R>& nxt, const LrWorkT<R>& w, int i0, int j0,
+                                            unsigned long long ntiles, unsigned char* lr_smem) {
   using O = RealOps<R>;
-  lr_pdl_enter();
-  extern __shared__ __align__(16) unsigned char lr_smem[];
   R* sm = reinterpret_cast<R*>(lr_smem);
   constexpr int SN = NR_SW * NR_SH, ON = NR_OW * NR_OH;
   R *sUX = sm, *sUY = sm + SN, *sDX = sm + 2 * SN, *sDY = sm + 3 * SN, *sMX = sm + 4 * SN, *sMY = sm + 5 * SN;
   R *sPP = sm + 6 * SN, *sPM = sm + 7 * SN, *sMC = sm + 8 * SN, *sCC = sm + 9 * SN;
   R* so = sm + NR_STAGED * SN;  // objects: dX[3], dY[3], dPP[3], dPM[3]
   const int tid = threadIdx.x;
-  const int i0 = blockIdx.x * TTX, j0 = blockIdx.y * TTY;
   const int ta = tid % TTX, tb = tid / TTX;
   const int i = i0 + ta, j = j0 + tb;
   const bool act = i < g.nxu && j < g.nyu;
@@ -2367,7 +2365,15 @@ __global__ void __launch_bounds__(TTHREADS, MinBlocks<R, LR_MINB_D_DUAL>::value)
     R cm = rmax(rmax(sCC[s0 - NR_SW - 1], sCC[s0 - NR_SW]), rmax(sCC[s0 - 1], sCC[s0]));
     val = cm + O::sqrt(ux1 * ux1 + uy1 * uy1);
   }
-  cfl_finalize(g, kc, w, val, true, (unsigned long long)gridDim.x * gridDim.y);
+  cfl_finalize(g, kc, w, val, true, ntiles);
+}
+template <class R>
+__global__ void __launch_bounds__(TTHREADS, MinBlocks<R, LR_MINB_D_DUAL>::value)
+    lr_t_node_remap(LrGrid g, KC<R> kc, LrStateT<R> cur, LrStateT<R> nxt, LrWorkT<R> w) {
+  lr_pdl_enter();
+  extern __shared__ __align__(16) unsigned char lr_smem[];
+  t_node_tile<R>(g, kc, cur, nxt, w, blockIdx.x * TTX, blockIdx.y * TTY, (unsigned long long)gridDim.x * gridDim.y,
+                 lr_smem);
 }
 
 // Cell data a flux object reads, staged with the boundary conditions
@@ -2461,11 +2467,10 @@ template <class R, int M> constexpr size_t cell_remap_smem() {
 // are read from the arrays lr_t_lagrange's interface phase stored.  Then the
 // cell update of cell_update_at.
 template <class R, int M>
-__global__ void __launch_bounds__(TTHREADS, MinBlocks<R, LR_MINB_D_UPDATE>::value)
-    lr_t_cell_remap(LrGrid g, KC<R> kc, LrStateT<R> cur, LrStateT<R> nxt, LrWorkT<R> w) {
+__device__ __forceinline__ void t_cell_tile(const LrGrid& g, const KC<R>& kc, const LrStateT<R>& cur,
+                                            const LrStateT<R>& nxt, const LrWorkT<R>& w, int i0, int j0,
+                                            unsigned char* lr_smem) {
   using O = RealOps<R>;
-  lr_pdl_enter();
-  extern __shared__ __align__(16) unsigned char lr_smem[];
   constexpr int SN = CR_SW * CR_SH, ON = CR_OW * CR_OH;
   R* sm = reinterpret_cast<R*>(lr_smem);
   R *sOX = sm, *sOY = sm + SN, *sWX = sm + 2 * SN, *sWY = sm + 3 * SN, *sDX = sm + 4 * SN, *sDY = sm + 5 * SN;
@@ -2476,7 +2481,7 @@ __global__ void __launch_bounds__(TTHREADS, MinBlocks<R, LR_MINB_D_UPDATE>::valu
   unsigned char* sMK = reinterpret_cast<unsigned char*>(oE + 3 * ON);
   signed char* oMat = reinterpret_cast<signed char*>(sMK + SN);  // material, -1 none, -2 mixed donor
   const int tid = threadIdx.x;
-  const int i0 = blockIdx.x * TTX, j0 = blockIdx.y * TTY;
+
   const int ta = tid % TTX, tb = tid / TTX;
   const int i = i0 + ta, j = j0 + tb;
   const bool act = i < g.nx && j < g.ny;
@@ -2735,6 +2740,13 @@ __global__ void __launch_bounds__(TTHREADS, MinBlocks<R, LR_MINB_D_UPDATE>::valu
   }
   w.cc[c] = cmax;
 }
+template <class R, int M>
+__global__ void __launch_bounds__(TTHREADS, MinBlocks<R, LR_MINB_D_UPDATE>::value)
+    lr_t_cell_remap(LrGrid g, KC<R> kc, LrStateT<R> cur, LrStateT<R> nxt, LrWorkT<R> w) {
+  lr_pdl_enter();
+  extern __shared__ __align__(16) unsigned char lr_smem[];
+  t_cell_tile<R, M>(g, kc, cur, nxt, w, blockIdx.x * TTX, blockIdx.y * TTY, lr_smem);
+}
 
 constexpr int LG_CW = TTX + 2, LG_CH = TTY + 2, LG_NW = TTX + 3, LG_NH = TTY + 3, LG_OW = TTX + 1,
               LG_OH = TTY + 1;
@@ -2809,11 +2821,9 @@ __device__ __forceinline__ void lagrange_cell(const LrGrid& g, const KC<R>& kc, 
 // kernels read are stored for the cells, nodes and faces the tile owns.
 // Mixed cells join the interface work list of lr_t_mixed.
 template <class R, int M>
-__global__ void __launch_bounds__(TTHREADS, MinBlocks<R, 1>::value)
-    lr_t_lagrange(LrGrid g, KC<R> kc, LrStateT<R> cur, LrStateT<R> nxt, LrWorkT<R> w) {
+__device__ __forceinline__ void t_lagrange_tile(const LrGrid& g, const KC<R>& kc, const LrStateT<R>& cur,
+                                                const LrWorkT<R>& w, int i0, int j0, unsigned char* lr_smem) {
   using O = RealOps<R>;
-  lr_pdl_enter();
-  extern __shared__ __align__(16) unsigned char lr_smem[];
   constexpr int NN = LG_NW * LG_NH, CN = LG_CW * LG_CH, ON = LG_OW * LG_OH;
   R* sm = reinterpret_cast<R*>(lr_smem);
   R *sUX = sm, *sUY = sm + NN;
@@ -2821,7 +2831,6 @@ __global__ void __launch_bounds__(TTHREADS, MinBlocks<R, 1>::value)
   R *sDX = sElc + M * CN, *sDY = sDX + ON, *sFX = sDY + ON, *sFY = sFX + ON;
   unsigned char* sMK = reinterpret_cast<unsigned char*>(sFY + ON);
   const int tid = threadIdx.x;
-  const int i0 = blockIdx.x * TTX, j0 = blockIdx.y * TTY;
   if (!step_live(g, w.scal)) return;
   const R Z = O::c(0.0f), H = O::c(0.5f);
   const R dt = w.dtR[g.inst];
@@ -3000,6 +3009,13 @@ __global__ void __launch_bounds__(TTHREADS, MinBlocks<R, 1>::value)
   const int i = i0 + ta, j = j0 + tb;
   if (i < g.nx && j < g.ny) lagrange_cell<R, M>(g, kc, cur, w, i, j, ta, tb, sDX, sDY, sFX, sFY, sElc, sMK, CN);
 }
+template <class R, int M>
+__global__ void __launch_bounds__(TTHREADS, MinBlocks<R, 1>::value)
+    lr_t_lagrange(LrGrid g, KC<R> kc, LrStateT<R> cur, LrStateT<R> nxt, LrWorkT<R> w) {
+  lr_pdl_enter();
+  extern __shared__ __align__(16) unsigned char lr_smem[];
+  t_lagrange_tile<R, M>(g, kc, cur, w, blockIdx.x * TTX, blockIdx.y * TTY, lr_smem);
+}
 
 // The interface work of the mixed cells lr_t_lagrange listed, in double,
 // eight lanes per cell (one launch instead of lb_mixed_place and lb_mixed):
@@ -3009,21 +3025,141 @@ __global__ void __launch_bounds__(TTHREADS, MinBlocks<R, 1>::value)
 // lr_t_cell_remap reads.  A warp's groups iterate together (mixed_at's
 // shuffles span the warp); a group past the end of the list works on a copy
 // of the first entry and stores nothing.
-template <class R, int M>
-__global__ void __launch_bounds__(128) lr_t_mixed(LrGrid g, LrStateT<R> cur, LrWorkT<R> w) {
-  lr_pdl_enter();
-  int count = (int)w.red[g.mslot];
+// One pass over a mixed-cell list (count in red[mslot], entries from moff):
+// lane group `group` of `ngroups` takes entries group, group + ngroups, ...;
+// getg(e) gives entry e's grid.
+template <class R, int M, class G>
+__device__ __forceinline__ void t_mixed_list(G getg, const LrStateT<R>& cur, const LrWorkT<R>& w, int mslot,
+                                             int moff, int group, int ngroups) {
+  int count = (int)w.red[mslot];
   int lane = threadIdx.x & 7;
-  int group = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 3);
-  int ngroups = (int)((gridDim.x * blockDim.x) >> 3);
   for (int k = 0;; ++k) {
     if ((group & ~3) + k * ngroups >= count) break;  // uniform over the warp (four groups)
     int t = group + k * ngroups;
     bool valid = t < count;
-    int c = w.mixed[g.moff + (valid ? t : 0)];
+    int e = moff + (valid ? t : 0);
+    const LrGrid& g = getg(e);
+    int c = w.mixed[e];
     place_lanes<R, M>(g, cur, w, c, valid, lane);
     __syncwarp();
     mixed_at<R, M>(g, cur, w, c, valid, lane, 8);
+  }
+}
+template <class R, int M>
+__global__ void __launch_bounds__(128) lr_t_mixed(LrGrid g, LrStateT<R> cur, LrWorkT<R> w) {
+  lr_pdl_enter();
+  t_mixed_list<R, M>([&](int) -> const LrGrid& { return g; }, cur, w, g.mslot, g.moff,
+                     (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 3), (int)((gridDim.x * blockDim.x) >> 3));
+}
+
+// ---------------------------------------------------- persistent batch step
+// One launch per step of a batch: co-resident blocks (a cooperative launch)
+// walk every member's tiles through the tiled step's phases -- the Lagrange
+// phase and remap geometry (cell tiles), the interface work (the mixed-cell
+// lists of the two- and three-material groups), the material fluxes and cell
+// update (cell tiles), the dual remap and node update with each member's
+// CFL rule (node tiles) -- with a grid-wide barrier between phases.  A block
+// takes every gridDim-th tile of a phase; each tile runs the same device
+// function as the lone simulation's tiled kernel, with its member's grid
+// and constants staged in shared memory.
+
+__device__ __forceinline__ unsigned long long lr_gtime() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier with a bounded wait: thread 0 of each block counts its
+// arrival; the last of nblocks + extra arrivals opens the next generation.
+// A block that has waited limit_ns (or sees that another block gave up)
+// records LR_BAR_TIMEOUT in the barrier's status and returns false, and the
+// kernel returns: no wait lasts longer than the limit.  extra > 0 (a test)
+// asks for arrivals no block makes.
+__device__ bool lr_grid_sync(LrGridBar* bar, unsigned int nblocks, unsigned int extra, unsigned long long limit_ns) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile LrGridBar* vb = bar;
+    unsigned int gen = vb->gen;
+    __threadfence();
+    int res = 1;
+    if (atomicAdd(&bar->count, 1u) + 1u == nblocks + extra) {
+      atomicExch(&bar->count, 0u);
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      unsigned long long t0 = lr_gtime();
+      while (vb->gen == gen) {
+        if (vb->status != 0) { res = 0; break; }
+        if (lr_gtime() - t0 > limit_ns) { atomicCAS(&bar->status, 0, LR_BAR_TIMEOUT); res = 0; break; }
+        __nanosleep(256);
+      }
+    }
+    __threadfence();
+    ok = res;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// Resident blocks of the persistent kernel the register budget is set for:
+// four in float (64 registers), two in double and double-float (128).
+template <class R> struct PersistMinB { static constexpr int value = 2; };
+template <> struct PersistMinB<float> { static constexpr int value = 4; };
+template <class R> constexpr size_t persistent_smem() {
+  size_t a = lagrange_smem<R, 3>(), b = cell_remap_smem<R, 3>(), c = node_remap_smem<R>();
+  return a > b ? (a > c ? a : c) : (b > c ? b : c);
+}
+
+template <class R>
+__global__ void __launch_bounds__(TTHREADS, PersistMinB<R>::value)
+    lb_t_step(const LrGrid* __restrict__ gs, const KC<R>* __restrict__ kcs, const LrTile* __restrict__ ctl, int nct,
+              const LrTile* __restrict__ ntl, int nnt, LrStateT<R> cur, LrStateT<R> nxt, LrWorkT<R> w,
+              LrGridBar* bar, unsigned int extra, unsigned long long limit_ns, int groups, int P) {
+  extern __shared__ __align__(16) unsigned char lr_smem[];
+  __shared__ Staged<R> sd;
+  const int nb = (int)gridDim.x;
+  int staged = -1;
+  auto member = [&](const LrTile& T) {
+    __syncthreads();  // the previous tile no longer reads shared memory
+    if (T.inst != staged) {
+      sd.load(gs + T.inst, kcs + T.inst);
+      staged = T.inst;
+    }
+  };
+  // ---- Lagrange phase and remap geometry; mixed cells join their group's list
+  for (int t = blockIdx.x; t < nct; t += nb) {
+    LrTile T = ctl[t];
+    member(T);
+    const LrGrid& g = sd.g();
+    if (g.M == 1) t_lagrange_tile<R, 1>(g, sd.kc(), cur, w, T.i0, T.j0, lr_smem);
+    else if (g.M == 2) t_lagrange_tile<R, 2>(g, sd.kc(), cur, w, T.i0, T.j0, lr_smem);
+    else t_lagrange_tile<R, 3>(g, sd.kc(), cur, w, T.i0, T.j0, lr_smem);
+  }
+  if (!lr_grid_sync(bar, nb, extra, limit_ns)) return;
+  // ---- interface work of every member's mixed cells
+  {
+    int group = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 3), ngroups = (int)((nb * blockDim.x) >> 3);
+    auto getg = [&](int e) -> const LrGrid& { return gs[w.minst[e]]; };
+    if (groups & 4) t_mixed_list<R, 2>(getg, cur, w, 1, 0, group, ngroups);
+    if (groups & 8) t_mixed_list<R, 3>(getg, cur, w, 2, P, group, ngroups);
+  }
+  if (!lr_grid_sync(bar, nb, extra, limit_ns)) return;
+  // ---- material fluxes and cell update
+  for (int t = blockIdx.x; t < nct; t += nb) {
+    LrTile T = ctl[t];
+    member(T);
+    const LrGrid& g = sd.g();
+    if (g.M == 1) t_cell_tile<R, 1>(g, sd.kc(), cur, nxt, w, T.i0, T.j0, lr_smem);
+    else if (g.M == 2) t_cell_tile<R, 2>(g, sd.kc(), cur, nxt, w, T.i0, T.j0, lr_smem);
+    else t_cell_tile<R, 3>(g, sd.kc(), cur, nxt, w, T.i0, T.j0, lr_smem);
+  }
+  if (!lr_grid_sync(bar, nb, extra, limit_ns)) return;
+  // ---- dual remap, node update and each member's CFL rule
+  for (int t = blockIdx.x; t < nnt; t += nb) {
+    LrTile T = ntl[t];
+    member(T);
+    t_node_tile<R>(sd.g(), sd.kc(), cur, nxt, w, T.i0, T.j0, (unsigned long long)T.n, lr_smem);
   }
 }
 
@@ -3233,6 +3369,9 @@ cudaError_t lr_tiled_setup() {
   LR_SMEM((lr_t_lagrange<df64, 1>), (lagrange_smem<df64, 1>()));
   LR_SMEM((lr_t_lagrange<df64, 2>), (lagrange_smem<df64, 2>()));
   LR_SMEM((lr_t_lagrange<df64, 3>), (lagrange_smem<df64, 3>()));
+  LR_SMEM(lb_t_step<float>, persistent_smem<float>());
+  LR_SMEM(lb_t_step<double>, persistent_smem<double>());
+  LR_SMEM(lb_t_step<df64>, persistent_smem<df64>());
 #undef LR_SMEM
   return cudaSuccess;
 }
@@ -3251,6 +3390,41 @@ cudaError_t lr_launch(int kid, const LrGrid& g, const LrState& cur, const LrStat
 cudaError_t lr_launch_init(const LrGrid& g, const LrState& st, const LrWork& w, cudaStream_t s) {
   cudaError_t e = lr_launch(LRK_PREPARE, g, st, st, w, s);
   return e != cudaSuccess ? e : lr_launch(LRK_CFL_ONLY, g, st, st, w, s);
+}
+
+template <class R>
+cudaError_t launch_persistent_t(const LrPersistArgs& p, const LrState& cur0, const LrState& nxt0, const LrWork& w0,
+                                cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(p.grid);
+  cfg.blockDim = dim3(TTHREADS);
+  cfg.dynamicSmemBytes = persistent_smem<R>();
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, lb_t_step<R>, p.gs, static_cast<const KC<R>*>(p.kcs), p.ctiles, p.nct, p.ntiles,
+                            p.nnt, typed<R>(cur0), typed<R>(nxt0), typed<R>(w0), p.bar, p.extra, p.limit_ns,
+                            p.groups, p.P);
+}
+
+cudaError_t lr_launch_batch_persistent(int mode, const LrPersistArgs& p, const LrState& cur, const LrState& nxt,
+                                       const LrWork& w, cudaStream_t s) {
+  return mode == LR_MODE_FP32 ? launch_persistent_t<float>(p, cur, nxt, w, s)
+       : mode == LR_MODE_DF64 ? launch_persistent_t<df64>(p, cur, nxt, w, s)
+                              : launch_persistent_t<double>(p, cur, nxt, w, s);
+}
+
+int lr_persistent_blocks_per_sm(int mode) {
+  int n = 0;
+  cudaError_t e = mode == LR_MODE_FP32
+      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lb_t_step<float>, TTHREADS, persistent_smem<float>())
+      : mode == LR_MODE_DF64
+      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lb_t_step<df64>, TTHREADS, persistent_smem<df64>())
+      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lb_t_step<double>, TTHREADS, persistent_smem<double>());
+  return e == cudaSuccess ? n : 0;
 }
 
 cudaError_t lr_launch_batch(int kid, const LrBatchArgs& a, const LrState& cur, const LrState& nxt,

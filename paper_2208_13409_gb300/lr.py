@@ -172,6 +172,12 @@ def load(build_if_missing: bool = True):
     L.lr_batch_launches_per_step.argtypes = [vp]
     L.lr_batch_launches_per_step.restype = ctypes.c_int
     L.lr_batch_set_profiling.argtypes = [vp, ctypes.c_int]
+    L.lr_batch_set_persistent.argtypes = [vp, ctypes.c_int]
+    L.lr_batch_set_persistent.restype = ctypes.c_int
+    L.lr_batch_get_persistent.argtypes = [vp]
+    L.lr_batch_get_persistent.restype = ctypes.c_int
+    L.lr_batch_test_barrier.argtypes = [vp, ctypes.c_uint, ctypes.c_double]
+    L.lr_batch_test_barrier.restype = ctypes.c_int
     L.lr_batch_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_long),
                                         _dp, ctypes.c_int]
     L.lr_batch_kernel_times.restype = ctypes.c_int
@@ -554,6 +560,19 @@ class Batch:
 
     def launches_per_step(self) -> int:
         return load().lr_batch_launches_per_step(self._h)
+
+    def set_persistent(self, on: bool):
+        """One cooperative launch per step (on) or one launch per kernel."""
+        self._check(load().lr_batch_set_persistent(self._h, 1 if on else 0))
+
+    @property
+    def persistent(self) -> bool:
+        return bool(load().lr_batch_get_persistent(self._h))
+
+    def test_barrier(self, extra_arrivals: int, limit_s: float):
+        """Test hook: the persistent step's barriers wait for arrivals no
+        block makes and give up after limit_s."""
+        self._check(load().lr_batch_test_barrier(self._h, extra_arrivals, limit_s))
 
     def set_profiling(self, on: bool):
         self._check(load().lr_batch_set_profiling(self._h, 1 if on else 0))

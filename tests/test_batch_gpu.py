@@ -1,7 +1,11 @@
 """The batched step (include/lr_batch.h) against lone simulations and the
 oracle: every member's result is the same alone and in any mix (same
-kernels, same arithmetic, its own CFL time step), under every schedule the
-autotuner can pick, across admission, removal, step limits and t_end."""
+arithmetic, its own CFL time step), in the persistent step (one cooperative
+launch per step, the tiled step's tile functions; compared with lone tiled
+runs) and in the per-kernel step (one launch per kernel and group, under
+every schedule the autotuner can pick; compared with lone unfused runs),
+across admission, removal, step limits and t_end.  The persistent step's
+barriers give up after their limit with LR_ERR_TIMEOUT."""
 import numpy as np
 import pytest
 
@@ -30,8 +34,11 @@ def _units(probs):
     return sum(lr.batch_units(p) for p in probs)
 
 
-def _alone(pr, nsteps, precision=lr.FP64):
+def _alone(pr, nsteps, precision=lr.FP64, tiled=False):
+    """The problem run alone, on the path the batch runs: the tiled step for
+    a persistent batch, the unfused one otherwise."""
     sim = lr.Sim(pr, precision=precision)
+    sim.set_tiled(tiled)
     for _ in range(nsteps):
         sim.step(1e300, sync=False)
     sim.sync()
@@ -55,27 +62,40 @@ def _same(bt, m, sim, tol=0.0, tol_l1=0.0):
 # flip), still far inside the FP32 mode's own error against the FP64 oracle.
 TOL_ALONE = {lr.FP64: 0.0, lr.DF64: 0.0, lr.FP32: 1e-3}
 TOL_ALONE_L1 = {lr.FP64: 0.0, lr.DF64: 0.0, lr.FP32: 1e-5}
+# The persistent step and the lone tiled kernels run the same tile functions;
+# in double-float arithmetic (float operations) the two instantiations may
+# also contract differently, so those members agree to the FP64 parity bar.
+TOL_ALONE_PERSIST = {lr.FP64: 0.0, lr.DF64: 1e-11, lr.FP32: 1e-3}
+TOL_ALONE_PERSIST_L1 = {lr.FP64: 0.0, lr.DF64: 1e-12, lr.FP32: 1e-5}
 
 
+@pytest.mark.parametrize("persistent", [True, False])
 @pytest.mark.parametrize("prec", [lr.FP64, lr.DF64, lr.FP32])
-def test_members_equal_alone(prec):
+def test_members_equal_alone(prec, persistent):
     probs = _mix()
     bt = lr.Batch(_units(probs), 8, precision=prec)
+    bt.set_persistent(persistent)
+    assert bt.persistent == persistent
     ids = [bt.add(p, t_end=1e300) for p in probs]
     assert all(i is not None for i in ids)
     bt.step(12)
     bt.sync()
+    assert bt.launches_per_step() == (1 if persistent else bt.launches_per_step())
     for pr, m in zip(probs, ids):
         t, n, st = bt.status(m)
         assert n == 12 and st == lr.RUNNING
-        sim = _alone(pr, 12, prec)
-        assert t == pytest.approx(sim.t, rel=TOL_ALONE_L1[prec], abs=0.0)
-        _same(bt, m, sim, TOL_ALONE[prec], TOL_ALONE_L1[prec])
+        sim = _alone(pr, 12, prec, tiled=persistent)
+        tol = TOL_ALONE_PERSIST if persistent else TOL_ALONE
+        tol_l1 = TOL_ALONE_PERSIST_L1 if persistent else TOL_ALONE_L1
+        assert t == pytest.approx(sim.t, rel=tol_l1[prec], abs=0.0)
+        _same(bt, m, sim, tol[prec], tol_l1[prec])
 
 
-def test_members_match_oracle():
+@pytest.mark.parametrize("persistent", [True, False])
+def test_members_match_oracle(persistent):
     probs = [P.random_box(111, nx=30, ny=26, nmat=3, velocity=0.3), P.sod(nx=64), P.triple_point(70, 30)]
     bt = lr.Batch(_units(probs), 4)
+    bt.set_persistent(persistent)
     ids = [bt.add(p, t_end=1e300) for p in probs]
     orcs = [oracle.Oracle(p) for p in probs]
     for q in range(5):
@@ -114,13 +134,14 @@ def test_step_limit_and_t_end():
     bt.sync()
     t, n, st = bt.status(ma)
     assert (n, st) == (5, lr.DONE)
-    _same(bt, ma, _alone(a, 5))
+    _same(bt, ma, _alone(a, 5, tiled=bt.persistent))
     t, n, st = bt.status(mb)
     assert (n, st) == (11, lr.RUNNING)
-    _same(bt, mb, _alone(b, 11))
+    _same(bt, mb, _alone(b, 11, tiled=bt.persistent))
     t, n, st = bt.status(mc)
     assert st == lr.DONE and n == 7 and t == t7
     sim_c2 = lr.Sim(c)   # the same t_end caps the last step alone too
+    sim_c2.set_tiled(bt.persistent)
     for _ in range(9):
         sim_c2.step(t7)
     assert sim_c2.t == t7
@@ -142,8 +163,8 @@ def test_admission_by_pool_units_and_reuse():
     assert mc is not None
     bt.step(4)
     bt.sync()
-    _same(bt, mb, _alone(b, 7))
-    _same(bt, mc, _alone(c, 4))
+    _same(bt, mb, _alone(b, 7, tiled=bt.persistent))
+    _same(bt, mc, _alone(c, 4, tiled=bt.persistent))
     # slots: a batch of one member slot admits one member
     bt1 = lr.Batch(10 * cap, 1)
     assert bt1.add(a) is not None and bt1.add(b) is None
@@ -162,7 +183,7 @@ def test_autotune_keeps_results_and_state():
     bt.step(6)
     bt.sync()
     for pr, m in zip(probs, ids):
-        _same(bt, m, _alone(pr, 8))
+        _same(bt, m, _alone(pr, 8, tiled=bt.persistent))
 
 
 def test_invalid_member_is_refused_and_failure_stays_local():
@@ -179,4 +200,48 @@ def test_invalid_member_is_refused_and_failure_stays_local():
     bt.step(6)
     bt.sync()
     assert bt.status(mw)[2] == lr.FAILED
-    _same(bt, mg, _alone(good, 6))
+    _same(bt, mg, _alone(good, 6, tiled=bt.persistent))
+
+
+def test_persistent_is_one_launch_per_step():
+    probs = _mix()
+    bt = lr.Batch(_units(probs), 8, precision=lr.FP32)
+    assert bt.persistent  # the default
+    for p in probs:
+        bt.add(p, t_end=1e300)
+    bt.step(3)
+    bt.sync()
+    assert bt.launches_per_step() == 1
+    bt.set_persistent(False)
+    bt.step(1)
+    bt.sync()
+    assert bt.launches_per_step() > 1
+
+
+def test_persistent_barrier_limit_runs_out():
+    """A barrier waiting for an arrival no block makes gives up after its
+    limit: the step is abandoned and reported as LR_ERR_TIMEOUT, the device
+    stays usable (a fresh batch steps normally afterwards)."""
+    import time
+    probs = _mix()[:3]
+    bt = lr.Batch(_units(probs), 4)
+    for p in probs:
+        bt.add(p, t_end=1e300)
+    bt.step(2)
+    bt.sync()
+    bt.test_barrier(1, 0.2)
+    t0 = time.perf_counter()
+    bt.step(1)
+    with pytest.raises(lr.LrError) as ei:
+        bt.sync()
+    assert ei.value.status == lr.ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    with pytest.raises(lr.LrError):        # the batch stays in error
+        bt.step(1)
+    bt.close()
+    fresh = lr.Batch(_units(probs), 4)
+    ids = [fresh.add(p, t_end=1e300) for p in probs]
+    fresh.step(2)
+    fresh.sync()
+    for pr, m in zip(probs, ids):
+        _same(fresh, m, _alone(pr, 2, tiled=True))
