@@ -48,6 +48,9 @@ def parse():
                     help="advance the workload to this time before warm-up and timing (run ends at t=5)")
     ap.add_argument("--kernels-only", action="store_true",
                     help="init + warm-up + K steps of the workload and exit (for ncu captures)")
+    ap.add_argument("--workload", default="triple_point", choices=["triple_point", "shock_bubble"],
+                    help="--kernels-only: the triple point (advanced to --t-start) or the 4096x1024 "
+                         "shock-bubble (advanced 200 steps)")
     ap.add_argument("--kernels-only-ensemble", action="store_true",
                     help="the batched ensemble: admission + warm-up + K steps and exit (for ncu captures)")
     ap.add_argument("--extras", type=int, default=1,
@@ -611,42 +614,60 @@ def run_lr(args, world, rank, local):
 
 def ensemble_bench(args):
     """The batched ensemble: 512 independent 2-3 material problems (grid sides
-    drawn from 64..512, seeded), one batched launch per kernel and material
-    group per step, per-member CFL dt; timed over a bounded number of steps
-    after the autotuner and warm-up, in FP64 and in the FP32 bulk mode."""
+    drawn from 64..512, seeded), 500 steps per member with per-member CFL dt,
+    in FP64 and in the FP32 bulk mode, each with the persistent step (one
+    cooperative launch per step) and with the per-kernel step (one launch per
+    kernel and material-count group, autotuned).  A fresh batch per run; the
+    first step is untimed (graph capture), the other steps are timed with
+    CUDA events (inputs far above L2)."""
     import torch
     from paper_2208_13409_gb300 import lr, problems as P
 
     probs = P.ensemble(512)
     cells = sum(p.cells for p in probs)
     units = sum(lr.batch_units(p) for p in probs)
+    nsteps = args.ensemble_steps
     out = {"workload": "ensemble_512_random_2-3mat_sides64-512", "members": len(probs), "cells": cells,
-           "steps_timed": args.ensemble_steps, "l2": "inputs far above L2 (no flush needed)"}
+           "steps_per_member": nsteps, "steps_timed": nsteps - 1,
+           "l2": "inputs far above L2 (no flush needed)"}
     for name in ("fp64", "fp32"):
         mode = MODES[name]
-        bt = lr.Batch(units, len(probs), precision=mode, max_member_cells=512 * 512)
-        t0 = time.perf_counter()
-        for p in probs:
-            bt.add(p, t_end=1e300, max_steps=500)
-        t_add = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        bt.autotune(2)
-        t_tune = time.perf_counter() - t0
-        bt.step(3)
-        bt.sync()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(bt.stream)
-        bt.step(args.ensemble_steps)
-        e1.record(bt.stream)
-        bt.sync()
-        ms = e0.elapsed_time(e1) / args.ensemble_steps
-        shapes, bps, lanes = bt.schedule()
-        out[name] = {"value": cells / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
-                     "launches_per_step": bt.launches_per_step(), "admit_s": t_add, "autotune_s": t_tune,
-                     "pool_gb": units * lr.Batch.unit_bytes(mode) / 1e9,
-                     "schedule": {"tile": [f"{a}x{b}" for a, b in shapes], "blocks_per_sm": bps, "lanes": lanes}}
-        bt.close()
-        torch.cuda.empty_cache()
+        rec = {}
+        for path in ("persistent", "per_kernel"):
+            bt = lr.Batch(units, len(probs), precision=mode, max_member_cells=512 * 512)
+            bt.set_persistent(path == "persistent")
+            t0 = time.perf_counter()
+            for p in probs:
+                bt.add(p, t_end=1e300, max_steps=nsteps)
+            t_add = time.perf_counter() - t0
+            t_tune = 0.0
+            if path == "per_kernel":
+                t0 = time.perf_counter()
+                bt.autotune(2)
+                t_tune = time.perf_counter() - t0
+            bt.step(1)
+            bt.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(bt.stream)
+            bt.step(nsteps - 1)
+            e1.record(bt.stream)
+            bt.sync()
+            ms = e0.elapsed_time(e1) / (nsteps - 1)
+            st, nst = bt.status_all()
+            r = {"value": cells / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                 "launches_per_step": bt.launches_per_step(), "admit_s": t_add,
+                 "pool_gb": units * lr.Batch.unit_bytes(mode) / 1e9,
+                 "members_done_after_steps": int(sum(1 for x in st if x == lr.DONE)),
+                 "members_failed": int(sum(1 for x in st if x == lr.FAILED))}
+            if path == "per_kernel":
+                shapes, bps, lanes = bt.schedule()
+                r["autotune_s"] = t_tune
+                r["schedule"] = {"tile": [f"{a}x{b}" for a, b in shapes], "blocks_per_sm": bps, "lanes": lanes}
+            rec[path] = r
+            bt.close()
+            torch.cuda.empty_cache()
+        rec["value"] = max(rec["persistent"]["value"], rec["per_kernel"]["value"])
+        out[name] = rec
     return out
 
 
@@ -822,9 +843,13 @@ def run_kernels_only(args):
     import torch
     from paper_2208_13409_gb300 import lr, problems as P
 
-    sim = lr.Sim(P.triple_point(), precision=MODES[args.precision])
-    if args.t_start > 0:
-        sim.run(1 << 30, args.t_start)
+    if args.workload == "shock_bubble":
+        sim = lr.Sim(P.shock_bubble(), precision=MODES[args.precision])
+        sim.run(200)
+    else:
+        sim = lr.Sim(P.triple_point(), precision=MODES[args.precision])
+        if args.t_start > 0:
+            sim.run(1 << 30, args.t_start)
     for _ in range(args.warmup):
         sim.step(sync=False)
     sim.sync()

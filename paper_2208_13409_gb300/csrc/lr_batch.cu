@@ -66,6 +66,7 @@ struct lr_batch {
   LrTile* d_tiles = nullptr;
   size_t tiles_cap = 0;
   Range rng[NSHAPE][LR_NDOM][LR_MAXM + 1];   // [shape][domain][M], M=0: all groups
+  Range prc, prn;                            // the persistent step's cell and node tiles (tiled-step shape)
   bool need_rebuild = true;
   long group_units[LR_MAXM + 1] = {0, 0, 0, 0};
   int group_members[LR_MAXM + 1] = {0, 0, 0, 0};
@@ -250,12 +251,15 @@ void dom_size(const LrGrid& g, int d, int* w, int* h) {
     default: *w = g.nx + 1; *h = g.ny + 1; break;
   }
 }
-void tiles_of(const LrGrid& g, int slot, int d, int s, std::vector<LrTile>& out) {
+void tiles_wh(const LrGrid& g, int slot, int d, int tw, int th, std::vector<LrTile>& out) {
   int w, h;
   dom_size(g, d, &w, &h);
-  int tx = (w + SHAPE_X[s] - 1) / SHAPE_X[s], ty = (h + SHAPE_Y[s] - 1) / SHAPE_Y[s];
+  int tx = (w + tw - 1) / tw, ty = (h + th - 1) / th;
   for (int j = 0; j < ty; ++j)
-    for (int i = 0; i < tx; ++i) out.push_back(LrTile{slot, i * SHAPE_X[s], j * SHAPE_Y[s], tx * ty});
+    for (int i = 0; i < tx; ++i) out.push_back(LrTile{slot, i * tw, j * th, tx * ty});
+}
+void tiles_of(const LrGrid& g, int slot, int d, int s, std::vector<LrTile>& out) {
+  tiles_wh(g, slot, d, SHAPE_X[s], SHAPE_Y[s], out);
 }
 
 lr_status rebuild(lr_batch* b) {
@@ -263,8 +267,7 @@ lr_status rebuild(lr_batch* b) {
   memset(use, 0, sizeof(use));
   for (int k = 0; k < LRK_COUNT; ++k)
     if (k != LRK_MIXED) use[b->sch.shape[k]][lr_kernel_domain(k)] = true;
-  // the persistent step walks 32 x 8 cell tiles and node tiles
-  use[0][LR_DOM_CELLS] = use[0][LR_DOM_NODES] = true;
+
   std::vector<LrTile> all;
   memset(b->rng, 0, sizeof(b->rng));
   for (int M = 0; M <= LR_MAXM; ++M) { b->group_units[M] = 0; b->group_members[M] = 0; }
@@ -282,6 +285,18 @@ lr_status rebuild(lr_batch* b) {
       }
       b->rng[s][d][0].count = (int)all.size() - b->rng[s][d][0].start;
     }
+  // the persistent step's tables: every member's cell and node tiles in the
+  // tiled step's tile shape
+  int tw = 0, th = 0;
+  lr_tiled_tile_shape(&tw, &th);
+  b->prc.start = (int)all.size();
+  for (size_t q = 0; q < b->mem.size(); ++q)
+    if (b->mem[q].used) tiles_wh(b->mem[q].g, (int)q, LR_DOM_CELLS, tw, th, all);
+  b->prc.count = (int)all.size() - b->prc.start;
+  b->prn.start = (int)all.size();
+  for (size_t q = 0; q < b->mem.size(); ++q)
+    if (b->mem[q].used) tiles_wh(b->mem[q].g, (int)q, LR_DOM_NODES, tw, th, all);
+  b->prn.count = (int)all.size() - b->prn.start;
   if (all.size() > b->tiles_cap) {
     if (b->d_tiles) cudaFree(b->d_tiles);
     b->d_tiles = nullptr;
@@ -347,8 +362,8 @@ bool persistent_on(const lr_batch* b) { return b->persistent && b->pers_bps > 0;
 cudaError_t enqueue_persistent(lr_batch* b, int from) {
   const LrState& cur = b->st[from];
   const LrState& nxt = b->st[1 - from];
-  const Range& rc = b->rng[0][LR_DOM_CELLS][0];
-  const Range& rn = b->rng[0][LR_DOM_NODES][0];
+  const Range& rc = b->prc;
+  const Range& rn = b->prn;
   b->launches = 0;
   if (rc.count == 0) return cudaSuccess;
   LrPersistArgs p;

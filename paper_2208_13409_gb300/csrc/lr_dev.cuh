@@ -214,6 +214,8 @@ cudaError_t lr_launch_batch_persistent(int mode, const LrPersistArgs& p, const L
                                        const LrWork& w, cudaStream_t s);
 // Resident blocks of lb_t_step per SM (0 when it cannot run).
 int lr_persistent_blocks_per_sm(int mode);
+// Tile of the tiled step and of lb_t_step: cells (or nodes) per block.
+void lr_tiled_tile_shape(int* tw, int* th);
 size_t lr_kc_bytes(int mode);
 void lr_make_kc(const LrGrid& g, void* out);
 // Field views: convert a real array (element type from g.mode) to double,

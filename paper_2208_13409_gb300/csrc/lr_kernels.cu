@@ -2113,7 +2113,16 @@ __global__ void __launch_bounds__(128) lb_mixed(const LrGrid* __restrict__ gs, L
 // object on the tile's edge is evaluated by both tiles that share it), and
 // finally updates its own points.  Staging and object loops run over the
 // block's threads linearly; the update runs one thread per point.
-constexpr int TTX = 32, TTY = 8, TTHREADS = TTX * TTY;
+#ifndef LR_TILE_Y
+#define LR_TILE_Y 8
+#endif
+constexpr int TTX = 32, TTY = LR_TILE_Y, TTHREADS = TTX * TTY;
+// Resident blocks the tiled kernels' register budget is set for: the
+// step's setting for 256-thread blocks, scaled to the tile's thread count.
+template <class R, int D> struct TileMinB {
+  static constexpr int v = MinBlocks<R, D>::value * 256 / TTHREADS;
+  static constexpr int value = v > 0 ? v : 1;
+};
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 // Staging coordinates beyond the reach of any live point are clamped to the
@@ -2368,7 +2377,7 @@ __device__ __forceinline__ void t_node_tile(const LrGrid& g, const KC<R>& kc, co
   cfl_finalize(g, kc, w, val, true, ntiles);
 }
 template <class R>
-__global__ void __launch_bounds__(TTHREADS, MinBlocks<R, LR_MINB_D_DUAL>::value)
+__global__ void __launch_bounds__(TTHREADS, TileMinB<R, LR_MINB_D_DUAL>::value)
     lr_t_node_remap(LrGrid g, KC<R> kc, LrStateT<R> cur, LrStateT<R> nxt, LrWorkT<R> w) {
   lr_pdl_enter();
   extern __shared__ __align__(16) unsigned char lr_smem[];
@@ -2741,7 +2750,7 @@ __device__ __forceinline__ void t_cell_tile(const LrGrid& g, const KC<R>& kc, co
   w.cc[c] = cmax;
 }
 template <class R, int M>
-__global__ void __launch_bounds__(TTHREADS, MinBlocks<R, LR_MINB_D_UPDATE>::value)
+__global__ void __launch_bounds__(TTHREADS, TileMinB<R, LR_MINB_D_UPDATE>::value)
     lr_t_cell_remap(LrGrid g, KC<R> kc, LrStateT<R> cur, LrStateT<R> nxt, LrWorkT<R> w) {
   lr_pdl_enter();
   extern __shared__ __align__(16) unsigned char lr_smem[];
@@ -3010,7 +3019,7 @@ __device__ __forceinline__ void t_lagrange_tile(const LrGrid& g, const KC<R>& kc
   if (i < g.nx && j < g.ny) lagrange_cell<R, M>(g, kc, cur, w, i, j, ta, tb, sDX, sDY, sFX, sFY, sElc, sMK, CN);
 }
 template <class R, int M>
-__global__ void __launch_bounds__(TTHREADS, MinBlocks<R, 1>::value)
+__global__ void __launch_bounds__(TTHREADS, TileMinB<R, 1>::value)
     lr_t_lagrange(LrGrid g, KC<R> kc, LrStateT<R> cur, LrStateT<R> nxt, LrWorkT<R> w) {
   lr_pdl_enter();
   extern __shared__ __align__(16) unsigned char lr_smem[];
@@ -3415,6 +3424,11 @@ cudaError_t lr_launch_batch_persistent(int mode, const LrPersistArgs& p, const L
   return mode == LR_MODE_FP32 ? launch_persistent_t<float>(p, cur, nxt, w, s)
        : mode == LR_MODE_DF64 ? launch_persistent_t<df64>(p, cur, nxt, w, s)
                               : launch_persistent_t<double>(p, cur, nxt, w, s);
+}
+
+void lr_tiled_tile_shape(int* tw, int* th) {
+  *tw = TTX;
+  *th = TTY;
 }
 
 int lr_persistent_blocks_per_sm(int mode) {
