@@ -33,8 +33,8 @@ struct lr_ctx {
   bool tiled;       // the tiled (fused, shared-memory) kernels replace kernel pairs of the step
   struct Pend { int kid; cudaEvent_t a, b; };
   std::vector<Pend> pend;
-  double acc_ms[LRK_COUNT + 3];  // per kernel, then the tiled kernels
-  long acc_n[LRK_COUNT + 3];
+  double acc_ms[LRK_COUNT + 4];  // per kernel, then the tiled kernels and the interface-line placement
+  long acc_n[LRK_COUNT + 4];
   double* tmp;      // device scratch for field views (max field size)
   size_t tmp_elems;
   double* rows;     // device scratch for conservation partial sums
@@ -344,18 +344,19 @@ lr_status check_sticky(lr_ctx* ctx) {
 }
 
 // Timing slots: the step's kernels, then the tiled kernels.
-enum { SLOT_T_LAG = LRK_COUNT, SLOT_T_CELL, SLOT_T_NODE, NSLOT };
+enum { SLOT_T_LAG = LRK_COUNT, SLOT_T_CELL, SLOT_T_NODE, SLOT_PLACE, NSLOT };
 const char* slot_name(int k) {
   switch (k) {
     case SLOT_T_LAG: return "lr_t_lagrange";
     case SLOT_T_CELL: return "lr_t_cell_remap";
     case SLOT_T_NODE: return "lr_t_node_remap";
+    case SLOT_PLACE: return "lb_mixed_place";
     default: return lr_kernel_names[k];
   }
 }
 int slot_of(int k) {
   switch (k) {
-    case LRK_MIXED_PLACE: case LRK_T_MIXED: return LRK_MIXED;  // the interface kernels time as lr_mixed
+    case LRK_MIXED_PLACE: return SLOT_PLACE;  // lr_mixed is the flux split that follows
     case LRK_T_LAGRANGE: return SLOT_T_LAG;
     case LRK_T_CELL_REMAP: return SLOT_T_CELL;
     case LRK_T_NODE_REMAP: return SLOT_T_NODE;

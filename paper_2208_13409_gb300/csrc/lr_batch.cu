@@ -473,7 +473,7 @@ cudaError_t enqueue_step(lr_batch* b, int from) {
       for (int M = 2; M <= LR_MAXM; ++M) {
         if (b->group_members[M] == 0) continue;
         LrBatchArgs pa = base_args(b);
-        set_mixed_args(b, M, 8, pa);
+        set_mixed_args(b, M, 8, pa);  // enough warps for four cells each
         e = launch_timed(b, LRK_MIXED_PLACE, pa, cur, nxt, side);
         if (e != cudaSuccess) return e;
       }

@@ -157,9 +157,13 @@ enum LrKernelId {
   // tiled step (lone simulations): fused kernel pairs over shared-memory tiles
   LRK_T_NODE_REMAP = 110,  // lr_dual_flux + lr_node_update
   LRK_T_CELL_REMAP = 111,  // lr_mat_flux + lr_cell_update
-  LRK_T_LAGRANGE = 112,    // lr_cell_pre + lr_node_half + lr_cell_lag + lr_cell_cf
-  LRK_T_MIXED = 113        // lb_mixed_place + lb_mixed (interface lines and flux split) in one launch
+  LRK_T_LAGRANGE = 112     // lr_cell_pre + lr_node_half + lr_cell_lag + lr_cell_cf
 };
+// Interface-line placement spreads a short mixed-cell list over about this
+// many warps (two per SM sub-partition of a 152-SM GPU), one lane per cell.
+#ifndef LR_PLACE_SPREAD
+#define LR_PLACE_SPREAD 1216
+#endif
 // Dynamic shared-memory limits of the tiled kernels (once per device, before
 // their first launch).
 cudaError_t lr_tiled_setup();

@@ -718,129 +718,100 @@ __device__ __forceinline__ int donated_flux(const LrGrid& g, const LrWorkT<R>& w
   return 2;
 }
 
-// Interface lines of a mixed cell in the rectangle [xl,xr] x [yb,yt] of
-// area `area`: the first present material's line by the closed-form PLIC,
-// a second one (three materials) cut from what the first left.  nrm: the
-// Youngs normals of the first two present materials; k0, k1 their fractions.
-__device__ __forceinline__ void place_cuts(int ncut, double k0, double k1, const double (*nrm)[2], double xl,
-                                           double xr, double yb, double yt, double area, double (*cut)[3],
-                                           int lane) {
-  cut[0][0] = nrm[0][0]; cut[0][1] = nrm[0][1];
-  cut[0][2] = rect_plic(xl, xr, yb, yt, nrm[0][0], nrm[0][1], k0);
-  if (ncut == 2) {
-    Poly rect, rest;
-    poly_rect(rect, xl, xr, yb, yt);
-    poly_clip(rect, cut[0][0], cut[0][1], cut[0][2], -1.0, rest);
-    double target = k1 * area;
-    double ra = poly_area(rest);
-    if (target > ra) target = ra;
-    cut[1][0] = nrm[1][0]; cut[1][1] = nrm[1][1];
-    cut[1][2] = poly_plic8(rest, nrm[1][0], nrm[1][1], target, lane);
-  }
-}
-
-// K4b: the flux work of mixed cells only (the list built by lr_cell_pre), in
-// double whatever the step's arithmetic, after place_at has placed their
-// interface lines: the split of every flux the cell donates by those lines,
-// and the clipping of a material's outgoing volume to what it holds (excess
-// to the dominant material).  L lanes (1, 2, 4 or 8) work on one cell: all
-// place the interface, lane l splits fluxes 8l/L .. 8(l+1)/L - 1; the
-// outgoing volumes per material are summed across the L lanes with shuffles.
-// More lanes hide more latency (the list is short) but repeat the interface
-// placement L times per warp instruction, so L is chosen per arithmetic.
-// Splits are stored unclipped; the rare cell whose material runs short
-// rescales its own stored splits in a second pass.
-// Interface lines of mixed cell c (sections 4.1 and 4.4), in double
-// whatever the step's arithmetic: Youngs normals and PLIC lines in the
-// rectangular Lagrangian cell (three materials by nested cuts in material
-// order); the Direct remap places one set in the X-Lagrangian cell
+// Interface lines of the mixed cells of a list (sections 4.1 and 4.4), in
+// double whatever the step's arithmetic: Youngs normals and PLIC lines in the
+// rectangular Lagrangian cell, three materials by nested cuts in material
+// order; the Direct remap places one set in the X-Lagrangian cell
 // [xl, xr] x [0, dy] for the X faces and one in the Y-Lagrangian cell
-// [0, dx] x [yb, yt] for the Y faces.  Stored in w.cut (and w.cutY).  The
-// eight lanes of a group share the cell (the three-material solve spreads
-// its vertex levels over them); lane 0 stores.
-template <class R, int M>
-__device__ __forceinline__ void place_at(const LrGrid& g, const LrStateT<R>& cur, const LrWorkT<R>& w, int c,
-                                         bool valid, int lane) {
+// [0, dx] x [yb, yt] for the Y faces.  Stored in w.cut (and w.cutY).
+// A warp takes the P entries [base, base + P) of the list (P = 4, 8, 16 or
+// 32), one lane per cell: the lane forms its cell's normals and the first
+// line constant (closed form).  The nested cut of the three-material cells
+// among them (a polygon solve) is then shared out to the warp's four groups
+// of eight lanes, four cells at a time; a group spreads the polygon's vertex
+// levels over its lanes (poly_plic8) and the cell's lane takes the result
+// back.  One lane per cell keeps the double-precision work per cell to one
+// lane's worth.  Lanes past `count` (and lanes >= P) store nothing.
+template <class R, int M, class G>
+__device__ __forceinline__ void place_chunk(G getg, const LrStateT<R>& cur, const LrWorkT<R>& w, int moff,
+                                            int count, int base, int P) {
   using O = RealOps<R>;
-  int i = (c - g.coff) % g.nx, j = (c - g.coff) / g.nx;
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int t = base + lane;
+  const bool valid = lane < P && t < count;
+  const int e = moff + (valid ? t : base);
+  const LrGrid& g = getg(e);
+  const int c = w.mixed[e];
+  const int i = (c - g.coff) % g.nx, j = (c - g.coff) / g.nx;
   double kk[M];
   int np = 0, order[LR_MAXM] = {0, 0, 0};
-  unsigned msk = w.mask[c];
+  const unsigned msk = w.mask[c];
 #pragma unroll
   for (int a = 0; a < M; ++a) {
     kk[a] = (msk & (1u << a)) ? O::todouble(cur.k[a][c]) : 0.0;
     if (msk & (1u << a)) order[np++] = a;
   }
-  double wxc = O::todouble(w.wx[c]), wyc = O::todouble(w.wy[c]);
-  double xl = 0.5 * g.dx - 0.5 * wxc + O::todouble(w.ox[c]), xr = xl + wxc;
-  double yb = 0.5 * g.dy - 0.5 * wyc + O::todouble(w.oy[c]), yt = yb + wyc;
-  int ncut = np - 1;
-  double cut[2][3], nrm[2][2];
-  youngs(g, cur.k[order[0]], i, j, nrm[0][0], nrm[0][1]);
-  if (ncut == 2) youngs(g, cur.k[order[1]], i, j, nrm[1][0], nrm[1][1]);
-  double k1 = ncut == 2 ? kk[order[1]] : 0.0;
-  if (g.remap == LR_REMAP_DIRECT) {
-    place_cuts(ncut, kk[order[0]], k1, nrm, xl, xr, 0.0, g.dy, wxc * g.dy, cut, lane);
-    if (valid && lane == 0)
-      for (int q = 0; q < ncut; ++q)
-        for (int z = 0; z < 3; ++z) w.cut[3 * q + z][c] = cut[q][z];
-    place_cuts(ncut, kk[order[0]], k1, nrm, 0.0, g.dx, yb, yt, g.dx * wyc, cut, lane);
-    if (valid && lane == 0)
-      for (int q = 0; q < ncut; ++q)
-        for (int z = 0; z < 3; ++z) w.cutY[3 * q + z][c] = cut[q][z];
-  } else {
-    place_cuts(ncut, kk[order[0]], k1, nrm, xl, xr, yb, yt, wxc * wyc, cut, lane);
-    if (valid && lane == 0)
-      for (int q = 0; q < ncut; ++q)
-        for (int z = 0; z < 3; ++z) w.cut[3 * q + z][c] = cut[q][z];
+  const double wxc = O::todouble(w.wx[c]), wyc = O::todouble(w.wy[c]);
+  const double xl = 0.5 * g.dx - 0.5 * wxc + O::todouble(w.ox[c]), xr = xl + wxc;
+  const double yb = 0.5 * g.dy - 0.5 * wyc + O::todouble(w.oy[c]), yt = yb + wyc;
+  const bool direct = g.remap == LR_REMAP_DIRECT;
+  const bool two = np == 3;  // a second, nested cut
+  double n0x = 1.0, n0y = 0.0, n1x = 0.0, n1y = 0.0;
+  if (valid) youngs(g, cur.k[order[0]], i, j, n0x, n0y);
+  if (valid && two) youngs(g, cur.k[order[1]], i, j, n1x, n1y);
+  for (int set = 0; set < 2; ++set) {  // the X set (or the only one), then the Direct remap's Y set
+    const bool on = valid && (set == 0 || direct);
+    double rx0 = xl, rx1 = xr, ry0 = yb, ry1 = yt, area = wxc * wyc;
+    if (direct) {
+      if (set == 0) { ry0 = 0.0; ry1 = g.dy; area = wxc * g.dy; }
+      else { rx0 = 0.0; rx1 = g.dx; area = g.dx * wyc; }
+    }
+    double d0 = 0.0, d1 = 0.0, tgt = 0.0;
+    if (on) d0 = rect_plic(rx0, rx1, ry0, ry1, n0x, n0y, kk[order[0]]);
+    if (on && two) tgt = kk[order[1]] * area;
+    unsigned need = __ballot_sync(full, on && two);
+    while (need) {  // uniform over the warp
+      const int q = lane >> 3;
+      unsigned rem = need;
+      for (int s = 0; s < q; ++s) rem &= rem - 1u;
+      const int owner = rem ? __ffs(rem) - 1 : -1;  // the group's cell: the q-th cell still to do
+      const int src = owner >= 0 ? owner : 0;
+      const double bx0 = __shfl_sync(full, rx0, src), bx1 = __shfl_sync(full, rx1, src);
+      const double by0 = __shfl_sync(full, ry0, src), by1 = __shfl_sync(full, ry1, src);
+      const double bnx = __shfl_sync(full, n0x, src), bny = __shfl_sync(full, n0y, src);
+      const double bd0 = __shfl_sync(full, d0, src), btg = __shfl_sync(full, tgt, src);
+      const double mnx = __shfl_sync(full, n1x, src), mny = __shfl_sync(full, n1y, src);
+      double r = 0.0;
+      if (owner >= 0) {  // uniform over the group
+        Poly rect, rest;
+        poly_rect(rect, bx0, bx1, by0, by1);
+        poly_clip(rect, bnx, bny, bd0, -1.0, rest);
+        const double ra = poly_area(rest);
+        r = poly_plic8(rest, mnx, mny, btg > ra ? ra : btg, lane & 7);
+      }
+      const int rank = __popc(need & ((1u << lane) - 1u));
+      const double got = __shfl_sync(full, r, (rank & 3) << 3);
+      if (((need >> lane) & 1u) && rank < 4) d1 = got;
+      for (int s = 0; s < 4 && need; ++s) need &= need - 1u;
+    }
+    if (on) {
+      double* const* dst = set == 0 ? w.cut : w.cutY;
+      dst[0][c] = n0x; dst[1][c] = n0y; dst[2][c] = d0;
+      if (two) { dst[3][c] = n1x; dst[4][c] = n1y; dst[5][c] = d1; }
+    }
   }
 }
 
-// The same interface lines as place_at (DirectCF remap: the Lagrangian
-// rectangle), with the eight lanes of the group sharing the work instead of
-// repeating it: lane 0 (and lane 1 for a second cut) forms a Youngs normal,
-// lane 0 the first line constant, broadcast to the group; the nested cut of a
-// three-material cell spreads its vertex levels over the lanes as before.
-template <class R, int M>
-__device__ __forceinline__ void place_lanes(const LrGrid& g, const LrStateT<R>& cur, const LrWorkT<R>& w, int c,
-                                            bool valid, int lane) {
-  using O = RealOps<R>;
-  const unsigned gm = 0xffu << (threadIdx.x & 24u);
-  int i = (c - g.coff) % g.nx, j = (c - g.coff) / g.nx;
-  double kk[M];
-  int np = 0, order[LR_MAXM] = {0, 0, 0};
-  unsigned msk = w.mask[c];
-#pragma unroll
-  for (int a = 0; a < M; ++a) {
-    kk[a] = (msk & (1u << a)) ? O::todouble(cur.k[a][c]) : 0.0;
-    if (msk & (1u << a)) order[np++] = a;
-  }
-  double wxc = O::todouble(w.wx[c]), wyc = O::todouble(w.wy[c]);
-  double xl = 0.5 * g.dx - 0.5 * wxc + O::todouble(w.ox[c]), xr = xl + wxc;
-  double yb = 0.5 * g.dy - 0.5 * wyc + O::todouble(w.oy[c]), yt = yb + wyc;
-  int ncut = np - 1;
-  double nxv = 1.0, nyv = 0.0, d0 = 0.0;
-  if (lane < ncut) youngs(g, cur.k[order[lane]], i, j, nxv, nyv);
-  if (lane == 0) d0 = rect_plic(xl, xr, yb, yt, nxv, nyv, kk[order[0]]);
-  double n0x = __shfl_sync(gm, nxv, 0, 8), n0y = __shfl_sync(gm, nyv, 0, 8);
-  double n1x = __shfl_sync(gm, nxv, 1, 8), n1y = __shfl_sync(gm, nyv, 1, 8);
-  d0 = __shfl_sync(gm, d0, 0, 8);
-  double d1 = 0.0;
-  if (ncut == 2) {  // uniform over the group
-    Poly rect, rest;
-    poly_rect(rect, xl, xr, yb, yt);
-    poly_clip(rect, n0x, n0y, d0, -1.0, rest);
-    double target = kk[order[1]] * (wxc * wyc);
-    double ra = poly_area(rest);
-    if (target > ra) target = ra;
-    d1 = poly_plic8(rest, n1x, n1y, target, lane);
-  }
-  if (valid && lane == 0) {
-    w.cut[0][c] = n0x; w.cut[1][c] = n0y; w.cut[2][c] = d0;
-    if (ncut == 2) { w.cut[3][c] = n1x; w.cut[4][c] = n1y; w.cut[5][c] = d1; }
-  }
-}
-
+// K4b: the flux work of mixed cells only (the list the Lagrange phase
+// built), in double whatever the step's arithmetic, after place_chunk has
+// placed their interface lines: the split of every flux the cell donates by
+// those lines, and the clipping of a material's outgoing volume to what it
+// holds (excess to the dominant material).  L lanes (1, 2, 4 or 8) work on
+// one cell: lane l splits fluxes 8l/L .. 8(l+1)/L - 1; the outgoing volumes
+// per material are summed across the L lanes with shuffles.  Splits are
+// stored unclipped; the rare cell whose material runs short rescales its own
+// stored splits in a second pass.
 template <class R, int M>
 __device__ __forceinline__ void mixed_at(const LrGrid& g, const LrStateT<R>& cur, const LrWorkT<R>& w, int c,
                                          bool valid, int lane, int L) {
@@ -857,7 +828,7 @@ __device__ __forceinline__ void mixed_at(const LrGrid& g, const LrStateT<R>& cur
       if (msk & (1u << a)) order[np++] = a;
       if (kk[a] > kk[dom]) dom = a;
     }
-    // ---- interface lines placed by lr_mixed_place (place_at)
+    // ---- interface lines placed by lb_mixed_place (place_chunk)
     int ncut = np - 1;
     const bool direct = g.remap == LR_REMAP_DIRECT;
     double cut[2][3], cutY[2][3];
@@ -2079,22 +2050,20 @@ __global__ void __launch_bounds__(256) lr_sweep_prep(LrGrid g, KC<R> kc, LrState
 // passes a one-entry grid array), so both run the same compiled code and
 // give bit-identical results (separately inlined copies may fuse
 // multiply-adds differently).
-// Eight lanes per mixed cell; a warp's groups iterate together.
+// A warp takes P consecutive list entries at a time, one lane per cell, P
+// chosen from the list's length: a short list is spread over about `spread`
+// warps (at least four cells per warp), a long one fills whole warps.
 template <class R, int M>
 __global__ void __launch_bounds__(128) lb_mixed_place(const LrGrid* __restrict__ gs, LrStateT<R> cur,
-                                                      LrWorkT<R> w, int mslot, int moff) {
+                                                      LrWorkT<R> w, int mslot, int moff, int spread) {
   lr_pdl_enter();
-  int count = (int)w.red[mslot];
-  int lane = threadIdx.x & 7;
-  int group = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 3);
-  int ngroups = (int)((gridDim.x * blockDim.x) >> 3);
-  for (int k = 0;; ++k) {
-    if ((group & ~3) + k * ngroups >= count) break;
-    int t = group + k * ngroups;
-    bool valid = t < count;
-    int e = moff + (valid ? t : 0);
-    place_at<R, M>(gs[w.minst[e]], cur, w, w.mixed[e], valid, lane);
-  }
+  const int count = (int)w.red[mslot];
+  const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+  int P = 4;
+  while (P < 32 && (long long)P * spread < count) P <<= 1;
+  for (int base = warp * P; base < count; base += nwarps * P)
+    place_chunk<R, M>([&](int e) -> const LrGrid& { return gs[w.minst[e]]; }, cur, w, moff, count, base, P);
 }
 template <class R, int M>
 __global__ void __launch_bounds__(128) lb_mixed(const LrGrid* __restrict__ gs, LrStateT<R> cur, LrWorkT<R> w,
@@ -2828,7 +2797,7 @@ __device__ __forceinline__ void lagrange_cell(const LrGrid& g, const KC<R>& kc, 
 // Intermediates that only the next phase reads (P+Q, the e^{lag}
 // coefficients, the face volumes) stay in shared memory; the results later
 // kernels read are stored for the cells, nodes and faces the tile owns.
-// Mixed cells join the interface work list of lr_t_mixed.
+// Mixed cells join the interface work list (lb_mixed_place, lb_mixed).
 template <class R, int M>
 __device__ __forceinline__ void t_lagrange_tile(const LrGrid& g, const KC<R>& kc, const LrStateT<R>& cur,
                                                 const LrWorkT<R>& w, int i0, int j0, unsigned char* lr_smem) {
@@ -3026,39 +2995,25 @@ __global__ void __launch_bounds__(TTHREADS, TileMinB<R, 1>::value)
   t_lagrange_tile<R, M>(g, kc, cur, w, blockIdx.x * TTX, blockIdx.y * TTY, lr_smem);
 }
 
-// The interface work of the mixed cells lr_t_lagrange listed, in double,
-// eight lanes per cell (one launch instead of lb_mixed_place and lb_mixed):
-// the interface lines (place_lanes), then the split of every flux the cell
-// donates by those lines, the clipping of a material's outgoing volume to
-// what it holds and the donor's final material fluxes (mixed_at), which
-// lr_t_cell_remap reads.  A warp's groups iterate together (mixed_at's
-// shuffles span the warp); a group past the end of the list works on a copy
-// of the first entry and stores nothing.
-// One pass over a mixed-cell list (count in red[mslot], entries from moff):
-// lane group `group` of `ngroups` takes entries group, group + ngroups, ...;
-// getg(e) gives entry e's grid.
+// The interface work of a mixed-cell list inside the persistent step (count
+// in red[mslot], entries from moff; getg(e) gives entry e's grid): warp
+// `warp` of `nwarps` takes four entries at a time, places their interface
+// lines one lane per cell (place_chunk), then splits and clips their fluxes
+// eight lanes per cell (mixed_at) -- the same device functions as the
+// separate interface kernels, so the results are the same.
 template <class R, int M, class G>
 __device__ __forceinline__ void t_mixed_list(G getg, const LrStateT<R>& cur, const LrWorkT<R>& w, int mslot,
-                                             int moff, int group, int ngroups) {
-  int count = (int)w.red[mslot];
-  int lane = threadIdx.x & 7;
-  for (int k = 0;; ++k) {
-    if ((group & ~3) + k * ngroups >= count) break;  // uniform over the warp (four groups)
-    int t = group + k * ngroups;
-    bool valid = t < count;
-    int e = moff + (valid ? t : 0);
-    const LrGrid& g = getg(e);
-    int c = w.mixed[e];
-    place_lanes<R, M>(g, cur, w, c, valid, lane);
+                                             int moff, int warp, int nwarps) {
+  const int count = (int)w.red[mslot];
+  const int lane = threadIdx.x & 31;
+  for (int base = warp * 4; base < count; base += nwarps * 4) {
+    place_chunk<R, M>(getg, cur, w, moff, count, base, 4);
     __syncwarp();
-    mixed_at<R, M>(g, cur, w, c, valid, lane, 8);
+    const int t = base + (lane >> 3);
+    const bool valid = t < count;
+    const int e = moff + (valid ? t : base);
+    mixed_at<R, M>(getg(e), cur, w, w.mixed[e], valid, lane & 7, 8);
   }
-}
-template <class R, int M>
-__global__ void __launch_bounds__(128) lr_t_mixed(LrGrid g, LrStateT<R> cur, LrWorkT<R> w) {
-  lr_pdl_enter();
-  t_mixed_list<R, M>([&](int) -> const LrGrid& { return g; }, cur, w, g.mslot, g.moff,
-                     (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 3), (int)((gridDim.x * blockDim.x) >> 3));
 }
 
 // ---------------------------------------------------- persistent batch step
@@ -3148,10 +3103,10 @@ __global__ void __launch_bounds__(TTHREADS, PersistMinB<R>::value)
   if (!lr_grid_sync(bar, nb, extra, limit_ns)) return;
   // ---- interface work of every member's mixed cells
   {
-    int group = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 3), ngroups = (int)((nb * blockDim.x) >> 3);
+    int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), nwarps = (int)((nb * blockDim.x) >> 5);
     auto getg = [&](int e) -> const LrGrid& { return gs[w.minst[e]]; };
-    if (groups & 4) t_mixed_list<R, 2>(getg, cur, w, 1, 0, group, ngroups);
-    if (groups & 8) t_mixed_list<R, 3>(getg, cur, w, 2, P, group, ngroups);
+    if (groups & 4) t_mixed_list<R, 2>(getg, cur, w, 1, 0, warp, nwarps);
+    if (groups & 8) t_mixed_list<R, 3>(getg, cur, w, 2, P, warp, nwarps);
   }
   if (!lr_grid_sync(bar, nb, extra, limit_ns)) return;
   // ---- material fluxes and cell update
@@ -3223,11 +3178,11 @@ cudaError_t launch_t(int kid, const LrGrid& g, const LrState& cur0, const LrStat
       if (g.M == 1) break;  // one material: no interfaces
       if (!w.gdev) return cudaErrorInvalidValue;
       if (kid == LRK_MIXED_PLACE) {
-        long long cells = 8ll * g.nx * g.ny;  // a group of eight lanes per cell
-        int np = (int)((cells + 127) / 128);
+        long long lanes = 8ll * g.nx * g.ny;  // enough warps for four cells each
+        int np = (int)((lanes + 127) / 128);
         if (np > 152 * 16) np = 152 * 16;
-        if (g.M == 2) lb_mixed_place<R, 2><<<np, 128, 0, s>>>(w.gdev, cur, w, g.mslot, g.moff);
-        else lb_mixed_place<R, 3><<<np, 128, 0, s>>>(w.gdev, cur, w, g.mslot, g.moff);
+        if (g.M == 2) lb_mixed_place<R, 2><<<np, 128, 0, s>>>(w.gdev, cur, w, g.mslot, g.moff, LR_PLACE_SPREAD);
+        else lb_mixed_place<R, 3><<<np, 128, 0, s>>>(w.gdev, cur, w, g.mslot, g.moff, LR_PLACE_SPREAD);
         break;
       }
       long long lanes = (long long)g.mixed_lanes * g.nx * g.ny;
@@ -3255,16 +3210,6 @@ cudaError_t launch_t(int kid, const LrGrid& g, const LrState& cur0, const LrStat
                                                  g, kc, cur, nxt, w)
                                : launch_pdl_smem(lr_t_cell_remap<R, 3>, gr, dim3(TTHREADS), cell_remap_smem<R, 3>(), s,
                                                  g, kc, cur, nxt, w);
-      if (e != cudaSuccess) return e;
-      break;
-    }
-    case LRK_T_MIXED: {
-      if (g.M == 1) break;
-      long long lanes = 8ll * g.nx * g.ny;
-      int nb = (int)((lanes + 127) / 128);
-      if (nb > 152 * 8) nb = 152 * 8;
-      cudaError_t e = g.M == 2 ? launch_pdl(lr_t_mixed<R, 2>, dim3(nb), dim3(128), s, g, cur, w)
-                               : launch_pdl(lr_t_mixed<R, 3>, dim3(nb), dim3(128), s, g, cur, w);
       if (e != cudaSuccess) return e;
       break;
     }
@@ -3301,9 +3246,9 @@ cudaError_t launch_batch_t(int kid, const LrBatchArgs& a, const LrState& cur0, c
   const KC<R>* kcs = static_cast<const KC<R>*>(a.kcs);
   if (kid == LRK_MIXED_PLACE || kid == LRK_MIXED) {
     if (a.M == 1 || a.grid <= 0) return cudaSuccess;
-    if (kid == LRK_MIXED_PLACE) {  // a.grid: blocks of 128 threads, eight lanes per cell
-      if (a.M == 2) lb_mixed_place<R, 2><<<a.grid, 128, 0, s>>>(a.gs, cur, w, a.mslot, a.moff);
-      else lb_mixed_place<R, 3><<<a.grid, 128, 0, s>>>(a.gs, cur, w, a.mslot, a.moff);
+    if (kid == LRK_MIXED_PLACE) {  // a.grid: blocks of 128 threads, enough warps for four cells each
+      if (a.M == 2) lb_mixed_place<R, 2><<<a.grid, 128, 0, s>>>(a.gs, cur, w, a.mslot, a.moff, LR_PLACE_SPREAD);
+      else lb_mixed_place<R, 3><<<a.grid, 128, 0, s>>>(a.gs, cur, w, a.mslot, a.moff, LR_PLACE_SPREAD);
     } else {  // a.grid: blocks of 128 threads, a.lanes per cell
       if (a.M == 2) lb_mixed<R, 2><<<a.grid, 128, 0, s>>>(a.gs, cur, w, a.lanes, a.mslot, a.moff);
       else lb_mixed<R, 3><<<a.grid, 128, 0, s>>>(a.gs, cur, w, a.lanes, a.mslot, a.moff);
