@@ -33,8 +33,8 @@ struct lr_ctx {
   bool tiled;       // the tiled (fused, shared-memory) kernels replace kernel pairs of the step
   struct Pend { int kid; cudaEvent_t a, b; };
   std::vector<Pend> pend;
-  double acc_ms[LRK_COUNT + 4];  // per kernel, then the tiled kernels and the interface-line placement
-  long acc_n[LRK_COUNT + 4];
+  double acc_ms[LRK_COUNT + 5];  // per kernel, then the tiled kernels and the interface-line placement
+  long acc_n[LRK_COUNT + 5];
   double* tmp;      // device scratch for field views (max field size)
   size_t tmp_elems;
   double* rows;     // device scratch for conservation partial sums
@@ -279,6 +279,14 @@ size_t layout(const lr_config* cfg, char* base, LrState* st, LrWork* w, double**
   W.minst = b.take<int>(nc);
   W.gdev = b.take<LrGrid>(1);
   W.mask = b.take<unsigned char>(nc);
+  {
+    int tw = 0, th = 0;
+    lr_tiled_tile_shape(&tw, &th);
+    size_t nt = ((nx + tw - 1) / tw) * ((ny + th - 1) / th);
+    W.tflag = b.take<unsigned int>(nt);
+    W.tlist = b.take<int>(nt);
+    W.tcount = b.take<unsigned int>(2);
+  }
   for (int q = 0; q < 6; ++q) W.cut[q] = b.take<double>(nc);
   if (cfg->remap == LR_REMAP_DIRECT)
     for (int q = 0; q < 6; ++q) W.cutY[q] = b.take<double>(nc);
@@ -344,13 +352,14 @@ lr_status check_sticky(lr_ctx* ctx) {
 }
 
 // Timing slots: the step's kernels, then the tiled kernels.
-enum { SLOT_T_LAG = LRK_COUNT, SLOT_T_CELL, SLOT_T_NODE, SLOT_PLACE, NSLOT };
+enum { SLOT_T_LAG = LRK_COUNT, SLOT_T_CELL, SLOT_T_NODE, SLOT_PLACE, SLOT_T_FLAGGED, NSLOT };
 const char* slot_name(int k) {
   switch (k) {
     case SLOT_T_LAG: return "lr_t_lagrange";
     case SLOT_T_CELL: return "lr_t_cell_remap";
     case SLOT_T_NODE: return "lr_t_node_remap";
     case SLOT_PLACE: return "lb_mixed_place";
+    case SLOT_T_FLAGGED: return "lr_t_cell_flagged";
     default: return lr_kernel_names[k];
   }
 }
@@ -358,7 +367,8 @@ int slot_of(int k) {
   switch (k) {
     case LRK_MIXED_PLACE: return SLOT_PLACE;  // lr_mixed is the flux split that follows
     case LRK_T_LAGRANGE: return SLOT_T_LAG;
-    case LRK_T_CELL_REMAP: return SLOT_T_CELL;
+    case LRK_T_CELL_REMAP: case LRK_T_CELL_CLEAN: return SLOT_T_CELL;
+    case LRK_T_CELL_DIRTY: return SLOT_T_FLAGGED;
     case LRK_T_NODE_REMAP: return SLOT_T_NODE;
     default: return k < LRK_COUNT ? k : -1;
   }
@@ -367,6 +377,21 @@ int slot_of(int k) {
 // diagonal corner values.
 bool tiled_ok(const LrGrid& g) {
   return g.remap == LR_REMAP_DIRECTCF && (g.corner_kind == LR_CORNER_UPWIND || g.corner_kind == LR_CORNER_DIAG);
+}
+// The tiled step splits its cell remap around the interface kernels (tiles
+// no mixed cell reaches beside them, the listed tiles after them) for three
+// materials: there the nested cut of three-material cells makes the
+// interface kernels a long FP64 latency chain (about 65 us on the 1400 x 600
+// triple point) that the clean tiles hide, for about 20 us of latency-bound
+// work on the listed tiles afterwards.  With two materials the interface
+// kernels are short (about 30 us on the 4096 x 1024 shock-bubble) and the
+// split costs more than it hides (measured on GB300).
+bool split_cell_remap(const LrGrid& g) { return g.M == 3; }
+// Cell tiles of the tiled step (one flag each).
+size_t tile_count(const LrGrid& g) {
+  int tw = 0, th = 0;
+  lr_tiled_tile_shape(&tw, &th);
+  return (size_t)((g.nx + tw - 1) / tw) * (size_t)((g.ny + th - 1) / th);
 }
 
 cudaError_t launch_on(lr_ctx* ctx, int k, const LrGrid& g, const LrState& cur, const LrState& nxt, cudaStream_t st) {
@@ -431,18 +456,37 @@ cudaError_t enqueue_step(lr_ctx* ctx, int from) {
   const LrState& cur = ctx->st[from];
   const LrState& nxt = ctx->st[1 - from];
   if (ctx->tiled) {
-    // Tiled step on one stream: the Lagrange phase and remap geometry; the
-    // interface kernels of the mixed cells; the material fluxes and cell
-    // update; the dual remap and node update (it reads the new sound speeds
-    // for the CFL rule).
+    // Tiled step: the Lagrange phase and remap geometry (it flags the cell
+    // tiles a mixed cell reaches and lists them); the interface kernels of
+    // the mixed cells on the second (high-priority) stream, beside the
+    // material fluxes and cell update of the tiles no mixed cell reaches; the
+    // listed tiles once the interface work is done; the dual remap and node
+    // update (it reads the new sound speeds for the CFL rule).  The interface
+    // kernels are latency-bound on the FP64 pipe and leave most issue slots
+    // free, so the clean tiles run in their shadow.  Profiling mode runs
+    // everything on one stream.
     const LrGrid& g = ctx->g;
     cudaError_t e;
     if ((e = launch_on(ctx, LRK_T_LAGRANGE, g, cur, nxt, ctx->stream)) != cudaSuccess) return e;
-    if (g.M > 1) {  // the interface lines, then the split of the fluxes mixed cells donate
+    if (g.M == 1) {
+      if ((e = launch_on(ctx, LRK_T_CELL_REMAP, g, cur, nxt, ctx->stream)) != cudaSuccess) return e;
+      return launch_on(ctx, LRK_T_NODE_REMAP, g, cur, nxt, ctx->stream);
+    }
+    if (!split_cell_remap(g)) {  // one stream: interface kernels, then every tile
       if ((e = launch_on(ctx, LRK_MIXED_PLACE, g, cur, nxt, ctx->stream)) != cudaSuccess) return e;
       if ((e = launch_on(ctx, LRK_MIXED, g, cur, nxt, ctx->stream)) != cudaSuccess) return e;
+      if ((e = launch_on(ctx, LRK_T_CELL_REMAP, g, cur, nxt, ctx->stream)) != cudaSuccess) return e;
+      return launch_on(ctx, LRK_T_NODE_REMAP, g, cur, nxt, ctx->stream);
     }
-    if ((e = launch_on(ctx, LRK_T_CELL_REMAP, g, cur, nxt, ctx->stream)) != cudaSuccess) return e;
+    cudaStream_t side = ctx->prof ? ctx->stream : ctx->aux;
+    if ((e = cudaEventRecord(ctx->ev_fork, ctx->stream)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(side, ctx->ev_fork, 0)) != cudaSuccess) return e;
+    if ((e = launch_on(ctx, LRK_MIXED_PLACE, g, cur, nxt, side)) != cudaSuccess) return e;
+    if ((e = launch_on(ctx, LRK_MIXED, g, cur, nxt, side)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(ctx->ev_join, side)) != cudaSuccess) return e;
+    if ((e = launch_on(ctx, LRK_T_CELL_CLEAN, g, cur, nxt, ctx->stream)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0)) != cudaSuccess) return e;
+    if ((e = launch_on(ctx, LRK_T_CELL_DIRTY, g, cur, nxt, ctx->stream)) != cudaSuccess) return e;
     return launch_on(ctx, LRK_T_NODE_REMAP, g, cur, nxt, ctx->stream);
   }
   if (ctx->g.remap != LR_REMAP_AD) {
@@ -536,6 +580,8 @@ lr_status create_common(const lr_config* cfg, void* mem, size_t bytes, bool own,
       lr_launch_reset(ctx->g.mode, ctx->w, 1, ctx->stream) != cudaSuccess ||
       cudaMemsetAsync(ctx->w.pux, 0, lr_real_size(ctx->g.mode) * (cfg->nx + 1) * (cfg->ny + 1), ctx->stream) != cudaSuccess ||
       cudaMemsetAsync(ctx->w.puy, 0, lr_real_size(ctx->g.mode) * (cfg->nx + 1) * (cfg->ny + 1), ctx->stream) != cudaSuccess ||
+      cudaMemsetAsync(ctx->w.tflag, 0, sizeof(unsigned int) * tile_count(ctx->g), ctx->stream) != cudaSuccess ||
+      cudaMemsetAsync(ctx->w.tcount, 0, 2 * sizeof(unsigned int), ctx->stream) != cudaSuccess ||
       cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     if (own) cudaFree(mem);
@@ -865,9 +911,10 @@ int lr_launches_per_step(const lr_ctx* ctx) {
   if (!ctx) return 0;
   // the interface work is two kernels (placement, then the flux split)
   int one = (int)LRK_COUNT + (ctx->g.M == 1 ? -1 : 1);
-  // tiled: t_end/dt, Lagrange, interface lines and flux split (two or more
-  // materials), cell remap, node remap
-  if (ctx->tiled) return ctx->g.M == 1 ? 4 : 6;
+  // tiled: t_end/dt, Lagrange, cell remap, node remap; with two or more
+  // materials the interface lines and flux split; with three the cell remap
+  // in two launches (the tiles no mixed cell reaches, then the listed ones)
+  if (ctx->tiled) return ctx->g.M == 1 ? 4 : ctx->g.M == 2 ? 6 : 7;
   return 1 + one + (ctx->g.remap == LR_REMAP_AD ? one - 1 : 0);
 }
 

@@ -100,6 +100,9 @@ struct LrWorkT {
   int* minst;              // simulation slot of each list entry
   const LrGrid* gdev;      // lone simulation: its grid in device memory (the interface kernel reads it)
   unsigned char* mask;     // bit a set when material a is present in the cell at t^n
+  unsigned int* tflag;     // tiled step: 1 for a cell tile with a mixed cell within one cell (else null)
+  int* tlist;              // the flagged tiles, tcount[0] of them, each once
+  unsigned int* tcount;    // [0] listed tiles, [1] blocks of the flagged-tile kernel that finished
   double* cut[6];          // interface lines of mixed cells (n0x, n0y, d0, n1x, n1y, d1)
   double* cutY[6];         // Direct remap: the lines that cut the Y faces (else null)
   double* stage;           // init staging: k, rho, p [3][nmat][nc] then ux, uy [2][nn]
@@ -130,6 +133,7 @@ inline LrWorkT<R> typed(const LrWork& w) {
   LrWorkT<R> t;
   t.scal = w.scal; t.red = w.red; t.err = w.err; t.mixed = w.mixed; t.minst = w.minst; t.gdev = w.gdev;
   t.mask = w.mask;
+  t.tflag = w.tflag; t.tlist = w.tlist; t.tcount = w.tcount;
   t.stage = w.stage;
   for (int q = 0; q < 6; ++q) { t.cut[q] = w.cut[q]; t.cutY[q] = w.cutY[q]; }
 #define LR_F1(n) t.n = static_cast<R*>(w.n);
@@ -157,7 +161,9 @@ enum LrKernelId {
   // tiled step (lone simulations): fused kernel pairs over shared-memory tiles
   LRK_T_NODE_REMAP = 110,  // lr_dual_flux + lr_node_update
   LRK_T_CELL_REMAP = 111,  // lr_mat_flux + lr_cell_update
-  LRK_T_LAGRANGE = 112     // lr_cell_pre + lr_node_half + lr_cell_lag + lr_cell_cf
+  LRK_T_LAGRANGE = 112,    // lr_cell_pre + lr_node_half + lr_cell_lag + lr_cell_cf
+  LRK_T_CELL_CLEAN = 113,  // lr_t_cell_remap over the tiles no mixed cell reaches (beside the interface kernels)
+  LRK_T_CELL_DIRTY = 114   // lr_t_cell_flagged: the other tiles (after the interface kernels)
 };
 // Interface-line placement spreads a short mixed-cell list over about this
 // many warps (two per SM sub-partition of a 152-SM GPU), one lane per cell.

@@ -2718,12 +2718,43 @@ __device__ __forceinline__ void t_cell_tile(const LrGrid& g, const KC<R>& kc, co
   }
   w.cc[c] = cmax;
 }
+// pass 0: every tile; pass 1: the tiles the Lagrange phase left unflagged
+// (no mixed cell within one cell of the tile, so no flux object with a
+// mixed donor).  One block per tile.
 template <class R, int M>
 __global__ void __launch_bounds__(TTHREADS, TileMinB<R, LR_MINB_D_UPDATE>::value)
-    lr_t_cell_remap(LrGrid g, KC<R> kc, LrStateT<R> cur, LrStateT<R> nxt, LrWorkT<R> w) {
+    lr_t_cell_remap(LrGrid g, KC<R> kc, LrStateT<R> cur, LrStateT<R> nxt, LrWorkT<R> w, int pass) {
   lr_pdl_enter();
   extern __shared__ __align__(16) unsigned char lr_smem[];
+  if (pass == 1 && w.tflag[blockIdx.y * gridDim.x + blockIdx.x] != 0u) return;  // uniform over the block
   t_cell_tile<R, M>(g, kc, cur, nxt, w, blockIdx.x * TTX, blockIdx.y * TTY, lr_smem);
+}
+// The flagged tiles, from their list, in a grid-stride loop; each flag is
+// cleared for the next step, and the last block to finish empties the list
+// (tcount[0]: listed tiles, tcount[1]: finished blocks; every block has read
+// the length before it counts itself finished).  Few tiles: a larger
+// register budget than the full-grid kernel's.
+#ifndef LR_FLAGGED_MINB
+#define LR_FLAGGED_MINB 4
+#endif
+template <class R, int M>
+__global__ void __launch_bounds__(TTHREADS, LR_FLAGGED_MINB)
+    lr_t_cell_flagged(LrGrid g, KC<R> kc, LrStateT<R> cur, LrStateT<R> nxt, LrWorkT<R> w) {
+  lr_pdl_enter();
+  extern __shared__ __align__(16) unsigned char lr_smem[];
+  const int ntx = (g.nx + TTX - 1) / TTX;
+  const int count = (int)*w.tcount;
+  for (int q = blockIdx.x; q < count; q += gridDim.x) {
+    const int tix = w.tlist[q];
+    __syncthreads();  // the previous tile no longer reads shared memory
+    t_cell_tile<R, M>(g, kc, cur, nxt, w, (tix % ntx) * TTX, (tix / ntx) * TTY, lr_smem);
+    if (threadIdx.x == 0) w.tflag[tix] = 0u;
+  }
+  __syncthreads();  // every thread of the block has read the length
+  if (threadIdx.x == 0 && atomicAdd(&w.tcount[1], 1u) == gridDim.x - 1) {
+    w.tcount[0] = 0u;
+    w.tcount[1] = 0u;
+  }
 }
 
 constexpr int LG_CW = TTX + 2, LG_CH = TTY + 2, LG_NW = TTX + 3, LG_NH = TTY + 3, LG_OW = TTX + 1,
@@ -2731,6 +2762,32 @@ constexpr int LG_CW = TTX + 2, LG_CH = TTY + 2, LG_NW = TTX + 3, LG_NH = TTY + 3
 template <class R, int M> constexpr size_t lagrange_smem() {
   return sizeof(R) * ((size_t)2 * LG_NW * LG_NH + (size_t)(2 + M) * LG_CW * LG_CH + (size_t)4 * LG_OW * LG_OH) +
          (size_t)LG_CW * LG_CH;
+}
+
+// Flags the cell tiles whose flux objects can have mixed cell (ci, cj) as
+// donor: the tiles of the cells within one cell of it (wrapped across a
+// periodic boundary; beyond a wall the ghost mirrors a cell of the same
+// tile).  Their material fluxes wait for the interface kernels.  The first
+// flagging of a tile appends it to the list.
+template <class R>
+__device__ __forceinline__ void mark_dirty_tiles(const LrGrid& g, const LrWorkT<R>& w, int ci, int cj) {
+  const int ntx = (g.nx + TTX - 1) / TTX;
+  for (int dj = -1; dj <= 1; ++dj) {
+    int y = cj + dj;
+    if (y < 0 || y >= g.ny) {
+      if (!g.pery) continue;
+      y = y < 0 ? y + g.ny : y - g.ny;
+    }
+    for (int di = -1; di <= 1; ++di) {
+      int x = ci + di;
+      if (x < 0 || x >= g.nx) {
+        if (!g.perx) continue;
+        x = x < 0 ? x + g.nx : x - g.nx;
+      }
+      const int tix = (y / TTY) * ntx + x / TTX;
+      if (w.tflag[tix] == 0u && atomicExch(&w.tflag[tix], 1u) == 0u) w.tlist[atomicAdd(w.tcount, 1u)] = tix;
+    }
+  }
 }
 
 // The cell part of lr_t_lagrange (phases 3b and 4) for cell (i, j), thread
@@ -2887,6 +2944,7 @@ __device__ __forceinline__ void t_lagrange_tile(const LrGrid& g, const KC<R>& kc
         int slot = g.moff + (int)atomicAdd(&w.red[g.mslot], 1ull);
         w.mixed[slot] = c;
         if (w.minst) w.minst[slot] = g.inst;
+        if (M == 3 && w.tflag) mark_dirty_tiles(g, w, ci, cj);  // the split cell remap (three materials)
       }
     }
   }
@@ -3202,14 +3260,37 @@ cudaError_t launch_t(int kid, const LrGrid& g, const LrState& cur0, const LrStat
     case LRK_PREPARE: LR_M(lr_prepare, grid_for(g.nx + 1, g.ny + 1)); break;
     case LRK_CFL_ONLY: LR_1(lr_cfl_only, grid_for(g.nxu, g.nyu)); break;
     case LRK_SWEEP_PREP: LR_M(lr_sweep_prep, grid_for(g.nxu, g.nyu)); break;
-    case LRK_T_CELL_REMAP: {
+    case LRK_T_CELL_REMAP:
+    case LRK_T_CELL_CLEAN:
+    case LRK_T_CELL_DIRTY: {
+      if (kid != LRK_T_CELL_REMAP && !w.tflag) return cudaErrorInvalidValue;
       dim3 gr((g.nx + TTX - 1) / TTX, (g.ny + TTY - 1) / TTY);
-      cudaError_t e = g.M == 1 ? launch_pdl_smem(lr_t_cell_remap<R, 1>, gr, dim3(TTHREADS), cell_remap_smem<R, 1>(), s,
-                                                 g, kc, cur, nxt, w)
-                    : g.M == 2 ? launch_pdl_smem(lr_t_cell_remap<R, 2>, gr, dim3(TTHREADS), cell_remap_smem<R, 2>(), s,
-                                                 g, kc, cur, nxt, w)
-                               : launch_pdl_smem(lr_t_cell_remap<R, 3>, gr, dim3(TTHREADS), cell_remap_smem<R, 3>(), s,
-                                                 g, kc, cur, nxt, w);
+      cudaError_t e;
+      if (kid == LRK_T_CELL_DIRTY) {  // a grid-stride loop over the listed tiles: resident blocks at most
+        if (g.M == 1) break;
+        unsigned int most = 152u * LR_FLAGGED_MINB;
+        unsigned int nt = gr.x * gr.y;
+        dim3 gf(nt < most ? nt : most);
+        e = g.M == 2 ? launch_pdl_smem(lr_t_cell_flagged<R, 2>, gf, dim3(TTHREADS), cell_remap_smem<R, 2>(), s, g, kc,
+                                       cur, nxt, w)
+                     : launch_pdl_smem(lr_t_cell_flagged<R, 3>, gf, dim3(TTHREADS), cell_remap_smem<R, 3>(), s, g, kc,
+                                       cur, nxt, w);
+        if (e != cudaSuccess) return e;
+        break;
+      }
+      const int pass = kid == LRK_T_CELL_CLEAN ? 1 : 0;
+      if (pass == 1) {  // launched plainly: its blocks must not fill the GPU before the interface kernels start
+        if (g.M == 1) return cudaErrorInvalidValue;
+        if (g.M == 2) lr_t_cell_remap<R, 2><<<gr, TTHREADS, cell_remap_smem<R, 2>(), s>>>(g, kc, cur, nxt, w, pass);
+        else lr_t_cell_remap<R, 3><<<gr, TTHREADS, cell_remap_smem<R, 3>(), s>>>(g, kc, cur, nxt, w, pass);
+        break;
+      }
+      e = g.M == 1 ? launch_pdl_smem(lr_t_cell_remap<R, 1>, gr, dim3(TTHREADS), cell_remap_smem<R, 1>(), s, g, kc, cur,
+                                     nxt, w, pass)
+        : g.M == 2 ? launch_pdl_smem(lr_t_cell_remap<R, 2>, gr, dim3(TTHREADS), cell_remap_smem<R, 2>(), s, g, kc, cur,
+                                     nxt, w, pass)
+                   : launch_pdl_smem(lr_t_cell_remap<R, 3>, gr, dim3(TTHREADS), cell_remap_smem<R, 3>(), s, g, kc, cur,
+                                     nxt, w, pass);
       if (e != cudaSuccess) return e;
       break;
     }
@@ -3314,6 +3395,12 @@ cudaError_t lr_tiled_setup() {
   LR_SMEM((lr_t_cell_remap<df64, 1>), (cell_remap_smem<df64, 1>()));
   LR_SMEM((lr_t_cell_remap<df64, 2>), (cell_remap_smem<df64, 2>()));
   LR_SMEM((lr_t_cell_remap<df64, 3>), (cell_remap_smem<df64, 3>()));
+  LR_SMEM((lr_t_cell_flagged<double, 2>), (cell_remap_smem<double, 2>()));
+  LR_SMEM((lr_t_cell_flagged<double, 3>), (cell_remap_smem<double, 3>()));
+  LR_SMEM((lr_t_cell_flagged<float, 2>), (cell_remap_smem<float, 2>()));
+  LR_SMEM((lr_t_cell_flagged<float, 3>), (cell_remap_smem<float, 3>()));
+  LR_SMEM((lr_t_cell_flagged<df64, 2>), (cell_remap_smem<df64, 2>()));
+  LR_SMEM((lr_t_cell_flagged<df64, 3>), (cell_remap_smem<df64, 3>()));
   LR_SMEM((lr_t_lagrange<double, 1>), (lagrange_smem<double, 1>()));
   LR_SMEM((lr_t_lagrange<double, 2>), (lagrange_smem<double, 2>()));
   LR_SMEM((lr_t_lagrange<double, 3>), (lagrange_smem<double, 3>()));
