@@ -365,7 +365,8 @@ const char* slot_name(int k) {
 }
 int slot_of(int k) {
   switch (k) {
-    case LRK_MIXED_PLACE: return SLOT_PLACE;  // lr_mixed is the flux split that follows
+    case LRK_MIXED_PLACE: case LRK_MIXED_PLACE_PDL: return SLOT_PLACE;  // lr_mixed: the flux split after it
+    case LRK_MIXED_PDL: return LRK_MIXED;
     case LRK_T_LAGRANGE: return SLOT_T_LAG;
     case LRK_T_CELL_REMAP: case LRK_T_CELL_CLEAN: return SLOT_T_CELL;
     case LRK_T_CELL_DIRTY: return SLOT_T_FLAGGED;
@@ -473,14 +474,17 @@ cudaError_t enqueue_step(lr_ctx* ctx, int from) {
       return launch_on(ctx, LRK_T_NODE_REMAP, g, cur, nxt, ctx->stream);
     }
     if (!split_cell_remap(g)) {  // one stream: interface kernels, then every tile
-      if ((e = launch_on(ctx, LRK_MIXED_PLACE, g, cur, nxt, ctx->stream)) != cudaSuccess) return e;
-      if ((e = launch_on(ctx, LRK_MIXED, g, cur, nxt, ctx->stream)) != cudaSuccess) return e;
+      if ((e = launch_on(ctx, LRK_MIXED_PLACE_PDL, g, cur, nxt, ctx->stream)) != cudaSuccess) return e;
+      if ((e = launch_on(ctx, LRK_MIXED_PDL, g, cur, nxt, ctx->stream)) != cudaSuccess) return e;
       if ((e = launch_on(ctx, LRK_T_CELL_REMAP, g, cur, nxt, ctx->stream)) != cudaSuccess) return e;
       return launch_on(ctx, LRK_T_NODE_REMAP, g, cur, nxt, ctx->stream);
     }
     cudaStream_t side = ctx->prof ? ctx->stream : ctx->aux;
     if ((e = cudaEventRecord(ctx->ev_fork, ctx->stream)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(side, ctx->ev_fork, 0)) != cudaSuccess) return e;
+    // plain launches here: a programmatic launch of the flux split keeps its
+    // blocks resident (and their registers held) through the placement,
+    // taking them from the clean tiles that run meanwhile
     if ((e = launch_on(ctx, LRK_MIXED_PLACE, g, cur, nxt, side)) != cudaSuccess) return e;
     if ((e = launch_on(ctx, LRK_MIXED, g, cur, nxt, side)) != cudaSuccess) return e;
     if ((e = cudaEventRecord(ctx->ev_join, side)) != cudaSuccess) return e;

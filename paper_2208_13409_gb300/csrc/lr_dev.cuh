@@ -163,7 +163,9 @@ enum LrKernelId {
   LRK_T_CELL_REMAP = 111,  // lr_mat_flux + lr_cell_update
   LRK_T_LAGRANGE = 112,    // lr_cell_pre + lr_node_half + lr_cell_lag + lr_cell_cf
   LRK_T_CELL_CLEAN = 113,  // lr_t_cell_remap over the tiles no mixed cell reaches (beside the interface kernels)
-  LRK_T_CELL_DIRTY = 114   // lr_t_cell_flagged: the other tiles (after the interface kernels)
+  LRK_T_CELL_DIRTY = 114,  // lr_t_cell_flagged: the other tiles (after the interface kernels)
+  LRK_MIXED_PLACE_PDL = 115,  // lb_mixed_place right after a kernel of the same stream (programmatic launch)
+  LRK_MIXED_PDL = 116         // lb_mixed right after lb_mixed_place (programmatic launch)
 };
 // Interface-line placement spreads a short mixed-cell list over about this
 // many warps (two per SM sub-partition of a 152-SM GPU), one lane per cell.

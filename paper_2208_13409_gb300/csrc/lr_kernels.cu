@@ -3232,22 +3232,33 @@ cudaError_t launch_t(int kid, const LrGrid& g, const LrState& cur0, const LrStat
     case LRK_CELL_LAG: LR_M(lr_cell_lag, grid_for(g.nxu, g.nyu)); break;
     case LRK_CELL_CF: LR_M(lr_cell_cf, grid_for(g.nx, g.ny)); break;
     case LRK_MIXED_PLACE:
-    case LRK_MIXED: {
+    case LRK_MIXED:
+    case LRK_MIXED_PLACE_PDL:
+    case LRK_MIXED_PDL: {
       if (g.M == 1) break;  // one material: no interfaces
       if (!w.gdev) return cudaErrorInvalidValue;
-      if (kid == LRK_MIXED_PLACE) {
+      // the _PDL forms directly follow a kernel of the same stream (the tiled
+      // step): launched programmatically, they start as it drains
+      const bool pdl = kid == LRK_MIXED_PLACE_PDL || kid == LRK_MIXED_PDL;
+      cudaError_t e;
+      if (kid == LRK_MIXED_PLACE || kid == LRK_MIXED_PLACE_PDL) {
         long long lanes = 8ll * g.nx * g.ny;  // enough warps for four cells each
         int np = (int)((lanes + 127) / 128);
         if (np > 152 * 16) np = 152 * 16;
-        if (g.M == 2) lb_mixed_place<R, 2><<<np, 128, 0, s>>>(w.gdev, cur, w, g.mslot, g.moff, LR_PLACE_SPREAD);
-        else lb_mixed_place<R, 3><<<np, 128, 0, s>>>(w.gdev, cur, w, g.mslot, g.moff, LR_PLACE_SPREAD);
+        auto k = g.M == 2 ? lb_mixed_place<R, 2> : lb_mixed_place<R, 3>;
+        if (pdl) e = launch_pdl(k, dim3(np), dim3(128), s, (const LrGrid*)w.gdev, cur, w, g.mslot, g.moff,
+                                (int)LR_PLACE_SPREAD);
+        else { k<<<np, 128, 0, s>>>(w.gdev, cur, w, g.mslot, g.moff, LR_PLACE_SPREAD); e = cudaSuccess; }
+        if (e != cudaSuccess) return e;
         break;
       }
       long long lanes = (long long)g.mixed_lanes * g.nx * g.ny;
       int nb = (int)((lanes + 127) / 128);
       if (nb > 152 * 16) nb = 152 * 16;
-      if (g.M == 2) lb_mixed<R, 2><<<nb, 128, 0, s>>>(w.gdev, cur, w, g.mixed_lanes, g.mslot, g.moff);
-      else lb_mixed<R, 3><<<nb, 128, 0, s>>>(w.gdev, cur, w, g.mixed_lanes, g.mslot, g.moff);
+      auto k = g.M == 2 ? lb_mixed<R, 2> : lb_mixed<R, 3>;
+      if (pdl) e = launch_pdl(k, dim3(nb), dim3(128), s, (const LrGrid*)w.gdev, cur, w, g.mixed_lanes, g.mslot, g.moff);
+      else { k<<<nb, 128, 0, s>>>(w.gdev, cur, w, g.mixed_lanes, g.mslot, g.moff); e = cudaSuccess; }
+      if (e != cudaSuccess) return e;
       break;
     }
     case LRK_MAT_FLUX:
