@@ -2491,8 +2491,57 @@ __device__ __forceinline__ void t_cell_tile(const LrGrid& g, const KC<R>& kc, co
       sDY[t] = O::flip(n.fy, w.ddy[n.idx]);
     }
   };
-  if (inner) stage(std::true_type{});
-  else stage(std::false_type{});
+  // In FP32 with one or two materials, an interior tile of a grid whose
+  // rows start on 16-byte boundaries reads its cell-centred fields as float4
+  // (the masks as uchar4) from column i0 - 4 (aligned), ten vectors per
+  // staged row, a thread per (row, vector); the node-centred displacements
+  // (rows of nx + 1) go element by element.  (With three materials the
+  // extra registers cost more than the loads save: measured on GB300.)
+  constexpr bool kVec = std::is_same<R, float>::value && M <= 2;
+  bool vec = false;
+  if constexpr (kVec) vec = inner && (g.nx & 3) == 0 && (g.coff & 3) == 0 && i0 + TTX + 3 < g.nx;
+  if (vec) {
+    if constexpr (kVec) {
+      constexpr int NV = (CR_SW + 7) / 4;  // columns i0-4 .. i0+4 NV-5 cover the staged i0-2 .. i0+TX+1
+      for (int q = tid; q < CR_SH * NV; q += TTHREADS) {
+        const int r = q / NV, v = q % NV;
+        const size_t idx = (size_t)g.coff + (size_t)(j0 - 2 + r) * g.nx + (size_t)(i0 - 4 + 4 * v);
+        auto put = [&](R* dst, const float4& x) {
+          const float e[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int sc = 4 * v + c - 2;
+            if (sc >= 0 && sc < CR_SW) dst[r * CR_SW + sc] = e[c];
+          }
+        };
+        put(sOX, *reinterpret_cast<const float4*>(w.ox + idx));
+        put(sOY, *reinterpret_cast<const float4*>(w.oy + idx));
+        put(sWX, *reinterpret_cast<const float4*>(w.wx + idx));
+        put(sWY, *reinterpret_cast<const float4*>(w.wy + idx));
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+          put(sQ + a * SN, *reinterpret_cast<const float4*>(w.rcf[a] + idx));
+          put(sQ + (M + a) * SN, *reinterpret_cast<const float4*>(w.elag[a] + idx));
+        }
+        const uchar4 mk = *reinterpret_cast<const uchar4*>(w.mask + idx);
+        const unsigned char me[4] = {mk.x, mk.y, mk.z, mk.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int sc = 4 * v + c - 2;
+          if (sc >= 0 && sc < CR_SW) sMK[r * CR_SW + sc] = me[c];
+        }
+      }
+      for (int t = tid; t < SN; t += TTHREADS) {
+        Ix n = snix<true>(g, i0 - 2 + t % CR_SW, j0 - 2 + t / CR_SW);
+        sDX[t] = w.ddx[n.idx];
+        sDY[t] = w.ddy[n.idx];
+      }
+    }
+  } else if (inner) {
+    stage(std::true_type{});
+  } else {
+    stage(std::false_type{});
+  }
   __syncthreads();
   CellTile<R, M> T;
   T.ox = sOX; T.oy = sOY; T.wx = sWX; T.wy = sWY; T.dx_ = sDX; T.dy_ = sDY; T.mk = sMK;

@@ -35,6 +35,7 @@ CASES = {
     "tile_edges_32x8_periodic": lambda: P.random_box(30, nx=32, ny=8, nmat=2, velocity=0.3).copy(
         bc=(P.BC_PERIODIC,) * 4),
     "air_water_128": lambda: P.air_water(5, side=128),
+    "random2_128x40": lambda: P.random_box(32, nx=128, ny=40, nmat=2, velocity=0.3),
 }
 
 
@@ -80,8 +81,11 @@ def test_tiled_parity_100_steps_graphs(name):
     sim.close()
 
 
-@pytest.mark.parametrize("name", ["triple_point_140x60", "random3_periodic", "mixed_bc_yper", "tiny_2x2"])
+@pytest.mark.parametrize("name", ["triple_point_140x60", "random3_periodic", "mixed_bc_yper", "tiny_2x2",
+                                  "shock_bubble_256x64", "random2_128x40"])
 def test_tiled_fp32_matches_unfused_fp32(name):
+    """Also the FP32 staging by float4 (two materials, rows of a multiple of
+    four cells, interior tiles: the shock-bubble and the 128 x 40 box)."""
     pr = CASES[name]()
     a = lr.Sim(pr, precision=lr.FP32)
     assert a.tiled  # the default in FP32
