@@ -2444,7 +2444,11 @@ template <class R, int M> constexpr size_t cell_remap_smem() {
 // the dual remap; objects with a mixed donor were finished by the donor's
 // are read from the arrays lr_t_lagrange's interface phase stored.  Then the
 // cell update of cell_update_at.
-template <class R, int M>
+// PF: the cell update first gathers the eight objects' values of a material
+// (the loads of mixed donors' fluxes issue together), then accumulates them
+// in the same order -- for the listed tiles, whose update waits on those
+// loads; the same arithmetic either way.
+template <class R, int M, bool PF = false>
 __device__ __forceinline__ void t_cell_tile(const LrGrid& g, const KC<R>& kc, const LrStateT<R>& cur,
                                             const LrStateT<R>& nxt, const LrWorkT<R>& w, int i0, int j0,
                                             unsigned char* lr_smem) {
@@ -2689,6 +2693,13 @@ __device__ __forceinline__ void t_cell_tile(const LrGrid& g, const KC<R>& kc, co
     }
   };
   R vcf = w.vcf[c];
+  int gix[8];  // PF: where the interface kernels stored object l's fluxes
+  if constexpr (PF) {
+    gix[0] = xix(g, i, j).idx; gix[1] = xix(g, i + 1, j).idx;
+    gix[2] = yix(g, i, j).idx; gix[3] = yix(g, i, j + 1).idx;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) gix[4 + q] = nix(g, i + (q & 1), j + (q >> 1)).idx;
+  }
   R vol[M], mas[M], ene[M];
 #pragma unroll
   for (int a = 0; a < M; ++a) {
@@ -2703,19 +2714,46 @@ __device__ __forceinline__ void t_cell_tile(const LrGrid& g, const KC<R>& kc, co
       vv.init(ka * vcf);
       ee.init(m0 * pick<M>(T.eq, a)[s0]);
     }
-    R Al, Ml, El, Ar, Mr, Er;
-    obj(0, a, Al, Ml, El); obj(1, a, Ar, Mr, Er);
-    R Ab, Mb, Eb, At, Mt, Et;
-    obj(2, a, Ab, Mb, Eb); obj(3, a, At, Mt, Et);
-    vv.add(Al - Ar); vv.add(Ab - At);
-    mm.add(Ml - Mr); mm.add(Mb - Mt);
-    ee.add(El - Er); ee.add(Eb - Et);
+    if constexpr (PF) {
+      R oAv[8], oMv[8], oEv[8];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      bool on = cs[q] != 0, ng = cs[q] < 0;
-      R ca, cm, ce;
-      obj(4 + q, a, ca, cm, ce);
-      vv.add(on ? O::flip(ng, ca) : Z); mm.add(on ? O::flip(ng, cm) : Z); ee.add(on ? O::flip(ng, ce) : Z);
+      for (int l = 0; l < 8; ++l) {
+        const int sI = sl[l], m = oMat[sI];
+        if (m == a) {
+          oAv[l] = oA[sI]; oMv[l] = oM[sI]; oEv[l] = oE[sI];
+        } else if (m == -2) {
+          const R* sa = l < 2 ? w.xA[a] : l < 4 ? w.yA[a] : w.cA[a];
+          const R* sm = l < 2 ? w.xMm[a] : l < 4 ? w.yMm[a] : w.cMm[a];
+          const R* se = l < 2 ? w.xE[a] : l < 4 ? w.yE[a] : w.cE[a];
+          oAv[l] = sa[gix[l]]; oMv[l] = sm[gix[l]]; oEv[l] = se[gix[l]];
+        } else {
+          oAv[l] = Z; oMv[l] = Z; oEv[l] = Z;
+        }
+      }
+      vv.add(oAv[0] - oAv[1]); vv.add(oAv[2] - oAv[3]);
+      mm.add(oMv[0] - oMv[1]); mm.add(oMv[2] - oMv[3]);
+      ee.add(oEv[0] - oEv[1]); ee.add(oEv[2] - oEv[3]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        bool on = cs[q] != 0, ng = cs[q] < 0;
+        vv.add(on ? O::flip(ng, oAv[4 + q]) : Z); mm.add(on ? O::flip(ng, oMv[4 + q]) : Z);
+        ee.add(on ? O::flip(ng, oEv[4 + q]) : Z);
+      }
+    } else {
+      R Al, Ml, El, Ar, Mr, Er;
+      obj(0, a, Al, Ml, El); obj(1, a, Ar, Mr, Er);
+      R Ab, Mb, Eb, At, Mt, Et;
+      obj(2, a, Ab, Mb, Eb); obj(3, a, At, Mt, Et);
+      vv.add(Al - Ar); vv.add(Ab - At);
+      mm.add(Ml - Mr); mm.add(Mb - Mt);
+      ee.add(El - Er); ee.add(Eb - Et);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        bool on = cs[q] != 0, ng = cs[q] < 0;
+        R ca, cm, ce;
+        obj(4 + q, a, ca, cm, ce);
+        vv.add(on ? O::flip(ng, ca) : Z); mm.add(on ? O::flip(ng, cm) : Z); ee.add(on ? O::flip(ng, ce) : Z);
+      }
     }
     vol[a] = vv.get(); mas[a] = mm.get(); ene[a] = ee.get();
   }
@@ -2796,7 +2834,7 @@ __global__ void __launch_bounds__(TTHREADS, LR_FLAGGED_MINB)
   for (int q = blockIdx.x; q < count; q += gridDim.x) {
     const int tix = w.tlist[q];
     __syncthreads();  // the previous tile no longer reads shared memory
-    t_cell_tile<R, M>(g, kc, cur, nxt, w, (tix % ntx) * TTX, (tix / ntx) * TTY, lr_smem);
+    t_cell_tile<R, M, true>(g, kc, cur, nxt, w, (tix % ntx) * TTX, (tix / ntx) * TTY, lr_smem);
     if (threadIdx.x == 0) w.tflag[tix] = 0u;
   }
   __syncthreads();  // every thread of the block has read the length
