@@ -256,7 +256,10 @@ int lr_kernel_times(lr_ctx* ctx, const char** names, long* launches, double* ms,
  * upwind or diagonal corner values (LR_ERR_ARG otherwise); on by default in
  * LR_FP32, off in LR_FP64 and LR_DF64.  Intermediate per-material flux
  * fields (LR_F_XA, LR_F_YA, LR_F_CA) of a tiled step hold only the objects
- * with a mixed donor.  lr_get_tiled returns the current setting. */
+ * with a mixed donor.  Launches per step: 4 with one material, 6 with two;
+ * with three the interface kernels run on the context's second stream
+ * beside the cell tiles no mixed cell reaches, and the other tiles follow
+ * them (7 launches).  lr_get_tiled returns the current setting. */
 lr_status lr_set_tiled(lr_ctx* ctx, int on);
 int lr_get_tiled(const lr_ctx* ctx);
 
