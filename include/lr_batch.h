@@ -103,8 +103,10 @@ lr_status lr_batch_get_fields(lr_batch* b, int member, int field, double* host_o
 
 /* Choose, per kernel, the tile shape (32x8, 64x4, 16x16, 128x2 threads) and
  * the number of persistent blocks, and the lanes per mixed cell, by timing
- * trial steps of the current members (trial_steps each, at least 1).  The
- * members' state, time and step counts are restored afterwards. */
+ * trial steps of the current members (trial_steps each, at least 1); then,
+ * unless lr_batch_set_persistent was called, time whole steps of that
+ * schedule against the persistent step and keep the faster.  The members'
+ * state, time and step counts are restored afterwards. */
 lr_status lr_batch_autotune(lr_batch* b, int trial_steps);
 
 /* The schedule in use: for each of the nine step kernels (the order of
@@ -115,7 +117,9 @@ lr_status lr_batch_schedule(const lr_batch* b, int* tile_shape, int* blocks_per_
 /* Kernel launches the last step enqueued (all groups). */
 int lr_batch_launches_per_step(const lr_batch* b);
 
-/* Persistent step (on by default where the device can hold it resident):
+/* Persistent step (on by default in LR_FP32 where the device can hold it
+ * resident, off in LR_FP64 and LR_DF64; lr_batch_autotune picks between the
+ * two paths unless this call has set one):
  * each step is one cooperative launch of co-resident blocks that walk every
  * member's 32 x 8 cell tiles and node tiles through the phases of the tiled
  * step (the Lagrange phase and remap geometry of section 1.2 and 2.3; the

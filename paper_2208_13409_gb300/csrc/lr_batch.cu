@@ -83,8 +83,10 @@ struct lr_batch {
   bool gvalid[2] = {false, false};
   int launches = 0;
   bool prof = false;
-  // persistent step: one cooperative launch per step (lb_t_step)
+  // persistent step: one cooperative launch per step (lb_t_step); by
+  // default in FP32, and chosen by lr_batch_autotune unless the caller set it
   bool persistent = true;
+  bool persistent_set = false;
   int pers_bps = 0;                 // resident blocks per SM of lb_t_step
   LrGridBar* bar = nullptr;         // its grid barrier (count, generation, status)
   unsigned int bar_extra = 0;       // test hook: arrivals no block makes
@@ -653,6 +655,11 @@ lr_status lr_batch_create(const lr_batch_config* cfg, lr_batch** out) {
   if (lr_tiled_setup() != cudaSuccess) cudaGetLastError();
   b->pers_bps = lr_persistent_blocks_per_sm(b->mode);
   if (b->pers_bps > 4) b->pers_bps = 4;
+  // the persistent step is the faster one in FP32 and the slower one in FP64
+  // (the 512-member ensemble on GB300: 4.3e9 against 3.9e9 cell-updates/s in
+  // FP32, 0.92e9 against 1.28e9 in FP64, whose interface phase inside the
+  // persistent kernel runs with a fraction of the registers it needs)
+  b->persistent = b->mode == LR_MODE_FP32;
   b->msg[0] = 0;
   if (lr_launch_reset(b->mode, b->w, b->S, b->stream) != cudaSuccess ||
       cudaStreamSynchronize(b->stream) != cudaSuccess) {
@@ -826,6 +833,7 @@ lr_status lr_batch_set_persistent(lr_batch* b, int on) {
   if (on && b->pers_bps <= 0) { setmsg(b, "the persistent step cannot be resident on this device"); return LR_ERR_ARG; }
   CK(cudaStreamSynchronize(b->stream), "sync");
   b->persistent = on != 0;
+  b->persistent_set = true;
   b->need_rebuild = true;
   return LR_OK;
 }
@@ -1050,9 +1058,38 @@ lr_status lr_batch_autotune(lr_batch* b, int trial_steps) {
     rs = trial(c, t);
     if (rs == LR_OK && t[LRK_MIXED] < bestt[LRK_MIXED]) { bestt[LRK_MIXED] = t[LRK_MIXED]; best.lanes = c.lanes; }
   }
+  // 4. unless the caller chose, the whole step: the tuned per-kernel step
+  // against the persistent step (CUDA events around trial_steps steps each)
+  bool pers = pers0;
+  if (rs == LR_OK && !b->persistent_set && b->pers_bps > 0) {
+    double ms[2] = {0.0, 0.0};
+    for (int q = 0; q < 2 && rs == LR_OK; ++q) {
+      b->sch = best;
+      b->persistent = q == 1;
+      b->need_rebuild = true;
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        rs = LR_ERR_CUDA;
+      } else {
+        rs = run_steps(b, 1);  // warm-up (tables and graphs)
+        if (rs == LR_OK && cudaEventRecord(e0, b->stream) != cudaSuccess) rs = LR_ERR_CUDA;
+        if (rs == LR_OK) rs = run_steps(b, trial_steps);
+        if (rs == LR_OK && cudaEventRecord(e1, b->stream) != cudaSuccess) rs = LR_ERR_CUDA;
+        float el = 0.0f;
+        if (rs == LR_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&el, e0, e1) != cudaSuccess))
+          rs = LR_ERR_CUDA;
+        ms[q] = el;
+        if (rs == LR_OK) rs = check_barrier(b);
+        if (rs == LR_OK) rs = restore();
+      }
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+    }
+    if (rs == LR_OK) pers = ms[1] < ms[0];
+  }
   cudaFree(snap);
   b->sch = best;
-  b->persistent = pers0;
+  b->persistent = pers;
   b->need_rebuild = true;
   if (rs != LR_OK) return rs;
   // the members' grids carry the lanes of lr_mixed only through the launch

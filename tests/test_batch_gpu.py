@@ -186,6 +186,32 @@ def test_autotune_keeps_results_and_state():
         _same(bt, m, _alone(pr, 8, tiled=bt.persistent))
 
 
+def test_persistent_default_by_arithmetic():
+    """The persistent step is the default where it is the faster path
+    (FP32); FP64 and double-float batches start with one launch per kernel."""
+    probs = _mix()
+    for prec, want in ((lr.FP32, True), (lr.FP64, False), (lr.DF64, False)):
+        bt = lr.Batch(_units(probs), 8, precision=prec)
+        assert bt.persistent == want, prec
+        bt.close()
+
+
+@pytest.mark.parametrize("on", [True, False])
+def test_autotune_keeps_an_explicit_step_path(on):
+    """The autotuner chooses between the per-kernel and the persistent step
+    only when the caller has not set one."""
+    probs = _mix()
+    bt = lr.Batch(_units(probs), 8, precision=lr.FP32)
+    bt.set_persistent(on)
+    ids = [bt.add(p, t_end=1e300) for p in probs]
+    bt.step(1)
+    bt.autotune(trial_steps=1)
+    assert bt.persistent == on
+    for m in ids:
+        assert bt.status(m)[1] == 1
+    bt.close()
+
+
 def test_invalid_member_is_refused_and_failure_stays_local():
     good = P.random_box(141, nx=32, ny=24, nmat=2, velocity=0.3)
     bad = good.copy()
@@ -225,6 +251,7 @@ def test_persistent_barrier_limit_runs_out():
     import time
     probs = _mix()[:3]
     bt = lr.Batch(_units(probs), 4)
+    bt.set_persistent(True)
     for p in probs:
         bt.add(p, t_end=1e300)
     bt.step(2)
@@ -240,6 +267,7 @@ def test_persistent_barrier_limit_runs_out():
         bt.step(1)
     bt.close()
     fresh = lr.Batch(_units(probs), 4)
+    fresh.set_persistent(True)
     ids = [fresh.add(p, t_end=1e300) for p in probs]
     fresh.step(2)
     fresh.sync()
