@@ -2958,11 +2958,21 @@ __device__ __forceinline__ void t_lagrange_tile(const LrGrid& g, const KC<R>& kc
   const R dt = w.dtR[g.inst];
   const int nn = g.nx + 1;
   // ---- stage u^n over the nodes [i0-1, i0+TX+1] x [j0-1, j0+TY+1]
-  for (int t = tid; t < NN; t += TTHREADS) {
-    int gi = i0 - 1 + t % LG_NW, gj = j0 - 1 + t / LG_NW;
-    Ix n = nix(g, nclamp(gi, g.nx), nclamp(gj, g.ny));
-    sUX[t] = O::flip(n.fx, cur.ux[n.idx]);
-    sUY[t] = O::flip(n.fy, cur.uy[n.idx]);
+  // (plain indices in a tile two cells inside the grid)
+  const bool inner = tile_interior(g, i0, j0);
+  if (inner) {
+    for (int t = tid; t < NN; t += TTHREADS) {
+      const int n = g.noff + (j0 - 1 + t / LG_NW) * nn + (i0 - 1 + t % LG_NW);
+      sUX[t] = cur.ux[n];
+      sUY[t] = cur.uy[n];
+    }
+  } else {
+    for (int t = tid; t < NN; t += TTHREADS) {
+      int gi = i0 - 1 + t % LG_NW, gj = j0 - 1 + t / LG_NW;
+      Ix n = nix(g, nclamp(gi, g.nx), nclamp(gj, g.ny));
+      sUX[t] = O::flip(n.fx, cur.ux[n.idx]);
+      sUY[t] = O::flip(n.fy, cur.uy[n.idx]);
+    }
   }
   __syncthreads();
   // ---- 1. cell_pre over the cells [i0-1, i0+TX] x [j0-1, j0+TY]
@@ -2971,7 +2981,7 @@ __device__ __forceinline__ void t_lagrange_tile(const LrGrid& g, const KC<R>& kc
     int ci = i0 - 1 + a, cj = j0 - 1 + b;
     bool gx = !g.perx && (ci < 0 || ci >= g.nx), gy = !g.pery && (cj < 0 || cj >= g.ny);
     if (gx || gy) continue;  // a wall ghost: copied from its image below
-    int c = cix(g, cclamp(ci, g.nx), cclamp(cj, g.ny)).idx;
+    int c = inner ? g.coff + cj * g.nx + ci : cix(g, cclamp(ci, g.nx), cclamp(cj, g.ny)).idx;
     int ll = b * LG_NW + a, lr = ll + 1, ul = ll + LG_NW, ur = ul + 1;
     R uxll = sUX[ll], uxlr = sUX[lr], uxul = sUX[ul], uxur = sUX[ur];
     R uyll = sUY[ll], uylr = sUY[lr], uyul = sUY[ul], uyur = sUY[ur];
