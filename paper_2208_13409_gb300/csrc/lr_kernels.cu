@@ -3046,21 +3046,24 @@ __device__ __forceinline__ void t_lagrange_tile(const LrGrid& g, const KC<R>& kc
     }
   }
   __syncthreads();
-  // wall ghosts: the values of their mirror images (scalars)
-  for (int t = tid; t < CN; t += TTHREADS) {
-    int a = t % LG_CW, b = t / LG_CW;
-    int ci = i0 - 1 + a, cj = j0 - 1 + b;
-    bool gx = !g.perx && (ci < 0 || ci >= g.nx), gy = !g.pery && (cj < 0 || cj >= g.ny);
-    if (!(gx || gy)) continue;
-    int mi = gx ? (ci < 0 ? -1 - ci : 2 * g.nx - 1 - ci) : ci;
-    int mj = gy ? (cj < 0 ? -1 - cj : 2 * g.ny - 1 - cj) : cj;
-    int ma = mi - (i0 - 1), mb = mj - (j0 - 1);
-    if (ma < 0 || ma >= LG_CW || mb < 0 || mb >= LG_CH) continue;  // beyond any live point's reach
-    int u = mb * LG_CW + ma;
-    sPi[t] = sPi[u];
-    sMC[t] = sMC[u];
+  // wall ghosts: the values of their mirror images (scalars; an interior
+  // tile has none -- the condition is uniform over the block)
+  if (!inner) {
+    for (int t = tid; t < CN; t += TTHREADS) {
+      int a = t % LG_CW, b = t / LG_CW;
+      int ci = i0 - 1 + a, cj = j0 - 1 + b;
+      bool gx = !g.perx && (ci < 0 || ci >= g.nx), gy = !g.pery && (cj < 0 || cj >= g.ny);
+      if (!(gx || gy)) continue;
+      int mi = gx ? (ci < 0 ? -1 - ci : 2 * g.nx - 1 - ci) : ci;
+      int mj = gy ? (cj < 0 ? -1 - cj : 2 * g.ny - 1 - cj) : cj;
+      int ma = mi - (i0 - 1), mb = mj - (j0 - 1);
+      if (ma < 0 || ma >= LG_CW || mb < 0 || mb >= LG_CH) continue;  // beyond any live point's reach
+      int u = mb * LG_CW + ma;
+      sPi[t] = sPi[u];
+      sMC[t] = sMC[u];
+    }
+    __syncthreads();
   }
-  __syncthreads();
   // ---- 2. node_half over the nodes [i0, i0+TX] x [j0, j0+TY]
   for (int t = tid; t < ON; t += TTHREADS) {
     int a = t % LG_OW, b = t / LG_OW;
