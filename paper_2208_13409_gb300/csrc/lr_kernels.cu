@@ -1569,7 +1569,6 @@ __device__ void cfl_finalize(const LrGrid& g, const KC<R>& kc, const LrWorkT<R>&
                              unsigned long long ntiles) {
   using O = RealOps<R>;
   __shared__ unsigned long long sm[32];
-  __shared__ int last;
   int tid = threadIdx.y * blockDim.x + threadIdx.x;
   unsigned long long* red = w.red + LR_RED_INST + 2 * g.inst;
   unsigned long long key = Key<R>::enc(v);
@@ -1586,35 +1585,33 @@ __device__ void cfl_finalize(const LrGrid& g, const KC<R>& kc, const LrWorkT<R>&
       unsigned long long o = __shfl_xor_sync(0xffffffffu, x, off);
       x = o > x ? o : x;
     }
+    // thread 0 alone: contributes the block's maximum, and in the block that
+    // counts last finalizes (no other thread takes part, so no barrier)
     if (tid == 0) {
       atomicMax(&red[0], x);
       __threadfence();
-      unsigned long long prev = atomicAdd(&red[1], 1ull);
-      last = prev == ntiles - 1;
+      if (atomicAdd(&red[1], 1ull) != ntiles - 1) return;
+      __threadfence();
+      double* sc = scal_of(g, w.scal);
+      R mx = Key<R>::dec(atomicAdd(&red[0], 0ull));
+      double dtc = O::pos(mx) ? O::todouble(kc.cfl * (kc.hmin / mx)) : g.cfl * 1e300;
+      double t = sc[0];
+      if (advance) { t = t + sc[5]; sc[2] = sc[5]; sc[4] += 1.0; }
+      sc[0] = t;
+      sc[1] = dtc;
+      double dn = g.dt_fixed > 0.0 ? g.dt_fixed : dtc;
+      if (sc[3] - t < dn) dn = sc[3] - t;
+      if (sc[7] > 0.0 && sc[4] >= sc[7]) dn = 0.0;
+      dn = dn > 0.0 ? dn : 0.0;
+      sc[5] = dn;
+      w.dtR[g.inst] = from_double<R>(dn);
+      if (advance) sc[6] = (double)w.red[g.mslot];
+      red[0] = 0ull;
+      red[1] = 0ull;
+      // the list is consumed (lr_mixed ran before this kernel); every
+      // simulation of a group clears it, the next step's lr_cell_pre refills it
+      w.red[g.mslot] = 0ull;
     }
-  }
-  __syncthreads();
-  if (last && tid == 0) {
-    __threadfence();
-    double* sc = scal_of(g, w.scal);
-    R mx = Key<R>::dec(atomicAdd(&red[0], 0ull));
-    double dtc = O::pos(mx) ? O::todouble(kc.cfl * (kc.hmin / mx)) : g.cfl * 1e300;
-    double t = sc[0];
-    if (advance) { t = t + sc[5]; sc[2] = sc[5]; sc[4] += 1.0; }
-    sc[0] = t;
-    sc[1] = dtc;
-    double dn = g.dt_fixed > 0.0 ? g.dt_fixed : dtc;
-    if (sc[3] - t < dn) dn = sc[3] - t;
-    if (sc[7] > 0.0 && sc[4] >= sc[7]) dn = 0.0;
-    dn = dn > 0.0 ? dn : 0.0;
-    sc[5] = dn;
-    w.dtR[g.inst] = from_double<R>(dn);
-    if (advance) sc[6] = (double)w.red[g.mslot];
-    red[0] = 0ull;
-    red[1] = 0ull;
-    // the list is consumed (lr_mixed ran before this kernel); every
-    // simulation of a group clears it, the next step's lr_cell_pre refills it
-    w.red[g.mslot] = 0ull;
   }
 }
 
